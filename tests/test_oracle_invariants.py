@@ -1,0 +1,150 @@
+"""Pins P2-P5 of the FP64 oracle: properties the discrete method must have.
+
+  P2  reciprocity: the second-order Yee system with volume weights is
+      complex-symmetric (A^T = A, Sec. 3.2), so swapping a point source and a
+      point receiver leaves the response unchanged, also across components;
+  P3  point injection is the dual-volume-weighted transpose of point sampling;
+  P4  with perfectly conducting walls, no source and no CPML the leap-frog
+      scheme conserves the discrete energy
+      sum_f mu0 dV~_f (H_f^{n+1/2})^2 + sum_e eps_e dV_e E_e^n E_e^{n+1};
+  P5  the normalised field does not depend on the source wavelet, superposes
+      linearly and does not change when nt grows past the decay of the
+      transform weights (Sec. 2, Eq. 2-6).
+A planted mistake in the oracle's dual spacings (checked last) breaks P4,
+showing the energy pin sees the stencil's geometry.
+"""
+import numpy as np
+import pytest
+
+from oracle import fdtd
+from paper_2211_16665_gb300.workloads import Points, small_box, stretched_axis
+
+
+@pytest.fixture(scope="module")
+def box():
+    wl = small_box(n_core=20, h=100.0, npml=8, ratio=1.08, n_st=4)
+    return wl, fdtd.problem_from_workload(wl)
+
+
+def test_reciprocity_same_and_cross_component(box):
+    wl, pb = box
+    A = Points.make([[130.0, -220.0, 777.0]], 0)
+    Ay = Points.make([[130.0, -220.0, 777.0]], 1)
+    B = Points.make([[-480.0, 310.0, 1120.0]], 0)
+    d_ab, tr_ab = fdtd.forward(pb, wl.rho_true, B, A, return_trace=True)
+    d_ba, tr_ba = fdtd.forward(pb, wl.rho_true, A, B, return_trace=True)
+    assert np.abs(d_ab - d_ba).max() <= 1e-9 * np.abs(d_ab).max()
+    # the time-domain traces are reciprocal too: the discrete operator is symmetric
+    assert np.abs(tr_ab - tr_ba).max() <= 1e-9 * np.abs(tr_ab).max()
+    d_ayb = fdtd.forward(pb, wl.rho_true, B, Ay)
+    d_bay = fdtd.forward(pb, wl.rho_true, Ay, B)
+    assert np.abs(d_ayb - d_bay).max() <= 1e-9 * np.abs(d_ayb).max()
+
+
+def test_injection_is_weighted_transpose_of_sampling(box):
+    wl, pb = box
+    rng = np.random.default_rng(0)
+    st = fdtd.Stepper(pb, wl.rho)
+    pts = Points.make([[35.0, -72.0, 640.0], [-410.0, 95.0, 1210.0]], [0, 2])
+    u = rng.standard_normal((3,) + pb.shape_nodes)
+    for p in range(pts.n):
+        samp = fdtd.point_taps(pb, pts, p)
+        inj = fdtd.point_taps(pb, pts, p, scale_by_dV=st.dV)
+        r = rng.standard_normal()
+        lhs = r * sum(w * u[c, k, j, i] for (c, k, j, i, w, _) in samp)
+        field = np.zeros_like(u)
+        for (c, k, j, i, w, _) in inj:
+            field[c, k, j, i] += r * w
+        rhs = np.sum(u * field * st.dV)
+        assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+        assert abs(sum(t[4] for t in samp) - 1.0) <= 1e-14
+
+
+def _energy_setup(seed=3):
+    rng = np.random.default_rng(seed)
+    xn = stretched_axis(100.0, 10, 3, 4, 0, 1.1, 0.0)
+    yn = stretched_axis(80.0, 9, 2, 3, 0, 1.2, 0.0)
+    zn = stretched_axis(120.0, 8, 4, 2, 0, 1.05, 0.0)
+    nx, ny, nz = xn.size - 1, yn.size - 1, zn.size - 1
+    rho = 10 ** rng.uniform(-0.5, 1.5, (nz, ny, nx))
+    pb = fdtd.make_problem(xn, yn, zn, 0, [0.5], 1.0, rho_max=rho.max(), nt=400)
+    st = fdtd.Stepper(pb, rho)
+    fields, psi = st.new_state()
+    F = fields.reshape((6,) + pb.shape_nodes)
+    F[0][1:nz, 1:ny, :nx] = rng.standard_normal((nz - 1, ny - 1, nx))
+    F[1][1:nz, :ny, 1:nx] = rng.standard_normal((nz - 1, ny, nx - 1))
+    F[2][:nz, 1:ny, 1:nx] = rng.standard_normal((nz, ny - 1, nx - 1))
+    F[3][:nz, :ny, :] = rng.standard_normal((nz, ny, nx + 1))
+    F[4][:nz, :, :nx] = rng.standard_normal((nz, ny + 1, nx))
+    F[5][:, :ny, :nx] = rng.standard_normal((nz + 1, ny, nx))
+    hx, hxt = fdtd.spacings(xn)
+    hy, hyt = fdtd.spacings(yn)
+    hz, hzt = fdtd.spacings(zn)
+    dVH = np.zeros((3,) + pb.shape_nodes)
+    dVH[0][:nz, :ny, :] = hz[:, None, None] * hy[None, :, None] * hxt[None, None, :]
+    dVH[1][:nz, :, :nx] = hz[:, None, None] * hyt[None, :, None] * hx[None, None, :]
+    dVH[2][:, :ny, :nx] = hzt[:, None, None] * hy[None, :, None] * hx[None, None, :]
+    eps = np.zeros((3,) + pb.shape_nodes)
+    m = st.cE > 0
+    eps[m] = pb.dt / st.cE[m]
+    return pb, st, fields, psi, F, dVH, eps * st.dV
+
+
+def _energy_drift(st, fields, psi, F, dVH, w_e, steps=250):
+    vals = []
+    for n in range(steps):
+        e_old = F[:3].copy()
+        st.run(fields, psi, n, n + 1)
+        vals.append(np.sum(fdtd.MU0 * dVH * F[3:] ** 2) + np.sum(w_e * e_old * F[:3]))
+    vals = np.array(vals)
+    return np.abs(vals - vals[0]).max() / abs(vals[0])
+
+
+def test_discrete_energy_conserved_with_pec_walls():
+    pb, st, fields, psi, F, dVH, w_e = _energy_setup()
+    assert _energy_drift(st, fields, psi, F, dVH, w_e) <= 1e-12
+
+
+def test_energy_pin_detects_a_wrong_dual_spacing():
+    # plant a plausible mistake in the oracle: primal instead of dual widths at x nodes
+    pb, st, fields, psi, F, dVH, w_e = _energy_setup()
+    ihx_n = st._keep[1]
+    ihx_n[1:-1] = 1.0 / np.diff(pb.xn)[1:]
+    assert _energy_drift(st, fields, psi, F, dVH, w_e) > 1e-6
+
+
+def _ricker(pb, fp=5.0):
+    t = (np.arange(pb.nt) + 0.5) * pb.dt
+    a = (np.pi * fp * (t - 1.5 / fp)) ** 2
+    return (1 - 2 * a) * np.exp(-a)
+
+
+def test_wavelet_invariance_linearity_and_nt(box):
+    wl, pb = box
+    A = Points.make([[130.0, -220.0, 777.0]], 0)
+    rec = Points.make([[x, 20.0, 800.0] for x in (-800.0, -300.0, 400.0, 900.0)], [0, 1, 2, 0])
+    d_imp = fdtd.forward(pb, wl.rho_true, A, rec)
+    d_ric = fdtd.forward(pb, wl.rho_true, A, rec, wavelet=_ricker(pb))
+    assert np.abs(d_imp - d_ric).max() <= 1e-8 * np.abs(d_imp).max()
+    pb2 = fdtd.make_problem(pb.xn, pb.yn, pb.zn, pb.npml, pb.freqs, pb.f0, pb.rho_max, nt=2 * pb.nt)
+    d_long = fdtd.forward(pb2, wl.rho_true, A, rec)
+    assert np.abs(d_imp - d_long).max() <= 1e-10 * np.abs(d_imp).max()
+
+
+def test_two_sources_superpose(box):
+    wl, pb = box
+    st = fdtd.Stepper(pb, wl.rho_true)
+    pts = Points.make([[130.0, -220.0, 777.0], [-300.0, 150.0, 900.0]], [0, 1])
+    rec = Points.make([[500.0, 0.0, 1000.0]], 2)
+    taps = fdtd.point_taps(pb, rec, 0)
+    wav = pb.impulse()
+    traces = []
+    for sel in ([0], [1], [0, 1]):
+        inj = []
+        for p in sel:
+            inj += fdtd.point_taps(pb, pts, p, scale_by_dV=st.dV, tag=0)
+        fields, psi = st.new_state()
+        tr = np.zeros(pb.nt)
+        st.run(fields, psi, 0, pb.nt, inj=inj, series=wav[None, :], taps=taps, n_rec=1, trace=tr)
+        traces.append(tr)
+    assert np.abs(traces[0] + traces[1] - traces[2]).max() <= 1e-12 * np.abs(traces[2]).max()
