@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Benchmark of the fictitious-wave CSEM gradient hot path.
+
+One step = one full gradient for the workload's source batch, every row of
+the hot path: coefficient set-up from the model, forward run with the fused
+damped transform into all frequencies (volumes kept), misfit and weighted
+residual, adjoint-source basis (CGNR), adjoint run driven by the basis
+series, and the cell gradient with respect to ln(rho).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` counts cell updates of both runs
+(cells incl. CPML x nt x sources x 2) per second of device time, inputs
+resident in HBM.  `e2e` repeats the measurement through the same public calls
+with the model and observed data copied from pinned host memory and the
+gradient and misfit copied back inside the timed region.  The reference arm
+times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gcell-updates/s; batched gradient s/source vs plain path; % of HBM roofline"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="thin_reservoir")
+    ap.add_argument("--cpu-steps", type=int, default=300, help="time steps in the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                if self.uuid and self.uuid not in p[0]:
+                    continue
+                rows.append(p)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_workload(name, rank, world):
+    from paper_2211_16665_gb300 import workloads as W
+    wl = W.ALL[name]()
+    if world > 1:
+        # weak scaling: every rank models its own source of a towline on the same model
+        x = wl.src.x[0] + 250.0 * (rank - world // 2)
+        wl.src = W.Points.make([[x, wl.src.y[0], wl.src.z[0]]], int(wl.src.comp[0]))
+    return wl
+
+
+def hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_bytes(wl, eng):
+    """Algorithmic bytes of one launch of the H half-step with the fused transform.
+
+    Per lattice node and source: read E (12 B), read + write H (24 B), the CPML
+    memory of the H update inside its slabs (two arrays per axis, read + write,
+    on the fraction 2 npml / n of that axis), and the damped-transform
+    accumulators: 3 components x n_freq complex values read + written, twice
+    with the Kahan compensation.
+    """
+    r = 4 if eng.precision == 32 else 8
+    nodes = (wl.nx + 1) * (wl.ny + 1) * (wl.nz + 1)
+    frac = sum(2 * wl.npml / n for n in (wl.nx, wl.ny, wl.nz))
+    per = 9 * r + 2 * 2 * r * frac + 3 * eng.nf * 2 * (2 * r) * (2 if eng.info.kahan else 1)
+    return per * nodes * wl.src.n, per
+
+
+def cpu_baseline(wl, nt_sample):
+    from oracle import fdtd
+    pb = fdtd.problem_from_workload(wl)
+    nt_sample = min(nt_sample, pb.nt)
+    t0 = time.perf_counter()
+    fdtd.forward(pb, wl.rho, wl.src.subset([0]), wl.rec, keep_volume=True, nt_run=nt_sample)
+    t = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": wl.cells * nt_sample / t / 1e9, "unit": "Gcell-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 oracle, {nt_sample} of {pb.nt} steps of one source with the volumetric transform "
+                      f"into {wl.freqs.size} frequencies on the full {wl.nx}x{wl.ny}x{wl.nz} grid "
+                      f"(a gradient is 2 such runs per source); {t:.1f} s"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2211_16665_gb300 import _capi
+    from paper_2211_16665_gb300 import workloads as W
+    from paper_2211_16665_gb300.engine import Engine, misfit
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    wl = make_workload(args.workload, rank, world)
+    eng = Engine.from_workload(wl)
+    S = wl.src.n
+    rho = eng.model_tensor(wl.rho)
+    rho_true = eng.model_tensor(wl.rho_true)
+    d_obs = eng.fwd_model(rho_true, wl.src, wl.rec)
+    d_obs = torch.as_tensor(W.add_noise(d_obs.cpu().numpy(), wl.noise, wl.noise_seed), device=dev)
+    torch.cuda.synchronize()
+
+    def step(rho_in, d_obs_in):
+        d, E = eng.fwd_model(rho_in, wl.src, wl.rec, keep_volume=True)
+        phi, r = misfit(d_obs_in, d)
+        basis, fit, its = eng.estimate_adjoint_basis(gamma=1e-12, relative=True)
+        V = eng.adjoint_model(rho_in, wl.rec, r, basis)
+        g = eng.gradient(rho_in, E, V, wrt="lnrho")
+        if world > 1:
+            dist.all_reduce(g)
+            dist.all_reduce(phi)
+        return phi, g, fit
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(rho, d_obs)
+    barrier()
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    n0 = _capi.launch_count()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        phi, g, fit = step(rho, d_obs)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = (_capi.launch_count() - n0) // args.steps
+    clk = clocks.stop()
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+
+    cell_updates = 2.0 * wl.cells * eng.nt * S * world
+    value = cell_updates / (ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel, timed live with CUDA events on its stream
+    _, E = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)
+    from paper_2211_16665_gb300.engine import _ptr, _stream
+    kms = _capi.time_step_kernels(eng.ctx, S, _ptr(E), 200, _stream())
+    bytes_launch, per_node = kernel_bytes(wl, eng)
+    peak, peak_kind = hbm_peak()
+    achieved = bytes_launch / (kms[0] / 1e3) / 1e9
+    roof = {"kernel": "k_h (H half-step + damped transform, Kahan)", "bound": "hbm",
+            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "peak_kind": peak_kind, "traffic": None, "bytes_per_node": round(per_node, 1),
+            "ms_per_launch": {"k_h": kms[0], "k_points": kms[1], "k_e": kms[2]}}
+
+    # end to end: host model in, host gradient out
+    e2e = None
+    if not args.no_e2e:
+        rho_h = rho.cpu().pin_memory()
+        dobs_h = d_obs.cpu().pin_memory()
+        g_h = torch.empty(g.shape, dtype=g.dtype).pin_memory()
+        phi_h = torch.empty((), dtype=torch.float64).pin_memory()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            r_dev = rho_h.to(dev, non_blocking=True)
+            o_dev = dobs_h.to(dev, non_blocking=True)
+            phi2, g2, _ = step(r_dev, o_dev)
+            g_h.copy_(g2, non_blocking=True)
+            phi_h.copy_(phi2, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1) / args.steps
+        t = torch.tensor([ems], device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ems = float(t.item())
+        e2e = {"value": round(cell_updates / (ems / 1e3) / 1e9, 3), "unit": "Gcell-updates/s",
+               "ms_per_step": round(ems, 3),
+               "h2d_bytes_per_step": int(rho_h.numel() * rho_h.element_size() + dobs_h.numel() * dobs_h.element_size()),
+               "d2h_bytes_per_step": int(g_h.numel() * g_h.element_size() + 8)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, args.cpu_steps)
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": round(value, 3), "unit": "Gcell-updates/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32" if eng.precision == 32 else "f64",
+               "data": "synthetic",
+               "config": {"workload": wl.name, "cells": wl.cells, "grid": [wl.nx, wl.ny, wl.nz], "nt": eng.nt,
+                          "dt": eng.dt, "n_src_per_gpu": S, "n_rec": wl.rec.n, "freqs_hz": list(map(float, wl.freqs)),
+                          "kahan": bool(eng.info.kahan), "l2": "inputs larger than L2 (each step streams "
+                          f"{2 * 3 * eng.nf * eng.vol * 8 * S * (2 if eng.info.kahan else 1) / 2**20:.0f} MiB of "
+                          "transform volumes)", "parallelism": f"sources sharded, dp{world}"},
+               "grad_s_per_source": round(ms / 1e3 / S, 4),
+               "basis_fit": fit,
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+               "clocks": clk}
+        print(json.dumps(out), flush=True)
+    eng.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    from oracle import fdtd
+    wl = make_workload(args.workload, 0, 1)
+    pb = fdtd.problem_from_workload(wl)
+    src = wl.src.subset([0])
+    # calibrate: size each step so that warmup + steps take ~2.5 minutes
+    t0 = time.perf_counter()
+    fdtd.forward(pb, wl.rho, src, wl.rec, keep_volume=True, nt_run=3)
+    per = (time.perf_counter() - t0) / 3
+    nt_s = int(max(5, min(pb.nt, 150.0 / max(1, args.steps + args.warmup) / per)))
+    for _ in range(args.warmup):
+        fdtd.forward(pb, wl.rho, src, wl.rec, keep_volume=True, nt_run=nt_s)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        fdtd.forward(pb, wl.rho, src, wl.rec, keep_volume=True, nt_run=nt_s)
+    t = (time.perf_counter() - t0) / args.steps
+    value = wl.cells * nt_s / t / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "Gcell-updates/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl.name, "cells": wl.cells, "grid": [wl.nx, wl.ny, wl.nz], "nt": pb.nt,
+                      "nt_sample": nt_s},
+           "cpu_baseline": {"value": round(value, 5), "unit": "Gcell-updates/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{nt_s} of {pb.nt} steps of one forward run with the volumetric transform"},
+           "e2e": {"value": round(value, 5), "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

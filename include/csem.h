@@ -1,0 +1,207 @@
+/*
+ * csem.h -- C ABI of the GB300 fictitious-wave CSEM gradient engine.
+ *
+ * The engine computes, for a cell-centred resistivity model on a stretched
+ * tensor-product grid, the frequency-domain electric field of point dipoles
+ * through the fictitious-wave correspondence of Yang (2211.16665):
+ *   Sec. 2, Eq. 1      diffusive Maxwell system, time convention d/dt <-> -i w;
+ *   Sec. 2, Eq. 2-3    sigma = 2 w0 eps, J' = k J, E' = E, k = sqrt(-i w / 2 w0);
+ *   Sec. 2, Eq. 4      fictitious-time wave system, leap-frog staggered grid;
+ *   Sec. 2, Eq. 6      on-the-fly damped transform into every frequency at once;
+ * the misfit and weighted residual (Sec. 3.1, Eq. 7), the adjoint field
+ * from the same engine (Sec. 3.2, Eq. 14) driven by time series built from
+ * the regularised basis functions (Sec. 3.3, Eq. 8-13), and the resistivity
+ * gradient (Sec. 3.1 isotropic gradient, Sec. 3.5 ln-rho chain rule).
+ *
+ * Conventions shared by every call
+ *  - Grid: nx, ny, nz cells including an npml-cell CPML on every face; node
+ *    coordinates x_0..x_nx etc. (metres, z down).  Yee placement:
+ *    Ex(i,j,k) at (x_{i+1/2}, y_j, z_k), Ey at (x_i, y_{j+1/2}, z_k),
+ *    Ez at (x_i, y_j, z_{k+1/2}); rho(i,j,k) at the cell centre.
+ *  - Cell arrays (rho, gradient): [nz][ny][nx], x fastest.
+ *  - Edge volumes ("vol"): per (source, component, frequency) a block of
+ *    (nz+1)*(ny+1)*pitch complex entries, index (k*(ny+1) + j)*pitch + i,
+ *    pitch >= nx+1 from csem_get_info(); entries off a component's lattice
+ *    and in the row padding are zero.  Layout [n_src][3][n_freq][block].
+ *  - Complex numbers are interleaved (re, im).  "real" below means float
+ *    when the context's precision is 32 and double when it is 64; receiver
+ *    data and residuals are always complex128.
+ *  - Device pointers (suffix _dev) are CUDA global memory on the current
+ *    device; the caller owns them.  The library owns only what a context
+ *    allocates (fields, CPML memory, tables, graphs).
+ *  - stream is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  Calls are asynchronous on it unless stated otherwise.
+ *  - Every call returns CSEM_OK (0) or a negative status and never throws;
+ *    csem_last_error() then holds a message for the calling thread.
+ */
+#ifndef CSEM_H
+#define CSEM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CSEM_OK                 0
+#define CSEM_ERR_INVALID_ARG   -1   /* bad size, pointer, ordering or option */
+#define CSEM_ERR_OUT_OF_DOMAIN -2   /* a source or receiver lies outside the grid */
+#define CSEM_ERR_CFL           -3   /* explicit dt above the stability limit */
+#define CSEM_ERR_OOM           -4   /* device allocation failed */
+#define CSEM_ERR_NONFINITE     -5   /* non-finite input or result */
+#define CSEM_ERR_TIMEOUT       -6   /* a bounded device wait gave up */
+#define CSEM_ERR_CUDA          -7   /* a CUDA runtime call failed */
+
+typedef struct csem_ctx csem_ctx;
+
+/* Stretched tensor-product grid (Sec. 2 and Sec. 4.2: non-uniform grid with
+ * PML padding).  Host arrays, read during csem_create only. */
+typedef struct {
+    int nx, ny, nz;               /* cells per axis including the CPML, >= 2*npml + 2 */
+    const double *xn, *yn, *zn;   /* node coordinates, strictly increasing */
+    int npml;                     /* CPML thickness in cells on every face, >= 0 */
+} csem_grid;
+
+/* Point sources or receivers (Sec. 3.1: restriction operator R).  Host arrays. */
+typedef struct {
+    int n;                        /* number of points */
+    const double *x, *y, *z;      /* coordinates [m] */
+    const int *comp;              /* electric component per point: 0 = x, 1 = y, 2 = z */
+} csem_points;
+
+/* Problem options.  Host data, read during csem_create only. */
+typedef struct {
+    double f0;          /* reference frequency of the correspondence [Hz], w0 = 2 pi f0 (Eq. 2) */
+    double rho_max;     /* resistivity that freezes the CFL step and the CPML damping [ohm-m] */
+    double dt;          /* fictitious time step [s]; <= 0: s / (v(rho_max) sqrt(max 1/hx^2+1/hy^2+1/hz^2)) */
+    int nt;             /* steps per run; <= 0: ceil(35 / (min_k sqrt(w_k w0) dt)) */
+    double cfl_safety;  /* s above; <= 0 means 0.99 */
+    int precision;      /* 32 (FP32 stencil) or 64 (FP64 stencil) */
+    int kahan;          /* 1: compensated volumetric transform (FP32 only) */
+    int n_freq;         /* number of inversion frequencies, 1..8 */
+    const double *freqs;/* [n_freq] frequencies [Hz] */
+    int max_src;        /* largest source batch any call will pass */
+    int max_rec;        /* largest receiver (or adjoint-source) count */
+} csem_opts;
+
+typedef struct {
+    int nx, ny, nz, npml;
+    int pitch;                    /* row pitch of edge volumes (elements) */
+    long long vol_elems;          /* (nz+1)*(ny+1)*pitch: complex entries per (src, comp, freq) */
+    double dt;                    /* time step in use */
+    int nt;                       /* steps per run */
+    int precision, kahan, n_freq, max_src, max_rec;
+    long long workspace_bytes;    /* device memory the context holds */
+} csem_info;
+
+/* Creates a context on the current device: validates the grid and options,
+ * derives dt / nt, builds the spacing, CPML and transform tables and
+ * allocates the workspaces for max_src sources.  *ctx is set on success.
+ * Errors: INVALID_ARG, CFL (dt given above the limit), OOM, CUDA. */
+int csem_create(csem_ctx **ctx, const csem_grid *grid, const csem_opts *opts);
+
+/* Releases every device and host resource of ctx (synchronises the device).  NULL is a no-op. */
+void csem_destroy(csem_ctx *ctx);
+
+/* Fills *info with the layout and derived quantities of ctx. */
+int csem_get_info(const csem_ctx *ctx, csem_info *info);
+
+/* Forward modelling (Sec. 2, Eq. 2-6; data d_syn = R u, Sec. 3.1).
+ *  rho_dev   [nz][ny][nx] real resistivity [ohm-m], > 0.
+ *  src       src->n unit x/y/z electric dipoles (1 A m), one per batch entry
+ *            (1 <= src->n <= max_src); each is injected trilinearly on its
+ *            component's lattice at t_{n+1/2}.
+ *  rec       receivers (0 <= rec->n <= max_rec), sampled trilinearly at t_n.
+ *  d_syn_dev [src->n][rec->n][n_freq] complex128 out: E(x_r, w_k) per source,
+ *            normalised to a unit diffusive dipole, E = k_k Ehat_k / What_k.
+ *  Evol_dev  NULL, or [src->n][3][n_freq][vol] complex(real) out: the same
+ *            normalised E(w_k) on every edge, kept for the gradient.
+ * Errors: INVALID_ARG, OUT_OF_DOMAIN, NONFINITE (rho), CUDA. */
+int csem_fwd_model(csem_ctx *ctx, const void *rho_dev, const csem_points *src, const csem_points *rec,
+                   double *d_syn_dev, void *Evol_dev, void *stream);
+
+/* Adjoint-source basis (Sec. 3.3, Eq. 8-13), FP64 on the device, solved by
+ * conjugate gradients on the regularised normal equations (CGNR) with B
+ * formed on the fly; one unit right-hand side per column.
+ *  B rows: exp(-a_k t_n) cos(a_k t_n), then exp(-a_k t_n) sin(a_k t_n),
+ *          a_k = sqrt(2 pi f_k 2 pi f0), t_n = (n + 1/2) dt (injection times).
+ *  gamma     regularisation; if gamma_is_relative it multiplies the largest
+ *            eigenvalue of B B^T.
+ *  max_iter, tol  CG stops when ||B^T(e_j - B x) - gamma x|| <= tol ||B^T e_j||.
+ *  basis_dev [nt][2 n_freq] double out: the columns b_j of B+.
+ *  fit_residual_host  out (may be NULL): max |B B+ - I|.
+ *  iters_host         out (may be NULL): largest CG iteration count used.
+ * Blocks the calling thread until the result is on the host.  Allocates
+ * (and frees) 2 n_freq * nt * 16 bytes of scratch on the stream.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int csem_estimate_adjoint_basis(double dt, int nt, const double *freqs_host, int n_freq, double f0,
+                                double gamma, int gamma_is_relative, int max_iter, double tol,
+                                double *basis_dev, double *fit_residual_host, int *iters_host,
+                                void *stream);
+
+/* Misfit and weighted residual (Sec. 3.1, Eq. 7):
+ *   phi = 1/2 sum |w (d_obs - d_syn)|^2,  resid = w^2 (d_obs - d_syn).
+ *  n            number of complex entries.
+ *  weight_dev   NULL (w = 1) or [n] double real weights.
+ *  resid_dev    [n] complex128 out;  phi_dev  1 double out.
+ * Errors: INVALID_ARG, CUDA. */
+int csem_misfit(int n, const double *d_obs_dev, const double *d_syn_dev, const double *weight_dev,
+                double *resid_dev, double *phi_dev, void *stream);
+
+/* Adjoint modelling (Sec. 3.2, Eq. 14 with the conjugation trick; Sec. 3.3).
+ * Each receiver becomes an electric dipole whose diffusive moment is
+ * conj(resid); its fictitious series is B+ [Re c; Im c] with
+ * c_k = k_k conj(resid_k) / dt, injected like a forward source, and the
+ * output is conj(v) = dt * (damped transform of the adjoint field).
+ *  rho_dev    as in csem_fwd_model.
+ *  rec        the receivers of the residual (0 < rec->n <= max_rec).
+ *  n_src      batch size (1..max_src).
+ *  resid_dev  [n_src][rec->n][n_freq] complex128 weighted residual W^T W (d - R u).
+ *  basis_dev  [nt][2 n_freq] double from csem_estimate_adjoint_basis.
+ *  Vvol_dev   [n_src][3][n_freq][vol] complex(real) out: conj(v) on every edge.
+ * Errors: INVALID_ARG, OUT_OF_DOMAIN, NONFINITE, CUDA. */
+int csem_adjoint_model(csem_ctx *ctx, const void *rho_dev, const csem_points *rec, int n_src,
+                       const double *resid_dev, const double *basis_dev, void *Vvol_dev, void *stream);
+
+/* Resistivity gradient (Sec. 3.1 isotropic form, scaled by the cell volume;
+ * Sec. 3.5 chain rule).  Edge form -Re sum_s sum_k conj(v)_e E_e dV_e mapped
+ * to cells by the transpose of the edge conductivity average
+ * sigma_e = sum_c V_c sigma_c / sum_c V_c.
+ *  Evol_dev, Vvol_dev  [n_src][3][n_freq][vol] from the two runs.
+ *  wrt        0: d phi / d sigma_c;  1: d phi / d ln(rho_c) = -sigma_c d phi / d sigma_c.
+ *  grad_dev   [nz][ny][nx] real, ACCUMULATED (+=) so batches can be summed.
+ * Errors: INVALID_ARG, CUDA. */
+int csem_gradient(csem_ctx *ctx, const void *rho_dev, const void *Evol_dev, const void *Vvol_dev,
+                  int n_src, int wrt, void *grad_dev, void *stream);
+
+/* Test hooks.
+ * csem_set_wavelet: forward source time function J'(t_{n+1/2}) (host [nt]
+ * doubles, copied), or NULL for the unit impulse J'_0 = 1/dt.  The forward
+ * normalisation divides by its damped transform, so E does not depend on it.
+ * csem_set_trace: when trace_dev ([max_src][rec n][nt] double) is non-NULL,
+ * later forward runs also store the sampled E(x_r, t_n). */
+int csem_set_wavelet(csem_ctx *ctx, const double *wavelet_host);
+int csem_set_trace(csem_ctx *ctx, double *trace_dev);
+
+/* Synchronises stream and reports input problems seen by the set-up kernels
+ * since the last check: NONFINITE if a resistivity was non-positive or
+ * non-finite (such cells get zero conductivity in the run). */
+int csem_check(csem_ctx *ctx, void *stream);
+
+/* Measurement hooks.
+ * csem_launch_count: number of CUDA kernels this library has launched in the
+ * process so far (each replay of a captured chunk counts its kernel nodes).
+ * csem_time_step_kernels: on the state left by the last run of ctx, launches
+ * each stepping kernel `launches` times for n_src sources and returns the mean
+ * duration of one launch in milliseconds, from CUDA events on stream:
+ * ms_out[0] = H half-step with the fused damped transform into vol_dev
+ * ([n_src][3][n_freq][vol] complex(real), overwritten), ms_out[1] = point
+ * operators, ms_out[2] = E step.  Field values are overwritten. */
+long long csem_launch_count(void);
+int csem_time_step_kernels(csem_ctx *ctx, int n_src, void *vol_dev, int launches, double *ms_out, void *stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *csem_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSEM_H */

@@ -1,0 +1,697 @@
+// Host side of the C ABI declared in include/csem.h: context set-up (grid
+// widths, CFL step, CPML recursion tables, transform weights), point
+// operators, and the run loop that replays CUDA-graph chunks of time steps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/csem.h"
+#include "csem_internal.cuh"
+
+using csem::C2;
+using csem::Tap;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(e_ == cudaErrorMemoryAllocation ? CSEM_ERR_OOM : CSEM_ERR_CUDA,          \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+    } while (0)
+
+constexpr double kMu0 = 4e-7 * M_PI;
+constexpr double kCpmlR = 1e-6;
+constexpr double kDecaySpan = 35.0;
+constexpr int kChunk = 64;
+
+struct Axis {
+    int n = 0;
+    std::vector<double> x, h, ht;   // nodes, primal widths (n), dual widths (n+1)
+    std::vector<double> bh, ah, bn, an;
+};
+
+// CPML recursion coefficients psi <- b psi + a du (Komatitsch & Martin 2007 with
+// kappa = 1): d = d0 (xi/L)^2, d0 = -3 v ln(R) / (2 L), alpha = pi f0 (1 - xi/L),
+// b = exp(-(d + alpha) dt), a = d (b - 1) / (d + alpha); zero outside the layer.
+void cpml_axis(Axis &A, int npml, double dt, double v, double f0) {
+    const int n = A.n;
+    A.bh.assign(n, 0.0); A.ah.assign(n, 0.0); A.bn.assign(n + 1, 0.0); A.an.assign(n + 1, 0.0);
+    if (npml == 0) return;
+    const double lo = A.x[npml], hi = A.x[n - npml];
+    const double Llo = lo - A.x[0], Lhi = A.x[n] - hi;
+    auto eval = [&](double p, double &b, double &a) {
+        double xi = 0.0, L = 1.0;
+        if (p < lo) { xi = lo - p; L = Llo; }
+        else if (p > hi) { xi = p - hi; L = Lhi; }
+        if (!(xi > 0.0)) { b = 0.0; a = 0.0; return; }
+        const double d0 = -3.0 * v * std::log(kCpmlR) / (2.0 * L);
+        const double d = d0 * (xi / L) * (xi / L);
+        const double al = M_PI * f0 * (1.0 - xi / L);
+        b = std::exp(-(d + al) * dt);
+        a = d * (b - 1.0) / (d + al);
+    };
+    for (int i = 0; i < n; ++i) eval(0.5 * (A.x[i] + A.x[i + 1]), A.bh[i], A.ah[i]);
+    for (int i = 0; i <= n; ++i) eval(A.x[i], A.bn[i], A.an[i]);
+}
+
+}  // namespace
+
+struct csem_ctx {
+    int device = 0;
+    int nx, ny, nz, npml, NX, NY, NZ, pitch;
+    long long plane, vol;
+    Axis ax[3];
+    double f0, w0, rho_max, dt, safety;
+    int nt, precision, kahan, nf, max_src, max_rec;
+    std::vector<double> freqs, a;        // a_k = sqrt(w_k w0)
+    std::vector<std::complex<double>> kf, alpha_fwd;
+    std::vector<double> wavelet;         // J'(t_{n+1/2})
+    int KZ = 8;
+    long long psi_stride = 0, sx = 0, sy = 0, sz = 0;
+    size_t rsize = 4;
+    // device memory
+    void *d_tab = nullptr;               // per-axis stepping tables (real)
+    double *d_h = nullptr;               // primal widths (double) hx|hy|hz
+    void *d_cE = nullptr, *d_fields = nullptr, *d_psi = nullptr, *d_comp = nullptr, *d_edge = nullptr;
+    void *d_wR = nullptr;                // [nt][nf] complex real
+    double2 *d_w64 = nullptr;            // [nt][nf]
+    double2 *d_alpha = nullptr;          // [0..nf): forward, [nf..2nf): adjoint, [2nf..3nf): k_f
+    double2 *d_racc = nullptr;
+    double *d_coef = nullptr, *d_T = nullptr, *d_ones = nullptr;
+    Tap *d_rtaps = nullptr, *d_itaps = nullptr;
+    int *d_step = nullptr, *d_bad = nullptr;
+    double *d_trace = nullptr;
+    int last_nrec = 0;
+    long long bytes = 0;
+    cudaStream_t cap = nullptr;
+    struct GraphSlot { int key[6]; cudaGraphExec_t exec; };
+    std::vector<GraphSlot> graphs;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(csem_ctx *c, T **p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc((void **)p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CSEM_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    c->bytes += (long long)bytes;
+    return CSEM_OK;
+}
+
+#define TRY(x)                  \
+    do {                        \
+        int r_ = (x);           \
+        if (r_ != CSEM_OK) return r_; \
+    } while (0)
+
+template <typename R>
+void axis_tab(const csem_ctx *c, int a, csem::AxisTab<R> &t) {
+    const R *base = (const R *)c->d_tab;
+    long long off = 0;
+    for (int b = 0; b < a; ++b) off += 6LL * (c->ax[b].n + 1);
+    const int n = c->ax[a].n;
+    t.ih_h = base + off;
+    t.ih_n = base + off + (n + 1);
+    t.b_h = base + off + 2 * (n + 1);
+    t.a_h = base + off + 3 * (n + 1);
+    t.b_n = base + off + 4 * (n + 1);
+    t.a_n = base + off + 5 * (n + 1);
+}
+
+template <typename R>
+int upload_tables(csem_ctx *c) {
+    std::vector<R> tab;
+    for (int a = 0; a < 3; ++a) {
+        const Axis &A = c->ax[a];
+        const int n = A.n;
+        std::vector<R> ih_h(n + 1, R(0)), ih_n(n + 1, R(0)), bh(n + 1, R(0)), ah(n + 1, R(0)), bn(n + 1), an(n + 1);
+        for (int i = 0; i < n; ++i) { ih_h[i] = (R)(1.0 / A.h[i]); bh[i] = (R)A.bh[i]; ah[i] = (R)A.ah[i]; }
+        for (int i = 0; i <= n; ++i) { ih_n[i] = (R)(1.0 / A.ht[i]); bn[i] = (R)A.bn[i]; an[i] = (R)A.an[i]; }
+        for (auto *v : {&ih_h, &ih_n, &bh, &ah, &bn, &an}) tab.insert(tab.end(), v->begin(), v->end());
+    }
+    TRY(dalloc(c, (R **)&c->d_tab, tab.size() * sizeof(R)));
+    CK(cudaMemcpy(c->d_tab, tab.data(), tab.size() * sizeof(R), cudaMemcpyHostToDevice));
+    // transform weights exp((-1 + i) a_k n dt), n = 0..nt-1  (Eq. 6)
+    std::vector<typename C2<R>::T> wR((size_t)c->nt * c->nf);
+    std::vector<double2> w64((size_t)c->nt * c->nf);
+    for (int n = 0; n < c->nt; ++n)
+        for (int f = 0; f < c->nf; ++f) {
+            const double t = n * c->dt;
+            const double e = std::exp(-c->a[f] * t);
+            const double re = e * std::cos(c->a[f] * t), im = e * std::sin(c->a[f] * t);
+            w64[(size_t)n * c->nf + f] = make_double2(re, im);
+            wR[(size_t)n * c->nf + f].x = (R)re;
+            wR[(size_t)n * c->nf + f].y = (R)im;
+        }
+    TRY(dalloc(c, (typename C2<R>::T **)&c->d_wR, wR.size() * sizeof(wR[0])));
+    CK(cudaMemcpy(c->d_wR, wR.data(), wR.size() * sizeof(wR[0]), cudaMemcpyHostToDevice));
+    TRY(dalloc(c, &c->d_w64, w64.size() * sizeof(double2)));
+    CK(cudaMemcpy(c->d_w64, w64.data(), w64.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    return CSEM_OK;
+}
+
+// forward normalisation alpha_k = k_k / What_k with What_k the damped transform
+// of the wavelet at the injection times (n + 1/2) dt (Eq. 3 and Eq. 6)
+int update_wavelet(csem_ctx *c) {
+    c->alpha_fwd.assign(c->nf, 0.0);
+    for (int f = 0; f < c->nf; ++f) {
+        std::complex<double> W(0.0, 0.0);
+        for (int n = 0; n < c->nt; ++n) {
+            if (c->wavelet[n] == 0.0) continue;
+            const double t = (n + 0.5) * c->dt;
+            W += c->wavelet[n] * std::exp(std::complex<double>(-c->a[f] * t, c->a[f] * t));
+        }
+        if (std::abs(W) == 0.0) return fail(CSEM_ERR_INVALID_ARG, "wavelet has a zero transform at a frequency");
+        c->alpha_fwd[f] = c->kf[f] / W;
+    }
+    std::vector<double2> al(3 * c->nf);
+    for (int f = 0; f < c->nf; ++f) {
+        al[f] = make_double2(c->alpha_fwd[f].real(), c->alpha_fwd[f].imag());
+        al[c->nf + f] = make_double2(c->dt, 0.0);
+        al[2 * c->nf + f] = make_double2(c->kf[f].real(), c->kf[f].imag());
+    }
+    CK(cudaMemcpy(c->d_alpha, al.data(), al.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_T, c->wavelet.data(), c->nt * sizeof(double), cudaMemcpyHostToDevice));
+    return CSEM_OK;
+}
+
+// Trilinear taps of a point on component comp's lattice.  inject: divide by the edge's dual volume.
+int point_taps(const csem_ctx *c, double px, double py, double pz, int comp, bool inject, int emit, Tap *out) {
+    if (comp < 0 || comp > 2) return fail(CSEM_ERR_INVALID_ARG, "point component must be 0, 1 or 2");
+    const double p[3] = {px, py, pz};
+    int lo[3];
+    double wt[3][2];
+    for (int a = 0; a < 3; ++a) {
+        const Axis &A = c->ax[a];
+        const bool half = (a == comp);
+        const int len = half ? A.n : A.n + 1;
+        auto g = [&](int m) { return half ? 0.5 * (A.x[m] + A.x[m + 1]) : A.x[m]; };
+        if (!std::isfinite(p[a])) return fail(CSEM_ERR_OUT_OF_DOMAIN, "non-finite point coordinate");
+        int m = 0;
+        {   // largest m with g(m) <= p, clamped to [0, len-2]
+            int l = 0, r = len - 1;
+            while (r - l > 1) { int mid = (l + r) / 2; if (g(mid) <= p[a]) l = mid; else r = mid; }
+            m = l;
+        }
+        const double t = (p[a] - g(m)) / (g(m + 1) - g(m));
+        if (t < -1e-9 || t > 1.0 + 1e-9) return fail(CSEM_ERR_OUT_OF_DOMAIN, "point outside the grid");
+        lo[a] = m;
+        wt[a][0] = 1.0 - t;
+        wt[a][1] = t;
+    }
+    int q = 0;
+    for (int dk = 0; dk < 2; ++dk)
+        for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+                const int i = lo[0] + di, j = lo[1] + dj, k = lo[2] + dk;
+                double w = wt[0][di] * wt[1][dj] * wt[2][dk];
+                // an edge on the outer boundary is never updated: only zero weights may land there
+                bool upd = true;
+                if (comp == 0) upd = (j >= 1 && j < c->ny && k >= 1 && k < c->nz);
+                if (comp == 1) upd = (i >= 1 && i < c->nx && k >= 1 && k < c->nz);
+                if (comp == 2) upd = (i >= 1 && i < c->nx && j >= 1 && j < c->ny);
+                if (!upd) {
+                    if (std::fabs(w) > 1e-12) return fail(CSEM_ERR_OUT_OF_DOMAIN, "point touches the outer boundary");
+                    w = 0.0;
+                }
+                if (inject && w != 0.0) {
+                    const Axis &X = c->ax[0], &Y = c->ax[1], &Z = c->ax[2];
+                    double dV = 0.0;
+                    if (comp == 0) dV = X.h[i] * Y.ht[j] * Z.ht[k];
+                    if (comp == 1) dV = X.ht[i] * Y.h[j] * Z.ht[k];
+                    if (comp == 2) dV = X.ht[i] * Y.ht[j] * Z.h[k];
+                    w /= dV;
+                }
+                Tap &tp = out[q++];
+                tp.idx = ((long long)k * c->NY + j) * c->pitch + i;
+                tp.w = w;
+                tp.comp = comp;
+                tp.emit = emit;
+                tp.pad0 = tp.pad1 = 0;
+            }
+    return CSEM_OK;
+}
+
+int check_points(const csem_points *p, int max_n, const char *what, bool allow_empty) {
+    if (!p) return fail(CSEM_ERR_INVALID_ARG, std::string(what) + " is NULL");
+    if (p->n < (allow_empty ? 0 : 1) || p->n > max_n)
+        return fail(CSEM_ERR_INVALID_ARG, std::string(what) + " count out of range");
+    if (p->n > 0 && (!p->x || !p->y || !p->z || !p->comp))
+        return fail(CSEM_ERR_INVALID_ARG, std::string(what) + " has NULL arrays");
+    return CSEM_OK;
+}
+
+template <typename R>
+csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
+    csem::StepParams<R> p;
+    p.nx = c->nx; p.ny = c->ny; p.nz = c->nz; p.NX = c->NX; p.NY = c->NY; p.NZ = c->NZ;
+    p.pitch = c->pitch; p.npml = c->npml; p.plane = c->plane; p.vol = c->vol;
+    axis_tab<R>(c, 0, p.ax); axis_tab<R>(c, 1, p.ay); axis_tab<R>(c, 2, p.az);
+    p.fields = (R *)c->d_fields;
+    p.psi = (R *)c->d_psi;
+    p.psi_stride = c->psi_stride; p.sx = c->sx; p.sy = c->sy; p.sz = c->sz;
+    p.cE = (const R *)c->d_cE;
+    p.cH = (R)(c->dt / kMu0);
+    p.step = c->d_step;
+    p.KZ = c->KZ;
+    p.nf = c->nf;
+    p.w = (const typename C2<R>::T *)c->d_wR;
+    p.acc = dft ? (typename C2<R>::T *)acc : nullptr;
+    p.comp = (dft && c->kahan) ? (typename C2<R>::T *)c->d_comp : nullptr;
+    return p;
+}
+
+template <typename R>
+int run_steps(csem_ctx *c, int S, bool dft, const csem::StepParams<R> &p, const csem::PointParams<R> &q,
+              cudaStream_t st) {
+    const bool kahan = dft && c->kahan;
+    CK(cudaMemsetAsync(c->d_step, 0, sizeof(int), st));
+    const int full = c->nt / kChunk, rem = c->nt % kChunk;
+    if (full > 0) {
+        const int key[6] = {S, dft ? 1 : 0, kahan ? 1 : 0, (q.n_rec > 0 || q.n_itaps > 0) ? 1 : 0,
+                            (int)sizeof(R), c->KZ};
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t le = cudaSuccess;
+        for (int j = 0; j < kChunk && le == cudaSuccess; ++j) le = csem::launch_step<R>(p, q, S, j, dft, kahan, c->cap);
+        if (le == cudaSuccess) le = csem::launch_advance(c->d_step, kChunk, c->cap);
+        cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
+        if (le != cudaSuccess) return fail(CSEM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(le));
+        CK(ee);
+        cudaGraphExec_t exec = nullptr;
+        for (auto &slot : c->graphs)
+            if (std::equal(key, key + 6, slot.key)) {
+                cudaGraphExecUpdateResultInfo info;
+                if (cudaGraphExecUpdate(slot.exec, g, &info) == cudaSuccess) exec = slot.exec;
+                else {
+                    cudaGetLastError();
+                    CK(cudaDeviceSynchronize());
+                    cudaGraphExecDestroy(slot.exec);
+                    CK(cudaGraphInstantiate(&slot.exec, g, 0));
+                    exec = slot.exec;
+                }
+                break;
+            }
+        if (!exec) {
+            csem_ctx::GraphSlot slot;
+            std::copy(key, key + 6, slot.key);
+            CK(cudaGraphInstantiate(&slot.exec, g, 0));
+            c->graphs.push_back(slot);
+            exec = slot.exec;
+        }
+        cudaGraphDestroy(g);
+        for (int ch = 0; ch < full; ++ch) CK(cudaGraphLaunch(exec, st));
+    }
+    for (int j = 0; j < rem; ++j) CK(csem::launch_step<R>(p, q, S, j, dft, kahan, st));
+    return CSEM_OK;
+}
+
+csem::GeoD geo(const csem_ctx *c) {
+    csem::GeoD g;
+    g.nx = c->nx; g.ny = c->ny; g.nz = c->nz; g.NX = c->NX; g.NY = c->NY; g.NZ = c->NZ;
+    g.pitch = c->pitch; g.plane = c->plane; g.vol = c->vol;
+    g.hx = c->d_h; g.hy = c->d_h + c->nx; g.hz = c->d_h + c->nx + c->ny;
+    return g;
+}
+
+template <typename R>
+int fwd_impl(csem_ctx *c, const void *rho, const csem_points *src, const csem_points *rec, double *d_syn,
+             void *Evol, cudaStream_t st) {
+    const int S = src->n, NR = rec->n;
+    std::vector<Tap> itaps((size_t)S * 8), rtaps((size_t)std::max(NR, 1) * 8);
+    for (int s = 0; s < S; ++s)
+        TRY(point_taps(c, src->x[s], src->y[s], src->z[s], src->comp[s], true, 0, &itaps[(size_t)s * 8]));
+    for (int r = 0; r < NR; ++r)
+        TRY(point_taps(c, rec->x[r], rec->y[r], rec->z[r], rec->comp[r], false, r, &rtaps[(size_t)r * 8]));
+    CK(cudaMemcpyAsync(c->d_itaps, itaps.data(), itaps.size() * sizeof(Tap), cudaMemcpyHostToDevice, st));
+    if (NR > 0) CK(cudaMemcpyAsync(c->d_rtaps, rtaps.data(), (size_t)NR * 8 * sizeof(Tap), cudaMemcpyHostToDevice, st));
+    CK(csem::launch_coef_init<R>(geo(c), (const R *)rho, (R *)c->d_cE, 2.0 * c->w0 * c->dt, c->d_bad, st));
+    CK(cudaMemsetAsync(c->d_fields, 0, (size_t)S * 6 * c->vol * sizeof(R), st));
+    CK(cudaMemsetAsync(c->d_psi, 0, (size_t)S * c->psi_stride * sizeof(R), st));
+    const bool dft = (Evol != nullptr);
+    const size_t vbytes = (size_t)S * 3 * c->nf * c->vol * sizeof(typename C2<R>::T);
+    if (dft) CK(cudaMemsetAsync(Evol, 0, vbytes, st));
+    if (dft && c->kahan) CK(cudaMemsetAsync(c->d_comp, 0, vbytes, st));
+    if (NR > 0) CK(cudaMemsetAsync(c->d_racc, 0, (size_t)S * NR * c->nf * sizeof(double2), st));
+    if (c->d_trace && NR > 0) CK(cudaMemsetAsync(c->d_trace, 0, (size_t)S * NR * c->nt * sizeof(double), st));
+
+    csem::StepParams<R> p = step_params<R>(c, dft, Evol);
+    csem::PointParams<R> q;
+    q.fields = (R *)c->d_fields; q.vol = c->vol; q.cE = (const R *)c->d_cE; q.step = c->d_step;
+    q.nt = c->nt; q.nf = c->nf;
+    q.n_rec = NR; q.rtaps = c->d_rtaps; q.racc = c->d_racc; q.w64 = c->d_w64; q.trace = c->d_trace;
+    q.n_itaps = 8; q.itaps = c->d_itaps; q.itap_stride = 8;
+    q.n_emit = 1; q.J = 1; q.coef = c->d_ones; q.T = c->d_T;   // unit moment for every source
+    TRY(run_steps<R>(c, S, dft, p, q, st));
+    c->last_nrec = NR;
+    if (NR > 0) CK(csem::launch_finalize_receivers(c->d_racc, d_syn, S, NR, c->nf, c->d_alpha, st));
+    if (dft)
+        CK(csem::launch_finalize_volume<R>((typename C2<R>::T *)Evol,
+                                           c->kahan ? (const typename C2<R>::T *)c->d_comp : nullptr, c->vol, S,
+                                           c->nf, c->d_alpha, st));
+    return CSEM_OK;
+}
+
+template <typename R>
+int adj_impl(csem_ctx *c, const void *rho, const csem_points *rec, int S, const double *resid, const double *basis,
+             void *Vvol, cudaStream_t st) {
+    const int NR = rec->n;
+    std::vector<Tap> itaps((size_t)NR * 8);
+    for (int r = 0; r < NR; ++r)
+        TRY(point_taps(c, rec->x[r], rec->y[r], rec->z[r], rec->comp[r], true, r, &itaps[(size_t)r * 8]));
+    CK(cudaMemcpyAsync(c->d_itaps, itaps.data(), itaps.size() * sizeof(Tap), cudaMemcpyHostToDevice, st));
+    CK(csem::launch_adjoint_coef(resid, c->d_coef, S, NR, c->nf, c->d_alpha + 2 * c->nf, 1.0 / c->dt, st));
+    CK(csem::launch_coef_init<R>(geo(c), (const R *)rho, (R *)c->d_cE, 2.0 * c->w0 * c->dt, c->d_bad, st));
+    CK(cudaMemsetAsync(c->d_fields, 0, (size_t)S * 6 * c->vol * sizeof(R), st));
+    CK(cudaMemsetAsync(c->d_psi, 0, (size_t)S * c->psi_stride * sizeof(R), st));
+    const size_t vbytes = (size_t)S * 3 * c->nf * c->vol * sizeof(typename C2<R>::T);
+    CK(cudaMemsetAsync(Vvol, 0, vbytes, st));
+    if (c->kahan) CK(cudaMemsetAsync(c->d_comp, 0, vbytes, st));
+    csem::StepParams<R> p = step_params<R>(c, true, Vvol);
+    csem::PointParams<R> q;
+    q.fields = (R *)c->d_fields; q.vol = c->vol; q.cE = (const R *)c->d_cE; q.step = c->d_step;
+    q.nt = c->nt; q.nf = c->nf;
+    q.n_rec = 0; q.rtaps = nullptr; q.racc = nullptr; q.w64 = c->d_w64; q.trace = nullptr;
+    q.n_itaps = NR * 8; q.itaps = c->d_itaps; q.itap_stride = 0;
+    q.n_emit = NR; q.J = 2 * c->nf; q.coef = c->d_coef; q.T = basis;
+    TRY(run_steps<R>(c, S, true, p, q, st));
+    CK(csem::launch_finalize_volume<R>((typename C2<R>::T *)Vvol,
+                                       c->kahan ? (const typename C2<R>::T *)c->d_comp : nullptr, c->vol, S, c->nf,
+                                       c->d_alpha + c->nf, st));
+    return CSEM_OK;
+}
+
+template <typename R>
+int time_impl(csem_ctx *c, int S, void *vol, int launches, double *ms, cudaStream_t st) {
+    csem::StepParams<R> p = step_params<R>(c, true, vol);
+    csem::PointParams<R> q;
+    q.fields = (R *)c->d_fields; q.vol = c->vol; q.cE = (const R *)c->d_cE; q.step = c->d_step;
+    q.nt = c->nt; q.nf = c->nf;
+    q.n_rec = c->last_nrec; q.rtaps = c->d_rtaps; q.racc = c->d_racc; q.w64 = c->d_w64; q.trace = nullptr;
+    q.n_itaps = 8; q.itaps = c->d_itaps; q.itap_stride = 8;
+    q.n_emit = 1; q.J = 1; q.coef = c->d_ones; q.T = c->d_T;
+    CK(cudaMemsetAsync(c->d_step, 0, sizeof(int), st));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int which[3] = {1, 2, 4};
+    for (int w = 0; w < 3; ++w) {
+        for (int j = 0; j < 2; ++j) CK(csem::launch_step<R>(p, q, S, j % c->nt, true, c->kahan != 0, st, which[w]));
+        CK(cudaEventRecord(e0, st));
+        for (int j = 0; j < launches; ++j)
+            CK(csem::launch_step<R>(p, q, S, j % c->nt, true, c->kahan != 0, st, which[w]));
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, e0, e1));
+        ms[w] = (double)t / launches;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return CSEM_OK;
+}
+
+void free_ctx(csem_ctx *c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+    void *ptrs[] = {c->d_tab, c->d_h, c->d_cE, c->d_fields, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
+                    c->d_alpha, c->d_racc, c->d_coef, c->d_T, c->d_ones, c->d_rtaps, c->d_itaps, c->d_step, c->d_bad};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *csem_last_error(void) { return g_err.c_str(); }
+
+int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
+    if (!out || !g || !o) return fail(CSEM_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (g->npml < 0 || g->nx < 2 * g->npml + 2 || g->ny < 2 * g->npml + 2 || g->nz < 2 * g->npml + 2)
+        return fail(CSEM_ERR_INVALID_ARG, "grid too small for its CPML");
+    if (!g->xn || !g->yn || !g->zn) return fail(CSEM_ERR_INVALID_ARG, "NULL node coordinates");
+    if (o->precision != 32 && o->precision != 64) return fail(CSEM_ERR_INVALID_ARG, "precision must be 32 or 64");
+    if (o->n_freq < 1 || o->n_freq > csem::kMaxFreq || !o->freqs)
+        return fail(CSEM_ERR_INVALID_ARG, "n_freq must be in 1..8");
+    if (!(o->f0 > 0.0) || !(o->rho_max > 0.0)) return fail(CSEM_ERR_INVALID_ARG, "f0 and rho_max must be > 0");
+    if (o->max_src < 1 || o->max_rec < 0 || o->max_src > 65535)
+        return fail(CSEM_ERR_INVALID_ARG, "max_src must be >= 1, max_rec >= 0");
+    for (int f = 0; f < o->n_freq; ++f)
+        if (!(o->freqs[f] > 0.0) || !std::isfinite(o->freqs[f])) return fail(CSEM_ERR_INVALID_ARG, "bad frequency");
+
+    csem_ctx *c = new csem_ctx();
+    cudaGetDevice(&c->device);
+    c->nx = g->nx; c->ny = g->ny; c->nz = g->nz; c->npml = g->npml;
+    c->NX = c->nx + 1; c->NY = c->ny + 1; c->NZ = c->nz + 1;
+    c->pitch = (c->NX + 7) / 8 * 8;
+    c->plane = (long long)c->pitch * c->NY;
+    c->vol = c->plane * c->NZ;
+    const int ns[3] = {c->nx, c->ny, c->nz};
+    const double *xs[3] = {g->xn, g->yn, g->zn};
+    double inv2max[3] = {0, 0, 0};
+    for (int a = 0; a < 3; ++a) {
+        Axis &A = c->ax[a];
+        A.n = ns[a];
+        A.x.assign(xs[a], xs[a] + A.n + 1);
+        A.h.resize(A.n);
+        A.ht.resize(A.n + 1);
+        for (int i = 0; i < A.n; ++i) {
+            A.h[i] = A.x[i + 1] - A.x[i];
+            if (!(A.h[i] > 0.0) || !std::isfinite(A.h[i])) {
+                delete c;
+                return fail(CSEM_ERR_INVALID_ARG, "node coordinates must be finite and strictly increasing");
+            }
+            inv2max[a] = std::max(inv2max[a], 1.0 / (A.h[i] * A.h[i]));
+        }
+        A.ht[0] = 0.5 * A.h[0];
+        A.ht[A.n] = 0.5 * A.h[A.n - 1];
+        for (int i = 1; i < A.n; ++i) A.ht[i] = 0.5 * (A.h[i - 1] + A.h[i]);
+    }
+    c->f0 = o->f0;
+    c->w0 = 2.0 * M_PI * o->f0;
+    c->rho_max = o->rho_max;
+    c->safety = o->cfl_safety > 0.0 ? o->cfl_safety : 0.99;
+    // fictitious speed v = 1/sqrt(mu0 eps), eps = sigma/(2 w0)  (Eq. 2)
+    const double vmax = std::sqrt(2.0 * c->w0 * c->rho_max / kMu0);
+    const double dt_lim = 1.0 / (vmax * std::sqrt(inv2max[0] + inv2max[1] + inv2max[2]));
+    if (o->dt > 0.0) {
+        if (o->dt > dt_lim * (1.0 + 1e-12)) {
+            delete c;
+            return fail(CSEM_ERR_CFL, "dt above the CFL limit " + std::to_string(dt_lim));
+        }
+        c->dt = o->dt;
+    } else {
+        c->dt = c->safety * dt_lim;
+    }
+    c->nf = o->n_freq;
+    c->freqs.assign(o->freqs, o->freqs + c->nf);
+    c->a.resize(c->nf);
+    c->kf.resize(c->nf);
+    double amin = 1e300;
+    for (int f = 0; f < c->nf; ++f) {
+        const double w = 2.0 * M_PI * c->freqs[f];
+        c->a[f] = std::sqrt(w * c->w0);
+        amin = std::min(amin, c->a[f]);
+        // k = sqrt(-i w / (2 w0)) on the principal branch = (1 - i)/2 sqrt(w / w0)  (Eq. 3)
+        c->kf[f] = std::sqrt(std::complex<double>(0.0, -w / (2.0 * c->w0)));
+    }
+    c->nt = o->nt > 0 ? o->nt : (int)std::ceil(kDecaySpan / (amin * c->dt));
+    c->precision = o->precision;
+    c->kahan = (o->precision == 32 && o->kahan) ? 1 : 0;
+    c->max_src = o->max_src;
+    c->max_rec = o->max_rec;
+    c->rsize = (c->precision == 32) ? 4 : 8;
+    for (int a = 0; a < 3; ++a) cpml_axis(c->ax[a], c->npml, c->dt, vmax, c->f0);
+    const int np2 = 2 * c->npml;
+    c->sx = (long long)c->NZ * c->NY * np2;
+    c->sy = (long long)c->NZ * np2 * c->pitch;
+    c->sz = (long long)np2 * c->NY * c->pitch;
+    c->psi_stride = 4 * (c->sx + c->sy + c->sz);
+    c->wavelet.assign(c->nt, 0.0);
+    c->wavelet[0] = 1.0 / c->dt;
+
+    int rc = CSEM_OK;
+    auto step = [&](int r) { if (rc == CSEM_OK) rc = r; };
+    if (c->precision == 32) step(upload_tables<float>(c)); else step(upload_tables<double>(c));
+    const size_t R = c->rsize, C2s = 2 * R;
+    const int S = c->max_src, NR = std::max(c->max_rec, 1);
+    step(dalloc(c, &c->d_h, (size_t)(c->nx + c->ny + c->nz) * sizeof(double)));
+    step(dalloc(c, &c->d_cE, 3 * (size_t)c->vol * R));
+    step(dalloc(c, &c->d_edge, 3 * (size_t)c->vol * R));
+    step(dalloc(c, &c->d_fields, (size_t)S * 6 * c->vol * R));
+    step(dalloc(c, &c->d_psi, (size_t)S * c->psi_stride * R));
+    if (c->kahan) step(dalloc(c, &c->d_comp, (size_t)S * 3 * c->nf * c->vol * C2s));
+    step(dalloc(c, &c->d_alpha, 3 * (size_t)c->nf * sizeof(double2)));
+    step(dalloc(c, &c->d_racc, (size_t)S * NR * c->nf * sizeof(double2)));
+    step(dalloc(c, &c->d_coef, (size_t)S * NR * 2 * c->nf * sizeof(double)));
+    step(dalloc(c, &c->d_T, (size_t)c->nt * sizeof(double)));
+    step(dalloc(c, &c->d_ones, (size_t)S * sizeof(double)));
+    step(dalloc(c, &c->d_rtaps, (size_t)NR * 8 * sizeof(Tap)));
+    step(dalloc(c, &c->d_itaps, (size_t)std::max(S, NR) * 8 * sizeof(Tap)));
+    step(dalloc(c, &c->d_step, sizeof(int)));
+    step(dalloc(c, &c->d_bad, sizeof(int)));
+    if (rc != CSEM_OK) { free_ctx(c); return rc; }
+    std::vector<double> hcat;
+    for (int a = 0; a < 3; ++a) hcat.insert(hcat.end(), c->ax[a].h.begin(), c->ax[a].h.end());
+    std::vector<double> ones((size_t)S, 1.0);
+    if (cudaMemcpy(c->d_h, hcat.data(), hcat.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_ones, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(c->d_bad, 0, sizeof(int)) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        free_ctx(c);
+        return fail(CSEM_ERR_CUDA, "context initialisation failed");
+    }
+    rc = update_wavelet(c);
+    if (rc != CSEM_OK) { free_ctx(c); return rc; }
+    *out = c;
+    return CSEM_OK;
+}
+
+void csem_destroy(csem_ctx *c) { free_ctx(c); }
+
+int csem_get_info(const csem_ctx *c, csem_info *info) {
+    if (!c || !info) return fail(CSEM_ERR_INVALID_ARG, "NULL argument");
+    info->nx = c->nx; info->ny = c->ny; info->nz = c->nz; info->npml = c->npml;
+    info->pitch = c->pitch; info->vol_elems = c->vol; info->dt = c->dt; info->nt = c->nt;
+    info->precision = c->precision; info->kahan = c->kahan; info->n_freq = c->nf;
+    info->max_src = c->max_src; info->max_rec = c->max_rec; info->workspace_bytes = c->bytes;
+    return CSEM_OK;
+}
+
+int csem_set_wavelet(csem_ctx *c, const double *w) {
+    if (!c) return fail(CSEM_ERR_INVALID_ARG, "NULL context");
+    CK(cudaDeviceSynchronize());
+    if (w) c->wavelet.assign(w, w + c->nt);
+    else { c->wavelet.assign(c->nt, 0.0); c->wavelet[0] = 1.0 / c->dt; }
+    return update_wavelet(c);
+}
+
+int csem_set_trace(csem_ctx *c, double *trace_dev) {
+    if (!c) return fail(CSEM_ERR_INVALID_ARG, "NULL context");
+    c->d_trace = trace_dev;
+    return CSEM_OK;
+}
+
+int csem_check(csem_ctx *c, void *stream) {
+    if (!c) return fail(CSEM_ERR_INVALID_ARG, "NULL context");
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    int bad = 0;
+    CK(cudaMemcpy(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemset(c->d_bad, 0, sizeof(int)));
+    if (bad) return fail(CSEM_ERR_NONFINITE, "a resistivity was non-positive or non-finite");
+    return CSEM_OK;
+}
+
+int csem_fwd_model(csem_ctx *c, const void *rho_dev, const csem_points *src, const csem_points *rec,
+                   double *d_syn_dev, void *Evol_dev, void *stream) {
+    if (!c || !rho_dev) return fail(CSEM_ERR_INVALID_ARG, "NULL context or model");
+    TRY(check_points(src, c->max_src, "sources", false));
+    TRY(check_points(rec, c->max_rec, "receivers", true));
+    if (rec->n > 0 && !d_syn_dev) return fail(CSEM_ERR_INVALID_ARG, "d_syn_dev is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    return c->precision == 32 ? fwd_impl<float>(c, rho_dev, src, rec, d_syn_dev, Evol_dev, st)
+                              : fwd_impl<double>(c, rho_dev, src, rec, d_syn_dev, Evol_dev, st);
+}
+
+int csem_adjoint_model(csem_ctx *c, const void *rho_dev, const csem_points *rec, int n_src, const double *resid_dev,
+                       const double *basis_dev, void *Vvol_dev, void *stream) {
+    if (!c || !rho_dev || !resid_dev || !basis_dev || !Vvol_dev) return fail(CSEM_ERR_INVALID_ARG, "NULL argument");
+    TRY(check_points(rec, c->max_rec, "receivers", false));
+    if (n_src < 1 || n_src > c->max_src) return fail(CSEM_ERR_INVALID_ARG, "n_src out of range");
+    cudaStream_t st = (cudaStream_t)stream;
+    return c->precision == 32 ? adj_impl<float>(c, rho_dev, rec, n_src, resid_dev, basis_dev, Vvol_dev, st)
+                              : adj_impl<double>(c, rho_dev, rec, n_src, resid_dev, basis_dev, Vvol_dev, st);
+}
+
+int csem_gradient(csem_ctx *c, const void *rho_dev, const void *Evol_dev, const void *Vvol_dev, int n_src, int wrt,
+                  void *grad_dev, void *stream) {
+    if (!c || !rho_dev || !Evol_dev || !Vvol_dev || !grad_dev) return fail(CSEM_ERR_INVALID_ARG, "NULL argument");
+    if (n_src < 1 || (wrt != 0 && wrt != 1)) return fail(CSEM_ERR_INVALID_ARG, "bad n_src or wrt");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (c->precision == 32)
+        CK(csem::launch_gradient<float>(geo(c), (const float *)rho_dev, (const float2 *)Evol_dev,
+                                        (const float2 *)Vvol_dev, n_src, c->nf, wrt, (float *)c->d_edge,
+                                        (float *)grad_dev, st));
+    else
+        CK(csem::launch_gradient<double>(geo(c), (const double *)rho_dev, (const double2 *)Evol_dev,
+                                         (const double2 *)Vvol_dev, n_src, c->nf, wrt, (double *)c->d_edge,
+                                         (double *)grad_dev, st));
+    return CSEM_OK;
+}
+
+long long csem_launch_count(void) { return csem::g_launches.load(); }
+
+int csem_time_step_kernels(csem_ctx *c, int n_src, void *vol_dev, int launches, double *ms_out, void *stream) {
+    if (!c || !vol_dev || !ms_out || launches < 1 || n_src < 1 || n_src > c->max_src)
+        return fail(CSEM_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    return c->precision == 32 ? time_impl<float>(c, n_src, vol_dev, launches, ms_out, st)
+                              : time_impl<double>(c, n_src, vol_dev, launches, ms_out, st);
+}
+
+int csem_misfit(int n, const double *d_obs, const double *d_syn, const double *w, double *resid, double *phi,
+                void *stream) {
+    if (n < 0 || (n > 0 && (!d_obs || !d_syn || !resid)) || !phi) return fail(CSEM_ERR_INVALID_ARG, "bad argument");
+    CK(csem::launch_misfit(n, d_obs, d_syn, w, resid, phi, (cudaStream_t)stream));
+    return CSEM_OK;
+}
+
+int csem_estimate_adjoint_basis(double dt, int nt, const double *freqs, int nf, double f0, double gamma,
+                                int gamma_is_relative, int max_iter, double tol, double *basis_dev,
+                                double *fit_residual_host, int *iters_host, void *stream) {
+    if (!(dt > 0.0) || nt < 1 || !freqs || nf < 1 || nf > csem::kMaxFreq || !(f0 > 0.0) || !(gamma >= 0.0) ||
+        max_iter < 0 || !basis_dev)
+        return fail(CSEM_ERR_INVALID_ARG, "bad argument");
+    double a[csem::kMaxFreq];
+    for (int f = 0; f < nf; ++f) {
+        if (!(freqs[f] > 0.0)) return fail(CSEM_ERR_INVALID_ARG, "bad frequency");
+        a[f] = std::sqrt(2.0 * M_PI * freqs[f] * 2.0 * M_PI * f0);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int m = 2 * nf;
+    double *scratch = nullptr;
+    const size_t sbytes = (size_t)m * 2 * nt * sizeof(double) + (size_t)(m * m + 2 + m) * sizeof(double) +
+                          (size_t)m * sizeof(int) + 64;
+    CK(cudaMallocAsync((void **)&scratch, sbytes, st));
+    double *gram = scratch + (size_t)m * 2 * nt;
+    double *scal = gram + m * m;           // [0] gamma, [1..m] fit per column
+    int *iters = (int *)(scal + 1 + m);
+    cudaError_t e = csem::launch_basis(dt, nt, a, nf, gamma, gamma_is_relative, max_iter, tol, basis_dev, scratch,
+                                       gram, scal, iters, st);
+    std::vector<double> hs(1 + m);
+    std::vector<int> hi(m);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), scal, (1 + m) * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hi.data(), iters, m * sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(scratch, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return fail(CSEM_ERR_CUDA, std::string("adjoint basis: ") + cudaGetErrorString(e));
+    if (fit_residual_host) *fit_residual_host = *std::max_element(hs.begin() + 1, hs.end());
+    if (iters_host) *iters_host = *std::max_element(hi.begin(), hi.end());
+    return CSEM_OK;
+}
+
+}  // extern "C"

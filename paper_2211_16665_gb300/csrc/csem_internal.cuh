@@ -1,0 +1,126 @@
+// Internal declarations shared by the CUDA translation units of the engine.
+// Layout of one source's state in HBM (all per-source blocks are contiguous):
+//   fields  [6][vol]         Ex, Ey, Ez, Hx, Hy, Hz on the padded node lattice,
+//                            index (k*NY + j)*pitch + i, NY = ny+1, NZ = nz+1
+//   psi     12 CPML memory arrays, each only inside the slab of its axis:
+//           x-slabs [NZ][NY][2 npml]   : psi(Hy,dEz/dx) psi(Hz,dEy/dx) psi(Ey,dHz/dx) psi(Ez,dHy/dx)
+//           y-slabs [NZ][2 npml][pitch]: psi(Hx,dEz/dy) psi(Hz,dEx/dy) psi(Ex,dHz/dy) psi(Ez,dHx/dy)
+//           z-slabs [2 npml][NY][pitch]: psi(Hx,dEy/dz) psi(Hy,dEx/dz) psi(Ex,dHy/dz) psi(Ey,dHx/dz)
+//   acc     [3][nf][vol] complex damped-transform accumulators (the caller's volume buffer)
+//   comp    [3][nf][vol] complex Kahan compensation (context workspace, FP32 only)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+namespace csem {
+
+extern std::atomic<long long> g_launches;   // kernels launched by this library
+
+template <typename R> struct C2;
+template <> struct C2<float> { typedef float2 T; };
+template <> struct C2<double> { typedef double2 T; };
+
+constexpr int kMaxFreq = 8;
+constexpr int kBlock = 256;
+
+// Slab index of a half node i (between nodes i and i+1) on an axis of n cells:
+// the first npml and the last npml half nodes lie in the CPML.
+__host__ __device__ inline int slab_half(int i, int n, int npml) {
+    if (i < npml) return i;
+    if (i >= n - npml && i < n) return i - n + 2 * npml;
+    return -1;
+}
+// Slab index of an interior node i: nodes 1..npml-1 and n-npml+1..n-1 lie in the CPML
+// (node 0 / n carry no update, the interface nodes npml and n-npml have zero damping).
+__host__ __device__ inline int slab_node(int i, int n, int npml) {
+    if (i >= 1 && i < npml) return i;
+    if (i > n - npml && i < n) return i - n + 2 * npml - 1;
+    return -1;
+}
+
+template <typename R>
+struct AxisTab {          // per-axis stepping tables (device, type R)
+    const R *ih_h, *ih_n; // 1/h at half nodes [n], 1/h~ at nodes [n+1]
+    const R *b_h, *a_h;   // CPML recursion at half nodes [n]
+    const R *b_n, *a_n;   // CPML recursion at nodes [n+1]
+};
+
+template <typename R>
+struct StepParams {
+    int nx, ny, nz, NX, NY, NZ, pitch, npml;
+    long long plane, vol;          // pitch*NY, plane*NZ
+    AxisTab<R> ax, ay, az;
+    R *fields;                     // [S][6][vol]
+    R *psi;                        // [S][psi_stride]
+    long long psi_stride, sx, sy, sz;
+    const R *cE;                   // [3][vol] dt/eps on each E edge
+    R cH;                          // dt/mu0
+    const int *step;               // device step counter (chunk base)
+    int KZ;                        // z planes per thread
+    int nf;
+    const typename C2<R>::T *w;    // [nt][nf] exp((-1+i) a_k n dt)
+    typename C2<R>::T *acc;        // [S][3][nf][vol] or nullptr
+    typename C2<R>::T *comp;       // Kahan compensation or nullptr
+};
+
+struct Tap {                       // one trilinear tap of a point operator (32 bytes)
+    long long idx;                 // lattice index inside a component block
+    double w;                      // weight (divided by the edge's dual volume for injection)
+    int comp;                      // 0,1,2
+    int emit;                      // emitter (series) id for injection, receiver id for sampling
+    int pad0, pad1;
+};
+
+template <typename R>
+struct PointParams {
+    R *fields; long long vol;
+    const R *cE;
+    const int *step;
+    int nt, nf;
+    // sampling (receivers shared by all sources)
+    int n_rec; const Tap *rtaps;   // [n_rec][8]
+    double2 *racc;                 // [S][n_rec][nf]
+    const double2 *w64;            // [nt][nf]
+    double *trace;                 // [S][n_rec][nt] or nullptr
+    // injection
+    int n_itaps; const Tap *itaps; // source s uses itaps[s*itap_stride .. + n_itaps)
+    int itap_stride;
+    int n_emit, J;
+    const double *coef;            // [S][n_emit][J]
+    const double *T;               // [nt][J]
+};
+
+// ---- launchers (kern_step.cu) ----
+// which: bit 0 = H half-step (+ transform), bit 1 = point operators, bit 2 = E step
+template <typename R>
+cudaError_t launch_step(const StepParams<R> &p, const PointParams<R> &q, int S, int jstep,
+                        bool dft, bool kahan, cudaStream_t st, int which = 7);
+cudaError_t launch_advance(int *step, int by, cudaStream_t st);
+
+// ---- launchers (kern_aux.cu) ----
+struct GeoD {                      // double-precision geometry for set-up and gradient kernels
+    int nx, ny, nz, NX, NY, NZ, pitch;
+    long long plane, vol;
+    const double *hx, *hy, *hz;    // primal widths [n]
+};
+template <typename R>
+cudaError_t launch_coef_init(const GeoD &g, const R *rho, R *cE, double two_w0_dt, int *bad_flag, cudaStream_t st);
+template <typename R>
+cudaError_t launch_finalize_volume(typename C2<R>::T *acc, const typename C2<R>::T *comp, long long vol, int S,
+                                   int nf, const double2 *alpha, cudaStream_t st);
+cudaError_t launch_finalize_receivers(const double2 *racc, double *out, int S, int n_rec, int nf,
+                                      const double2 *alpha, cudaStream_t st);
+cudaError_t launch_adjoint_coef(const double *resid, double *coef, int S, int n_rec, int nf,
+                                const double2 *kf, double inv_dt, cudaStream_t st);
+template <typename R>
+cudaError_t launch_gradient(const GeoD &g, const R *rho, const typename C2<R>::T *E, const typename C2<R>::T *V,
+                            int S, int nf, int wrt, R *edge_scratch, R *grad, cudaStream_t st);
+cudaError_t launch_misfit(int n, const double *d_obs, const double *d_syn, const double *w, double *resid,
+                          double *phi, cudaStream_t st);
+cudaError_t launch_basis(double dt, int nt, const double *a, int nf, double gamma, int gamma_rel, int max_iter,
+                         double tol, double *basis, double *scratch, double *gram, double *out_scalars,
+                         int *out_iters, cudaStream_t st);
+
+}  // namespace csem

@@ -1,0 +1,146 @@
+"""Torch-facing wrapper of the C ABI: device memory and streams come from
+PyTorch, every computation from the CUDA library (no fallback path).
+
+  Engine(...)                 one context = one grid / frequency set / dt
+  .fwd_model(rho, src, rec)   -> d_syn [S, R, F] complex128 (+ E volumes)
+  .estimate_adjoint_basis()   -> B+ [nt, 2F] float64 (device), fit residual
+  .adjoint_model(rho, rec, resid, basis) -> conj(v) volumes
+  .gradient(rho, E, V, wrt)   -> [nz, ny, nx]
+  misfit(d_obs, d_syn, w)     -> phi (0-d tensor), resid
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _capi
+
+
+def _stream():
+    return ctypes_void(torch.cuda.current_stream().cuda_stream)
+
+
+def ctypes_void(v):
+    import ctypes
+    return ctypes.c_void_p(v)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    import ctypes
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Engine:
+    """One context: grid, frequencies, dt/nt, precision, batch capacity."""
+
+    def __init__(self, xn, yn, zn, npml, freqs, f0=1.0, rho_max=1.0, precision=32, kahan=1,
+                 max_src=1, max_rec=0, nt=0, dt=0.0, device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the CSEM engine needs a CUDA device")
+        self.device = torch.device(device or "cuda")
+        with torch.cuda.device(self.device):
+            self.ctx = _capi.create(xn, yn, zn, npml, freqs, f0=f0, rho_max=rho_max, dt=dt, nt=nt,
+                                    precision=precision, kahan=kahan, max_src=max_src, max_rec=max_rec)
+        info = _capi.get_info(self.ctx)
+        self.info = info
+        self.nx, self.ny, self.nz = info.nx, info.ny, info.nz
+        self.pitch, self.vol = info.pitch, info.vol_elems
+        self.dt, self.nt = info.dt, info.nt
+        self.precision = precision
+        self.freqs = np.asarray(freqs, np.float64)
+        self.nf = self.freqs.size
+        self.f0 = f0
+        self.real = torch.float32 if precision == 32 else torch.float64
+        self.cplx = torch.complex64 if precision == 32 else torch.complex128
+        self._wavelet = None
+
+    @classmethod
+    def from_workload(cls, wl, max_src=None, max_rec=None, nt=None, **kw):
+        return cls(wl.xn, wl.yn, wl.zn, wl.npml, wl.freqs, f0=wl.f0, rho_max=wl.rho_max,
+                   precision=kw.pop("precision", wl.precision), kahan=kw.pop("kahan", wl.kahan),
+                   max_src=max_src or wl.src.n, max_rec=max_rec if max_rec is not None else wl.rec.n,
+                   nt=nt if nt is not None else (wl.nt or 0), **kw)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            _capi.destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- shapes ------------------------------------------------------------
+    def volume_shape(self, n_src):
+        return (n_src, 3, self.nf, self.nz + 1, self.ny + 1, self.pitch)
+
+    def model_tensor(self, rho) -> torch.Tensor:
+        t = torch.as_tensor(np.asarray(rho), dtype=self.real) if not torch.is_tensor(rho) else rho.to(self.real)
+        return t.to(self.device).contiguous()
+
+    # -- C-ABI calls ---------------------------------------------------------
+    def fwd_model(self, rho: torch.Tensor, src, rec, keep_volume=False, trace=False):
+        S = src.n
+        d = torch.zeros((S, rec.n, self.nf), dtype=torch.complex128, device=self.device)
+        vol = torch.empty(self.volume_shape(S), dtype=self.cplx, device=self.device) if keep_volume else None
+        tr = None
+        if trace:
+            tr = torch.zeros((S, rec.n, self.nt), dtype=torch.float64, device=self.device)
+            _capi.set_trace(self.ctx, _ptr(tr))
+        try:
+            _capi.fwd_model(self.ctx, _ptr(rho), src, rec, _ptr(d) if rec.n else None, _ptr(vol), _stream())
+        finally:
+            if trace:
+                _capi.set_trace(self.ctx, None)
+        out = [d]
+        if keep_volume:
+            out.append(vol)
+        if trace:
+            out.append(tr)
+        return out[0] if len(out) == 1 else tuple(out)
+
+    def set_wavelet(self, wavelet=None):
+        _capi.set_wavelet(self.ctx, wavelet)
+
+    def estimate_adjoint_basis(self, gamma=1e-12, relative=True, max_iter=200, tol=1e-14):
+        basis = torch.empty((self.nt, 2 * self.nf), dtype=torch.float64, device=self.device)
+        fit, its = _capi.estimate_adjoint_basis(self.dt, self.nt, self.freqs, self.f0, gamma, int(relative),
+                                                max_iter, tol, _ptr(basis), _stream())
+        return basis, fit, its
+
+    def adjoint_model(self, rho, rec, resid: torch.Tensor, basis: torch.Tensor):
+        S = resid.shape[0]
+        assert resid.dtype == torch.complex128 and resid.shape[1:] == (rec.n, self.nf)
+        vol = torch.empty(self.volume_shape(S), dtype=self.cplx, device=self.device)
+        _capi.adjoint_model(self.ctx, _ptr(rho), rec, S, _ptr(resid.contiguous()), _ptr(basis), _ptr(vol), _stream())
+        return vol
+
+    def gradient(self, rho, Evol, Vvol, wrt="lnrho", out=None):
+        if out is None:
+            out = torch.zeros((self.nz, self.ny, self.nx), dtype=self.real, device=self.device)
+        _capi.gradient(self.ctx, _ptr(rho), _ptr(Evol), _ptr(Vvol), Evol.shape[0], 1 if wrt == "lnrho" else 0,
+                       _ptr(out), _stream())
+        return out
+
+    def check(self):
+        _capi.check(self.ctx, _stream())
+
+
+def misfit(d_obs: torch.Tensor, d_syn: torch.Tensor, weight: Optional[torch.Tensor] = None):
+    """phi = 1/2 sum |w (d_obs - d_syn)|^2 and resid = w^2 (d_obs - d_syn), on the device."""
+    d_obs = d_obs.contiguous()
+    d_syn = d_syn.contiguous()
+    resid = torch.empty_like(d_syn)
+    phi = torch.empty((), dtype=torch.float64, device=d_syn.device)
+    _capi.misfit(d_syn.numel(), _ptr(d_obs), _ptr(d_syn), _ptr(weight.contiguous()) if weight is not None else None,
+                 _ptr(resid), _ptr(phi), _stream())
+    return phi, resid

@@ -1,0 +1,187 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs, element by element.
+
+Tolerances (relative L2 over all outputs of a kind):
+  FP64 stencil: 1e-10 (same arithmetic, rounding order only);
+  FP32 stencil: receivers 1e-5, volumes / gradient 1e-3 (the targets stated
+  for the hot path; the FP32 field over a few thousand lossless steps carries
+  ~1e-6 relative round-off).
+Sizes span several thread blocks in every direction and ragged tails.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from oracle import fdtd  # noqa: E402
+from paper_2211_16665_gb300 import workloads as W  # noqa: E402
+from paper_2211_16665_gb300.engine import Engine, misfit  # noqa: E402
+from paper_2211_16665_gb300._capi import CsemError  # noqa: E402
+
+
+def rel_l2(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def gpu_volume(eng, v):
+    """[S,3,F,NZ,NY,pitch] device -> numpy [S,3,F,NZ,NY,NX]."""
+    return v.cpu().numpy()[..., : eng.nx + 1].astype(np.complex128)
+
+
+@pytest.fixture(scope="module")
+def box():
+    wl = W.small_box(n_core=24, h=100.0, npml=8, ratio=1.08, n_st=4, n_rec=6, n_freq=2)
+    pb = fdtd.problem_from_workload(wl)
+    return wl, pb
+
+
+@pytest.fixture(scope="module")
+def box_oracle(box):
+    wl, pb = box
+    d_obs = fdtd.forward(pb, wl.rho_true, wl.src, wl.rec)
+    d, E, tr = fdtd.forward(pb, wl.rho, wl.src, wl.rec, keep_volume=True, return_trace=True)
+    phi, r = fdtd.misfit(d_obs, d)
+    Bp, fit = fdtd.adjoint_basis(pb, 1e-12)
+    V = fdtd.adjoint(pb, wl.rho, wl.rec, r, Bp)
+    g = fdtd.gradient(pb, wl.rho, E, V, wrt="lnrho")
+    gs = fdtd.gradient(pb, wl.rho, E, V, wrt="sigma")
+    return dict(d_obs=d_obs, d=d, E=E, tr=tr, phi=phi, r=r, Bp=Bp, V=V, g=g, gs=gs)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_forward_receivers_traces_volumes(box, box_oracle, precision):
+    wl, pb = box
+    o = box_oracle
+    eng = Engine.from_workload(wl, precision=precision, kahan=1)
+    assert abs(eng.dt - pb.dt) <= 1e-14 * pb.dt and eng.nt == pb.nt
+    rho = eng.model_tensor(wl.rho)
+    d, E, tr = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True, trace=True)
+    torch.cuda.synchronize()
+    tol_r, tol_v = (1e-10, 1e-10) if precision == 64 else (1e-5, 1e-3)
+    assert rel_l2(tr.cpu().numpy(), o["tr"]) <= (1e-10 if precision == 64 else 1e-4)
+    assert rel_l2(d.cpu().numpy(), o["d"]) <= tol_r
+    Eg = gpu_volume(eng, E)
+    assert rel_l2(Eg, o["E"]) <= tol_v
+    # row padding and off-lattice entries stay zero
+    assert torch.count_nonzero(E[..., eng.nx + 1:]) == 0
+    eng.check()
+    eng.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_adjoint_and_gradient(box, box_oracle, precision):
+    wl, pb = box
+    o = box_oracle
+    eng = Engine.from_workload(wl, precision=precision, kahan=1)
+    rho = eng.model_tensor(wl.rho)
+    d, E = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)
+    d_obs = torch.as_tensor(o["d_obs"], device=eng.device)
+    phi, r = misfit(d_obs, d)
+    phi_tol = 1e-4 if precision == 32 else 1e-10
+    assert abs(phi.item() - o["phi"]) <= phi_tol * o["phi"]
+    basis, fit, its = eng.estimate_adjoint_basis(gamma=1e-12, relative=True)
+    assert rel_l2(basis.cpu().numpy(), o["Bp"]) <= 1e-7
+    V = eng.adjoint_model(rho, wl.rec, r, basis)
+    tol = 1e-9 if precision == 64 else 1e-3
+    assert rel_l2(gpu_volume(eng, V), o["V"]) <= tol
+    g = eng.gradient(rho, E, V, wrt="lnrho")
+    gs = eng.gradient(rho, E, V, wrt="sigma")
+    assert rel_l2(g.cpu().numpy(), o["g"]) <= tol
+    assert rel_l2(gs.cpu().numpy(), o["gs"]) <= tol
+    eng.close()
+
+
+def test_basis_matches_oracle_on_workload_sets():
+    from oracle import basis as ob
+    for (dt, nt, freqs) in ((0.004, 1000, [0.25, 0.75, 2.25]), (9.04e-4, 12328, [0.25, 0.5, 0.75, 1.0])):
+        B = ob.basis_matrix(dt, nt, freqs, 1.0)
+        g = ob.gamma_from_relative(B, 1e-12)
+        ref = ob.pinv_pushthrough(B, g)
+        eng_basis = torch.empty((nt, 2 * len(freqs)), dtype=torch.float64, device="cuda")
+        from paper_2211_16665_gb300 import _capi
+        import ctypes
+        fit, its = _capi.estimate_adjoint_basis(dt, nt, freqs, 1.0, 1e-12, 1, 200, 1e-15,
+                                                ctypes.c_void_p(eng_basis.data_ptr()),
+                                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rel_l2(eng_basis.cpu().numpy(), ref) <= 1e-7
+        assert abs(fit - ob.fit_residual(B, ref)) <= 1e-6 + 1e-3 * ob.fit_residual(B, ref)
+        assert 1 <= its <= 200
+
+
+def test_batched_equals_single_source_runs(box):
+    wl, pb = box
+    src = W.Points.make([[0.0, 0.0, wl.src.z[0]], [150.0, -120.0, wl.src.z[0]], [-260.0, 40.0, wl.src.z[0]]], [0, 1, 0])
+    eng = Engine.from_workload(wl, precision=32, kahan=1, max_src=3)
+    rho = eng.model_tensor(wl.rho)
+    d3, E3 = eng.fwd_model(rho, src, wl.rec, keep_volume=True)
+    for s in range(3):
+        d1, E1 = eng.fwd_model(rho, src.subset([s]), wl.rec, keep_volume=True)
+        assert torch.equal(d1[0], d3[s])
+        assert torch.equal(E1[0], E3[s])
+    eng.close()
+
+
+def test_wavelet_invariance_on_gpu(box):
+    wl, pb = box
+    eng = Engine.from_workload(wl, precision=64)
+    rho = eng.model_tensor(wl.rho_true)
+    d_imp = eng.fwd_model(rho, wl.src, wl.rec).cpu().numpy()
+    t = (np.arange(eng.nt) + 0.5) * eng.dt
+    a = (np.pi * 5.0 * (t - 0.3)) ** 2
+    eng.set_wavelet((1 - 2 * a) * np.exp(-a))
+    d_ric = eng.fwd_model(rho, wl.src, wl.rec).cpu().numpy()
+    assert rel_l2(d_ric, d_imp) <= 1e-9
+    eng.close()
+
+
+def test_plain_tiny_fp64_forward_adjoint_gradient():
+    wl = W.plain_tiny()
+    pb = fdtd.problem_from_workload(wl)
+    d_obs = fdtd.forward(pb, wl.rho_true, wl.src, wl.rec)
+    d, E = fdtd.forward(pb, wl.rho, wl.src, wl.rec, keep_volume=True)
+    phi, r = fdtd.misfit(d_obs, d)
+    Bp, fit = fdtd.adjoint_basis(pb, 1e-12)
+    V = fdtd.adjoint(pb, wl.rho, wl.rec, r, Bp)
+    g = fdtd.gradient(pb, wl.rho, E, V)
+
+    eng = Engine.from_workload(wl)
+    assert eng.precision == 64 and eng.nt == 1500
+    rho = eng.model_tensor(wl.rho)
+    dg, Eg = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)
+    assert rel_l2(dg.cpu().numpy(), d) <= 1e-10
+    phig, rg = misfit(torch.as_tensor(d_obs, device="cuda"), dg)
+    basis, fitg, _ = eng.estimate_adjoint_basis()
+    Vg = eng.adjoint_model(rho, wl.rec, rg, basis)
+    gg = eng.gradient(rho, Eg, Vg)
+    assert rel_l2(gg.cpu().numpy(), g) <= 1e-8
+    eng.close()
+
+
+def test_error_statuses(box):
+    wl, pb = box
+    eng = Engine.from_workload(wl, precision=32)
+    rho = eng.model_tensor(wl.rho)
+    outside = W.Points.make([[1e6, 0.0, 500.0]], 0)
+    with pytest.raises(CsemError) as e:
+        eng.fwd_model(rho, outside, wl.rec)
+    assert e.value.code == -2
+    too_many = W.Points.make([[0.0, 0.0, 500.0]] * 2, 0)
+    with pytest.raises(CsemError) as e:
+        eng.fwd_model(rho, too_many, wl.rec)
+    assert e.value.code == -1
+    bad = rho.clone()
+    bad[3, 4, 5] = float("nan")
+    eng.fwd_model(bad, wl.src, wl.rec)
+    with pytest.raises(CsemError) as e:
+        eng.check()
+    assert e.value.code == -5
+    eng.close()
+    with pytest.raises(CsemError) as e:
+        Engine(wl.xn, wl.yn, wl.zn, wl.npml, wl.freqs, rho_max=wl.rho_max, dt=1.0)
+    assert e.value.code == -3
