@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="thin_reservoir")
-    ap.add_argument("--cpu-steps", type=int, default=300, help="time steps in the oracle sample")
+    ap.add_argument("--cpu-steps", type=int, default=2000, help="time steps in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()

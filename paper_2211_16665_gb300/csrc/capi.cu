@@ -71,6 +71,10 @@ void cpml_axis(Axis &A, int npml, double dt, double v, double f0) {
 
 }  // namespace
 
+namespace csem {
+int set_last_error(int code, const std::string &msg) { return fail(code, msg); }
+}  // namespace csem
+
 struct csem_ctx {
     int device = 0;
     int nx, ny, nz, npml, NX, NY, NZ, pitch;
@@ -290,6 +294,7 @@ int run_steps(csem_ctx *c, int S, bool dft, const csem::StepParams<R> &p, const 
         const int key[6] = {S, dft ? 1 : 0, kahan ? 1 : 0, (q.n_rec > 0 || q.n_itaps > 0) ? 1 : 0,
                             (int)sizeof(R), c->KZ};
         cudaGraph_t g = nullptr;
+        const long long before = csem::g_launches.load();   // captured kernels are counted per replay
         CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
         cudaError_t le = cudaSuccess;
         for (int j = 0; j < kChunk && le == cudaSuccess; ++j) le = csem::launch_step<R>(p, q, S, j, dft, kahan, c->cap);
@@ -319,7 +324,12 @@ int run_steps(csem_ctx *c, int S, bool dft, const csem::StepParams<R> &p, const 
             exec = slot.exec;
         }
         cudaGraphDestroy(g);
-        for (int ch = 0; ch < full; ++ch) CK(cudaGraphLaunch(exec, st));
+        const long long per_chunk = csem::g_launches.load() - before;
+        csem::g_launches -= per_chunk;
+        for (int ch = 0; ch < full; ++ch) {
+            CK(cudaGraphLaunch(exec, st));
+            csem::g_launches += per_chunk;
+        }
     }
     for (int j = 0; j < rem; ++j) CK(csem::launch_step<R>(p, q, S, j, dft, kahan, st));
     return CSEM_OK;

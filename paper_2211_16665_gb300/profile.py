@@ -1,0 +1,39 @@
+"""One forward run with the volumetric transform on a workload, for profiler captures.
+
+    python -m paper_2211_16665_gb300.profile --workload thin_reservoir --nt 256
+
+Runs the same kernels as a gradient's runs (H half-step with the fused
+damped transform, point operators, E step), with nt limited so that a
+profiler capture of a few launches ends quickly.  Not a timing tool.
+"""
+import argparse
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main():
+    import torch
+
+    from paper_2211_16665_gb300 import workloads as W
+    from paper_2211_16665_gb300.engine import Engine
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="thin_reservoir")
+    ap.add_argument("--nt", type=int, default=256)
+    ap.add_argument("--kahan", type=int, default=1)
+    args = ap.parse_args()
+    wl = W.ALL[args.workload]()
+    eng = Engine.from_workload(wl, nt=args.nt, kahan=args.kahan)
+    rho = eng.model_tensor(wl.rho)
+    d, E = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)
+    torch.cuda.synchronize()
+    print(f"profile run ok: {wl.name}, nt={eng.nt}, |d|max={d.abs().max().item():.3e}")
+    eng.close()
+
+
+if __name__ == "__main__":
+    main()
