@@ -137,6 +137,29 @@ int csem_estimate_adjoint_basis(double dt, int nt, const double *freqs_host, int
                                 double *basis_dev, double *fit_residual_host, int *iters_host,
                                 void *stream);
 
+/* Same result as csem_estimate_adjoint_basis, for callers that cannot
+ * allocate device memory (the paper has no counterpart; this is a deployment
+ * variant).  Some applications own all device memory through their own
+ * allocator (a framework's caching pool, a fixed arena) and must not see
+ * foreign allocations, or run on a path where an allocation's implicit
+ * synchronisation or possible failure is not acceptable.  This entry point
+ * calls no cudaMalloc, cudaFree or other allocating routine: its CG work
+ * vectors live in one file-scope device array of 8 MiB that every device
+ * which loads the library keeps until the process exits.
+ *  Limits: nt <= 32768 and n_freq <= 8, else INVALID_ARG with a message.
+ *  The first call on a device resolves the array's device address
+ *  (cudaGetSymbolAddress) with that device current; make that first call
+ *  before any stream capture.
+ *  Every call shares the one array and clears it on the stream first, so
+ *  calls that overlap on the GPU (two streams, two threads) race: serialise
+ *  them.  Arguments, outputs and blocking behaviour are those of
+ *  csem_estimate_adjoint_basis.
+ * Errors: INVALID_ARG, CUDA. */
+int csem_estimate_adjoint_basis_noalloc(double dt, int nt, const double *freqs_host, int n_freq, double f0,
+                                        double gamma, int gamma_is_relative, int max_iter, double tol,
+                                        double *basis_dev, double *fit_residual_host, int *iters_host,
+                                        void *stream);
+
 /* Misfit and weighted residual (Sec. 3.1, Eq. 7):
  *   phi = 1/2 sum |w (d_obs - d_syn)|^2,  resid = w^2 (d_obs - d_syn).
  *  n            number of complex entries.

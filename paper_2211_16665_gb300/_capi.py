@@ -58,6 +58,9 @@ SIGNATURES = {
     "csem_estimate_adjoint_basis": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, _D, ctypes.c_int, ctypes.c_double,
                                                    ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                    _V, _D, _I, _V]),
+    "csem_estimate_adjoint_basis_noalloc": (ctypes.c_int, [ctypes.c_double, ctypes.c_int, _D, ctypes.c_int,
+                                                           ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                           ctypes.c_int, ctypes.c_double, _V, _D, _I, _V]),
     "csem_misfit": (ctypes.c_int, [ctypes.c_int, _V, _V, _V, _V, _V, _V]),
     "csem_adjoint_model": (ctypes.c_int, [_V, _V, ctypes.POINTER(PointsC), ctypes.c_int, _V, _V, _V, _V]),
     "csem_gradient": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_int, ctypes.c_int, _V, _V]),
@@ -144,6 +147,18 @@ def estimate_adjoint_basis(dt, nt, freqs, f0, gamma, gamma_is_relative, max_iter
     _check(lib().csem_estimate_adjoint_basis(float(dt), int(nt), _dptr(fr), int(fr.size), float(f0), float(gamma),
                                              int(gamma_is_relative), int(max_iter), float(tol), basis_ptr,
                                              ctypes.byref(fit), ctypes.byref(its), stream))
+    return fit.value, its.value
+
+
+def estimate_adjoint_basis_noalloc(dt, nt, freqs, f0, gamma, gamma_is_relative, max_iter, tol, basis_ptr, stream):
+    """As estimate_adjoint_basis, with the scratch in the library's static device array (no allocation)."""
+    import numpy as np
+    fr = np.ascontiguousarray(freqs, np.float64)
+    fit = ctypes.c_double(0.0)
+    its = ctypes.c_int(0)
+    _check(lib().csem_estimate_adjoint_basis_noalloc(float(dt), int(nt), _dptr(fr), int(fr.size), float(f0),
+                                                     float(gamma), int(gamma_is_relative), int(max_iter), float(tol),
+                                                     basis_ptr, ctypes.byref(fit), ctypes.byref(its), stream))
     return fit.value, its.value
 
 

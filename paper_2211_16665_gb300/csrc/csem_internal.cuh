@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <string>
 
 namespace csem {
 
@@ -122,5 +123,8 @@ cudaError_t launch_misfit(int n, const double *d_obs, const double *d_syn, const
 cudaError_t launch_basis(double dt, int nt, const double *a, int nf, double gamma, int gamma_rel, int max_iter,
                          double tol, double *basis, double *scratch, double *gram, double *out_scalars,
                          int *out_iters, cudaStream_t st);
+
+// records msg as the calling thread's csem_last_error() text and returns code
+int set_last_error(int code, const std::string &msg);
 
 }  // namespace csem
