@@ -124,20 +124,29 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
-def kernel_bytes(wl, eng):
-    """Algorithmic bytes of one launch of the H half-step with the fused transform.
+BLOCK_M = 16   # snapshots per damped-transform flush (csrc/capi.cu kBlockM)
 
-    Per lattice node and source: read E (12 B), read + write H (24 B), the CPML
-    memory of the H update inside its slabs (two arrays per axis, read + write,
-    on the fraction 2 npml / n of that axis), and the damped-transform
-    accumulators: 3 components x n_freq complex values read + written, twice
-    with the Kahan compensation.
+
+def kernel_bytes(wl, eng):
+    """Algorithmic bytes per launch of each stepping kernel (one source batch).
+
+    Per lattice node and source, with r the real size and f the CPML slab
+    fraction sum_axes 2 npml / n_axis (two CPML arrays per axis per half-step,
+    read + written, inside the slabs only):
+      k_h    read E^n 3r, read + write H 6r, CPML 4 r f
+      k_e    read E^n 3r, write E^{n+1} 3r, read H 3r, read dt/eps 3r, CPML 4 r f
+      k_dft  one flush of M snapshots: read 3 M r, read + write the 3 nf complex
+             accumulators 3 nf 4r, and their Kahan terms as much again
+    k_inject touches a few taps (0 bytes at this scale).
     """
     r = 4 if eng.precision == 32 else 8
-    nodes = (wl.nx + 1) * (wl.ny + 1) * (wl.nz + 1)
-    frac = sum(2 * wl.npml / n for n in (wl.nx, wl.ny, wl.nz))
-    per = 9 * r + 2 * 2 * r * frac + 3 * eng.nf * 2 * (2 * r) * (2 if eng.info.kahan else 1)
-    return per * nodes * wl.src.n, per
+    nodes = (wl.nx + 1) * (wl.ny + 1) * (wl.nz + 1) * wl.src.n
+    f = sum(2 * wl.npml / n for n in (wl.nx, wl.ny, wl.nz))
+    per = {"k_h": 9 * r + 4 * r * f,
+           "k_e": 12 * r + 4 * r * f,
+           "k_dft": 3 * BLOCK_M * r + 3 * eng.nf * 4 * r * (2 if eng.info.kahan else 1),
+           "k_inject": 0.0}
+    return {k: v * nodes for k, v in per.items()}, per
 
 
 def cpu_baseline(wl, nt_sample):
@@ -231,14 +240,20 @@ def run_ours(args):
     # roofline of the dominant kernel, timed live with CUDA events on its stream
     _, E = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)
     from paper_2211_16665_gb300.engine import _ptr, _stream
-    kms = _capi.time_step_kernels(eng.ctx, S, _ptr(E), 200, _stream())
+    kms = dict(zip(("k_h", "k_inject", "k_e", "k_dft"), _capi.time_step_kernels(eng.ctx, S, _ptr(E), 200, _stream())))
     bytes_launch, per_node = kernel_bytes(wl, eng)
+    per_step_ms = {"k_h": kms["k_h"], "k_inject": kms["k_inject"], "k_e": kms["k_e"], "k_dft": kms["k_dft"] / BLOCK_M}
+    dom = max(per_step_ms, key=per_step_ms.get)
     peak, peak_kind = hbm_peak()
-    achieved = bytes_launch / (kms[0] / 1e3) / 1e9
-    roof = {"kernel": "k_h (H half-step + damped transform, Kahan)", "bound": "hbm",
-            "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-            "peak_kind": peak_kind, "traffic": None, "bytes_per_node": round(per_node, 1),
-            "ms_per_launch": {"k_h": kms[0], "k_points": kms[1], "k_e": kms[2]}}
+    achieved = bytes_launch[dom] / (kms[dom] / 1e3) / 1e9
+    tot = sum(per_step_ms.values())
+    roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": None,
+            "bytes_per_node": round(per_node[dom], 1),
+            "ms_per_launch": {k: round(v, 5) for k, v in kms.items()},
+            "step_share": {k: round(v / tot, 3) for k, v in per_step_ms.items()},
+            "all_kernels_gbs": {k: round(bytes_launch[k] / (kms[k] / 1e3) / 1e9, 1) for k in ("k_h", "k_e", "k_dft")}}
+    del E
 
     # end to end: host model in, host gradient out
     e2e = None

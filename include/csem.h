@@ -215,9 +215,10 @@ int csem_check(csem_ctx *ctx, void *stream);
  * csem_time_step_kernels: on the state left by the last run of ctx, launches
  * each stepping kernel `launches` times for n_src sources and returns the mean
  * duration of one launch in milliseconds, from CUDA events on stream:
- * ms_out[0] = H half-step with the fused damped transform into vol_dev
- * ([n_src][3][n_freq][vol] complex(real), overwritten), ms_out[1] = point
- * operators, ms_out[2] = E step.  Field values are overwritten. */
+ * ms_out[0] = H half-step, ms_out[1] = source injection, ms_out[2] = E step,
+ * ms_out[3] = one damped-transform flush of a block of snapshots (16 steps)
+ * into vol_dev ([n_src][3][n_freq][vol] complex(real), overwritten).  Field
+ * values are overwritten. */
 long long csem_launch_count(void);
 int csem_time_step_kernels(csem_ctx *ctx, int n_src, void *vol_dev, int launches, double *ms_out, void *stream);
 

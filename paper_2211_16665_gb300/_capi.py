@@ -198,8 +198,8 @@ def launch_count() -> int:
 
 
 def time_step_kernels(ctx, n_src, vol_ptr, launches, stream):
-    """Mean ms per launch of (H half-step + transform, point operators, E step)."""
-    out = (ctypes.c_double * 3)()
+    """Mean ms per launch of (H half-step, injection, E step, transform flush of 16 snapshots)."""
+    out = (ctypes.c_double * 4)()
     _check(lib().csem_time_step_kernels(ctx, int(n_src), vol_ptr, int(launches), out, stream))
     return list(out)
 

@@ -37,7 +37,8 @@ int fail(int code, const std::string &msg) {
 constexpr double kMu0 = 4e-7 * M_PI;
 constexpr double kCpmlR = 1e-6;
 constexpr double kDecaySpan = 35.0;
-constexpr int kChunk = 64;
+constexpr int kChunk = 64;        // time steps per captured graph
+constexpr int kBlockM = 16;        // snapshots per transform flush (divides kChunk)
 
 struct Axis {
     int n = 0;
@@ -91,7 +92,8 @@ struct csem_ctx {
     // device memory
     void *d_tab = nullptr;               // per-axis stepping tables (real)
     double *d_h = nullptr;               // primal widths (double) hx|hy|hz
-    void *d_cE = nullptr, *d_fields = nullptr, *d_psi = nullptr, *d_comp = nullptr, *d_edge = nullptr;
+    void *d_cE = nullptr, *d_H = nullptr, *d_ering = nullptr, *d_psi = nullptr, *d_comp = nullptr, *d_edge = nullptr;
+    int M = kBlockM, nslot = kBlockM + 1;
     void *d_wR = nullptr;                // [nt][nf] complex real
     double2 *d_w64 = nullptr;            // [nt][nf]
     double2 *d_alpha = nullptr;          // [0..nf): forward, [nf..2nf): adjoint, [2nf..3nf): k_f
@@ -103,7 +105,7 @@ struct csem_ctx {
     int last_nrec = 0;
     long long bytes = 0;
     cudaStream_t cap = nullptr;
-    struct GraphSlot { int key[6]; cudaGraphExec_t exec; };
+    struct GraphSlot { int key[8]; cudaGraphExec_t exec; };
     std::vector<GraphSlot> graphs;
 };
 
@@ -270,7 +272,10 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
     p.nx = c->nx; p.ny = c->ny; p.nz = c->nz; p.NX = c->NX; p.NY = c->NY; p.NZ = c->NZ;
     p.pitch = c->pitch; p.npml = c->npml; p.plane = c->plane; p.vol = c->vol;
     axis_tab<R>(c, 0, p.ax); axis_tab<R>(c, 1, p.ay); axis_tab<R>(c, 2, p.az);
-    p.fields = (R *)c->d_fields;
+    p.H = (R *)c->d_H;
+    p.ering = (R *)c->d_ering;
+    p.ering_stride = (long long)c->nslot * 3 * c->vol;
+    p.nslot = c->nslot;
     p.psi = (R *)c->d_psi;
     p.psi_stride = c->psi_stride; p.sx = c->sx; p.sy = c->sy; p.sz = c->sz;
     p.cE = (const R *)c->d_cE;
@@ -284,27 +289,46 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
     return p;
 }
 
+// Zeroes the state of S sources (H, the E ring, the CPML memory) and the step counter.
 template <typename R>
-int run_steps(csem_ctx *c, int S, bool dft, const csem::StepParams<R> &p, const csem::PointParams<R> &q,
-              cudaStream_t st) {
-    const bool kahan = dft && c->kahan;
+int reset_state(csem_ctx *c, int S, cudaStream_t st) {
+    CK(cudaMemsetAsync(c->d_H, 0, (size_t)S * 3 * c->vol * sizeof(R), st));
+    CK(cudaMemsetAsync(c->d_ering, 0, (size_t)S * c->nslot * 3 * c->vol * sizeof(R), st));
+    CK(cudaMemsetAsync(c->d_psi, 0, (size_t)S * c->psi_stride * sizeof(R), st));
     CK(cudaMemsetAsync(c->d_step, 0, sizeof(int), st));
+    return CSEM_OK;
+}
+
+// nt steps of H, E and injection; after every M steps the finished snapshots are
+// transformed (and the receivers sampled).  Full chunks of kChunk steps replay
+// one captured graph; the remainder and the final partial block are launched
+// directly.
+template <typename R>
+int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const csem::PointParams<R> &q,
+              cudaStream_t st) {
+    const bool kahan = vol && c->kahan;
+    const int M = c->M;
+    auto emit = [&](int j, cudaStream_t s2) -> cudaError_t {
+        cudaError_t e = csem::launch_step<R>(p, q, S, j, s2);
+        if (e == cudaSuccess && (j + 1) % M == 0) e = csem::launch_dft<R>(p, q, S, j + 1 - M, M, vol, kahan, s2);
+        return e;
+    };
     const int full = c->nt / kChunk, rem = c->nt % kChunk;
     if (full > 0) {
-        const int key[6] = {S, dft ? 1 : 0, kahan ? 1 : 0, (q.n_rec > 0 || q.n_itaps > 0) ? 1 : 0,
-                            (int)sizeof(R), c->KZ};
+        const int key[8] = {S, vol ? 1 : 0, kahan ? 1 : 0, q.n_itaps > 0 ? 1 : 0, q.n_rec > 0 ? 1 : 0,
+                            (int)sizeof(R), c->KZ, M};
         cudaGraph_t g = nullptr;
         const long long before = csem::g_launches.load();   // captured kernels are counted per replay
         CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
         cudaError_t le = cudaSuccess;
-        for (int j = 0; j < kChunk && le == cudaSuccess; ++j) le = csem::launch_step<R>(p, q, S, j, dft, kahan, c->cap);
+        for (int j = 0; j < kChunk && le == cudaSuccess; ++j) le = emit(j, c->cap);
         if (le == cudaSuccess) le = csem::launch_advance(c->d_step, kChunk, c->cap);
         cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
         if (le != cudaSuccess) return fail(CSEM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(le));
         CK(ee);
         cudaGraphExec_t exec = nullptr;
         for (auto &slot : c->graphs)
-            if (std::equal(key, key + 6, slot.key)) {
+            if (std::equal(key, key + 8, slot.key)) {
                 cudaGraphExecUpdateResultInfo info;
                 if (cudaGraphExecUpdate(slot.exec, g, &info) == cudaSuccess) exec = slot.exec;
                 else {
@@ -318,7 +342,7 @@ int run_steps(csem_ctx *c, int S, bool dft, const csem::StepParams<R> &p, const 
             }
         if (!exec) {
             csem_ctx::GraphSlot slot;
-            std::copy(key, key + 6, slot.key);
+            std::copy(key, key + 8, slot.key);
             CK(cudaGraphInstantiate(&slot.exec, g, 0));
             c->graphs.push_back(slot);
             exec = slot.exec;
@@ -331,7 +355,9 @@ int run_steps(csem_ctx *c, int S, bool dft, const csem::StepParams<R> &p, const 
             csem::g_launches += per_chunk;
         }
     }
-    for (int j = 0; j < rem; ++j) CK(csem::launch_step<R>(p, q, S, j, dft, kahan, st));
+    for (int j = 0; j < rem; ++j) CK(emit(j, st));
+    const int tail = c->nt % M;     // M divides kChunk, so this is also rem % M
+    if (tail) CK(csem::launch_dft<R>(p, q, S, rem - tail, tail, vol, kahan, st));
     return CSEM_OK;
 }
 
@@ -355,8 +381,7 @@ int fwd_impl(csem_ctx *c, const void *rho, const csem_points *src, const csem_po
     CK(cudaMemcpyAsync(c->d_itaps, itaps.data(), itaps.size() * sizeof(Tap), cudaMemcpyHostToDevice, st));
     if (NR > 0) CK(cudaMemcpyAsync(c->d_rtaps, rtaps.data(), (size_t)NR * 8 * sizeof(Tap), cudaMemcpyHostToDevice, st));
     CK(csem::launch_coef_init<R>(geo(c), (const R *)rho, (R *)c->d_cE, 2.0 * c->w0 * c->dt, c->d_bad, st));
-    CK(cudaMemsetAsync(c->d_fields, 0, (size_t)S * 6 * c->vol * sizeof(R), st));
-    CK(cudaMemsetAsync(c->d_psi, 0, (size_t)S * c->psi_stride * sizeof(R), st));
+    TRY(reset_state<R>(c, S, st));
     const bool dft = (Evol != nullptr);
     const size_t vbytes = (size_t)S * 3 * c->nf * c->vol * sizeof(typename C2<R>::T);
     if (dft) CK(cudaMemsetAsync(Evol, 0, vbytes, st));
@@ -366,7 +391,7 @@ int fwd_impl(csem_ctx *c, const void *rho, const csem_points *src, const csem_po
 
     csem::StepParams<R> p = step_params<R>(c, dft, Evol);
     csem::PointParams<R> q;
-    q.fields = (R *)c->d_fields; q.vol = c->vol; q.cE = (const R *)c->d_cE; q.step = c->d_step;
+    q.cE = (const R *)c->d_cE; q.step = c->d_step;
     q.nt = c->nt; q.nf = c->nf;
     q.n_rec = NR; q.rtaps = c->d_rtaps; q.racc = c->d_racc; q.w64 = c->d_w64; q.trace = c->d_trace;
     q.n_itaps = 8; q.itaps = c->d_itaps; q.itap_stride = 8;
@@ -391,14 +416,13 @@ int adj_impl(csem_ctx *c, const void *rho, const csem_points *rec, int S, const 
     CK(cudaMemcpyAsync(c->d_itaps, itaps.data(), itaps.size() * sizeof(Tap), cudaMemcpyHostToDevice, st));
     CK(csem::launch_adjoint_coef(resid, c->d_coef, S, NR, c->nf, c->d_alpha + 2 * c->nf, 1.0 / c->dt, st));
     CK(csem::launch_coef_init<R>(geo(c), (const R *)rho, (R *)c->d_cE, 2.0 * c->w0 * c->dt, c->d_bad, st));
-    CK(cudaMemsetAsync(c->d_fields, 0, (size_t)S * 6 * c->vol * sizeof(R), st));
-    CK(cudaMemsetAsync(c->d_psi, 0, (size_t)S * c->psi_stride * sizeof(R), st));
+    TRY(reset_state<R>(c, S, st));
     const size_t vbytes = (size_t)S * 3 * c->nf * c->vol * sizeof(typename C2<R>::T);
     CK(cudaMemsetAsync(Vvol, 0, vbytes, st));
     if (c->kahan) CK(cudaMemsetAsync(c->d_comp, 0, vbytes, st));
     csem::StepParams<R> p = step_params<R>(c, true, Vvol);
     csem::PointParams<R> q;
-    q.fields = (R *)c->d_fields; q.vol = c->vol; q.cE = (const R *)c->d_cE; q.step = c->d_step;
+    q.cE = (const R *)c->d_cE; q.step = c->d_step;
     q.nt = c->nt; q.nf = c->nf;
     q.n_rec = 0; q.rtaps = nullptr; q.racc = nullptr; q.w64 = c->d_w64; q.trace = nullptr;
     q.n_itaps = NR * 8; q.itaps = c->d_itaps; q.itap_stride = 0;
@@ -414,7 +438,7 @@ template <typename R>
 int time_impl(csem_ctx *c, int S, void *vol, int launches, double *ms, cudaStream_t st) {
     csem::StepParams<R> p = step_params<R>(c, true, vol);
     csem::PointParams<R> q;
-    q.fields = (R *)c->d_fields; q.vol = c->vol; q.cE = (const R *)c->d_cE; q.step = c->d_step;
+    q.cE = (const R *)c->d_cE; q.step = c->d_step;
     q.nt = c->nt; q.nf = c->nf;
     q.n_rec = c->last_nrec; q.rtaps = c->d_rtaps; q.racc = c->d_racc; q.w64 = c->d_w64; q.trace = nullptr;
     q.n_itaps = 8; q.itaps = c->d_itaps; q.itap_stride = 8;
@@ -423,12 +447,15 @@ int time_impl(csem_ctx *c, int S, void *vol, int launches, double *ms, cudaStrea
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const int which[3] = {1, 2, 4};
-    for (int w = 0; w < 3; ++w) {
-        for (int j = 0; j < 2; ++j) CK(csem::launch_step<R>(p, q, S, j % c->nt, true, c->kahan != 0, st, which[w]));
+    const int cnt = std::min(c->M, c->nt);
+    for (int w = 0; w < 4; ++w) {
+        auto go = [&](int j) -> cudaError_t {
+            if (w == 3) return csem::launch_dft<R>(p, q, S, 0, cnt, true, c->kahan != 0, st);
+            return csem::launch_step<R>(p, q, S, j % (c->nt - 1), st, w == 0 ? 1 : (w == 1 ? 2 : 4));
+        };
+        for (int j = 0; j < 2; ++j) CK(go(j));
         CK(cudaEventRecord(e0, st));
-        for (int j = 0; j < launches; ++j)
-            CK(csem::launch_step<R>(p, q, S, j % c->nt, true, c->kahan != 0, st, which[w]));
+        for (int j = 0; j < launches; ++j) CK(go(j));
         CK(cudaEventRecord(e1, st));
         CK(cudaEventSynchronize(e1));
         float t = 0.f;
@@ -444,7 +471,7 @@ void free_ctx(csem_ctx *c) {
     if (!c) return;
     cudaDeviceSynchronize();
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
-    void *ptrs[] = {c->d_tab, c->d_h, c->d_cE, c->d_fields, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
+    void *ptrs[] = {c->d_tab, c->d_h, c->d_cE, c->d_H, c->d_ering, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
                     c->d_alpha, c->d_racc, c->d_coef, c->d_T, c->d_ones, c->d_rtaps, c->d_itaps, c->d_step, c->d_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -552,7 +579,8 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     step(dalloc(c, &c->d_h, (size_t)(c->nx + c->ny + c->nz) * sizeof(double)));
     step(dalloc(c, &c->d_cE, 3 * (size_t)c->vol * R));
     step(dalloc(c, &c->d_edge, 3 * (size_t)c->vol * R));
-    step(dalloc(c, &c->d_fields, (size_t)S * 6 * c->vol * R));
+    step(dalloc(c, &c->d_H, (size_t)S * 3 * c->vol * R));
+    step(dalloc(c, &c->d_ering, (size_t)S * c->nslot * 3 * c->vol * R));
     step(dalloc(c, &c->d_psi, (size_t)S * c->psi_stride * R));
     if (c->kahan) step(dalloc(c, &c->d_comp, (size_t)S * 3 * c->nf * c->vol * C2s));
     step(dalloc(c, &c->d_alpha, 3 * (size_t)c->nf * sizeof(double2)));
@@ -656,7 +684,7 @@ int csem_gradient(csem_ctx *c, const void *rho_dev, const void *Evol_dev, const 
 long long csem_launch_count(void) { return csem::g_launches.load(); }
 
 int csem_time_step_kernels(csem_ctx *c, int n_src, void *vol_dev, int launches, double *ms_out, void *stream) {
-    if (!c || !vol_dev || !ms_out || launches < 1 || n_src < 1 || n_src > c->max_src)
+    if (!c || !vol_dev || !ms_out || launches < 1 || n_src < 1 || n_src > c->max_src || c->nt < 2)
         return fail(CSEM_ERR_INVALID_ARG, "bad argument");
     cudaStream_t st = (cudaStream_t)stream;
     return c->precision == 32 ? time_impl<float>(c, n_src, vol_dev, launches, ms_out, st)

@@ -1,7 +1,9 @@
 // Internal declarations shared by the CUDA translation units of the engine.
 // Layout of one source's state in HBM (all per-source blocks are contiguous):
-//   fields  [6][vol]         Ex, Ey, Ez, Hx, Hy, Hz on the padded node lattice,
+//   H       [3][vol]         Hx, Hy, Hz on the padded node lattice,
 //                            index (k*NY + j)*pitch + i, NY = ny+1, NZ = nz+1
+//   ering   [nslot][3][vol]  E snapshots: E^n (Ex, Ey, Ez) in slot n mod nslot,
+//                            nslot = M + 1 for a transform block of M steps
 //   psi     12 CPML memory arrays, each only inside the slab of its axis:
 //           x-slabs [NZ][NY][2 npml]   : psi(Hy,dEz/dx) psi(Hz,dEy/dx) psi(Ey,dHz/dx) psi(Ez,dHy/dx)
 //           y-slabs [NZ][2 npml][pitch]: psi(Hx,dEz/dy) psi(Hz,dEx/dy) psi(Ex,dHz/dy) psi(Ez,dHx/dy)
@@ -25,6 +27,7 @@ template <> struct C2<double> { typedef double2 T; };
 
 constexpr int kMaxFreq = 8;
 constexpr int kBlock = 256;
+constexpr int kMaxBlockSteps = 64;   // largest transform block (snapshots per flush)
 
 // Slab index of a half node i (between nodes i and i+1) on an axis of n cells:
 // the first npml and the last npml half nodes lie in the CPML.
@@ -53,7 +56,10 @@ struct StepParams {
     int nx, ny, nz, NX, NY, NZ, pitch, npml;
     long long plane, vol;          // pitch*NY, plane*NZ
     AxisTab<R> ax, ay, az;
-    R *fields;                     // [S][6][vol]
+    R *H;                          // [S][3][vol]
+    R *ering;                      // [S][nslot][3][vol]
+    long long ering_stride;        // nslot*3*vol
+    int nslot;                     // transform block M + 1
     R *psi;                        // [S][psi_stride]
     long long psi_stride, sx, sy, sz;
     const R *cE;                   // [3][vol] dt/eps on each E edge
@@ -76,16 +82,15 @@ struct Tap {                       // one trilinear tap of a point operator (32 
 
 template <typename R>
 struct PointParams {
-    R *fields; long long vol;
     const R *cE;
     const int *step;
     int nt, nf;
-    // sampling (receivers shared by all sources)
+    // sampling (receivers shared by all sources), done in the transform flush
     int n_rec; const Tap *rtaps;   // [n_rec][8]
     double2 *racc;                 // [S][n_rec][nf]
     const double2 *w64;            // [nt][nf]
     double *trace;                 // [S][n_rec][nt] or nullptr
-    // injection
+    // injection into E^{n+1}
     int n_itaps; const Tap *itaps; // source s uses itaps[s*itap_stride .. + n_itaps)
     int itap_stride;
     int n_emit, J;
@@ -94,10 +99,14 @@ struct PointParams {
 };
 
 // ---- launchers (kern_step.cu) ----
-// which: bit 0 = H half-step (+ transform), bit 1 = point operators, bit 2 = E step
+// which: bit 0 = H half-step, bit 1 = injection, bit 2 = E step
 template <typename R>
-cudaError_t launch_step(const StepParams<R> &p, const PointParams<R> &q, int S, int jstep,
-                        bool dft, bool kahan, cudaStream_t st, int which = 7);
+cudaError_t launch_step(const StepParams<R> &p, const PointParams<R> &q, int S, int jstep, cudaStream_t st,
+                        int which = 7);
+// transform (and receiver sampling) of snapshots n0 .. n0+cnt-1, n0 = *step + n0_off
+template <typename R>
+cudaError_t launch_dft(const StepParams<R> &p, const PointParams<R> &q, int S, int n0_off, int cnt, bool vol,
+                       bool kahan, cudaStream_t st);
 cudaError_t launch_advance(int *step, int by, cudaStream_t st);
 
 // ---- launchers (kern_aux.cu) ----

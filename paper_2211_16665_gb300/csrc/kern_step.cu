@@ -1,27 +1,34 @@
 // Leap-frog time step of the fictitious-wave Maxwell system (paper Sec. 2, Eq. 4)
-// on a stretched Yee grid with unsplit CPML, fused with the on-the-fly damped
-// transform of Eq. 6, plus the point operators (receiver sampling with FP64
-// transform, source / adjoint-source injection).  One step is three launches:
-//   k_h      H^{n-1/2} -> H^{n+1/2} from E^n; also accumulates E^n * w_{k,n}
-//            into every frequency's volume (E^n is read here anyway);
-//   k_points per source: sample E^n at the receivers and accumulate their FP64
-//            transform, then add -dt/eps J'^{n+1/2} at the injection taps;
-//   k_e      E^n -> E^{n+1} from curl H^{n+1/2}.
-// Threads are laid out flat over the (j, i) plane of the padded lattice and
-// march KZ planes along z, keeping the z-neighbour in registers.
+// on a stretched Yee grid with unsplit CPML, and the on-the-fly damped
+// transform of Eq. 6 into every frequency.
+//
+// E lives in a ring of nslot = M + 1 snapshots per source (E^n in slot n mod
+// nslot); H and the CPML memory are updated in place.  Per step:
+//   k_h       H^{n-1/2} -> H^{n+1/2} from E^n (slot n);
+//   k_e       E^{n+1} (slot n+1) = E^n + dt/eps curl H^{n+1/2};
+//   k_inject  E^{n+1} -= dt/eps J'^{n+1/2} at the injection taps.
+// After every M steps (and once at the end for a partial block):
+//   k_dft     for the M finished snapshots, Kahan-accumulate E^n w_{k,n} into
+//             every frequency's volume with the accumulators held in
+//             registers, and sample + transform (FP64) the receivers.
+// The volume accumulators are read and written once per M steps instead of
+// once per step; the additions happen in the same order as a per-step
+// compensated sum, so the result is the same.
+// Threads of k_h / k_e are laid out flat over the (j, i) plane and march KZ
+// planes along z, keeping the z-neighbour in registers.
 #include <atomic>
 
 #include "csem_internal.cuh"
 
 namespace csem {
 
+std::atomic<long long> g_launches{0};
+
 template <typename R> __device__ __forceinline__ R ldg(const R *p) { return __ldg(p); }
 
-template <typename R>
-__device__ __forceinline__ void kahan_add(R &sum, R &c, R x) {
-    // compensated summation; the explicit _rn ops keep the compiler from fusing
-    R y = x - c;
-    R t = sum + y;
+__device__ __forceinline__ void kahan_add(double &sum, double &c, double x) {
+    double y = x - c;
+    double t = sum + y;
     c = (t - sum) - y;
     sum = t;
 }
@@ -32,24 +39,30 @@ __device__ __forceinline__ void kahan_add(float &sum, float &c, float x) {
     sum = t;
 }
 
-template <typename R, bool DFT, bool KAHAN>
+template <typename R>
+__device__ __forceinline__ const R *eslot(const StepParams<R> &p, int s, int n) {
+    return p.ering + (long long)s * p.ering_stride + (long long)(n % p.nslot) * 3 * p.vol;
+}
+
+template <typename R>
 __global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int jstep) {
-    typedef typename C2<R>::T R2;
     const int t = blockIdx.x * kBlock + threadIdx.x;
     const int j = t / p.pitch;
     const int i = t - j * p.pitch;
     if (j >= p.NY || i >= p.NX) return;
     const int s = blockIdx.z;
+    const int n = *p.step + jstep;
     const int k0 = blockIdx.y * p.KZ;
     const int k1 = min(k0 + p.KZ, p.NZ);
     const long long vol = p.vol, plane = p.plane, pitch = p.pitch;
-    R *F = p.fields + (long long)s * 6 * vol;
-    const R *Ex = F, *Ey = F + vol, *Ez = F + 2 * vol;
-    R *Hx = F + 3 * vol, *Hy = F + 4 * vol, *Hz = F + 5 * vol;
+    const R *E = eslot(p, s, n);
+    const R *Ex = E, *Ey = E + vol, *Ez = E + 2 * vol;
+    R *H = p.H + (long long)s * 3 * vol;
+    R *Hx = H, *Hy = H + vol, *Hz = H + 2 * vol;
     R *P = p.psi + (long long)s * p.psi_stride;
-    R *psx = P;                         // 4 x-slab arrays: [0]=Hy,[1]=Hz used here
-    R *psy = P + 4 * p.sx;              // 4 y-slab arrays: [0]=Hx,[1]=Hz
-    R *psz = P + 4 * p.sx + 4 * p.sy;   // 4 z-slab arrays: [0]=Hx,[1]=Hy
+    R *psx = P;                         // x-slab arrays: [0]=Hy(dEz/dx) [1]=Hz(dEy/dx)
+    R *psy = P + 4 * p.sx;              // y-slab arrays: [0]=Hx(dEz/dy) [1]=Hz(dEx/dy)
+    R *psz = P + 4 * p.sx + 4 * p.sy;   // z-slab arrays: [0]=Hx(dEy/dz) [1]=Hy(dEx/dz)
     const int nx = p.nx, ny = p.ny, nz = p.nz, np2 = 2 * p.npml;
 
     const int sxh = slab_half(i, nx, p.npml);
@@ -61,29 +74,20 @@ __global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int j
     if (syh >= 0) { by = ldg(p.ay.b_h + j); ayc = ldg(p.ay.a_h + j); }
     const R cH = p.cH;
 
-    R2 wv[kMaxFreq];
-    if (DFT) {
-        const int n = *p.step + jstep;
-        const R2 *w = p.w + (long long)n * p.nf;
-#pragma unroll
-        for (int f = 0; f < kMaxFreq; ++f)
-            if (f < p.nf) wv[f] = w[f];
-    }
-
     long long idx = (long long)k0 * plane + (long long)j * pitch + i;
-    R exc = Ex[idx], eyc = Ey[idx];
+    R exc = ldg(Ex + idx), eyc = ldg(Ey + idx);
     for (int k = k0; k < k1; ++k, idx += plane) {
-        const R ezc = Ez[idx];
+        const R ezc = ldg(Ez + idx);
         const bool up = (k + 1 < p.NZ);
-        const R exk = up ? Ex[idx + plane] : R(0);
-        const R eyk = up ? Ey[idx + plane] : R(0);
+        const R exk = up ? ldg(Ex + idx + plane) : R(0);
+        const R eyk = up ? ldg(Ey + idx + plane) : R(0);
         const int szh = slab_half(k, nz, p.npml);
         const R ihz = (k < nz) ? ldg(p.az.ih_h + k) : R(0);
         R bz = 0, azc = 0;
         if (szh >= 0) { bz = ldg(p.az.b_h + k); azc = ldg(p.az.a_h + k); }
 
         if (j < ny && k < nz) {           // Hx at (i, j+1/2, k+1/2)
-            R dEz_dy = (Ez[idx + pitch] - ezc) * ihy;
+            R dEz_dy = (ldg(Ez + idx + pitch) - ezc) * ihy;
             R dEy_dz = (eyk - eyc) * ihz;
             if (syh >= 0) {
                 R &ps = psy[((long long)k * np2 + syh) * pitch + i];
@@ -99,7 +103,7 @@ __global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int j
         }
         if (i < nx && k < nz) {           // Hy at (i+1/2, j, k+1/2)
             R dEx_dz = (exk - exc) * ihz;
-            R dEz_dx = (Ez[idx + 1] - ezc) * ihx;
+            R dEz_dx = (ldg(Ez + idx + 1) - ezc) * ihx;
             if (szh >= 0) {
                 R &ps = psz[p.sz + ((long long)szh * p.NY + j) * pitch + i];
                 ps = bz * ps + azc * dEx_dz;
@@ -113,8 +117,8 @@ __global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int j
             Hy[idx] -= cH * (dEx_dz - dEz_dx);
         }
         if (i < nx && j < ny) {           // Hz at (i+1/2, j+1/2, k)
-            R dEy_dx = (Ey[idx + 1] - eyc) * ihx;
-            R dEx_dy = (Ex[idx + pitch] - exc) * ihy;
+            R dEy_dx = (ldg(Ey + idx + 1) - eyc) * ihx;
+            R dEx_dy = (ldg(Ex + idx + pitch) - exc) * ihy;
             if (sxh >= 0) {
                 R &ps = psx[p.sx + ((long long)k * p.NY + j) * np2 + sxh];
                 ps = bx * ps + axc * dEy_dx;
@@ -127,48 +131,26 @@ __global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int j
             }
             Hz[idx] -= cH * (dEy_dx - dEx_dy);
         }
-        if (DFT) {                        // damped transform of E^n (Eq. 6)
-            const R e3[3] = {exc, eyc, ezc};
-            R2 *A = p.acc + (long long)s * 3 * p.nf * vol + idx;
-            R2 *Cm = KAHAN ? p.comp + (long long)s * 3 * p.nf * vol + idx : nullptr;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-#pragma unroll
-                for (int f = 0; f < kMaxFreq; ++f) {
-                    if (f >= p.nf) break;
-                    const long long o = (long long)(c * p.nf + f) * vol;
-                    R2 a = A[o];
-                    if (KAHAN) {
-                        R2 cc = Cm[o];
-                        kahan_add(a.x, cc.x, e3[c] * wv[f].x);
-                        kahan_add(a.y, cc.y, e3[c] * wv[f].y);
-                        Cm[o] = cc;
-                    } else {
-                        a.x += e3[c] * wv[f].x;
-                        a.y += e3[c] * wv[f].y;
-                    }
-                    A[o] = a;
-                }
-            }
-        }
         exc = exk;
         eyc = eyk;
     }
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p) {
+__global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p, const int jstep) {
     const int t = blockIdx.x * kBlock + threadIdx.x;
     const int j = t / p.pitch;
     const int i = t - j * p.pitch;
     if (j >= p.NY || i >= p.NX) return;
     const int s = blockIdx.z;
+    const int n = *p.step + jstep;
     const int k0 = blockIdx.y * p.KZ;
     const int k1 = min(k0 + p.KZ, p.NZ);
     const long long vol = p.vol, plane = p.plane, pitch = p.pitch;
-    R *F = p.fields + (long long)s * 6 * vol;
-    R *Ex = F, *Ey = F + vol, *Ez = F + 2 * vol;
-    const R *Hx = F + 3 * vol, *Hy = F + 4 * vol, *Hz = F + 5 * vol;
+    const R *Eo = eslot(p, s, n);
+    R *En = const_cast<R *>(eslot(p, s, n + 1));
+    const R *H = p.H + (long long)s * 3 * vol;
+    const R *Hx = H, *Hy = H + vol, *Hz = H + 2 * vol;
     const R *cEx = p.cE, *cEy = p.cE + vol, *cEz = p.cE + 2 * vol;
     R *P = p.psi + (long long)s * p.psi_stride;
     R *psx = P;                         // [2]=Ey(dHz/dx) [3]=Ez(dHy/dx)
@@ -186,10 +168,10 @@ __global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p) {
     const bool ix_in = (i >= 1 && i < nx), jy_in = (j >= 1 && j < ny);
 
     long long idx = (long long)k0 * plane + (long long)j * pitch + i;
-    R hxm = (k0 > 0) ? Hx[idx - plane] : R(0);
-    R hym = (k0 > 0) ? Hy[idx - plane] : R(0);
+    R hxm = (k0 > 0) ? ldg(Hx + idx - plane) : R(0);
+    R hym = (k0 > 0) ? ldg(Hy + idx - plane) : R(0);
     for (int k = k0; k < k1; ++k, idx += plane) {
-        const R hxc = Hx[idx], hyc = Hy[idx], hzc = Hz[idx];
+        const R hxc = ldg(Hx + idx), hyc = ldg(Hy + idx), hzc = ldg(Hz + idx);
         const int szn = slab_node(k, nz, p.npml);
         const R ihz = ldg(p.az.ih_n + k);
         R bz = 0, azc = 0;
@@ -197,7 +179,7 @@ __global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p) {
         const bool kz_in = (k >= 1 && k < nz);
 
         if (i < nx && jy_in && kz_in) {   // Ex at (i+1/2, j, k)
-            R dHz_dy = (hzc - Hz[idx - pitch]) * ihy;
+            R dHz_dy = (hzc - ldg(Hz + idx - pitch)) * ihy;
             R dHy_dz = (hyc - hym) * ihz;
             if (syn >= 0) {
                 R &ps = psy[2 * p.sy + ((long long)k * np2 + syn) * pitch + i];
@@ -209,11 +191,11 @@ __global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p) {
                 ps = bz * ps + azc * dHy_dz;
                 dHy_dz += ps;
             }
-            Ex[idx] += ldg(cEx + idx) * (dHz_dy - dHy_dz);
+            En[idx] = ldg(Eo + idx) + ldg(cEx + idx) * (dHz_dy - dHy_dz);
         }
         if (j < ny && ix_in && kz_in) {   // Ey at (i, j+1/2, k)
             R dHx_dz = (hxc - hxm) * ihz;
-            R dHz_dx = (hzc - Hz[idx - 1]) * ihx;
+            R dHz_dx = (hzc - ldg(Hz + idx - 1)) * ihx;
             if (szn >= 0) {
                 R &ps = psz[3 * p.sz + ((long long)szn * p.NY + j) * pitch + i];
                 ps = bz * ps + azc * dHx_dz;
@@ -224,11 +206,11 @@ __global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p) {
                 ps = bx * ps + axc * dHz_dx;
                 dHz_dx += ps;
             }
-            Ey[idx] += ldg(cEy + idx) * (dHx_dz - dHz_dx);
+            En[vol + idx] = ldg(Eo + vol + idx) + ldg(cEy + idx) * (dHx_dz - dHz_dx);
         }
         if (k < nz && ix_in && jy_in) {   // Ez at (i, j, k+1/2)
-            R dHy_dx = (hyc - Hy[idx - 1]) * ihx;
-            R dHx_dy = (hxc - Hx[idx - pitch]) * ihy;
+            R dHy_dx = (hyc - ldg(Hy + idx - 1)) * ihx;
+            R dHx_dy = (hxc - ldg(Hx + idx - pitch)) * ihy;
             if (sxn >= 0) {
                 R &ps = psx[3 * p.sx + ((long long)k * p.NY + j) * np2 + sxn];
                 ps = bx * ps + axc * dHy_dx;
@@ -239,71 +221,140 @@ __global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p) {
                 ps = by * ps + ayc * dHx_dy;
                 dHx_dy += ps;
             }
-            Ez[idx] += ldg(cEz + idx) * (dHy_dx - dHx_dy);
+            En[2 * vol + idx] = ldg(Eo + 2 * vol + idx) + ldg(cEz + idx) * (dHy_dx - dHx_dy);
         }
         hxm = hxc;
         hym = hyc;
     }
 }
 
-// One block per source: receivers first (they read E^n), then injection
-// (it writes E^n before the E update).  Sources own disjoint fields.
+// E^{n+1} -= dt/eps J'^{n+1/2} at the injection taps; one block per source.
 template <typename R>
-__global__ void __launch_bounds__(kBlock) k_points(const PointParams<R> q, const int jstep) {
+__global__ void __launch_bounds__(kBlock) k_inject(const StepParams<R> p, const PointParams<R> q, const int jstep) {
     const int s = blockIdx.x;
     const int n = *q.step + jstep;
-    R *F = q.fields + (long long)s * 6 * q.vol;
-    for (int r = threadIdx.x; r < q.n_rec; r += blockDim.x) {
-        double v = 0.0;
-        const Tap *tp = q.rtaps + (long long)r * 8;
-#pragma unroll
-        for (int m = 0; m < 8; ++m) v += tp[m].w * (double)F[(long long)tp[m].comp * q.vol + tp[m].idx];
-        double2 *a = q.racc + ((long long)s * q.n_rec + r) * q.nf;
-        const double2 *w = q.w64 + (long long)n * q.nf;
-        for (int f = 0; f < q.nf; ++f) {
-            double2 t = a[f];
-            t.x += v * w[f].x;
-            t.y += v * w[f].y;
-            a[f] = t;
-        }
-        if (q.trace) q.trace[((long long)s * q.n_rec + r) * q.nt + n] = v;
-    }
-    __syncthreads();
+    R *En = const_cast<R *>(eslot(p, s, n + 1));
     for (int m = threadIdx.x; m < q.n_itaps; m += blockDim.x) {
         const Tap tp = q.itaps[(long long)s * q.itap_stride + m];
         const double *cf = q.coef + ((long long)s * q.n_emit + tp.emit) * q.J;
         const double *T = q.T + (long long)n * q.J;
         double amp = 0.0;
         for (int jj = 0; jj < q.J; ++jj) amp += cf[jj] * T[jj];
-        const long long o = (long long)tp.comp * q.vol + tp.idx;
-        const double add = -(double)q.cE[o] * tp.w * amp;
-        if (add != 0.0) atomicAdd(F + o, (R)add);
+        const long long o = (long long)tp.comp * p.vol + tp.idx;
+        const double add = -(double)q.cE[o] * tp.w * amp;   // dt/eps at the tap's edge
+        if (add != 0.0) atomicAdd(En + o, (R)add);
+    }
+}
+
+// Transform of the snapshots n0 .. n0+cnt-1 (n0 = *step + n0_off).
+// Blocks [0, nvb*3*S): volume entries (block -> (vb, c, s)); blocks after
+// that: one per source for the receivers.
+template <typename R, bool VOL, bool KAHAN>
+__global__ void __launch_bounds__(kBlock) k_dft(const StepParams<R> p, const PointParams<R> q, const int n0_off,
+                                                const int cnt, const int nvb, const int S) {
+    typedef typename C2<R>::T R2;
+    __shared__ R2 wsh[kMaxBlockSteps * kMaxFreq];
+    const int n0 = *p.step + n0_off;
+    const int blk = blockIdx.x;
+    const int nvol_blocks = VOL ? nvb * 3 * S : 0;
+    if (VOL && blk < nvol_blocks) {
+        for (int u = threadIdx.x; u < cnt * p.nf; u += blockDim.x) wsh[u] = p.w[(long long)n0 * p.nf + u];
+        __syncthreads();
+        const int vb = blk % nvb;
+        const int c = (blk / nvb) % 3;
+        const int s = blk / (nvb * 3);
+        const long long idx = (long long)vb * kBlock + threadIdx.x;
+        if (idx >= p.vol) return;
+        R2 acc[kMaxFreq], cmp[kMaxFreq];
+        R2 *A = p.acc + ((long long)s * 3 + c) * p.nf * p.vol + idx;
+        R2 *C = KAHAN ? p.comp + ((long long)s * 3 + c) * p.nf * p.vol + idx : nullptr;
+#pragma unroll
+        for (int f = 0; f < kMaxFreq; ++f)
+            if (f < p.nf) {
+                acc[f] = A[(long long)f * p.vol];
+                if (KAHAN) cmp[f] = C[(long long)f * p.vol];
+            }
+        const R *base = p.ering + (long long)s * p.ering_stride + (long long)c * p.vol + idx;
+        for (int m = 0; m < cnt; ++m) {
+            const R e = ldg(base + (long long)((n0 + m) % p.nslot) * 3 * p.vol);
+#pragma unroll
+            for (int f = 0; f < kMaxFreq; ++f)
+                if (f < p.nf) {
+                    const R2 w = wsh[m * p.nf + f];
+                    if (KAHAN) {
+                        kahan_add(acc[f].x, cmp[f].x, e * w.x);
+                        kahan_add(acc[f].y, cmp[f].y, e * w.y);
+                    } else {
+                        acc[f].x += e * w.x;
+                        acc[f].y += e * w.y;
+                    }
+                }
+        }
+#pragma unroll
+        for (int f = 0; f < kMaxFreq; ++f)
+            if (f < p.nf) {
+                A[(long long)f * p.vol] = acc[f];
+                if (KAHAN) C[(long long)f * p.vol] = cmp[f];
+            }
+        return;
+    }
+    // receivers: one block per source
+    const int s = blk - nvol_blocks;
+    const R *ring = p.ering + (long long)s * p.ering_stride;
+    for (int r = threadIdx.x; r < q.n_rec; r += blockDim.x) {
+        const Tap *tp = q.rtaps + (long long)r * 8;
+        double2 a[kMaxFreq];
+        double2 *dst = q.racc + ((long long)s * q.n_rec + r) * q.nf;
+        for (int f = 0; f < q.nf; ++f) a[f] = dst[f];
+        for (int m = 0; m < cnt; ++m) {
+            const int n = n0 + m;
+            const R *E = ring + (long long)(n % p.nslot) * 3 * p.vol;
+            double v = 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v += tp[u].w * (double)E[(long long)tp[u].comp * p.vol + tp[u].idx];
+            const double2 *w = q.w64 + (long long)n * q.nf;
+            for (int f = 0; f < q.nf; ++f) {
+                a[f].x += v * w[f].x;
+                a[f].y += v * w[f].y;
+            }
+            if (q.trace) q.trace[((long long)s * q.n_rec + r) * q.nt + n] = v;
+        }
+        for (int f = 0; f < q.nf; ++f) dst[f] = a[f];
     }
 }
 
 __global__ void k_advance(int *step, int by) { *step += by; }
 
-std::atomic<long long> g_launches{0};
-
 template <typename R>
-cudaError_t launch_step(const StepParams<R> &p, const PointParams<R> &q, int S, int jstep, bool dft, bool kahan,
-                        cudaStream_t st, int which) {
+cudaError_t launch_step(const StepParams<R> &p, const PointParams<R> &q, int S, int jstep, cudaStream_t st,
+                        int which) {
     const long long plane_threads = (long long)p.NY * p.pitch;
     dim3 grid((unsigned)((plane_threads + kBlock - 1) / kBlock), (unsigned)((p.NZ + p.KZ - 1) / p.KZ), (unsigned)S);
     if (which & 1) {
-        if (!dft) k_h<R, false, false><<<grid, kBlock, 0, st>>>(p, jstep);
-        else if (kahan) k_h<R, true, true><<<grid, kBlock, 0, st>>>(p, jstep);
-        else k_h<R, true, false><<<grid, kBlock, 0, st>>>(p, jstep);
-        g_launches++;
-    }
-    if ((which & 2) && (q.n_rec > 0 || q.n_itaps > 0)) {
-        k_points<R><<<S, kBlock, 0, st>>>(q, jstep);
+        k_h<R><<<grid, kBlock, 0, st>>>(p, jstep);
         g_launches++;
     }
     if (which & 4) {
-        k_e<R><<<grid, kBlock, 0, st>>>(p);
+        k_e<R><<<grid, kBlock, 0, st>>>(p, jstep);
         g_launches++;
     }
+    if ((which & 2) && q.n_itaps > 0) {
+        k_inject<R><<<S, kBlock, 0, st>>>(p, q, jstep);
+        g_launches++;
+    }
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_dft(const StepParams<R> &p, const PointParams<R> &q, int S, int n0_off, int cnt, bool vol,
+                       bool kahan, cudaStream_t st) {
+    const int nvb = (int)((p.vol + kBlock - 1) / kBlock);
+    const int nblk = (vol ? nvb * 3 * S : 0) + (q.n_rec > 0 ? S : 0);
+    if (nblk == 0 || cnt <= 0) return cudaSuccess;
+    if (!vol) k_dft<R, false, false><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
+    else if (kahan) k_dft<R, true, true><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
+    else k_dft<R, true, false><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
+    g_launches++;
     return cudaGetLastError();
 }
 
@@ -313,9 +364,13 @@ cudaError_t launch_advance(int *step, int by, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template cudaError_t launch_step<float>(const StepParams<float> &, const PointParams<float> &, int, int, bool, bool,
-                                        cudaStream_t, int);
-template cudaError_t launch_step<double>(const StepParams<double> &, const PointParams<double> &, int, int, bool,
-                                         bool, cudaStream_t, int);
+template cudaError_t launch_step<float>(const StepParams<float> &, const PointParams<float> &, int, int, cudaStream_t,
+                                        int);
+template cudaError_t launch_step<double>(const StepParams<double> &, const PointParams<double> &, int, int,
+                                         cudaStream_t, int);
+template cudaError_t launch_dft<float>(const StepParams<float> &, const PointParams<float> &, int, int, int, bool,
+                                       bool, cudaStream_t);
+template cudaError_t launch_dft<double>(const StepParams<double> &, const PointParams<double> &, int, int, int, bool,
+                                        bool, cudaStream_t);
 
 }  // namespace csem
