@@ -294,7 +294,7 @@ def run_ours(args):
                "data": "synthetic",
                "config": {"workload": wl.name, "cells": wl.cells, "grid": [wl.nx, wl.ny, wl.nz], "nt": eng.nt,
                           "dt": eng.dt, "n_src_per_gpu": S, "n_rec": wl.rec.n, "freqs_hz": list(map(float, wl.freqs)),
-                          "kahan": bool(eng.info.kahan), "l2": "inputs larger than L2 (each step streams "
+                          "kahan": bool(eng.info.kahan), "kz_h_e": list(eng.kz) if eng.kz else None, "l2": "inputs larger than L2 (each step streams "
                           f"{2 * 3 * eng.nf * eng.vol * 8 * S * (2 if eng.info.kahan else 1) / 2**20:.0f} MiB of "
                           "transform volumes)", "parallelism": f"sources sharded, dp{world}"},
                "grad_s_per_source": round(ms / 1e3 / S, 4),

@@ -195,6 +195,13 @@ int csem_adjoint_model(csem_ctx *ctx, const void *rho_dev, const csem_points *re
 int csem_gradient(csem_ctx *ctx, const void *rho_dev, const void *Evol_dev, const void *Vvol_dev,
                   int n_src, int wrt, void *grad_dev, void *stream);
 
+/* Picks the z planes per thread of the H and E stepping kernels (1, 2, 4 or 8)
+ * by timing each candidate on n_src sources of this grid; later calls use the
+ * fastest.  kz_out (may be NULL) receives {H, E} choices.  Overwrites the
+ * context's field state and blocks until the timing is done.
+ * Errors: INVALID_ARG, CUDA. */
+int csem_autotune(csem_ctx *ctx, int n_src, int *kz_out, void *stream);
+
 /* Test hooks.
  * csem_set_wavelet: forward source time function J'(t_{n+1/2}) (host [nt]
  * doubles, copied), or NULL for the unit impulse J'_0 = 1/dt.  The forward

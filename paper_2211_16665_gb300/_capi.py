@@ -64,6 +64,7 @@ SIGNATURES = {
     "csem_misfit": (ctypes.c_int, [ctypes.c_int, _V, _V, _V, _V, _V, _V]),
     "csem_adjoint_model": (ctypes.c_int, [_V, _V, ctypes.POINTER(PointsC), ctypes.c_int, _V, _V, _V, _V]),
     "csem_gradient": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_int, ctypes.c_int, _V, _V]),
+    "csem_autotune": (ctypes.c_int, [_V, ctypes.c_int, _I, _V]),
     "csem_set_wavelet": (ctypes.c_int, [_V, _D]),
     "csem_set_trace": (ctypes.c_int, [_V, _V]),
     "csem_check": (ctypes.c_int, [_V, _V]),
@@ -174,6 +175,13 @@ def adjoint_model(ctx, rho_ptr, rec, n_src, resid_ptr, basis_ptr, vvol_ptr, stre
 
 def gradient(ctx, rho_ptr, evol_ptr, vvol_ptr, n_src, wrt, grad_ptr, stream):
     _check(lib().csem_gradient(ctx, rho_ptr, evol_ptr, vvol_ptr, int(n_src), int(wrt), grad_ptr, stream))
+
+
+def autotune(ctx, n_src, stream):
+    """Times the z-blocking candidates of the H and E kernels; returns the (H, E) choice."""
+    out = (ctypes.c_int * 2)()
+    _check(lib().csem_autotune(ctx, int(n_src), out, stream))
+    return int(out[0]), int(out[1])
 
 
 def set_wavelet(ctx, wavelet=None):

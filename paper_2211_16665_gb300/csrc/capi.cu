@@ -86,7 +86,7 @@ struct csem_ctx {
     std::vector<double> freqs, a;        // a_k = sqrt(w_k w0)
     std::vector<std::complex<double>> kf, alpha_fwd;
     std::vector<double> wavelet;         // J'(t_{n+1/2})
-    int KZ = 8;
+    int KZ_h = 4, KZ_e = 4;             // z planes per thread (autotuned)
     long long psi_stride = 0, sx = 0, sy = 0, sz = 0;
     size_t rsize = 4;
     // device memory
@@ -281,7 +281,8 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
     p.cE = (const R *)c->d_cE;
     p.cH = (R)(c->dt / kMu0);
     p.step = c->d_step;
-    p.KZ = c->KZ;
+    p.KZ_h = c->KZ_h;
+    p.KZ_e = c->KZ_e;
     p.nf = c->nf;
     p.w = (const typename C2<R>::T *)c->d_wR;
     p.acc = dft ? (typename C2<R>::T *)acc : nullptr;
@@ -316,7 +317,7 @@ int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const 
     const int full = c->nt / kChunk, rem = c->nt % kChunk;
     if (full > 0) {
         const int key[8] = {S, vol ? 1 : 0, kahan ? 1 : 0, q.n_itaps > 0 ? 1 : 0, q.n_rec > 0 ? 1 : 0,
-                            (int)sizeof(R), c->KZ, M};
+                            (int)sizeof(R), c->KZ_h * 16 + c->KZ_e, M};
         cudaGraph_t g = nullptr;
         const long long before = csem::g_launches.load();   // captured kernels are counted per replay
         CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
@@ -467,6 +468,40 @@ int time_impl(csem_ctx *c, int S, void *vol, int launches, double *ms, cudaStrea
     return CSEM_OK;
 }
 
+// Times the H and E kernels for every z-blocking candidate on S sources and keeps the fastest.
+template <typename R>
+int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
+    TRY(reset_state<R>(c, S, st));
+    csem::StepParams<R> p = step_params<R>(c, false, nullptr);
+    csem::PointParams<R> q;
+    std::memset(&q, 0, sizeof(q));
+    q.step = c->d_step;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int kzs[4] = {1, 2, 4, 8};
+    for (int which : {1, 4}) {
+        double best = 1e30;
+        int best_kz = 4;
+        for (int kz : kzs) {
+            p.KZ_h = p.KZ_e = kz;
+            for (int j = 0; j < 3; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, which));
+            CK(cudaEventRecord(e0, st));
+            const int reps = 20;
+            for (int j = 0; j < reps; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, which));
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, e0, e1));
+            if (t < best) { best = t; best_kz = kz; }
+        }
+        if (which == 1) c->KZ_h = best_kz; else c->KZ_e = best_kz;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return CSEM_OK;
+}
+
 void free_ctx(csem_ctx *c) {
     if (!c) return;
     cudaDeviceSynchronize();
@@ -599,6 +634,7 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     if (cudaMemcpy(c->d_h, hcat.data(), hcat.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->d_ones, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(c->d_bad, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->d_cE, 0, 3 * (size_t)c->vol * c->rsize) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
         free_ctx(c);
         return fail(CSEM_ERR_CUDA, "context initialisation failed");
@@ -682,6 +718,14 @@ int csem_gradient(csem_ctx *c, const void *rho_dev, const void *Evol_dev, const 
 }
 
 long long csem_launch_count(void) { return csem::g_launches.load(); }
+
+int csem_autotune(csem_ctx *c, int n_src, int *kz_out, void *stream) {
+    if (!c || n_src < 1 || n_src > c->max_src) return fail(CSEM_ERR_INVALID_ARG, "bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(c->precision == 32 ? autotune_impl<float>(c, n_src, st) : autotune_impl<double>(c, n_src, st));
+    if (kz_out) { kz_out[0] = c->KZ_h; kz_out[1] = c->KZ_e; }
+    return CSEM_OK;
+}
 
 int csem_time_step_kernels(csem_ctx *c, int n_src, void *vol_dev, int launches, double *ms_out, void *stream) {
     if (!c || !vol_dev || !ms_out || launches < 1 || n_src < 1 || n_src > c->max_src || c->nt < 2)

@@ -65,7 +65,7 @@ struct StepParams {
     const R *cE;                   // [3][vol] dt/eps on each E edge
     R cH;                          // dt/mu0
     const int *step;               // device step counter (chunk base)
-    int KZ;                        // z planes per thread
+    int KZ_h, KZ_e;                // z planes per thread of the H / E kernels (1, 2, 4 or 8)
     int nf;
     const typename C2<R>::T *w;    // [nt][nf] exp((-1+i) a_k n dt)
     typename C2<R>::T *acc;        // [S][3][nf][vol] or nullptr

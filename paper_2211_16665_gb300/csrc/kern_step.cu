@@ -44,7 +44,7 @@ __device__ __forceinline__ const R *eslot(const StepParams<R> &p, int s, int n) 
     return p.ering + (long long)s * p.ering_stride + (long long)(n % p.nslot) * 3 * p.vol;
 }
 
-template <typename R>
+template <typename R, int KZ>
 __global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int jstep) {
     const int t = blockIdx.x * kBlock + threadIdx.x;
     const int j = t / p.pitch;
@@ -52,17 +52,19 @@ __global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int j
     if (j >= p.NY || i >= p.NX) return;
     const int s = blockIdx.z;
     const int n = *p.step + jstep;
-    const int k0 = blockIdx.y * p.KZ;
-    const int k1 = min(k0 + p.KZ, p.NZ);
+    const int k0 = blockIdx.y * KZ;
     const long long vol = p.vol, plane = p.plane, pitch = p.pitch;
-    const R *E = eslot(p, s, n);
-    const R *Ex = E, *Ey = E + vol, *Ez = E + 2 * vol;
-    R *H = p.H + (long long)s * 3 * vol;
-    R *Hx = H, *Hy = H + vol, *Hz = H + 2 * vol;
-    R *P = p.psi + (long long)s * p.psi_stride;
-    R *psx = P;                         // x-slab arrays: [0]=Hy(dEz/dx) [1]=Hz(dEy/dx)
-    R *psy = P + 4 * p.sx;              // y-slab arrays: [0]=Hx(dEz/dy) [1]=Hz(dEx/dy)
-    R *psz = P + 4 * p.sx + 4 * p.sy;   // z-slab arrays: [0]=Hx(dEy/dz) [1]=Hy(dEx/dz)
+    const R *__restrict__ E = eslot(p, s, n);
+    const R *__restrict__ Ex = E;
+    const R *__restrict__ Ey = E + vol;
+    const R *__restrict__ Ez = E + 2 * vol;
+    R *__restrict__ Hx = p.H + (long long)s * 3 * vol;
+    R *__restrict__ Hy = Hx + vol;
+    R *__restrict__ Hz = Hx + 2 * vol;
+    R *__restrict__ P = p.psi + (long long)s * p.psi_stride;
+    R *__restrict__ psx = P;                         // x-slab arrays: [0]=Hy(dEz/dx) [1]=Hz(dEy/dx)
+    R *__restrict__ psy = P + 4 * p.sx;              // y-slab arrays: [0]=Hx(dEz/dy) [1]=Hz(dEx/dy)
+    R *__restrict__ psz = P + 4 * p.sx + 4 * p.sy;   // z-slab arrays: [0]=Hx(dEy/dz) [1]=Hy(dEx/dz)
     const int nx = p.nx, ny = p.ny, nz = p.nz, np2 = 2 * p.npml;
 
     const int sxh = slab_half(i, nx, p.npml);
@@ -76,7 +78,10 @@ __global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int j
 
     long long idx = (long long)k0 * plane + (long long)j * pitch + i;
     R exc = ldg(Ex + idx), eyc = ldg(Ey + idx);
-    for (int k = k0; k < k1; ++k, idx += plane) {
+#pragma unroll
+    for (int kk = 0; kk < KZ; ++kk, idx += plane) {
+        const int k = k0 + kk;
+        if (k >= p.NZ) break;
         const R ezc = ldg(Ez + idx);
         const bool up = (k + 1 < p.NZ);
         const R exk = up ? ldg(Ex + idx + plane) : R(0);
@@ -136,7 +141,7 @@ __global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int j
     }
 }
 
-template <typename R>
+template <typename R, int KZ>
 __global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p, const int jstep) {
     const int t = blockIdx.x * kBlock + threadIdx.x;
     const int j = t / p.pitch;
@@ -144,18 +149,20 @@ __global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p, const int j
     if (j >= p.NY || i >= p.NX) return;
     const int s = blockIdx.z;
     const int n = *p.step + jstep;
-    const int k0 = blockIdx.y * p.KZ;
-    const int k1 = min(k0 + p.KZ, p.NZ);
+    const int k0 = blockIdx.y * KZ;
     const long long vol = p.vol, plane = p.plane, pitch = p.pitch;
-    const R *Eo = eslot(p, s, n);
-    R *En = const_cast<R *>(eslot(p, s, n + 1));
-    const R *H = p.H + (long long)s * 3 * vol;
-    const R *Hx = H, *Hy = H + vol, *Hz = H + 2 * vol;
-    const R *cEx = p.cE, *cEy = p.cE + vol, *cEz = p.cE + 2 * vol;
-    R *P = p.psi + (long long)s * p.psi_stride;
-    R *psx = P;                         // [2]=Ey(dHz/dx) [3]=Ez(dHy/dx)
-    R *psy = P + 4 * p.sx;              // [2]=Ex(dHz/dy) [3]=Ez(dHx/dy)
-    R *psz = P + 4 * p.sx + 4 * p.sy;   // [2]=Ex(dHy/dz) [3]=Ey(dHx/dz)
+    const R *__restrict__ Eo = eslot(p, s, n);
+    R *__restrict__ En = const_cast<R *>(eslot(p, s, n + 1));
+    const R *__restrict__ Hx = p.H + (long long)s * 3 * vol;
+    const R *__restrict__ Hy = Hx + vol;
+    const R *__restrict__ Hz = Hx + 2 * vol;
+    const R *__restrict__ cEx = p.cE;
+    const R *__restrict__ cEy = p.cE + vol;
+    const R *__restrict__ cEz = p.cE + 2 * vol;
+    R *__restrict__ P = p.psi + (long long)s * p.psi_stride;
+    R *__restrict__ psx = P;                         // [2]=Ey(dHz/dx) [3]=Ez(dHy/dx)
+    R *__restrict__ psy = P + 4 * p.sx;              // [2]=Ex(dHz/dy) [3]=Ez(dHx/dy)
+    R *__restrict__ psz = P + 4 * p.sx + 4 * p.sy;   // [2]=Ex(dHy/dz) [3]=Ey(dHx/dz)
     const int nx = p.nx, ny = p.ny, nz = p.nz, np2 = 2 * p.npml;
 
     const int sxn = slab_node(i, nx, p.npml);
@@ -170,7 +177,10 @@ __global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p, const int j
     long long idx = (long long)k0 * plane + (long long)j * pitch + i;
     R hxm = (k0 > 0) ? ldg(Hx + idx - plane) : R(0);
     R hym = (k0 > 0) ? ldg(Hy + idx - plane) : R(0);
-    for (int k = k0; k < k1; ++k, idx += plane) {
+#pragma unroll
+    for (int kk = 0; kk < KZ; ++kk, idx += plane) {
+        const int k = k0 + kk;
+        if (k >= p.NZ) break;
         const R hxc = ldg(Hx + idx), hyc = ldg(Hy + idx), hzc = ldg(Hz + idx);
         const int szn = slab_node(k, nz, p.npml);
         const R ihz = ldg(p.az.ih_n + k);
@@ -247,36 +257,89 @@ __global__ void __launch_bounds__(kBlock) k_inject(const StepParams<R> p, const 
 }
 
 // Transform of the snapshots n0 .. n0+cnt-1 (n0 = *step + n0_off).
-// Blocks [0, nvb*3*S): volume entries (block -> (vb, c, s)); blocks after
-// that: one per source for the receivers.
-template <typename R, bool VOL, bool KAHAN>
+// Blocks [0, S): receivers, one block per source (they start first);
+// blocks [S, S + nvb*3*S): volume entries (block -> (vb, c, s)).  CNT > 0 is a
+// compile-time block length (all snapshot loads are issued before the
+// compensated sums); CNT = 0 takes the length from cnt.
+template <typename R, bool VOL, bool KAHAN, int CNT>
 __global__ void __launch_bounds__(kBlock) k_dft(const StepParams<R> p, const PointParams<R> q, const int n0_off,
-                                                const int cnt, const int nvb, const int S) {
+                                                const int cnt_rt, const int nvb, const int S) {
     typedef typename C2<R>::T R2;
     __shared__ R2 wsh[kMaxBlockSteps * kMaxFreq];
     const int n0 = *p.step + n0_off;
+    const int cnt = CNT > 0 ? CNT : cnt_rt;
+    const int nrec_blocks = q.n_rec > 0 ? S : 0;
     const int blk = blockIdx.x;
-    const int nvol_blocks = VOL ? nvb * 3 * S : 0;
-    if (VOL && blk < nvol_blocks) {
-        for (int u = threadIdx.x; u < cnt * p.nf; u += blockDim.x) wsh[u] = p.w[(long long)n0 * p.nf + u];
-        __syncthreads();
-        const int vb = blk % nvb;
-        const int c = (blk / nvb) % 3;
-        const int s = blk / (nvb * 3);
-        const long long idx = (long long)vb * kBlock + threadIdx.x;
-        if (idx >= p.vol) return;
-        R2 acc[kMaxFreq], cmp[kMaxFreq];
-        R2 *A = p.acc + ((long long)s * 3 + c) * p.nf * p.vol + idx;
-        R2 *C = KAHAN ? p.comp + ((long long)s * 3 + c) * p.nf * p.vol + idx : nullptr;
+    if (blk < nrec_blocks) {
+        const int s = blk;
+        const R *ring = p.ering + (long long)s * p.ering_stride;
+        for (int r = threadIdx.x; r < q.n_rec; r += blockDim.x) {
+            const Tap *tp = q.rtaps + (long long)r * 8;
+            double2 a[kMaxFreq];
+            double2 *dst = q.racc + ((long long)s * q.n_rec + r) * q.nf;
+            for (int f = 0; f < q.nf; ++f) a[f] = dst[f];
+            for (int m = 0; m < cnt; ++m) {
+                const int n = n0 + m;
+                const R *E = ring + (long long)(n % p.nslot) * 3 * p.vol;
+                double v = 0.0;
 #pragma unroll
-        for (int f = 0; f < kMaxFreq; ++f)
-            if (f < p.nf) {
-                acc[f] = A[(long long)f * p.vol];
-                if (KAHAN) cmp[f] = C[(long long)f * p.vol];
+                for (int u = 0; u < 8; ++u) v += tp[u].w * (double)E[(long long)tp[u].comp * p.vol + tp[u].idx];
+                const double2 *w = q.w64 + (long long)n * q.nf;
+                for (int f = 0; f < q.nf; ++f) {
+                    a[f].x += v * w[f].x;
+                    a[f].y += v * w[f].y;
+                }
+                if (q.trace) q.trace[((long long)s * q.n_rec + r) * q.nt + n] = v;
             }
-        const R *base = p.ering + (long long)s * p.ering_stride + (long long)c * p.vol + idx;
+            for (int f = 0; f < q.nf; ++f) dst[f] = a[f];
+        }
+        return;
+    }
+    if constexpr (VOL) {
+    for (int u = threadIdx.x; u < cnt * p.nf; u += blockDim.x) wsh[u] = p.w[(long long)n0 * p.nf + u];
+    __syncthreads();
+    const int vblk = blk - nrec_blocks;
+    const int vb = vblk % nvb;
+    const int c = (vblk / nvb) % 3;
+    const int s = vblk / (nvb * 3);
+    const long long idx = (long long)vb * kBlock + threadIdx.x;
+    if (idx >= p.vol) return;
+    R2 *__restrict__ A = p.acc + ((long long)s * 3 + c) * p.nf * p.vol + idx;
+    R2 *__restrict__ C = KAHAN ? p.comp + ((long long)s * 3 + c) * p.nf * p.vol + idx : nullptr;
+    const R *__restrict__ base = p.ering + (long long)s * p.ering_stride + (long long)c * p.vol + idx;
+    const long long slot = 3 * p.vol;
+    R2 acc[kMaxFreq], cmp[kMaxFreq];
+#pragma unroll
+    for (int f = 0; f < kMaxFreq; ++f)
+        if (f < p.nf) {
+            acc[f] = A[(long long)f * p.vol];
+            if (KAHAN) cmp[f] = C[(long long)f * p.vol];
+        }
+    if (CNT > 0) {
+        R e[CNT > 0 ? CNT : 1];
+        int sl = n0 % p.nslot;
+#pragma unroll
+        for (int m = 0; m < CNT; ++m) {
+            e[m] = ldg(base + (long long)sl * slot);
+            sl = (sl + 1 == p.nslot) ? 0 : sl + 1;
+        }
+#pragma unroll
+        for (int m = 0; m < CNT; ++m)
+#pragma unroll
+            for (int f = 0; f < kMaxFreq; ++f)
+                if (f < p.nf) {
+                    const R2 w = wsh[m * p.nf + f];
+                    if (KAHAN) {
+                        kahan_add(acc[f].x, cmp[f].x, e[m] * w.x);
+                        kahan_add(acc[f].y, cmp[f].y, e[m] * w.y);
+                    } else {
+                        acc[f].x += e[m] * w.x;
+                        acc[f].y += e[m] * w.y;
+                    }
+                }
+    } else {
         for (int m = 0; m < cnt; ++m) {
-            const R e = ldg(base + (long long)((n0 + m) % p.nslot) * 3 * p.vol);
+            const R e = ldg(base + (long long)((n0 + m) % p.nslot) * slot);
 #pragma unroll
             for (int f = 0; f < kMaxFreq; ++f)
                 if (f < p.nf) {
@@ -290,59 +353,51 @@ __global__ void __launch_bounds__(kBlock) k_dft(const StepParams<R> p, const Poi
                     }
                 }
         }
-#pragma unroll
-        for (int f = 0; f < kMaxFreq; ++f)
-            if (f < p.nf) {
-                A[(long long)f * p.vol] = acc[f];
-                if (KAHAN) C[(long long)f * p.vol] = cmp[f];
-            }
-        return;
     }
-    // receivers: one block per source
-    const int s = blk - nvol_blocks;
-    const R *ring = p.ering + (long long)s * p.ering_stride;
-    for (int r = threadIdx.x; r < q.n_rec; r += blockDim.x) {
-        const Tap *tp = q.rtaps + (long long)r * 8;
-        double2 a[kMaxFreq];
-        double2 *dst = q.racc + ((long long)s * q.n_rec + r) * q.nf;
-        for (int f = 0; f < q.nf; ++f) a[f] = dst[f];
-        for (int m = 0; m < cnt; ++m) {
-            const int n = n0 + m;
-            const R *E = ring + (long long)(n % p.nslot) * 3 * p.vol;
-            double v = 0.0;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v += tp[u].w * (double)E[(long long)tp[u].comp * p.vol + tp[u].idx];
-            const double2 *w = q.w64 + (long long)n * q.nf;
-            for (int f = 0; f < q.nf; ++f) {
-                a[f].x += v * w[f].x;
-                a[f].y += v * w[f].y;
-            }
-            if (q.trace) q.trace[((long long)s * q.n_rec + r) * q.nt + n] = v;
+    for (int f = 0; f < kMaxFreq; ++f)
+        if (f < p.nf) {
+            A[(long long)f * p.vol] = acc[f];
+            if (KAHAN) C[(long long)f * p.vol] = cmp[f];
         }
-        for (int f = 0; f < q.nf; ++f) dst[f] = a[f];
     }
 }
 
 __global__ void k_advance(int *step, int by) { *step += by; }
 
+template <typename R, int KZ>
+void launch_hz(const StepParams<R> &p, dim3 grid, int jstep, cudaStream_t st, bool h) {
+    if (h) k_h<R, KZ><<<grid, kBlock, 0, st>>>(p, jstep);
+    else k_e<R, KZ><<<grid, kBlock, 0, st>>>(p, jstep);
+}
+
+template <typename R>
+cudaError_t launch_field(const StepParams<R> &p, int S, int jstep, cudaStream_t st, bool h, int kz) {
+    const long long plane_threads = (long long)p.NY * p.pitch;
+    dim3 grid((unsigned)((plane_threads + kBlock - 1) / kBlock), (unsigned)((p.NZ + kz - 1) / kz), (unsigned)S);
+    switch (kz) {
+        case 1: launch_hz<R, 1>(p, grid, jstep, st, h); break;
+        case 2: launch_hz<R, 2>(p, grid, jstep, st, h); break;
+        case 4: launch_hz<R, 4>(p, grid, jstep, st, h); break;
+        case 8: launch_hz<R, 8>(p, grid, jstep, st, h); break;
+        default: return cudaErrorInvalidValue;
+    }
+    g_launches++;
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_step(const StepParams<R> &p, const PointParams<R> &q, int S, int jstep, cudaStream_t st,
                         int which) {
-    const long long plane_threads = (long long)p.NY * p.pitch;
-    dim3 grid((unsigned)((plane_threads + kBlock - 1) / kBlock), (unsigned)((p.NZ + p.KZ - 1) / p.KZ), (unsigned)S);
-    if (which & 1) {
-        k_h<R><<<grid, kBlock, 0, st>>>(p, jstep);
-        g_launches++;
-    }
-    if (which & 4) {
-        k_e<R><<<grid, kBlock, 0, st>>>(p, jstep);
-        g_launches++;
-    }
-    if ((which & 2) && q.n_itaps > 0) {
+    cudaError_t e = cudaSuccess;
+    if (which & 1) e = launch_field<R>(p, S, jstep, st, true, p.KZ_h);
+    if (e == cudaSuccess && (which & 4)) e = launch_field<R>(p, S, jstep, st, false, p.KZ_e);
+    if (e == cudaSuccess && (which & 2) && q.n_itaps > 0) {
         k_inject<R><<<S, kBlock, 0, st>>>(p, q, jstep);
         g_launches++;
+        e = cudaGetLastError();
     }
-    return cudaGetLastError();
+    return e;
 }
 
 template <typename R>
@@ -351,9 +406,12 @@ cudaError_t launch_dft(const StepParams<R> &p, const PointParams<R> &q, int S, i
     const int nvb = (int)((p.vol + kBlock - 1) / kBlock);
     const int nblk = (vol ? nvb * 3 * S : 0) + (q.n_rec > 0 ? S : 0);
     if (nblk == 0 || cnt <= 0) return cudaSuccess;
-    if (!vol) k_dft<R, false, false><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
-    else if (kahan) k_dft<R, true, true><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
-    else k_dft<R, true, false><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
+    const bool full = (cnt == 16);
+    if (!vol) k_dft<R, false, false, 0><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
+    else if (kahan && full) k_dft<R, true, true, 16><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
+    else if (kahan) k_dft<R, true, true, 0><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
+    else if (full) k_dft<R, true, false, 16><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
+    else k_dft<R, true, false, 0><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
     g_launches++;
     return cudaGetLastError();
 }

@@ -41,7 +41,7 @@ class Engine:
     """One context: grid, frequencies, dt/nt, precision, batch capacity."""
 
     def __init__(self, xn, yn, zn, npml, freqs, f0=1.0, rho_max=1.0, precision=32, kahan=1,
-                 max_src=1, max_rec=0, nt=0, dt=0.0, device=None):
+                 max_src=1, max_rec=0, nt=0, dt=0.0, device=None, autotune=True):
         if not torch.cuda.is_available():
             raise RuntimeError("the CSEM engine needs a CUDA device")
         self.device = torch.device(device or "cuda")
@@ -60,6 +60,7 @@ class Engine:
         self.real = torch.float32 if precision == 32 else torch.float64
         self.cplx = torch.complex64 if precision == 32 else torch.complex128
         self._wavelet = None
+        self.kz = _capi.autotune(self.ctx, max_src, _stream()) if autotune else None
 
     @classmethod
     def from_workload(cls, wl, max_src=None, max_rec=None, nt=None, **kw):
