@@ -195,9 +195,11 @@ int csem_adjoint_model(csem_ctx *ctx, const void *rho_dev, const csem_points *re
 int csem_gradient(csem_ctx *ctx, const void *rho_dev, const void *Evol_dev, const void *Vvol_dev,
                   int n_src, int wrt, void *grad_dev, void *stream);
 
-/* Picks the z planes per thread of the H and E stepping kernels (1, 2, 4 or 8)
- * by timing each candidate on n_src sources of this grid; later calls use the
- * fastest.  kz_out (may be NULL) receives {H, E} choices.  Overwrites the
+/* Picks the launch shape of the H and E stepping kernels -- z planes per
+ * thread (1, 2, 4, 8) and the register budget (4, 6 or 8 resident 256-thread
+ * blocks per SM) -- by timing each candidate on n_src sources of this grid;
+ * later calls use the fastest.  kz_out (may be NULL) receives, for H and E,
+ * 16 * planes + blocks.  Overwrites the
  * context's field state and blocks until the timing is done.
  * Errors: INVALID_ARG, CUDA. */
 int csem_autotune(csem_ctx *ctx, int n_src, int *kz_out, void *stream);
@@ -222,7 +224,8 @@ int csem_check(csem_ctx *ctx, void *stream);
  * csem_time_step_kernels: on the state left by the last run of ctx, launches
  * each stepping kernel `launches` times for n_src sources and returns the mean
  * duration of one launch in milliseconds, from CUDA events on stream:
- * ms_out[0] = H half-step, ms_out[1] = source injection, ms_out[2] = E step,
+ * ms_out[0] = H half-step, ms_out[1] = 0 (the source injection runs inside
+ * the E step), ms_out[2] = E step,
  * ms_out[3] = one damped-transform flush of a block of snapshots (16 steps)
  * into vol_dev ([n_src][3][n_freq][vol] complex(real), overwritten).  Field
  * values are overwritten. */

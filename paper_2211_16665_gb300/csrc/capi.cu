@@ -87,6 +87,7 @@ struct csem_ctx {
     std::vector<std::complex<double>> kf, alpha_fwd;
     std::vector<double> wavelet;         // J'(t_{n+1/2})
     int KZ_h = 4, KZ_e = 4;             // z planes per thread (autotuned)
+    int MB_h = 4, MB_e = 4;             // min resident blocks per SM of the compiled variant (autotuned)
     long long psi_stride = 0, sx = 0, sy = 0, sz = 0;
     size_t rsize = 4;
     // device memory
@@ -100,6 +101,9 @@ struct csem_ctx {
     double2 *d_racc = nullptr;
     double *d_coef = nullptr, *d_T = nullptr, *d_ones = nullptr;
     Tap *d_rtaps = nullptr, *d_itaps = nullptr;
+    int2 *d_colmap = nullptr;            // [max_src][plane] injection taps per lattice column
+    long long *d_cpos = nullptr;         // scatter positions / values for the column map
+    int2 *d_cval = nullptr;
     int *d_step = nullptr, *d_bad = nullptr;
     double *d_trace = nullptr;
     int last_nrec = 0;
@@ -283,6 +287,14 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
     p.step = c->d_step;
     p.KZ_h = c->KZ_h;
     p.KZ_e = c->KZ_e;
+    p.MB_h = c->MB_h;
+    p.MB_e = c->MB_e;
+    p.colmap = nullptr;
+    p.colmap_stride = 0;
+    p.itaps = nullptr;
+    p.itap_stride = 0;
+    p.n_emit = p.J = 0;
+    p.coef = p.T = nullptr;
     p.nf = c->nf;
     p.w = (const typename C2<R>::T *)c->d_wR;
     p.acc = dft ? (typename C2<R>::T *)acc : nullptr;
@@ -317,7 +329,7 @@ int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const 
     const int full = c->nt / kChunk, rem = c->nt % kChunk;
     if (full > 0) {
         const int key[8] = {S, vol ? 1 : 0, kahan ? 1 : 0, q.n_itaps > 0 ? 1 : 0, q.n_rec > 0 ? 1 : 0,
-                            (int)sizeof(R), c->KZ_h * 16 + c->KZ_e, M};
+                            (int)sizeof(R), ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e, M};
         cudaGraph_t g = nullptr;
         const long long before = csem::g_launches.load();   // captured kernels are counted per replay
         CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
@@ -370,6 +382,35 @@ csem::GeoD geo(const csem_ctx *c) {
     return g;
 }
 
+// Sorts each source's injection taps by lattice column (then index) and sets the
+// device column map: colmap[s*stride + col] = (first tap, count), zero elsewhere.
+int upload_injection(csem_ctx *c, std::vector<Tap> &taps, int n_lists, int per_list, bool shared, cudaStream_t st) {
+    const long long plane = c->plane;
+    std::vector<long long> pos;
+    std::vector<int2> val;
+    for (int s = 0; s < n_lists; ++s) {
+        auto b = taps.begin() + (size_t)s * per_list;
+        std::stable_sort(b, b + per_list, [&](const Tap &x, const Tap &y) {
+            const long long cx = x.idx % plane, cy = y.idx % plane;
+            return cx != cy ? cx < cy : x.idx < y.idx;
+        });
+        for (int u = 0; u < per_list; ++u) {
+            const long long col = b[u].idx % plane;
+            if (u == 0 || (b[u - 1].idx % plane) != col) {
+                pos.push_back((shared ? 0 : (long long)s * plane) + col);
+                val.push_back(make_int2(u, 0));
+            }
+            val.back().y += 1;
+        }
+    }
+    CK(cudaMemcpyAsync(c->d_itaps, taps.data(), taps.size() * sizeof(Tap), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(c->d_colmap, 0, (size_t)(shared ? 1 : n_lists) * plane * sizeof(int2), st));
+    CK(cudaMemcpyAsync(c->d_cpos, pos.data(), pos.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(c->d_cval, val.data(), val.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    CK(csem::launch_scatter_int2(c->d_colmap, c->d_cpos, c->d_cval, (int)pos.size(), st));
+    return CSEM_OK;
+}
+
 template <typename R>
 int fwd_impl(csem_ctx *c, const void *rho, const csem_points *src, const csem_points *rec, double *d_syn,
              void *Evol, cudaStream_t st) {
@@ -379,7 +420,7 @@ int fwd_impl(csem_ctx *c, const void *rho, const csem_points *src, const csem_po
         TRY(point_taps(c, src->x[s], src->y[s], src->z[s], src->comp[s], true, 0, &itaps[(size_t)s * 8]));
     for (int r = 0; r < NR; ++r)
         TRY(point_taps(c, rec->x[r], rec->y[r], rec->z[r], rec->comp[r], false, r, &rtaps[(size_t)r * 8]));
-    CK(cudaMemcpyAsync(c->d_itaps, itaps.data(), itaps.size() * sizeof(Tap), cudaMemcpyHostToDevice, st));
+    TRY(upload_injection(c, itaps, S, 8, false, st));
     if (NR > 0) CK(cudaMemcpyAsync(c->d_rtaps, rtaps.data(), (size_t)NR * 8 * sizeof(Tap), cudaMemcpyHostToDevice, st));
     CK(csem::launch_coef_init<R>(geo(c), (const R *)rho, (R *)c->d_cE, 2.0 * c->w0 * c->dt, c->d_bad, st));
     TRY(reset_state<R>(c, S, st));
@@ -391,12 +432,15 @@ int fwd_impl(csem_ctx *c, const void *rho, const csem_points *src, const csem_po
     if (c->d_trace && NR > 0) CK(cudaMemsetAsync(c->d_trace, 0, (size_t)S * NR * c->nt * sizeof(double), st));
 
     csem::StepParams<R> p = step_params<R>(c, dft, Evol);
+    p.colmap = c->d_colmap; p.colmap_stride = c->plane;
+    p.itaps = c->d_itaps; p.itap_stride = 8;
+    p.n_emit = 1; p.J = 1; p.coef = c->d_ones; p.T = c->d_T;   // unit moment for every source
     csem::PointParams<R> q;
     q.cE = (const R *)c->d_cE; q.step = c->d_step;
     q.nt = c->nt; q.nf = c->nf;
     q.n_rec = NR; q.rtaps = c->d_rtaps; q.racc = c->d_racc; q.w64 = c->d_w64; q.trace = c->d_trace;
     q.n_itaps = 8; q.itaps = c->d_itaps; q.itap_stride = 8;
-    q.n_emit = 1; q.J = 1; q.coef = c->d_ones; q.T = c->d_T;   // unit moment for every source
+    q.n_emit = 1; q.J = 1; q.coef = c->d_ones; q.T = c->d_T;
     TRY(run_steps<R>(c, S, dft, p, q, st));
     c->last_nrec = NR;
     if (NR > 0) CK(csem::launch_finalize_receivers(c->d_racc, d_syn, S, NR, c->nf, c->d_alpha, st));
@@ -414,7 +458,7 @@ int adj_impl(csem_ctx *c, const void *rho, const csem_points *rec, int S, const 
     std::vector<Tap> itaps((size_t)NR * 8);
     for (int r = 0; r < NR; ++r)
         TRY(point_taps(c, rec->x[r], rec->y[r], rec->z[r], rec->comp[r], true, r, &itaps[(size_t)r * 8]));
-    CK(cudaMemcpyAsync(c->d_itaps, itaps.data(), itaps.size() * sizeof(Tap), cudaMemcpyHostToDevice, st));
+    TRY(upload_injection(c, itaps, 1, NR * 8, true, st));
     CK(csem::launch_adjoint_coef(resid, c->d_coef, S, NR, c->nf, c->d_alpha + 2 * c->nf, 1.0 / c->dt, st));
     CK(csem::launch_coef_init<R>(geo(c), (const R *)rho, (R *)c->d_cE, 2.0 * c->w0 * c->dt, c->d_bad, st));
     TRY(reset_state<R>(c, S, st));
@@ -422,6 +466,9 @@ int adj_impl(csem_ctx *c, const void *rho, const csem_points *rec, int S, const 
     CK(cudaMemsetAsync(Vvol, 0, vbytes, st));
     if (c->kahan) CK(cudaMemsetAsync(c->d_comp, 0, vbytes, st));
     csem::StepParams<R> p = step_params<R>(c, true, Vvol);
+    p.colmap = c->d_colmap; p.colmap_stride = 0;
+    p.itaps = c->d_itaps; p.itap_stride = 0;
+    p.n_emit = NR; p.J = 2 * c->nf; p.coef = c->d_coef; p.T = basis;
     csem::PointParams<R> q;
     q.cE = (const R *)c->d_cE; q.step = c->d_step;
     q.nt = c->nt; q.nf = c->nf;
@@ -449,10 +496,14 @@ int time_impl(csem_ctx *c, int S, void *vol, int launches, double *ms, cudaStrea
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const int cnt = std::min(c->M, c->nt);
-    for (int w = 0; w < 4; ++w) {
+    p.colmap = c->d_colmap; p.colmap_stride = c->plane;     // the last forward run's taps
+    p.itaps = c->d_itaps; p.itap_stride = 8;
+    p.n_emit = 1; p.J = 1; p.coef = c->d_ones; p.T = c->d_T;
+    ms[1] = 0.0;                                             // injection runs inside the E step
+    for (int w : {0, 2, 3}) {
         auto go = [&](int j) -> cudaError_t {
             if (w == 3) return csem::launch_dft<R>(p, q, S, 0, cnt, true, c->kahan != 0, st);
-            return csem::launch_step<R>(p, q, S, j % (c->nt - 1), st, w == 0 ? 1 : (w == 1 ? 2 : 4));
+            return csem::launch_step<R>(p, q, S, j % (c->nt - 1), st, w == 0 ? 1 : 4);
         };
         for (int j = 0; j < 2; ++j) CK(go(j));
         CK(cudaEventRecord(e0, st));
@@ -480,11 +531,14 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const int kzs[4] = {1, 2, 4, 8};
+    const int mbs[3] = {4, 6, 8};
     for (int which : {1, 4}) {
         double best = 1e30;
-        int best_kz = 4;
-        for (int kz : kzs) {
+        int best_kz = 4, best_mb = 4;
+        for (int cand = 0; cand < 12; ++cand) {
+            const int kz = kzs[cand % 4], mb = mbs[cand / 4];
             p.KZ_h = p.KZ_e = kz;
+            p.MB_h = p.MB_e = mb;
             for (int j = 0; j < 3; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, which));
             CK(cudaEventRecord(e0, st));
             const int reps = 20;
@@ -493,9 +547,10 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
             CK(cudaEventSynchronize(e1));
             float t = 0.f;
             CK(cudaEventElapsedTime(&t, e0, e1));
-            if (t < best) { best = t; best_kz = kz; }
+            if (t < best) { best = t; best_kz = kz; best_mb = mb; }
         }
-        if (which == 1) c->KZ_h = best_kz; else c->KZ_e = best_kz;
+        if (which == 1) { c->KZ_h = best_kz; c->MB_h = best_mb; }
+        else { c->KZ_e = best_kz; c->MB_e = best_mb; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -507,7 +562,7 @@ void free_ctx(csem_ctx *c) {
     cudaDeviceSynchronize();
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
     void *ptrs[] = {c->d_tab, c->d_h, c->d_cE, c->d_H, c->d_ering, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
-                    c->d_alpha, c->d_racc, c->d_coef, c->d_T, c->d_ones, c->d_rtaps, c->d_itaps, c->d_step, c->d_bad};
+                    c->d_alpha, c->d_racc, c->d_coef, c->d_T, c->d_ones, c->d_rtaps, c->d_itaps, c->d_colmap, c->d_cpos, c->d_cval, c->d_step, c->d_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -625,6 +680,9 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     step(dalloc(c, &c->d_ones, (size_t)S * sizeof(double)));
     step(dalloc(c, &c->d_rtaps, (size_t)NR * 8 * sizeof(Tap)));
     step(dalloc(c, &c->d_itaps, (size_t)std::max(S, NR) * 8 * sizeof(Tap)));
+    step(dalloc(c, &c->d_colmap, (size_t)S * c->plane * sizeof(int2)));
+    step(dalloc(c, &c->d_cpos, (size_t)std::max(S, NR) * 8 * sizeof(long long)));
+    step(dalloc(c, &c->d_cval, (size_t)std::max(S, NR) * 8 * sizeof(int2)));
     step(dalloc(c, &c->d_step, sizeof(int)));
     step(dalloc(c, &c->d_bad, sizeof(int)));
     if (rc != CSEM_OK) { free_ctx(c); return rc; }
@@ -723,7 +781,7 @@ int csem_autotune(csem_ctx *c, int n_src, int *kz_out, void *stream) {
     if (!c || n_src < 1 || n_src > c->max_src) return fail(CSEM_ERR_INVALID_ARG, "bad argument");
     cudaStream_t st = (cudaStream_t)stream;
     TRY(c->precision == 32 ? autotune_impl<float>(c, n_src, st) : autotune_impl<double>(c, n_src, st));
-    if (kz_out) { kz_out[0] = c->KZ_h; kz_out[1] = c->KZ_e; }
+    if (kz_out) { kz_out[0] = c->KZ_h * 16 + c->MB_h; kz_out[1] = c->KZ_e * 16 + c->MB_e; }
     return CSEM_OK;
 }
 

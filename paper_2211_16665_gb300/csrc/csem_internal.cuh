@@ -66,10 +66,19 @@ struct StepParams {
     R cH;                          // dt/mu0
     const int *step;               // device step counter (chunk base)
     int KZ_h, KZ_e;                // z planes per thread of the H / E kernels (1, 2, 4 or 8)
+    int MB_h, MB_e;                // minimum resident blocks per SM the kernels are compiled for (4, 6, 8)
     int nf;
     const typename C2<R>::T *w;    // [nt][nf] exp((-1+i) a_k n dt)
     typename C2<R>::T *acc;        // [S][3][nf][vol] or nullptr
     typename C2<R>::T *comp;       // Kahan compensation or nullptr
+    // source injection into E^{n+1}, applied by the E kernel: taps sorted by
+    // lattice column; colmap[s*colmap_stride + (j*pitch + i)] = (first tap, count)
+    const int2 *colmap;            // nullptr: no injection
+    long long colmap_stride;       // plane, or 0 when every source shares the taps
+    const struct Tap *itaps;
+    int itap_stride, n_emit, J;
+    const double *coef;            // [S][n_emit][J]
+    const double *T;               // [nt][J]
 };
 
 struct Tap {                       // one trilinear tap of a point operator (32 bytes)
@@ -99,10 +108,10 @@ struct PointParams {
 };
 
 // ---- launchers (kern_step.cu) ----
-// which: bit 0 = H half-step, bit 1 = injection, bit 2 = E step
+// which: bit 0 = H half-step, bit 2 = E step (with the source injection)
 template <typename R>
 cudaError_t launch_step(const StepParams<R> &p, const PointParams<R> &q, int S, int jstep, cudaStream_t st,
-                        int which = 7);
+                        int which = 5);
 // transform (and receiver sampling) of snapshots n0 .. n0+cnt-1, n0 = *step + n0_off
 template <typename R>
 cudaError_t launch_dft(const StepParams<R> &p, const PointParams<R> &q, int S, int n0_off, int cnt, bool vol,
@@ -127,6 +136,7 @@ cudaError_t launch_adjoint_coef(const double *resid, double *coef, int S, int n_
 template <typename R>
 cudaError_t launch_gradient(const GeoD &g, const R *rho, const typename C2<R>::T *E, const typename C2<R>::T *V,
                             int S, int nf, int wrt, R *edge_scratch, R *grad, cudaStream_t st);
+cudaError_t launch_scatter_int2(int2 *dst, const long long *pos, const int2 *val, int n, cudaStream_t st);
 cudaError_t launch_misfit(int n, const double *d_obs, const double *d_syn, const double *w, double *resid,
                           double *phi, cudaStream_t st);
 cudaError_t launch_basis(double dt, int nt, const double *a, int nf, double gamma, int gamma_rel, int max_iter,

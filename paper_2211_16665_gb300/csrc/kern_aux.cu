@@ -424,6 +424,19 @@ cudaError_t launch_basis(double dt, int nt, const double *a, int nf, double gamm
     return cudaGetLastError();
 }
 
+// colmap[pos[u]] = val[u]: sets the column map of the injection taps
+__global__ void k_scatter_int2(int2 *dst, const long long *pos, const int2 *val, int n) {
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u < n) dst[pos[u]] = val[u];
+}
+
+cudaError_t launch_scatter_int2(int2 *dst, const long long *pos, const int2 *val, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_scatter_int2<<<(n + 255) / 256, 256, 0, st>>>(dst, pos, val, n);
+    g_launches++;
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_coef_init<float>(const GeoD &, const float *, float *, double, int *, cudaStream_t);
 template cudaError_t launch_coef_init<double>(const GeoD &, const double *, double *, double, int *, cudaStream_t);
 template cudaError_t launch_finalize_volume<float>(float2 *, const float2 *, long long, int, int, const double2 *,

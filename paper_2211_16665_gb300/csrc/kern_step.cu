@@ -5,15 +5,15 @@
 // E lives in a ring of nslot = M + 1 snapshots per source (E^n in slot n mod
 // nslot); H and the CPML memory are updated in place.  Per step:
 //   k_h       H^{n-1/2} -> H^{n+1/2} from E^n (slot n);
-//   k_e       E^{n+1} (slot n+1) = E^n + dt/eps curl H^{n+1/2};
-//   k_inject  E^{n+1} -= dt/eps J'^{n+1/2} at the injection taps.
+//   k_e       E^{n+1} (slot n+1) = E^n + dt/eps (curl H^{n+1/2} - J'^{n+1/2}),
+//             the source term added by the thread that owns the tap's column.
 // After every M steps (and once at the end for a partial block):
-//   k_dft     for the M finished snapshots, Kahan-accumulate E^n w_{k,n} into
-//             every frequency's volume with the accumulators held in
-//             registers, and sample + transform (FP64) the receivers.
+//   k_dft     for the M finished snapshots, sum E^n w_{k,n} over the block with
+//             FMAs in registers and add the block sum to every frequency's
+//             volume with Kahan compensation; sample + transform (FP64) the
+//             receivers.
 // The volume accumulators are read and written once per M steps instead of
-// once per step; the additions happen in the same order as a per-step
-// compensated sum, so the result is the same.
+// once per step, and the compensated addition runs once per block.
 // Threads of k_h / k_e are laid out flat over the (j, i) plane and march KZ
 // planes along z, keeping the z-neighbour in registers.
 #include <atomic>
@@ -44,8 +44,8 @@ __device__ __forceinline__ const R *eslot(const StepParams<R> &p, int s, int n) 
     return p.ering + (long long)s * p.ering_stride + (long long)(n % p.nslot) * 3 * p.vol;
 }
 
-template <typename R, int KZ>
-__global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int jstep) {
+template <typename R, int KZ, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_h(const StepParams<R> p, const int jstep) {
     const int t = blockIdx.x * kBlock + threadIdx.x;
     const int j = t / p.pitch;
     const int i = t - j * p.pitch;
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int j
     const int s = blockIdx.z;
     const int n = *p.step + jstep;
     const int k0 = blockIdx.y * KZ;
-    const long long vol = p.vol, plane = p.plane, pitch = p.pitch;
+    const int vol = (int)p.vol, plane = (int)p.plane, pitch = p.pitch;
     const R *__restrict__ E = eslot(p, s, n);
     const R *__restrict__ Ex = E;
     const R *__restrict__ Ey = E + vol;
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int j
     if (syh >= 0) { by = ldg(p.ay.b_h + j); ayc = ldg(p.ay.a_h + j); }
     const R cH = p.cH;
 
-    long long idx = (long long)k0 * plane + (long long)j * pitch + i;
+    int idx = k0 * plane + j * pitch + i;
     R exc = ldg(Ex + idx), eyc = ldg(Ey + idx);
 #pragma unroll
     for (int kk = 0; kk < KZ; ++kk, idx += plane) {
@@ -95,12 +95,12 @@ __global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int j
             R dEz_dy = (ldg(Ez + idx + pitch) - ezc) * ihy;
             R dEy_dz = (eyk - eyc) * ihz;
             if (syh >= 0) {
-                R &ps = psy[((long long)k * np2 + syh) * pitch + i];
+                R &ps = psy[(k * np2 + syh) * pitch + i];
                 ps = by * ps + ayc * dEz_dy;
                 dEz_dy += ps;
             }
             if (szh >= 0) {
-                R &ps = psz[((long long)szh * p.NY + j) * pitch + i];
+                R &ps = psz[(szh * p.NY + j) * pitch + i];
                 ps = bz * ps + azc * dEy_dz;
                 dEy_dz += ps;
             }
@@ -110,12 +110,12 @@ __global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int j
             R dEx_dz = (exk - exc) * ihz;
             R dEz_dx = (ldg(Ez + idx + 1) - ezc) * ihx;
             if (szh >= 0) {
-                R &ps = psz[p.sz + ((long long)szh * p.NY + j) * pitch + i];
+                R &ps = psz[p.sz + (szh * p.NY + j) * pitch + i];
                 ps = bz * ps + azc * dEx_dz;
                 dEx_dz += ps;
             }
             if (sxh >= 0) {
-                R &ps = psx[((long long)k * p.NY + j) * np2 + sxh];
+                R &ps = psx[(k * p.NY + j) * np2 + sxh];
                 ps = bx * ps + axc * dEz_dx;
                 dEz_dx += ps;
             }
@@ -125,12 +125,12 @@ __global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int j
             R dEy_dx = (ldg(Ey + idx + 1) - eyc) * ihx;
             R dEx_dy = (ldg(Ex + idx + pitch) - exc) * ihy;
             if (sxh >= 0) {
-                R &ps = psx[p.sx + ((long long)k * p.NY + j) * np2 + sxh];
+                R &ps = psx[p.sx + (k * p.NY + j) * np2 + sxh];
                 ps = bx * ps + axc * dEy_dx;
                 dEy_dx += ps;
             }
             if (syh >= 0) {
-                R &ps = psy[p.sy + ((long long)k * np2 + syh) * pitch + i];
+                R &ps = psy[p.sy + (k * np2 + syh) * pitch + i];
                 ps = by * ps + ayc * dEx_dy;
                 dEx_dy += ps;
             }
@@ -141,8 +141,8 @@ __global__ void __launch_bounds__(kBlock) k_h(const StepParams<R> p, const int j
     }
 }
 
-template <typename R, int KZ>
-__global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p, const int jstep) {
+template <typename R, int KZ, int MINB>
+__global__ void __launch_bounds__(kBlock, MINB) k_e(const StepParams<R> p, const int jstep) {
     const int t = blockIdx.x * kBlock + threadIdx.x;
     const int j = t / p.pitch;
     const int i = t - j * p.pitch;
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p, const int j
     const int s = blockIdx.z;
     const int n = *p.step + jstep;
     const int k0 = blockIdx.y * KZ;
-    const long long vol = p.vol, plane = p.plane, pitch = p.pitch;
+    const int vol = (int)p.vol, plane = (int)p.plane, pitch = p.pitch;
     const R *__restrict__ Eo = eslot(p, s, n);
     R *__restrict__ En = const_cast<R *>(eslot(p, s, n + 1));
     const R *__restrict__ Hx = p.H + (long long)s * 3 * vol;
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p, const int j
     if (syn >= 0) { by = ldg(p.ay.b_n + j); ayc = ldg(p.ay.a_n + j); }
     const bool ix_in = (i >= 1 && i < nx), jy_in = (j >= 1 && j < ny);
 
-    long long idx = (long long)k0 * plane + (long long)j * pitch + i;
+    int idx = k0 * plane + j * pitch + i;
     R hxm = (k0 > 0) ? ldg(Hx + idx - plane) : R(0);
     R hym = (k0 > 0) ? ldg(Hy + idx - plane) : R(0);
 #pragma unroll
@@ -192,12 +192,12 @@ __global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p, const int j
             R dHz_dy = (hzc - ldg(Hz + idx - pitch)) * ihy;
             R dHy_dz = (hyc - hym) * ihz;
             if (syn >= 0) {
-                R &ps = psy[2 * p.sy + ((long long)k * np2 + syn) * pitch + i];
+                R &ps = psy[2 * p.sy + (k * np2 + syn) * pitch + i];
                 ps = by * ps + ayc * dHz_dy;
                 dHz_dy += ps;
             }
             if (szn >= 0) {
-                R &ps = psz[2 * p.sz + ((long long)szn * p.NY + j) * pitch + i];
+                R &ps = psz[2 * p.sz + (szn * p.NY + j) * pitch + i];
                 ps = bz * ps + azc * dHy_dz;
                 dHy_dz += ps;
             }
@@ -207,12 +207,12 @@ __global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p, const int j
             R dHx_dz = (hxc - hxm) * ihz;
             R dHz_dx = (hzc - ldg(Hz + idx - 1)) * ihx;
             if (szn >= 0) {
-                R &ps = psz[3 * p.sz + ((long long)szn * p.NY + j) * pitch + i];
+                R &ps = psz[3 * p.sz + (szn * p.NY + j) * pitch + i];
                 ps = bz * ps + azc * dHx_dz;
                 dHx_dz += ps;
             }
             if (sxn >= 0) {
-                R &ps = psx[2 * p.sx + ((long long)k * p.NY + j) * np2 + sxn];
+                R &ps = psx[2 * p.sx + (k * p.NY + j) * np2 + sxn];
                 ps = bx * ps + axc * dHz_dx;
                 dHz_dx += ps;
             }
@@ -222,12 +222,12 @@ __global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p, const int j
             R dHy_dx = (hyc - ldg(Hy + idx - 1)) * ihx;
             R dHx_dy = (hxc - ldg(Hx + idx - pitch)) * ihy;
             if (sxn >= 0) {
-                R &ps = psx[3 * p.sx + ((long long)k * p.NY + j) * np2 + sxn];
+                R &ps = psx[3 * p.sx + (k * p.NY + j) * np2 + sxn];
                 ps = bx * ps + axc * dHy_dx;
                 dHy_dx += ps;
             }
             if (syn >= 0) {
-                R &ps = psy[3 * p.sy + ((long long)k * np2 + syn) * pitch + i];
+                R &ps = psy[3 * p.sy + (k * np2 + syn) * pitch + i];
                 ps = by * ps + ayc * dHx_dy;
                 dHx_dy += ps;
             }
@@ -236,23 +236,21 @@ __global__ void __launch_bounds__(kBlock) k_e(const StepParams<R> p, const int j
         hxm = hxc;
         hym = hyc;
     }
-}
-
-// E^{n+1} -= dt/eps J'^{n+1/2} at the injection taps; one block per source.
-template <typename R>
-__global__ void __launch_bounds__(kBlock) k_inject(const StepParams<R> p, const PointParams<R> q, const int jstep) {
-    const int s = blockIdx.x;
-    const int n = *q.step + jstep;
-    R *En = const_cast<R *>(eslot(p, s, n + 1));
-    for (int m = threadIdx.x; m < q.n_itaps; m += blockDim.x) {
-        const Tap tp = q.itaps[(long long)s * q.itap_stride + m];
-        const double *cf = q.coef + ((long long)s * q.n_emit + tp.emit) * q.J;
-        const double *T = q.T + (long long)n * q.J;
-        double amp = 0.0;
-        for (int jj = 0; jj < q.J; ++jj) amp += cf[jj] * T[jj];
-        const long long o = (long long)tp.comp * p.vol + tp.idx;
-        const double add = -(double)q.cE[o] * tp.w * amp;   // dt/eps at the tap's edge
-        if (add != 0.0) atomicAdd(En + o, (R)add);
+    // source term E^{n+1} -= dt/eps J'^{n+1/2}: this thread owns its column's taps
+    if (p.colmap) {
+        const int2 cm = p.colmap[s * p.colmap_stride + j * pitch + i];
+        for (int u = cm.x; u < cm.x + cm.y; ++u) {
+            const Tap tp = p.itaps[(long long)s * p.itap_stride + u];
+            const int k = (int)(tp.idx / plane);
+            if (k < k0 || k >= k0 + KZ) continue;
+            const double *cf = p.coef + ((long long)s * p.n_emit + tp.emit) * p.J;
+            const double *T = p.T + (long long)n * p.J;
+            double amp = 0.0;
+            for (int jj = 0; jj < p.J; ++jj) amp += cf[jj] * T[jj];
+            const int o = tp.comp * vol + (int)tp.idx;
+            const double add = -(double)p.cE[o] * tp.w * amp;   // dt/eps at the tap's edge
+            if (add != 0.0) En[o] += (R)add;
+        }
     }
 }
 
@@ -315,6 +313,11 @@ __global__ void __launch_bounds__(kBlock) k_dft(const StepParams<R> p, const Poi
             acc[f] = A[(long long)f * p.vol];
             if (KAHAN) cmp[f] = C[(long long)f * p.vol];
         }
+    // block sum of the products with plain FMAs, then one compensated addition
+    // of the block sum to the running accumulator
+    R2 bs[kMaxFreq];
+#pragma unroll
+    for (int f = 0; f < kMaxFreq; ++f) bs[f].x = bs[f].y = R(0);
     if (CNT > 0) {
         R e[CNT > 0 ? CNT : 1];
         int sl = n0 % p.nslot;
@@ -329,13 +332,8 @@ __global__ void __launch_bounds__(kBlock) k_dft(const StepParams<R> p, const Poi
             for (int f = 0; f < kMaxFreq; ++f)
                 if (f < p.nf) {
                     const R2 w = wsh[m * p.nf + f];
-                    if (KAHAN) {
-                        kahan_add(acc[f].x, cmp[f].x, e[m] * w.x);
-                        kahan_add(acc[f].y, cmp[f].y, e[m] * w.y);
-                    } else {
-                        acc[f].x += e[m] * w.x;
-                        acc[f].y += e[m] * w.y;
-                    }
+                    bs[f].x = fma(e[m], w.x, bs[f].x);
+                    bs[f].y = fma(e[m], w.y, bs[f].y);
                 }
     } else {
         for (int m = 0; m < cnt; ++m) {
@@ -344,16 +342,22 @@ __global__ void __launch_bounds__(kBlock) k_dft(const StepParams<R> p, const Poi
             for (int f = 0; f < kMaxFreq; ++f)
                 if (f < p.nf) {
                     const R2 w = wsh[m * p.nf + f];
-                    if (KAHAN) {
-                        kahan_add(acc[f].x, cmp[f].x, e * w.x);
-                        kahan_add(acc[f].y, cmp[f].y, e * w.y);
-                    } else {
-                        acc[f].x += e * w.x;
-                        acc[f].y += e * w.y;
-                    }
+                    bs[f].x = fma(e, w.x, bs[f].x);
+                    bs[f].y = fma(e, w.y, bs[f].y);
                 }
         }
     }
+#pragma unroll
+    for (int f = 0; f < kMaxFreq; ++f)
+        if (f < p.nf) {
+            if (KAHAN) {
+                kahan_add(acc[f].x, cmp[f].x, bs[f].x);
+                kahan_add(acc[f].y, cmp[f].y, bs[f].y);
+            } else {
+                acc[f].x += bs[f].x;
+                acc[f].y += bs[f].y;
+            }
+        }
 #pragma unroll
     for (int f = 0; f < kMaxFreq; ++f)
         if (f < p.nf) {
@@ -365,23 +369,32 @@ __global__ void __launch_bounds__(kBlock) k_dft(const StepParams<R> p, const Poi
 
 __global__ void k_advance(int *step, int by) { *step += by; }
 
-template <typename R, int KZ>
+template <typename R, int KZ, int MB>
 void launch_hz(const StepParams<R> &p, dim3 grid, int jstep, cudaStream_t st, bool h) {
-    if (h) k_h<R, KZ><<<grid, kBlock, 0, st>>>(p, jstep);
-    else k_e<R, KZ><<<grid, kBlock, 0, st>>>(p, jstep);
+    if (h) k_h<R, KZ, MB><<<grid, kBlock, 0, st>>>(p, jstep);
+    else k_e<R, KZ, MB><<<grid, kBlock, 0, st>>>(p, jstep);
+}
+
+template <typename R, int MB>
+bool launch_kz(const StepParams<R> &p, dim3 grid, int jstep, cudaStream_t st, bool h, int kz) {
+    switch (kz) {
+        case 1: launch_hz<R, 1, MB>(p, grid, jstep, st, h); return true;
+        case 2: launch_hz<R, 2, MB>(p, grid, jstep, st, h); return true;
+        case 4: launch_hz<R, 4, MB>(p, grid, jstep, st, h); return true;
+        case 8: launch_hz<R, 8, MB>(p, grid, jstep, st, h); return true;
+        default: return false;
+    }
 }
 
 template <typename R>
-cudaError_t launch_field(const StepParams<R> &p, int S, int jstep, cudaStream_t st, bool h, int kz) {
+cudaError_t launch_field(const StepParams<R> &p, int S, int jstep, cudaStream_t st, bool h, int kz, int mb) {
     const long long plane_threads = (long long)p.NY * p.pitch;
     dim3 grid((unsigned)((plane_threads + kBlock - 1) / kBlock), (unsigned)((p.NZ + kz - 1) / kz), (unsigned)S);
-    switch (kz) {
-        case 1: launch_hz<R, 1>(p, grid, jstep, st, h); break;
-        case 2: launch_hz<R, 2>(p, grid, jstep, st, h); break;
-        case 4: launch_hz<R, 4>(p, grid, jstep, st, h); break;
-        case 8: launch_hz<R, 8>(p, grid, jstep, st, h); break;
-        default: return cudaErrorInvalidValue;
-    }
+    bool ok = false;
+    if (mb == 4) ok = launch_kz<R, 4>(p, grid, jstep, st, h, kz);
+    else if (mb == 6) ok = launch_kz<R, 6>(p, grid, jstep, st, h, kz);
+    else if (mb == 8) ok = launch_kz<R, 8>(p, grid, jstep, st, h, kz);
+    if (!ok) return cudaErrorInvalidValue;
     g_launches++;
     return cudaGetLastError();
 }
@@ -389,14 +402,10 @@ cudaError_t launch_field(const StepParams<R> &p, int S, int jstep, cudaStream_t 
 template <typename R>
 cudaError_t launch_step(const StepParams<R> &p, const PointParams<R> &q, int S, int jstep, cudaStream_t st,
                         int which) {
+    (void)q;
     cudaError_t e = cudaSuccess;
-    if (which & 1) e = launch_field<R>(p, S, jstep, st, true, p.KZ_h);
-    if (e == cudaSuccess && (which & 4)) e = launch_field<R>(p, S, jstep, st, false, p.KZ_e);
-    if (e == cudaSuccess && (which & 2) && q.n_itaps > 0) {
-        k_inject<R><<<S, kBlock, 0, st>>>(p, q, jstep);
-        g_launches++;
-        e = cudaGetLastError();
-    }
+    if (which & 1) e = launch_field<R>(p, S, jstep, st, true, p.KZ_h, p.MB_h);
+    if (e == cudaSuccess && (which & 4)) e = launch_field<R>(p, S, jstep, st, false, p.KZ_e, p.MB_e);
     return e;
 }
 
