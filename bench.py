@@ -124,9 +124,6 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
-BLOCK_M = 16   # snapshots per damped-transform flush (csrc/capi.cu kBlockM)
-
-
 def kernel_bytes(wl, eng):
     """Algorithmic bytes per launch of each stepping kernel (one source batch).
 
@@ -144,7 +141,7 @@ def kernel_bytes(wl, eng):
     f = sum(2 * wl.npml / n for n in (wl.nx, wl.ny, wl.nz))
     per = {"k_h": 9 * r + 4 * r * f,
            "k_e": 12 * r + 4 * r * f,
-           "k_dft": 3 * BLOCK_M * r + 3 * eng.nf * 4 * r * (2 if eng.info.kahan else 1),
+           "k_dft": 3 * eng.info.transform_block * r + 3 * eng.nf * 4 * r * (2 if eng.info.kahan else 1),
            "k_inject": 0.0}
     return {k: v * nodes for k, v in per.items()}, per
 
@@ -242,7 +239,8 @@ def run_ours(args):
     from paper_2211_16665_gb300.engine import _ptr, _stream
     kms = dict(zip(("k_h", "k_inject", "k_e", "k_dft"), _capi.time_step_kernels(eng.ctx, S, _ptr(E), 200, _stream())))
     bytes_launch, per_node = kernel_bytes(wl, eng)
-    per_step_ms = {"k_h": kms["k_h"], "k_inject": kms["k_inject"], "k_e": kms["k_e"], "k_dft": kms["k_dft"] / BLOCK_M}
+    per_step_ms = {"k_h": kms["k_h"], "k_inject": kms["k_inject"], "k_e": kms["k_e"],
+                   "k_dft": kms["k_dft"] / eng.info.transform_block}
     dom = max(per_step_ms, key=per_step_ms.get)
     peak, peak_kind = hbm_peak()
     achieved = bytes_launch[dom] / (kms[dom] / 1e3) / 1e9
@@ -294,7 +292,7 @@ def run_ours(args):
                "data": "synthetic",
                "config": {"workload": wl.name, "cells": wl.cells, "grid": [wl.nx, wl.ny, wl.nz], "nt": eng.nt,
                           "dt": eng.dt, "n_src_per_gpu": S, "n_rec": wl.rec.n, "freqs_hz": list(map(float, wl.freqs)),
-                          "kahan": bool(eng.info.kahan), "kz_h_e": list(eng.kz) if eng.kz else None, "l2": "inputs larger than L2 (each step streams "
+                          "kahan": bool(eng.info.kahan), "kz_h_e": list(eng.kz) if eng.kz else None, "transform_block": eng.info.transform_block, "l2": "inputs larger than L2 (each step streams "
                           f"{2 * 3 * eng.nf * eng.vol * 8 * S * (2 if eng.info.kahan else 1) / 2**20:.0f} MiB of "
                           "transform volumes)", "parallelism": f"sources sharded, dp{world}"},
                "grad_s_per_source": round(ms / 1e3 / S, 4),

@@ -90,6 +90,7 @@ typedef struct {
     int nt;                       /* steps per run */
     int precision, kahan, n_freq, max_src, max_rec;
     long long workspace_bytes;    /* device memory the context holds */
+    int transform_block;          /* E snapshots per damped-transform flush (16 or 32) */
 } csem_info;
 
 /* Creates a context on the current device: validates the grid and options,
@@ -226,7 +227,7 @@ int csem_check(csem_ctx *ctx, void *stream);
  * duration of one launch in milliseconds, from CUDA events on stream:
  * ms_out[0] = H half-step, ms_out[1] = 0 (the source injection runs inside
  * the E step), ms_out[2] = E step,
- * ms_out[3] = one damped-transform flush of a block of snapshots (16 steps)
+ * ms_out[3] = one damped-transform flush of transform_block snapshots
  * into vol_dev ([n_src][3][n_freq][vol] complex(real), overwritten).  Field
  * values are overwritten. */
 long long csem_launch_count(void);

@@ -46,7 +46,7 @@ class Info(ctypes.Structure):
                 ("pitch", ctypes.c_int), ("vol_elems", ctypes.c_longlong), ("dt", ctypes.c_double),
                 ("nt", ctypes.c_int), ("precision", ctypes.c_int), ("kahan", ctypes.c_int),
                 ("n_freq", ctypes.c_int), ("max_src", ctypes.c_int), ("max_rec", ctypes.c_int),
-                ("workspace_bytes", ctypes.c_longlong)]
+                ("workspace_bytes", ctypes.c_longlong), ("transform_block", ctypes.c_int)]
 
 
 # name -> (restype, argtypes)

@@ -38,7 +38,7 @@ constexpr double kMu0 = 4e-7 * M_PI;
 constexpr double kCpmlR = 1e-6;
 constexpr double kDecaySpan = 35.0;
 constexpr int kChunk = 64;        // time steps per captured graph
-constexpr int kBlockM = 16;        // snapshots per transform flush (divides kChunk)
+constexpr int kBlockM = 32;        // largest snapshots per transform flush (divides kChunk)
 
 struct Axis {
     int n = 0;
@@ -94,7 +94,8 @@ struct csem_ctx {
     void *d_tab = nullptr;               // per-axis stepping tables (real)
     double *d_h = nullptr;               // primal widths (double) hx|hy|hz
     void *d_cE = nullptr, *d_H = nullptr, *d_ering = nullptr, *d_psi = nullptr, *d_comp = nullptr, *d_edge = nullptr;
-    int M = kBlockM, nslot = kBlockM + 1;
+    int M = 16, nslot = 17;
+    int flush_mode = 0;                  // 0: register flush (16 snapshots); 1: bulk-copy flush
     void *d_wR = nullptr;                // [nt][nf] complex real
     double2 *d_w64 = nullptr;            // [nt][nf]
     double2 *d_alpha = nullptr;          // [0..nf): forward, [nf..2nf): adjoint, [2nf..3nf): k_f
@@ -661,6 +662,15 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     c->wavelet.assign(c->nt, 0.0);
     c->wavelet[0] = 1.0 / c->dt;
 
+    // transform block: 32 snapshots when the ring leaves room, else 16
+    {
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        const double ring32 = (double)c->max_src * 33 * 3 * c->vol * c->rsize;
+        const double vols = (double)c->max_src * 3 * c->nf * c->vol * 2 * c->rsize * (c->kahan ? 3 : 2);
+        c->M = (c->flush_mode == 1 && ring32 + vols < 0.6 * (double)free_b) ? 32 : 16;
+        c->nslot = c->M + 1;
+    }
     int rc = CSEM_OK;
     auto step = [&](int r) { if (rc == CSEM_OK) rc = r; };
     if (c->precision == 32) step(upload_tables<float>(c)); else step(upload_tables<double>(c));
@@ -711,6 +721,7 @@ int csem_get_info(const csem_ctx *c, csem_info *info) {
     info->pitch = c->pitch; info->vol_elems = c->vol; info->dt = c->dt; info->nt = c->nt;
     info->precision = c->precision; info->kahan = c->kahan; info->n_freq = c->nf;
     info->max_src = c->max_src; info->max_rec = c->max_rec; info->workspace_bytes = c->bytes;
+    info->transform_block = c->M;
     return CSEM_OK;
 }
 

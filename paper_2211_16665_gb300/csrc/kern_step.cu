@@ -256,16 +256,16 @@ __global__ void __launch_bounds__(kBlock, MINB) k_e(const StepParams<R> p, const
 
 // Transform of the snapshots n0 .. n0+cnt-1 (n0 = *step + n0_off).
 // Blocks [0, S): receivers, one block per source (they start first);
-// blocks [S, S + nvb*3*S): volume entries (block -> (vb, c, s)).  CNT > 0 is a
-// compile-time block length (all snapshot loads are issued before the
-// compensated sums); CNT = 0 takes the length from cnt.
+// blocks [S, S + nvb*3*S): volume entries (block -> (vb, c, s)).  CNT > 0:
+// cnt is a multiple of CNT and the snapshots are read in unrolled groups of
+// CNT; CNT = 0: any cnt, one snapshot at a time.
 template <typename R, bool VOL, bool KAHAN, int CNT>
 __global__ void __launch_bounds__(kBlock) k_dft(const StepParams<R> p, const PointParams<R> q, const int n0_off,
                                                 const int cnt_rt, const int nvb, const int S) {
     typedef typename C2<R>::T R2;
     __shared__ R2 wsh[kMaxBlockSteps * kMaxFreq];
     const int n0 = *p.step + n0_off;
-    const int cnt = CNT > 0 ? CNT : cnt_rt;
+    const int cnt = cnt_rt;
     const int nrec_blocks = q.n_rec > 0 ? S : 0;
     const int blk = blockIdx.x;
     if (blk < nrec_blocks) {
@@ -319,22 +319,25 @@ __global__ void __launch_bounds__(kBlock) k_dft(const StepParams<R> p, const Poi
 #pragma unroll
     for (int f = 0; f < kMaxFreq; ++f) bs[f].x = bs[f].y = R(0);
     if (CNT > 0) {
-        R e[CNT > 0 ? CNT : 1];
+        // whole groups of CNT snapshots: every load of a group is issued before its FMAs
         int sl = n0 % p.nslot;
+        for (int g = 0; g < cnt; g += CNT) {
+            R e[CNT > 0 ? CNT : 1];
 #pragma unroll
-        for (int m = 0; m < CNT; ++m) {
-            e[m] = ldg(base + (long long)sl * slot);
-            sl = (sl + 1 == p.nslot) ? 0 : sl + 1;
+            for (int m = 0; m < CNT; ++m) {
+                e[m] = ldg(base + (long long)sl * slot);
+                sl = (sl + 1 == p.nslot) ? 0 : sl + 1;
+            }
+#pragma unroll
+            for (int m = 0; m < CNT; ++m)
+#pragma unroll
+                for (int f = 0; f < kMaxFreq; ++f)
+                    if (f < p.nf) {
+                        const R2 w = wsh[(g + m) * p.nf + f];
+                        bs[f].x = fma(e[m], w.x, bs[f].x);
+                        bs[f].y = fma(e[m], w.y, bs[f].y);
+                    }
         }
-#pragma unroll
-        for (int m = 0; m < CNT; ++m)
-#pragma unroll
-            for (int f = 0; f < kMaxFreq; ++f)
-                if (f < p.nf) {
-                    const R2 w = wsh[m * p.nf + f];
-                    bs[f].x = fma(e[m], w.x, bs[f].x);
-                    bs[f].y = fma(e[m], w.y, bs[f].y);
-                }
     } else {
         for (int m = 0; m < cnt; ++m) {
             const R e = ldg(base + (long long)((n0 + m) % p.nslot) * slot);
@@ -415,7 +418,7 @@ cudaError_t launch_dft(const StepParams<R> &p, const PointParams<R> &q, int S, i
     const int nvb = (int)((p.vol + kBlock - 1) / kBlock);
     const int nblk = (vol ? nvb * 3 * S : 0) + (q.n_rec > 0 ? S : 0);
     if (nblk == 0 || cnt <= 0) return cudaSuccess;
-    const bool full = (cnt == 16);
+    const bool full = (cnt % 16 == 0);
     if (!vol) k_dft<R, false, false, 0><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
     else if (kahan && full) k_dft<R, true, true, 16><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
     else if (kahan) k_dft<R, true, true, 0><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
