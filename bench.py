@@ -108,12 +108,13 @@ class ClockSampler:
 # workload
 # ---------------------------------------------------------------------------
 def make_workload(name, rank, world):
+    from paper_2211_16665_gb300 import dist as D
     from paper_2211_16665_gb300 import workloads as W
     wl = W.ALL[name]()
     if world > 1:
-        # weak scaling: every rank models its own source of a towline on the same model
-        x = wl.src.x[0] + 250.0 * (rank - world // 2)
-        wl.src = W.Points.make([[x, wl.src.y[0], wl.src.z[0]]], int(wl.src.comp[0]))
+        # weak scaling: a towline of `world` sources on the same model, one share per rank
+        line = D.towline(wl.src, world * wl.src.n)
+        wl.src = line.subset(list(D.shard(line.n, rank, world)))
     return wl
 
 
@@ -141,7 +142,7 @@ def kernel_bytes(wl, eng):
     f = sum(2 * wl.npml / n for n in (wl.nx, wl.ny, wl.nz))
     per = {"k_h": 9 * r + 4 * r * f,
            "k_e": 12 * r + 4 * r * f,
-           "k_dft": 3 * eng.info.transform_block * r + 3 * eng.nf * 4 * r * (2 if eng.info.kahan else 1),
+           "k_dft": 3 * eng.flush_block() * r + 3 * eng.nf * 4 * r * (2 if eng.info.kahan else 1),
            "k_inject": 0.0}
     return {k: v * nodes for k, v in per.items()}, per
 
@@ -167,6 +168,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
     from paper_2211_16665_gb300 import _capi
+    from paper_2211_16665_gb300 import dist as D
     from paper_2211_16665_gb300 import workloads as W
     from paper_2211_16665_gb300.engine import Engine, misfit
 
@@ -193,9 +195,7 @@ def run_ours(args):
         basis, fit, its = eng.estimate_adjoint_basis(gamma=1e-12, relative=True)
         V = eng.adjoint_model(rho_in, wl.rec, r, basis)
         g = eng.gradient(rho_in, E, V, wrt="lnrho")
-        if world > 1:
-            dist.all_reduce(g)
-            dist.all_reduce(phi)
+        D.sum_over_ranks(g, phi)          # the one exchange: sum of the per-source gradients
         return phi, g, fit
 
     def barrier():
@@ -226,10 +226,7 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = (_capi.launch_count() - n0) // args.steps
     clk = clocks.stop()
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = D.max_over_ranks(ms, device=dev)
 
     cell_updates = 2.0 * wl.cells * eng.nt * S * world
     value = cell_updates / (ms / 1e3) / 1e9
@@ -240,7 +237,7 @@ def run_ours(args):
     kms = dict(zip(("k_h", "k_inject", "k_e", "k_dft"), _capi.time_step_kernels(eng.ctx, S, _ptr(E), 200, _stream())))
     bytes_launch, per_node = kernel_bytes(wl, eng)
     per_step_ms = {"k_h": kms["k_h"], "k_inject": kms["k_inject"], "k_e": kms["k_e"],
-                   "k_dft": kms["k_dft"] / eng.info.transform_block}
+                   "k_dft": kms["k_dft"] / eng.flush_block()}
     dom = max(per_step_ms, key=per_step_ms.get)
     peak, peak_kind = hbm_peak()
     achieved = bytes_launch[dom] / (kms[dom] / 1e3) / 1e9
@@ -271,11 +268,7 @@ def run_ours(args):
             phi_h.copy_(phi2, non_blocking=True)
         e1.record(stream)
         barrier()
-        ems = e0.elapsed_time(e1) / args.steps
-        t = torch.tensor([ems], device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ems = float(t.item())
+        ems = D.max_over_ranks(e0.elapsed_time(e1) / args.steps, device=dev)
         e2e = {"value": round(cell_updates / (ems / 1e3) / 1e9, 3), "unit": "Gcell-updates/s",
                "ms_per_step": round(ems, 3),
                "h2d_bytes_per_step": int(rho_h.numel() * rho_h.element_size() + dobs_h.numel() * dobs_h.element_size()),
@@ -292,7 +285,7 @@ def run_ours(args):
                "data": "synthetic",
                "config": {"workload": wl.name, "cells": wl.cells, "grid": [wl.nx, wl.ny, wl.nz], "nt": eng.nt,
                           "dt": eng.dt, "n_src_per_gpu": S, "n_rec": wl.rec.n, "freqs_hz": list(map(float, wl.freqs)),
-                          "kahan": bool(eng.info.kahan), "kz_h_e": list(eng.kz) if eng.kz else None, "transform_block": eng.info.transform_block, "l2": "inputs larger than L2 (each step streams "
+                          "kahan": bool(eng.info.kahan), "launch": eng.launch_config(), "l2": "inputs larger than L2 (each step streams "
                           f"{2 * 3 * eng.nf * eng.vol * 8 * S * (2 if eng.info.kahan else 1) / 2**20:.0f} MiB of "
                           "transform volumes)", "parallelism": f"sources sharded, dp{world}"},
                "grad_s_per_source": round(ms / 1e3 / S, 4),

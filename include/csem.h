@@ -199,8 +199,10 @@ int csem_gradient(csem_ctx *ctx, const void *rho_dev, const void *Evol_dev, cons
 /* Picks the launch shape of the H and E stepping kernels -- z planes per
  * thread (1, 2, 4, 8) and the register budget (4, 6 or 8 resident 256-thread
  * blocks per SM) -- by timing each candidate on n_src sources of this grid;
- * later calls use the fastest.  kz_out (may be NULL) receives, for H and E,
- * 16 * planes + blocks.  Overwrites the
+ * later calls use the fastest; for FP32 it also picks the transform flush
+ * (register kernel over 16 snapshots, or the bulk-copy kernel over 16 or 32).
+ * kz_out (may be NULL, else 3 ints) receives, for H and E, 16 * planes +
+ * blocks, then 4 * snapshots per flush + (1 for the bulk-copy kernel).  Overwrites the
  * context's field state and blocks until the timing is done.
  * Errors: INVALID_ARG, CUDA. */
 int csem_autotune(csem_ctx *ctx, int n_src, int *kz_out, void *stream);
@@ -214,9 +216,10 @@ int csem_autotune(csem_ctx *ctx, int n_src, int *kz_out, void *stream);
 int csem_set_wavelet(csem_ctx *ctx, const double *wavelet_host);
 int csem_set_trace(csem_ctx *ctx, double *trace_dev);
 
-/* Synchronises stream and reports input problems seen by the set-up kernels
- * since the last check: NONFINITE if a resistivity was non-positive or
- * non-finite (such cells get zero conductivity in the run). */
+/* Synchronises stream and reports problems seen on the device since the last
+ * check: TIMEOUT if a transform flush gave up waiting for its bulk copies
+ * (its block's accumulators were left unchanged), NONFINITE if a resistivity
+ * was non-positive or non-finite (such cells get zero conductivity). */
 int csem_check(csem_ctx *ctx, void *stream);
 
 /* Measurement hooks.

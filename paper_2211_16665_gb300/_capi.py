@@ -178,10 +178,10 @@ def gradient(ctx, rho_ptr, evol_ptr, vvol_ptr, n_src, wrt, grad_ptr, stream):
 
 
 def autotune(ctx, n_src, stream):
-    """Times the z-blocking candidates of the H and E kernels; returns the (H, E) choice."""
-    out = (ctypes.c_int * 2)()
+    """Times the launch candidates; returns (H, E, flush) codes (see csem_autotune)."""
+    out = (ctypes.c_int * 3)()
     _check(lib().csem_autotune(ctx, int(n_src), out, stream))
-    return int(out[0]), int(out[1])
+    return int(out[0]), int(out[1]), int(out[2])
 
 
 def set_wavelet(ctx, wavelet=None):

@@ -95,7 +95,7 @@ struct csem_ctx {
     double *d_h = nullptr;               // primal widths (double) hx|hy|hz
     void *d_cE = nullptr, *d_H = nullptr, *d_ering = nullptr, *d_psi = nullptr, *d_comp = nullptr, *d_edge = nullptr;
     int M = 16, nslot = 17;
-    int flush_mode = 0;                  // 0: register flush (16 snapshots); 1: bulk-copy flush
+    int flush_mode = 0;                  // 0: register flush; 1: bulk-copy flush (FP32 only)
     void *d_wR = nullptr;                // [nt][nf] complex real
     double2 *d_w64 = nullptr;            // [nt][nf]
     double2 *d_alpha = nullptr;          // [0..nf): forward, [nf..2nf): adjoint, [2nf..3nf): k_f
@@ -313,6 +313,18 @@ int reset_state(csem_ctx *c, int S, cudaStream_t st) {
     return CSEM_OK;
 }
 
+// One transform flush of cnt snapshots: the bulk-copy kernel when selected and
+// applicable (FP32, volumes, a whole block), else the register kernel.
+template <typename R>
+cudaError_t flush(csem_ctx *c, const csem::StepParams<R> &p, const csem::PointParams<R> &q, int S, int n0_off,
+                  int cnt, bool vol, bool kahan, cudaStream_t st) {
+    if constexpr (sizeof(R) == 4) {
+        if (c->flush_mode == 1 && vol && (cnt == 16 || cnt == 32))
+            return csem::launch_dft_bulk(p, q, S, n0_off, cnt, kahan, c->d_bad, st);
+    }
+    return csem::launch_dft<R>(p, q, S, n0_off, cnt, vol, kahan, st);
+}
+
 // nt steps of H, E and injection; after every M steps the finished snapshots are
 // transformed (and the receivers sampled).  Full chunks of kChunk steps replay
 // one captured graph; the remainder and the final partial block are launched
@@ -324,13 +336,14 @@ int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const 
     const int M = c->M;
     auto emit = [&](int j, cudaStream_t s2) -> cudaError_t {
         cudaError_t e = csem::launch_step<R>(p, q, S, j, s2);
-        if (e == cudaSuccess && (j + 1) % M == 0) e = csem::launch_dft<R>(p, q, S, j + 1 - M, M, vol, kahan, s2);
+        if (e == cudaSuccess && (j + 1) % M == 0) e = flush<R>(c, p, q, S, j + 1 - M, M, vol, kahan, s2);
         return e;
     };
     const int full = c->nt / kChunk, rem = c->nt % kChunk;
     if (full > 0) {
         const int key[8] = {S, vol ? 1 : 0, kahan ? 1 : 0, q.n_itaps > 0 ? 1 : 0, q.n_rec > 0 ? 1 : 0,
-                            (int)sizeof(R), ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e, M};
+                            (int)sizeof(R), ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
+                            M * 4 + c->flush_mode};
         cudaGraph_t g = nullptr;
         const long long before = csem::g_launches.load();   // captured kernels are counted per replay
         CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
@@ -371,7 +384,7 @@ int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const 
     }
     for (int j = 0; j < rem; ++j) CK(emit(j, st));
     const int tail = c->nt % M;     // M divides kChunk, so this is also rem % M
-    if (tail) CK(csem::launch_dft<R>(p, q, S, rem - tail, tail, vol, kahan, st));
+    if (tail) CK(flush<R>(c, p, q, S, rem - tail, tail, vol, kahan, st));
     return CSEM_OK;
 }
 
@@ -503,7 +516,7 @@ int time_impl(csem_ctx *c, int S, void *vol, int launches, double *ms, cudaStrea
     ms[1] = 0.0;                                             // injection runs inside the E step
     for (int w : {0, 2, 3}) {
         auto go = [&](int j) -> cudaError_t {
-            if (w == 3) return csem::launch_dft<R>(p, q, S, 0, cnt, true, c->kahan != 0, st);
+            if (w == 3) return flush<R>(c, p, q, S, 0, cnt, true, c->kahan != 0, st);
             return csem::launch_step<R>(p, q, S, j % (c->nt - 1), st, w == 0 ? 1 : 4);
         };
         for (int j = 0; j < 2; ++j) CK(go(j));
@@ -552,6 +565,39 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
         }
         if (which == 1) { c->KZ_h = best_kz; c->MB_h = best_mb; }
         else { c->KZ_e = best_kz; c->MB_e = best_mb; }
+    }
+    // transform flush: register (16) vs bulk copy (16, 32 when the ring has room), per step
+    if (sizeof(R) == 4 && c->nt >= 64) {
+        typedef typename C2<R>::T R2;
+        R2 *vol_tmp = nullptr;
+        const size_t vb = (size_t)S * 3 * c->nf * c->vol * sizeof(R2);
+        if (cudaMallocAsync((void **)&vol_tmp, vb, st) == cudaSuccess) {
+            CK(cudaMemsetAsync(vol_tmp, 0, vb, st));
+            p.acc = vol_tmp;
+            p.comp = c->kahan ? (R2 *)c->d_comp : nullptr;
+            struct Cand { int mode, m; } cands[3] = {{0, 16}, {1, 16}, {1, 32}};
+            double best = 1e30;
+            int bm = 0, bM = 16;
+            for (const Cand &cd : cands) {
+                if (cd.m + 1 > c->nslot) continue;
+                c->flush_mode = cd.mode;
+                for (int j = 0; j < 2; ++j) CK(flush<R>(c, p, q, S, 0, cd.m, true, c->kahan != 0, st));
+                CK(cudaEventRecord(e0, st));
+                const int reps = 8;
+                for (int j = 0; j < reps; ++j) CK(flush<R>(c, p, q, S, 0, cd.m, true, c->kahan != 0, st));
+                CK(cudaEventRecord(e1, st));
+                CK(cudaEventSynchronize(e1));
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, e0, e1));
+                const double per_step = (double)t / reps / cd.m;
+                if (per_step < best) { best = per_step; bm = cd.mode; bM = cd.m; }
+            }
+            c->flush_mode = bm;
+            c->M = bM;
+            cudaFreeAsync(vol_tmp, st);
+        } else {
+            cudaGetLastError();
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -662,14 +708,14 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     c->wavelet.assign(c->nt, 0.0);
     c->wavelet[0] = 1.0 / c->dt;
 
-    // transform block: 32 snapshots when the ring leaves room, else 16
+    // E ring: 33 slots (room for 32-snapshot flushes) when it leaves room, else 17
     {
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
-        const double ring32 = (double)c->max_src * 33 * 3 * c->vol * c->rsize;
+        const double ring33 = (double)c->max_src * 33 * 3 * c->vol * c->rsize;
         const double vols = (double)c->max_src * 3 * c->nf * c->vol * 2 * c->rsize * (c->kahan ? 3 : 2);
-        c->M = (c->flush_mode == 1 && ring32 + vols < 0.6 * (double)free_b) ? 32 : 16;
-        c->nslot = c->M + 1;
+        c->nslot = (ring33 + vols < 0.6 * (double)free_b) ? 33 : 17;
+        c->M = 16;
     }
     int rc = CSEM_OK;
     auto step = [&](int r) { if (rc == CSEM_OK) rc = r; };
@@ -709,6 +755,11 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     }
     rc = update_wavelet(c);
     if (rc != CSEM_OK) { free_ctx(c); return rc; }
+    if (csem::prepare_bulk_flush() != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        return fail(CSEM_ERR_CUDA, "cannot configure the bulk-copy flush kernel");
+    }
     *out = c;
     return CSEM_OK;
 }
@@ -745,7 +796,8 @@ int csem_check(csem_ctx *c, void *stream) {
     int bad = 0;
     CK(cudaMemcpy(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost));
     CK(cudaMemset(c->d_bad, 0, sizeof(int)));
-    if (bad) return fail(CSEM_ERR_NONFINITE, "a resistivity was non-positive or non-finite");
+    if (bad & 2) return fail(CSEM_ERR_TIMEOUT, "a transform flush gave up waiting for its bulk copies");
+    if (bad & 1) return fail(CSEM_ERR_NONFINITE, "a resistivity was non-positive or non-finite");
     return CSEM_OK;
 }
 
@@ -792,7 +844,11 @@ int csem_autotune(csem_ctx *c, int n_src, int *kz_out, void *stream) {
     if (!c || n_src < 1 || n_src > c->max_src) return fail(CSEM_ERR_INVALID_ARG, "bad argument");
     cudaStream_t st = (cudaStream_t)stream;
     TRY(c->precision == 32 ? autotune_impl<float>(c, n_src, st) : autotune_impl<double>(c, n_src, st));
-    if (kz_out) { kz_out[0] = c->KZ_h * 16 + c->MB_h; kz_out[1] = c->KZ_e * 16 + c->MB_e; }
+    if (kz_out) {
+        kz_out[0] = c->KZ_h * 16 + c->MB_h;
+        kz_out[1] = c->KZ_e * 16 + c->MB_e;
+        kz_out[2] = c->M * 4 + c->flush_mode;
+    }
     return CSEM_OK;
 }
 

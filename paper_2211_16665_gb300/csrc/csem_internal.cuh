@@ -117,6 +117,11 @@ template <typename R>
 cudaError_t launch_dft(const StepParams<R> &p, const PointParams<R> &q, int S, int n0_off, int cnt, bool vol,
                        bool kahan, cudaStream_t st);
 cudaError_t launch_advance(int *step, int by, cudaStream_t st);
+// FP32 flush of exactly cnt (16 or 32) snapshots through bulk copies into shared memory;
+// a bounded barrier wait that gives up raises bit 1 of *err
+cudaError_t launch_dft_bulk(const StepParams<float> &p, const PointParams<float> &q, int S, int n0_off, int cnt,
+                            bool kahan, int *err, cudaStream_t st);
+cudaError_t prepare_bulk_flush();
 
 // ---- launchers (kern_aux.cu) ----
 struct GeoD {                      // double-precision geometry for set-up and gradient kernels

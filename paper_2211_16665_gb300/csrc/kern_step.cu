@@ -370,6 +370,185 @@ __global__ void __launch_bounds__(kBlock) k_dft(const StepParams<R> p, const Poi
     }
 }
 
+// ---------------------------------------------------------------------------
+// Bulk-copy flush (FP32): the tensor-memory-access engine streams each block's
+// rows -- MS snapshots of 256 lattice entries and the accumulator (and Kahan)
+// rows -- into shared memory with cp.async.bulk on one mbarrier, so every byte
+// of the block is in flight at once with few registers.  The wait on the
+// barrier is bounded: on timeout the block raises bit 1 of *err, waits once
+// more (bounded) for its own copies and returns.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    uint64_t g;
+    asm volatile("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(src));
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(g), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+constexpr int kWaitLimit = 1 << 22;   // try_wait rounds before a flush block gives up
+
+template <bool KAHAN, int MS>
+__global__ void __launch_bounds__(kBlock, 6) k_dft_bulk(const StepParams<float> p, const PointParams<float> q,
+                                                     const int n0_off, const int nvb, const int S, int *err) {
+    __shared__ __align__(8) uint64_t bar;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *ring_s = reinterpret_cast<float *>(smem);                        // [MS][256]
+    float2 *acc_s = reinterpret_cast<float2 *>(ring_s + MS * kBlock);       // [nf][256]
+    float2 *cmp_s = acc_s + p.nf * kBlock;                                  // [nf][256] (Kahan)
+    float2 *w_s = cmp_s + (KAHAN ? p.nf * kBlock : 0);                      // [MS][nf]
+    const int n0 = *p.step + n0_off;
+    const int nrec_blocks = q.n_rec > 0 ? S : 0;
+    const int blk = blockIdx.x;
+    if (blk < nrec_blocks) {          // receivers: same as the register flush
+        const int s = blk;
+        const float *ring = p.ering + (long long)s * p.ering_stride;
+        for (int r = threadIdx.x; r < q.n_rec; r += blockDim.x) {
+            const Tap *tp = q.rtaps + (long long)r * 8;
+            double2 a[kMaxFreq];
+            double2 *dst = q.racc + ((long long)s * q.n_rec + r) * q.nf;
+            for (int f = 0; f < q.nf; ++f) a[f] = dst[f];
+            for (int m = 0; m < MS; ++m) {
+                const int n = n0 + m;
+                const float *E = ring + (long long)(n % p.nslot) * 3 * p.vol;
+                double v = 0.0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v += tp[u].w * (double)E[(long long)tp[u].comp * p.vol + tp[u].idx];
+                const double2 *w = q.w64 + (long long)n * q.nf;
+                for (int f = 0; f < q.nf; ++f) {
+                    a[f].x += v * w[f].x;
+                    a[f].y += v * w[f].y;
+                }
+                if (q.trace) q.trace[((long long)s * q.n_rec + r) * q.nt + n] = v;
+            }
+            for (int f = 0; f < q.nf; ++f) dst[f] = a[f];
+        }
+        return;
+    }
+    const int vblk = blk - nrec_blocks;
+    const int vb = vblk % nvb;
+    const int c = (vblk / nvb) % 3;
+    const int s = vblk / (nvb * 3);
+    const long long i0 = (long long)vb * kBlock;
+    const int rows = (int)min((long long)kBlock, p.vol - i0);      // a multiple of 8 entries
+    float2 *A = p.acc + ((long long)s * 3 + c) * p.nf * p.vol + i0;
+    float2 *C = KAHAN ? p.comp + ((long long)s * 3 + c) * p.nf * p.vol + i0 : nullptr;
+    const float *ring = p.ering + (long long)s * p.ering_stride + (long long)c * p.vol + i0;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t rb = (uint32_t)rows * sizeof(float), cb = (uint32_t)rows * sizeof(float2);
+        mbar_expect_tx(&bar, MS * rb + p.nf * cb * (KAHAN ? 2u : 1u));
+        int sl = n0 % p.nslot;
+        for (int m = 0; m < MS; ++m) {
+            bulk_g2s(ring_s + m * kBlock, ring + (long long)sl * 3 * p.vol, rb, &bar);
+            sl = (sl + 1 == p.nslot) ? 0 : sl + 1;
+        }
+        for (int f = 0; f < p.nf; ++f) {
+            bulk_g2s(acc_s + f * kBlock, A + (long long)f * p.vol, cb, &bar);
+            if (KAHAN) bulk_g2s(cmp_s + f * kBlock, C + (long long)f * p.vol, cb, &bar);
+        }
+    }
+    for (int u = threadIdx.x; u < MS * p.nf; u += blockDim.x) w_s[u] = p.w[(long long)n0 * p.nf + u];
+    __syncthreads();
+    bool ok = false;
+    for (int it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(&bar, 0);
+    if (!ok) {
+        if (threadIdx.x == 0) atomicOr(err, 2);
+        for (int it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(&bar, 0);
+        return;
+    }
+    const int t = threadIdx.x;
+    if (t >= rows) return;
+    float2 bs[kMaxFreq];
+#pragma unroll
+    for (int f = 0; f < kMaxFreq; ++f) bs[f].x = bs[f].y = 0.f;
+#pragma unroll 8
+    for (int m = 0; m < MS; ++m) {
+        const float e = ring_s[m * kBlock + t];
+#pragma unroll
+        for (int f = 0; f < kMaxFreq; ++f)
+            if (f < p.nf) {
+                const float2 w = w_s[m * p.nf + f];
+                bs[f].x = fmaf(e, w.x, bs[f].x);
+                bs[f].y = fmaf(e, w.y, bs[f].y);
+            }
+    }
+#pragma unroll
+    for (int f = 0; f < kMaxFreq; ++f)
+        if (f < p.nf) {
+            float2 a = acc_s[f * kBlock + t];
+            if (KAHAN) {
+                float2 cc = cmp_s[f * kBlock + t];
+                kahan_add(a.x, cc.x, bs[f].x);
+                kahan_add(a.y, cc.y, bs[f].y);
+                C[(long long)f * p.vol + t] = cc;
+            } else {
+                a.x += bs[f].x;
+                a.y += bs[f].y;
+            }
+            A[(long long)f * p.vol + t] = a;
+        }
+}
+
+size_t bulk_smem_bytes(int ms, int nf, bool kahan) {
+    return (size_t)ms * kBlock * sizeof(float) + (size_t)nf * kBlock * sizeof(float2) * (kahan ? 2 : 1) +
+           (size_t)ms * nf * sizeof(float2);
+}
+
+cudaError_t prepare_bulk_flush() {
+    const int big = (int)bulk_smem_bytes(32, kMaxFreq, true);
+    cudaError_t e = cudaFuncSetAttribute(k_dft_bulk<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dft_bulk<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dft_bulk<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dft_bulk<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    return e;
+}
+
+cudaError_t launch_dft_bulk(const StepParams<float> &p, const PointParams<float> &q, int S, int n0_off, int cnt,
+                            bool kahan, int *err, cudaStream_t st) {
+    const int nvb = (int)((p.vol + kBlock - 1) / kBlock);
+    const int nblk = nvb * 3 * S + (q.n_rec > 0 ? S : 0);
+    const size_t sm = bulk_smem_bytes(cnt, p.nf, kahan);
+    if (cnt == 32) {
+        if (kahan) k_dft_bulk<true, 32><<<nblk, kBlock, sm, st>>>(p, q, n0_off, nvb, S, err);
+        else k_dft_bulk<false, 32><<<nblk, kBlock, sm, st>>>(p, q, n0_off, nvb, S, err);
+    } else if (cnt == 16) {
+        if (kahan) k_dft_bulk<true, 16><<<nblk, kBlock, sm, st>>>(p, q, n0_off, nvb, S, err);
+        else k_dft_bulk<false, 16><<<nblk, kBlock, sm, st>>>(p, q, n0_off, nvb, S, err);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    g_launches++;
+    return cudaGetLastError();
+}
+
 __global__ void k_advance(int *step, int by) { *step += by; }
 
 template <typename R, int KZ, int MB>

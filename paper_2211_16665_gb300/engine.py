@@ -135,6 +135,18 @@ class Engine:
     def check(self):
         _capi.check(self.ctx, _stream())
 
+    def flush_block(self) -> int:
+        """Snapshots per damped-transform flush chosen by the autotuner (16 if untuned)."""
+        return self.kz[2] // 4 if self.kz else 16
+
+    def launch_config(self) -> dict:
+        if not self.kz:
+            return {}
+        h, e, f = self.kz
+        return {"h": {"z_planes": h // 16, "blocks_per_sm": h % 16},
+                "e": {"z_planes": e // 16, "blocks_per_sm": e % 16},
+                "flush": {"snapshots": f // 4, "kernel": "bulk-copy" if f % 4 == 1 else "register"}}
+
 
 def misfit(d_obs: torch.Tensor, d_syn: torch.Tensor, weight: Optional[torch.Tensor] = None):
     """phi = 1/2 sum |w (d_obs - d_syn)|^2 and resid = w^2 (d_obs - d_syn), on the device."""

@@ -214,8 +214,8 @@ def heterogeneous(core_xy=460, core_z=224, n_st=16, n_st_top=6, n_st_bot=6, n_sr
 
 
 def heterogeneous_crop96() -> Workload:
-    """The heterogeneous model on a 96^3 core (+ stretch + CPML) that the oracle can finish."""
-    return heterogeneous(core_xy=76, core_z=64, n_st=10, n_st_top=6, n_st_bot=6, n_src=4)
+    """The heterogeneous model cropped to 96^3 cells inside the CPML (116^3 in all), 4 sources."""
+    return heterogeneous(core_xy=76, core_z=84, n_st=10, n_st_top=6, n_st_bot=6, n_src=4)
 
 
 def small_box(n_core=24, h=100.0, npml=8, rho_bg=1.0, layered_model=True, n_freq=2,
