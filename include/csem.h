@@ -201,11 +201,20 @@ int csem_gradient(csem_ctx *ctx, const void *rho_dev, const void *Evol_dev, cons
  * blocks per SM) -- by timing each candidate on n_src sources of this grid;
  * later calls use the fastest; for FP32 it also picks the transform flush
  * (register kernel over 16 snapshots, or the bulk-copy kernel over 16 or 32).
- * kz_out (may be NULL, else 3 ints) receives, for H and E, 16 * planes +
- * blocks, then 4 * snapshots per flush + (1 for the bulk-copy kernel).  Overwrites the
+ * It then times the fused H+E step kernel (z blocking 4, 8 or 16) against
+ * the best split pair and keeps the faster.  kz_out (may be NULL, else 4
+ * ints) receives, for H and E, 16 * planes + blocks, then 4 * snapshots per
+ * flush + (1 for the bulk-copy kernel), then the fused z blocking (0: split).  Overwrites the
  * context's field state and blocks until the timing is done.
  * Errors: INVALID_ARG, CUDA. */
 int csem_autotune(csem_ctx *ctx, int n_src, int *kz_out, void *stream);
+
+/* Sets the launch configuration by hand instead of csem_autotune (tests run
+ * every variant through it): cfg = {H z planes, H blocks/SM, E z planes,
+ * E blocks/SM, fused z blocking (0 = split kernels), flush kernel (0 register,
+ * 1 bulk copy, FP32 only), snapshots per flush (16, or 32 when the context's
+ * ring has 33 slots)}.  Synchronises the device.  Errors: INVALID_ARG. */
+int csem_set_launch(csem_ctx *ctx, const int *cfg);
 
 /* Test hooks.
  * csem_set_wavelet: forward source time function J'(t_{n+1/2}) (host [nt]
@@ -228,8 +237,8 @@ int csem_check(csem_ctx *ctx, void *stream);
  * csem_time_step_kernels: on the state left by the last run of ctx, launches
  * each stepping kernel `launches` times for n_src sources and returns the mean
  * duration of one launch in milliseconds, from CUDA events on stream:
- * ms_out[0] = H half-step, ms_out[1] = 0 (the source injection runs inside
- * the E step), ms_out[2] = E step,
+ * ms_out[0] = split H half-step, ms_out[1] = fused H+E step when the
+ * autotuner selected it (else 0), ms_out[2] = split E step (with injection),
  * ms_out[3] = one damped-transform flush of transform_block snapshots
  * into vol_dev ([n_src][3][n_freq][vol] complex(real), overwritten).  Field
  * values are overwritten. */

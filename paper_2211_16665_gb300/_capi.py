@@ -65,6 +65,7 @@ SIGNATURES = {
     "csem_adjoint_model": (ctypes.c_int, [_V, _V, ctypes.POINTER(PointsC), ctypes.c_int, _V, _V, _V, _V]),
     "csem_gradient": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_int, ctypes.c_int, _V, _V]),
     "csem_autotune": (ctypes.c_int, [_V, ctypes.c_int, _I, _V]),
+    "csem_set_launch": (ctypes.c_int, [_V, _I]),
     "csem_set_wavelet": (ctypes.c_int, [_V, _D]),
     "csem_set_trace": (ctypes.c_int, [_V, _V]),
     "csem_check": (ctypes.c_int, [_V, _V]),
@@ -179,9 +180,14 @@ def gradient(ctx, rho_ptr, evol_ptr, vvol_ptr, n_src, wrt, grad_ptr, stream):
 
 def autotune(ctx, n_src, stream):
     """Times the launch candidates; returns (H, E, flush) codes (see csem_autotune)."""
-    out = (ctypes.c_int * 3)()
+    out = (ctypes.c_int * 4)()
     _check(lib().csem_autotune(ctx, int(n_src), out, stream))
-    return int(out[0]), int(out[1]), int(out[2])
+    return int(out[0]), int(out[1]), int(out[2]), int(out[3])
+
+
+def set_launch(ctx, kz_h, mb_h, kz_e, mb_e, fused_kz, flush_mode, block):
+    cfg = (ctypes.c_int * 7)(kz_h, mb_h, kz_e, mb_e, fused_kz, flush_mode, block)
+    _check(lib().csem_set_launch(ctx, cfg))
 
 
 def set_wavelet(ctx, wavelet=None):

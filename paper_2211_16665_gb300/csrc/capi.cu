@@ -88,12 +88,13 @@ struct csem_ctx {
     std::vector<double> wavelet;         // J'(t_{n+1/2})
     int KZ_h = 4, KZ_e = 4;             // z planes per thread (autotuned)
     int MB_h = 4, MB_e = 4;             // min resident blocks per SM of the compiled variant (autotuned)
+    int fused_kz = 0;                   // > 0: fused H+E step with this z blocking (autotuned)
     long long psi_stride = 0, sx = 0, sy = 0, sz = 0;
     size_t rsize = 4;
     // device memory
     void *d_tab = nullptr;               // per-axis stepping tables (real)
     double *d_h = nullptr;               // primal widths (double) hx|hy|hz
-    void *d_cE = nullptr, *d_H = nullptr, *d_ering = nullptr, *d_psi = nullptr, *d_comp = nullptr, *d_edge = nullptr;
+    void *d_cE = nullptr, *d_H = nullptr, *d_H2 = nullptr, *d_ering = nullptr, *d_psi = nullptr, *d_comp = nullptr, *d_edge = nullptr;
     int M = 16, nslot = 17;
     int flush_mode = 0;                  // 0: register flush; 1: bulk-copy flush (FP32 only)
     void *d_wR = nullptr;                // [nt][nf] complex real
@@ -278,6 +279,8 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
     p.pitch = c->pitch; p.npml = c->npml; p.plane = c->plane; p.vol = c->vol;
     axis_tab<R>(c, 0, p.ax); axis_tab<R>(c, 1, p.ay); axis_tab<R>(c, 2, p.az);
     p.H = (R *)c->d_H;
+    p.H2 = (R *)c->d_H2;
+    p.fused_kz = c->fused_kz;
     p.ering = (R *)c->d_ering;
     p.ering_stride = (long long)c->nslot * 3 * c->vol;
     p.nslot = c->nslot;
@@ -307,6 +310,7 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
 template <typename R>
 int reset_state(csem_ctx *c, int S, cudaStream_t st) {
     CK(cudaMemsetAsync(c->d_H, 0, (size_t)S * 3 * c->vol * sizeof(R), st));
+    CK(cudaMemsetAsync(c->d_H2, 0, (size_t)S * 3 * c->vol * sizeof(R), st));
     CK(cudaMemsetAsync(c->d_ering, 0, (size_t)S * c->nslot * 3 * c->vol * sizeof(R), st));
     CK(cudaMemsetAsync(c->d_psi, 0, (size_t)S * c->psi_stride * sizeof(R), st));
     CK(cudaMemsetAsync(c->d_step, 0, sizeof(int), st));
@@ -343,7 +347,7 @@ int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const 
     if (full > 0) {
         const int key[8] = {S, vol ? 1 : 0, kahan ? 1 : 0, q.n_itaps > 0 ? 1 : 0, q.n_rec > 0 ? 1 : 0,
                             (int)sizeof(R), ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
-                            M * 4 + c->flush_mode};
+                            (M * 4 + c->flush_mode) * 32 + c->fused_kz};
         cudaGraph_t g = nullptr;
         const long long before = csem::g_launches.load();   // captured kernels are counted per replay
         CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
@@ -513,11 +517,14 @@ int time_impl(csem_ctx *c, int S, void *vol, int launches, double *ms, cudaStrea
     p.colmap = c->d_colmap; p.colmap_stride = c->plane;     // the last forward run's taps
     p.itaps = c->d_itaps; p.itap_stride = 8;
     p.n_emit = 1; p.J = 1; p.coef = c->d_ones; p.T = c->d_T;
-    ms[1] = 0.0;                                             // injection runs inside the E step
-    for (int w : {0, 2, 3}) {
+    const int fkz = p.fused_kz;
+    for (int w : {0, 1, 2, 3}) {
+        if (w == 1 && fkz == 0) { ms[1] = 0.0; continue; }
         auto go = [&](int j) -> cudaError_t {
             if (w == 3) return flush<R>(c, p, q, S, 0, cnt, true, c->kahan != 0, st);
-            return csem::launch_step<R>(p, q, S, j % (c->nt - 1), st, w == 0 ? 1 : 4);
+            csem::StepParams<R> pp = p;
+            pp.fused_kz = (w == 1) ? fkz : 0;
+            return csem::launch_step<R>(pp, q, S, j % (c->nt - 1), st, w == 1 ? 5 : (w == 0 ? 1 : 4));
         };
         for (int j = 0; j < 2; ++j) CK(go(j));
         CK(cudaEventRecord(e0, st));
@@ -566,6 +573,26 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
         if (which == 1) { c->KZ_h = best_kz; c->MB_h = best_mb; }
         else { c->KZ_e = best_kz; c->MB_e = best_mb; }
     }
+    // fused H+E step (kz 4, 8, 16) against the best split pair
+    {
+        p.KZ_h = c->KZ_h; p.KZ_e = c->KZ_e; p.MB_h = c->MB_h; p.MB_e = c->MB_e;
+        double best = 1e30;
+        int best_f = 0;
+        for (int f : {0, 4, 8, 16}) {
+            p.fused_kz = f;
+            for (int j = 0; j < 3; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, 5));
+            CK(cudaEventRecord(e0, st));
+            const int reps = 20;
+            for (int j = 0; j < reps; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, 5));
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, e0, e1));
+            if (t < best) { best = t; best_f = f; }
+        }
+        c->fused_kz = best_f;
+        p.fused_kz = 0;
+    }
     // transform flush: register (16) vs bulk copy (16, 32 when the ring has room), per step
     if (sizeof(R) == 4 && c->nt >= 64) {
         typedef typename C2<R>::T R2;
@@ -608,7 +635,7 @@ void free_ctx(csem_ctx *c) {
     if (!c) return;
     cudaDeviceSynchronize();
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
-    void *ptrs[] = {c->d_tab, c->d_h, c->d_cE, c->d_H, c->d_ering, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
+    void *ptrs[] = {c->d_tab, c->d_h, c->d_cE, c->d_H, c->d_H2, c->d_ering, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
                     c->d_alpha, c->d_racc, c->d_coef, c->d_T, c->d_ones, c->d_rtaps, c->d_itaps, c->d_colmap, c->d_cpos, c->d_cval, c->d_step, c->d_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -704,7 +731,7 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     c->sx = (long long)c->NZ * c->NY * np2;
     c->sy = (long long)c->NZ * np2 * c->pitch;
     c->sz = (long long)np2 * c->NY * c->pitch;
-    c->psi_stride = 4 * (c->sx + c->sy + c->sz);
+    c->psi_stride = 6 * (c->sx + c->sy + c->sz);
     c->wavelet.assign(c->nt, 0.0);
     c->wavelet[0] = 1.0 / c->dt;
 
@@ -726,6 +753,7 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     step(dalloc(c, &c->d_cE, 3 * (size_t)c->vol * R));
     step(dalloc(c, &c->d_edge, 3 * (size_t)c->vol * R));
     step(dalloc(c, &c->d_H, (size_t)S * 3 * c->vol * R));
+    step(dalloc(c, &c->d_H2, (size_t)S * 3 * c->vol * R));
     step(dalloc(c, &c->d_ering, (size_t)S * c->nslot * 3 * c->vol * R));
     step(dalloc(c, &c->d_psi, (size_t)S * c->psi_stride * R));
     if (c->kahan) step(dalloc(c, &c->d_comp, (size_t)S * 3 * c->nf * c->vol * C2s));
@@ -755,7 +783,7 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     }
     rc = update_wavelet(c);
     if (rc != CSEM_OK) { free_ctx(c); return rc; }
-    if (csem::prepare_bulk_flush() != cudaSuccess) {
+    if (csem::prepare_bulk_flush() != cudaSuccess || csem::prepare_fused_all() != cudaSuccess) {
         cudaGetLastError();
         free_ctx(c);
         return fail(CSEM_ERR_CUDA, "cannot configure the bulk-copy flush kernel");
@@ -840,6 +868,20 @@ int csem_gradient(csem_ctx *c, const void *rho_dev, const void *Evol_dev, const 
 
 long long csem_launch_count(void) { return csem::g_launches.load(); }
 
+int csem_set_launch(csem_ctx *c, const int *cfg) {
+    if (!c || !cfg) return fail(CSEM_ERR_INVALID_ARG, "NULL argument");
+    const int kzh = cfg[0], mbh = cfg[1], kze = cfg[2], mbe = cfg[3], fkz = cfg[4], fm = cfg[5], M = cfg[6];
+    auto kz_ok = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8; };
+    auto mb_ok = [](int v) { return v == 4 || v == 6 || v == 8; };
+    if (!kz_ok(kzh) || !kz_ok(kze) || !mb_ok(mbh) || !mb_ok(mbe) || !(fkz == 0 || fkz == 4 || fkz == 8 || fkz == 16) ||
+        !(fm == 0 || (fm == 1 && c->precision == 32)) || !(M == 16 || M == 32) || M + 1 > c->nslot)
+        return fail(CSEM_ERR_INVALID_ARG, "launch configuration not supported by this context");
+    CK(cudaDeviceSynchronize());
+    c->KZ_h = kzh; c->MB_h = mbh; c->KZ_e = kze; c->MB_e = mbe;
+    c->fused_kz = fkz; c->flush_mode = fm; c->M = M;
+    return CSEM_OK;
+}
+
 int csem_autotune(csem_ctx *c, int n_src, int *kz_out, void *stream) {
     if (!c || n_src < 1 || n_src > c->max_src) return fail(CSEM_ERR_INVALID_ARG, "bad argument");
     cudaStream_t st = (cudaStream_t)stream;
@@ -848,6 +890,7 @@ int csem_autotune(csem_ctx *c, int n_src, int *kz_out, void *stream) {
         kz_out[0] = c->KZ_h * 16 + c->MB_h;
         kz_out[1] = c->KZ_e * 16 + c->MB_e;
         kz_out[2] = c->M * 4 + c->flush_mode;
+        kz_out[3] = c->fused_kz;
     }
     return CSEM_OK;
 }

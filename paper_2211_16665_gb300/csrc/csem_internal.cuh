@@ -4,10 +4,12 @@
 //                            index (k*NY + j)*pitch + i, NY = ny+1, NZ = nz+1
 //   ering   [nslot][3][vol]  E snapshots: E^n (Ex, Ey, Ez) in slot n mod nslot,
 //                            nslot = M + 1 for a transform block of M steps
-//   psi     12 CPML memory arrays, each only inside the slab of its axis:
-//           x-slabs [NZ][NY][2 npml]   : psi(Hy,dEz/dx) psi(Hz,dEy/dx) psi(Ey,dHz/dx) psi(Ez,dHy/dx)
-//           y-slabs [NZ][2 npml][pitch]: psi(Hx,dEz/dy) psi(Hz,dEx/dy) psi(Ex,dHz/dy) psi(Ez,dHx/dy)
-//           z-slabs [2 npml][NY][pitch]: psi(Hx,dEy/dz) psi(Hy,dEx/dz) psi(Ex,dHy/dz) psi(Ey,dHx/dz)
+//   H2      [3][vol]         second H buffer (the fused step reads one, writes the other)
+//   psi     CPML memory arrays, each only inside the slab of its axis, six per axis:
+//           x-slabs [NZ][NY][2 npml]   : psi(Hy,dEz/dx) psi(Hz,dEy/dx) psi(Ey,dHz/dx) psi(Ez,dHy/dx) + H pair B
+//           y-slabs [NZ][2 npml][pitch]: psi(Hx,dEz/dy) psi(Hz,dEx/dy) psi(Ex,dHz/dy) psi(Ez,dHx/dy) + H pair B
+//           z-slabs [2 npml][NY][pitch]: psi(Hx,dEy/dz) psi(Hy,dEx/dz) psi(Ex,dHy/dz) psi(Ey,dHx/dz) + H pair B
+//           (arrays [0],[1] and [4],[5] are the two buffers of the H-update memory)
 //   acc     [3][nf][vol] complex damped-transform accumulators (the caller's volume buffer)
 //   comp    [3][nf][vol] complex Kahan compensation (context workspace, FP32 only)
 #pragma once
@@ -20,6 +22,9 @@
 namespace csem {
 
 extern std::atomic<long long> g_launches;   // kernels launched by this library
+
+template <typename R> __device__ __forceinline__ R ldg_r(const R *p) { return __ldg(p); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 template <typename R> struct C2;
 template <> struct C2<float> { typedef float2 T; };
@@ -57,6 +62,8 @@ struct StepParams {
     long long plane, vol;          // pitch*NY, plane*NZ
     AxisTab<R> ax, ay, az;
     R *H;                          // [S][3][vol]
+    R *H2;                         // [S][3][vol] second H buffer (fused step)
+    int fused_kz;                  // > 0: one fused H+E kernel per step with this z blocking
     R *ering;                      // [S][nslot][3][vol]
     long long ering_stride;        // nslot*3*vol
     int nslot;                     // transform block M + 1
@@ -122,6 +129,11 @@ cudaError_t launch_advance(int *step, int by, cudaStream_t st);
 cudaError_t launch_dft_bulk(const StepParams<float> &p, const PointParams<float> &q, int S, int n0_off, int cnt,
                             bool kahan, int *err, cudaStream_t st);
 cudaError_t prepare_bulk_flush();
+// fused H+E step (kern_fused.cu), kz in {4, 8, 16}
+template <typename R>
+cudaError_t launch_fused(const StepParams<R> &p, int S, int jstep, int kz, cudaStream_t st);
+cudaError_t prepare_fused_all();
+size_t fused_smem_bytes(int real_size);
 
 // ---- launchers (kern_aux.cu) ----
 struct GeoD {                      // double-precision geometry for set-up and gradient kernels

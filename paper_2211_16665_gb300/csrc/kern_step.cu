@@ -63,8 +63,8 @@ __global__ void __launch_bounds__(kBlock, MINB) k_h(const StepParams<R> p, const
     R *__restrict__ Hz = Hx + 2 * vol;
     R *__restrict__ P = p.psi + (long long)s * p.psi_stride;
     R *__restrict__ psx = P;                         // x-slab arrays: [0]=Hy(dEz/dx) [1]=Hz(dEy/dx)
-    R *__restrict__ psy = P + 4 * p.sx;              // y-slab arrays: [0]=Hx(dEz/dy) [1]=Hz(dEx/dy)
-    R *__restrict__ psz = P + 4 * p.sx + 4 * p.sy;   // z-slab arrays: [0]=Hx(dEy/dz) [1]=Hy(dEx/dz)
+    R *__restrict__ psy = P + 6 * p.sx;              // y-slab arrays: [0]=Hx(dEz/dy) [1]=Hz(dEx/dy)
+    R *__restrict__ psz = P + 6 * p.sx + 6 * p.sy;   // z-slab arrays: [0]=Hx(dEy/dz) [1]=Hy(dEx/dz)
     const int nx = p.nx, ny = p.ny, nz = p.nz, np2 = 2 * p.npml;
 
     const int sxh = slab_half(i, nx, p.npml);
@@ -161,8 +161,8 @@ __global__ void __launch_bounds__(kBlock, MINB) k_e(const StepParams<R> p, const
     const R *__restrict__ cEz = p.cE + 2 * vol;
     R *__restrict__ P = p.psi + (long long)s * p.psi_stride;
     R *__restrict__ psx = P;                         // [2]=Ey(dHz/dx) [3]=Ez(dHy/dx)
-    R *__restrict__ psy = P + 4 * p.sx;              // [2]=Ex(dHz/dy) [3]=Ez(dHx/dy)
-    R *__restrict__ psz = P + 4 * p.sx + 4 * p.sy;   // [2]=Ex(dHy/dz) [3]=Ey(dHx/dz)
+    R *__restrict__ psy = P + 6 * p.sx;              // [2]=Ex(dHz/dy) [3]=Ez(dHx/dy)
+    R *__restrict__ psz = P + 6 * p.sx + 6 * p.sy;   // [2]=Ex(dHy/dz) [3]=Ey(dHx/dz)
     const int nx = p.nx, ny = p.ny, nz = p.nz, np2 = 2 * p.npml;
 
     const int sxn = slab_node(i, nx, p.npml);
@@ -586,6 +586,7 @@ cudaError_t launch_step(const StepParams<R> &p, const PointParams<R> &q, int S, 
                         int which) {
     (void)q;
     cudaError_t e = cudaSuccess;
+    if (p.fused_kz > 0 && (which & 5) == 5) return launch_fused<R>(p, S, jstep, p.fused_kz, st);
     if (which & 1) e = launch_field<R>(p, S, jstep, st, true, p.KZ_h, p.MB_h);
     if (e == cudaSuccess && (which & 4)) e = launch_field<R>(p, S, jstep, st, false, p.KZ_e, p.MB_e);
     return e;

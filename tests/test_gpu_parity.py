@@ -97,6 +97,50 @@ def test_adjoint_and_gradient(box, box_oracle, precision):
     eng.close()
 
 
+LAUNCH_VARIANTS = [
+    dict(kz_h=1, mb_h=8, kz_e=4, mb_e=6, fused_kz=0, flush_mode=0, block=16),
+    dict(kz_h=8, mb_h=4, kz_e=2, mb_e=4, fused_kz=0, flush_mode=1, block=16),
+    dict(fused_kz=4, flush_mode=1, block=32),
+    dict(fused_kz=8, flush_mode=0, block=16),
+    dict(fused_kz=16, flush_mode=1, block=16),
+]
+
+
+@pytest.mark.parametrize("variant", range(len(LAUNCH_VARIANTS)))
+def test_every_launch_variant_matches_oracle(box, box_oracle, variant):
+    """Split / fused step kernels and register / bulk-copy flushes give the oracle's results."""
+    wl, pb = box
+    o = box_oracle
+    eng = Engine.from_workload(wl, precision=32, kahan=1, autotune=False)
+    eng.set_launch(**LAUNCH_VARIANTS[variant])
+    rho = eng.model_tensor(wl.rho)
+    d, E, tr = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True, trace=True)
+    assert rel_l2(tr.cpu().numpy(), o["tr"]) <= 1e-4
+    assert rel_l2(d.cpu().numpy(), o["d"]) <= 1e-5
+    assert rel_l2(gpu_volume(eng, E), o["E"]) <= 1e-3
+    basis, _, _ = eng.estimate_adjoint_basis()
+    d_obs = torch.as_tensor(o["d_obs"], device=eng.device)
+    phi, r = misfit(d_obs, d)
+    V = eng.adjoint_model(rho, wl.rec, r, basis)
+    assert rel_l2(gpu_volume(eng, V), o["V"]) <= 1e-3
+    assert rel_l2(eng.gradient(rho, E, V).cpu().numpy(), o["g"]) <= 1e-3
+    eng.check()
+    eng.close()
+
+
+def test_fused_and_split_steps_agree_in_fp64(box):
+    wl, pb = box
+    out = []
+    for fused in (0, 8):
+        eng = Engine.from_workload(wl, precision=64, autotune=False)
+        eng.set_launch(fused_kz=fused)
+        d, E = eng.fwd_model(eng.model_tensor(wl.rho), wl.src, wl.rec, keep_volume=True)
+        out.append((d.cpu().numpy(), E.cpu().numpy()))
+        eng.close()
+    assert rel_l2(out[1][0], out[0][0]) <= 1e-13
+    assert rel_l2(out[1][1], out[0][1]) <= 1e-13
+
+
 def test_basis_matches_oracle_on_workload_sets():
     from oracle import basis as ob
     for (dt, nt, freqs) in ((0.004, 1000, [0.25, 0.75, 2.25]), (9.04e-4, 12328, [0.25, 0.5, 0.75, 1.0])):
