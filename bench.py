@@ -48,6 +48,10 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=2000, help="time steps in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batched-vs-plain", action="store_true",
+                    help="side measurement on batched_towline: one batched Kahan gradient vs one source per launch")
+    ap.add_argument("--nt", type=int, default=0, help="time steps for --batched-vs-plain (0: the workload's)")
+    ap.add_argument("--check-sources", type=int, default=4, help="sources scored against FP64 in --batched-vs-plain")
     return ap.parse_args()
 
 
@@ -339,8 +343,84 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batched_vs_plain(args):
+    """Gradient seconds per source: all sources in one launch (FP32 + Kahan) against one
+    source per launch (FP32, plain transform), and each gradient's error against FP64."""
+    import torch
+    from paper_2211_16665_gb300 import workloads as W
+    from paper_2211_16665_gb300.engine import Engine, misfit
+
+    torch.cuda.set_device(0)
+    wl = W.batched_towline()
+    S = wl.src.n
+
+    def gradient(eng, src, d_obs, out):
+        rho = eng.model_tensor(wl.rho)
+        d, E = eng.fwd_model(rho, src, wl.rec, keep_volume=True)
+        phi, r = misfit(d_obs, d)
+        basis, _, _ = eng.estimate_adjoint_basis()
+        V = eng.adjoint_model(rho, wl.rec, r, basis)
+        eng.gradient(rho, E, V, out=out)
+        del E, V
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    Z = W.cell_centres(wl.xn, wl.yn, wl.zn)[2]
+    rho_obs = np.where(Z >= 1000.0, 1.3 * wl.rho, wl.rho)     # observed data: sediment 30 % more resistive
+    out = {"mode": "batched_vs_plain", "workload": wl.name, "n_src": S, "nt": None}
+    # batched: every source in each launch, compensated transform
+    eb = Engine.from_workload(wl, nt=args.nt or None, max_src=S, kahan=1)
+    out["nt"] = eb.nt
+    d_obs = eb.fwd_model(eb.model_tensor(rho_obs), wl.src, wl.rec)
+    gb = torch.zeros((wl.nz, wl.ny, wl.nx), dtype=torch.float32, device="cuda")
+    gradient(eb, wl.src, d_obs, gb)                       # warm-up
+    gb.zero_()
+    tb = timed(lambda: gradient(eb, wl.src, d_obs, gb))
+    out["batched"] = {"s_per_source": tb / S, "launch": eb.launch_config(), "kahan": True}
+    eb.close()
+    # plain: one source per launch, plain FP32 transform
+    ep = Engine.from_workload(wl, nt=args.nt or None, max_src=1, kahan=0)
+    gp = torch.zeros_like(gb)
+    gradient(ep, wl.src.subset([0]), d_obs[:1].contiguous(), gp)
+    gp.zero_()
+    tp = timed(lambda: [gradient(ep, wl.src.subset([s]), d_obs[s:s + 1].contiguous(), gp) for s in range(S)])
+    out["plain"] = {"s_per_source": tp / S, "launch": ep.launch_config(), "kahan": False}
+    ep.close()
+    # error of each path's gradient on the first sources against the FP64 engine
+    k = min(args.check_sources, S)
+    sub = wl.src.subset(list(range(k)))
+    errs = {}
+    ref = None
+    for name, prec, kahan in (("fp64", 64, 0), ("batched", 32, 1), ("plain", 32, 0)):
+        e = Engine.from_workload(wl, nt=args.nt or None, max_src=k, precision=prec, kahan=kahan)
+        g = torch.zeros((wl.nz, wl.ny, wl.nx), dtype=e.real, device="cuda")
+        gradient(e, sub, d_obs[:k].contiguous(), g)
+        g = g.double().cpu().numpy()
+        e.close()
+        if ref is None:
+            ref = g
+        else:
+            errs[name] = float(np.linalg.norm(g - ref) / np.linalg.norm(ref))
+    out["batched"]["grad_rel_l2_vs_fp64"] = errs["batched"]
+    out["plain"]["grad_rel_l2_vs_fp64"] = errs["plain"]
+    out["speedup_per_source"] = out["plain"]["s_per_source"] / out["batched"]["s_per_source"]
+    out["note"] = (f"nt = {out['nt']} time steps per run; the per-step cost does not depend on nt; errors on the "
+                   f"first {k} sources")
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.batched_vs_plain:
+        run_batched_vs_plain(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
