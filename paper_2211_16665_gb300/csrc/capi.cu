@@ -89,6 +89,7 @@ struct csem_ctx {
     int KZ_h = 4, KZ_e = 4;             // z planes per thread (autotuned)
     int MB_h = 4, MB_e = 4;             // min resident blocks per SM of the compiled variant (autotuned)
     int fused_kz = 0;                   // > 0: fused H+E step with this z blocking (autotuned)
+    int VEC_h = 0, VEC_e = 0;           // 1: four-cells-per-thread FP32 kernels (autotuned)
     long long psi_stride = 0, sx = 0, sy = 0, sz = 0;
     size_t rsize = 4;
     // device memory
@@ -293,6 +294,8 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
     p.KZ_e = c->KZ_e;
     p.MB_h = c->MB_h;
     p.MB_e = c->MB_e;
+    p.VEC_h = c->VEC_h;
+    p.VEC_e = c->VEC_e;
     p.colmap = nullptr;
     p.colmap_stride = 0;
     p.itaps = nullptr;
@@ -347,7 +350,7 @@ int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const 
     if (full > 0) {
         const int key[8] = {S, vol ? 1 : 0, kahan ? 1 : 0, q.n_itaps > 0 ? 1 : 0, q.n_rec > 0 ? 1 : 0,
                             (int)sizeof(R), ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
-                            (M * 4 + c->flush_mode) * 32 + c->fused_kz};
+                            ((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e};
         cudaGraph_t g = nullptr;
         const long long before = csem::g_launches.load();   // captured kernels are counted per replay
         CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
@@ -555,11 +558,14 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
     const int mbs[3] = {4, 6, 8};
     for (int which : {1, 4}) {
         double best = 1e30;
-        int best_kz = 4, best_mb = 4;
-        for (int cand = 0; cand < 12; ++cand) {
-            const int kz = kzs[cand % 4], mb = mbs[cand / 4];
+        int best_kz = 4, best_mb = 4, best_vec = 0;
+        const int ncand = (sizeof(R) == 4) ? 20 : 12;   // 12 scalar shapes, then 8 four-cell shapes
+        for (int cand = 0; cand < ncand; ++cand) {
+            const int vec = cand >= 12 ? 1 : 0;
+            const int kz = kzs[cand % 4], mb = vec ? mbs[(cand - 12) / 4] : mbs[cand / 4];
             p.KZ_h = p.KZ_e = kz;
             p.MB_h = p.MB_e = mb;
+            p.VEC_h = p.VEC_e = vec;
             for (int j = 0; j < 3; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, which));
             CK(cudaEventRecord(e0, st));
             const int reps = 20;
@@ -568,14 +574,15 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
             CK(cudaEventSynchronize(e1));
             float t = 0.f;
             CK(cudaEventElapsedTime(&t, e0, e1));
-            if (t < best) { best = t; best_kz = kz; best_mb = mb; }
+            if (t < best) { best = t; best_kz = kz; best_mb = mb; best_vec = vec; }
         }
-        if (which == 1) { c->KZ_h = best_kz; c->MB_h = best_mb; }
-        else { c->KZ_e = best_kz; c->MB_e = best_mb; }
+        if (which == 1) { c->KZ_h = best_kz; c->MB_h = best_mb; c->VEC_h = best_vec; }
+        else { c->KZ_e = best_kz; c->MB_e = best_mb; c->VEC_e = best_vec; }
     }
     // fused H+E step (kz 4, 8, 16) against the best split pair
     {
         p.KZ_h = c->KZ_h; p.KZ_e = c->KZ_e; p.MB_h = c->MB_h; p.MB_e = c->MB_e;
+        p.VEC_h = c->VEC_h; p.VEC_e = c->VEC_e;
         double best = 1e30;
         int best_f = 0;
         for (int f : {0, 4, 8, 16}) {
@@ -728,9 +735,10 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     c->rsize = (c->precision == 32) ? 4 : 8;
     for (int a = 0; a < 3; ++a) cpml_axis(c->ax[a], c->npml, c->dt, vmax, c->f0);
     const int np2 = 2 * c->npml;
-    c->sx = (long long)c->NZ * c->NY * np2;
-    c->sy = (long long)c->NZ * np2 * c->pitch;
-    c->sz = (long long)np2 * c->NY * c->pitch;
+    auto pad8 = [](long long v) { return (v + 7) / 8 * 8; };   // keeps every slab array 32-byte aligned
+    c->sx = pad8((long long)c->NZ * c->NY * np2);
+    c->sy = pad8((long long)c->NZ * np2 * c->pitch);
+    c->sz = pad8((long long)np2 * c->NY * c->pitch);
     c->psi_stride = 6 * (c->sx + c->sy + c->sz);
     c->wavelet.assign(c->nt, 0.0);
     c->wavelet[0] = 1.0 / c->dt;
@@ -871,6 +879,9 @@ long long csem_launch_count(void) { return csem::g_launches.load(); }
 int csem_set_launch(csem_ctx *c, const int *cfg) {
     if (!c || !cfg) return fail(CSEM_ERR_INVALID_ARG, "NULL argument");
     const int kzh = cfg[0], mbh = cfg[1], kze = cfg[2], mbe = cfg[3], fkz = cfg[4], fm = cfg[5], M = cfg[6];
+    const int vh = cfg[7], ve = cfg[8];
+    if ((vh || ve) && (c->precision != 32 || (vh && mbh == 8) || (ve && mbe == 8) || vh < 0 || vh > 1 || ve < 0 || ve > 1))
+        return fail(CSEM_ERR_INVALID_ARG, "four-cell kernels: FP32 only, 4 or 6 blocks per SM");
     auto kz_ok = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8; };
     auto mb_ok = [](int v) { return v == 4 || v == 6 || v == 8; };
     if (!kz_ok(kzh) || !kz_ok(kze) || !mb_ok(mbh) || !mb_ok(mbe) || !(fkz == 0 || fkz == 4 || fkz == 8 || fkz == 16) ||
@@ -879,6 +890,7 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
     CK(cudaDeviceSynchronize());
     c->KZ_h = kzh; c->MB_h = mbh; c->KZ_e = kze; c->MB_e = mbe;
     c->fused_kz = fkz; c->flush_mode = fm; c->M = M;
+    c->VEC_h = vh; c->VEC_e = ve;
     return CSEM_OK;
 }
 
@@ -887,8 +899,8 @@ int csem_autotune(csem_ctx *c, int n_src, int *kz_out, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     TRY(c->precision == 32 ? autotune_impl<float>(c, n_src, st) : autotune_impl<double>(c, n_src, st));
     if (kz_out) {
-        kz_out[0] = c->KZ_h * 16 + c->MB_h;
-        kz_out[1] = c->KZ_e * 16 + c->MB_e;
+        kz_out[0] = (c->KZ_h * 16 + c->MB_h) + 256 * c->VEC_h;
+        kz_out[1] = (c->KZ_e * 16 + c->MB_e) + 256 * c->VEC_e;
         kz_out[2] = c->M * 4 + c->flush_mode;
         kz_out[3] = c->fused_kz;
     }

@@ -74,6 +74,7 @@ struct StepParams {
     const int *step;               // device step counter (chunk base)
     int KZ_h, KZ_e;                // z planes per thread of the H / E kernels (1, 2, 4 or 8)
     int MB_h, MB_e;                // minimum resident blocks per SM the kernels are compiled for (4, 6, 8)
+    int VEC_h, VEC_e;              // 1: FP32 kernels with four cells per thread along x
     int nf;
     const typename C2<R>::T *w;    // [nt][nf] exp((-1+i) a_k n dt)
     typename C2<R>::T *acc;        // [S][3][nf][vol] or nullptr
@@ -133,6 +134,8 @@ cudaError_t prepare_bulk_flush();
 template <typename R>
 cudaError_t launch_fused(const StepParams<R> &p, int S, int jstep, int kz, cudaStream_t st);
 cudaError_t prepare_fused_all();
+// FP32 H / E kernels with four cells per thread (kern_vec.cu), kz in {1,2,4,8}, mb in {4,6}
+cudaError_t launch_field_vec(const StepParams<float> &p, int S, int jstep, cudaStream_t st, bool h, int kz, int mb);
 size_t fused_smem_bytes(int real_size);
 
 // ---- launchers (kern_aux.cu) ----

@@ -570,6 +570,9 @@ bool launch_kz(const StepParams<R> &p, dim3 grid, int jstep, cudaStream_t st, bo
 
 template <typename R>
 cudaError_t launch_field(const StepParams<R> &p, int S, int jstep, cudaStream_t st, bool h, int kz, int mb) {
+    if constexpr (sizeof(R) == 4) {
+        if (h ? p.VEC_h : p.VEC_e) return launch_field_vec(p, S, jstep, st, h, kz, mb);
+    }
     const long long plane_threads = (long long)p.NY * p.pitch;
     dim3 grid((unsigned)((plane_threads + kBlock - 1) / kBlock), (unsigned)((p.NZ + kz - 1) / kz), (unsigned)S);
     bool ok = false;
