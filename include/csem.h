@@ -198,15 +198,17 @@ int csem_gradient(csem_ctx *ctx, const void *rho_dev, const void *Evol_dev, cons
 
 /* Picks the launch shape of the H and E stepping kernels -- z planes per
  * thread (1, 2, 4, 8), the register budget (4, 6 or 8 resident 256-thread
- * blocks per SM), and for FP32 one or four cells per thread along x -- by
+ * blocks per SM), and for FP32 one or four cells per thread along x or the
+ * bulk-copy-staged kernels (1, 2 or 4 rows per block, 2-16 planes) -- by
  * timing each candidate on n_src sources of this grid;
  * later calls use the fastest; for FP32 it also picks the transform flush
  * (register kernel over 16 snapshots, or the bulk-copy kernel over 16 or 32).
  * It then times the fused H+E step kernel (z blocking 4, 8 or 16) against
  * the best split pair and keeps the faster.  kz_out (may be NULL, else 4
  * ints) receives, for H and E, 16 * planes + blocks (+ 256 for the FP32
- * four-cells-per-thread kernel), then 4 * snapshots per flush + (1 for the
- * bulk-copy kernel), then the fused z blocking (0: split).  Overwrites the
+ * four-cells-per-thread kernel, + 1024 * rows for the bulk-copy-staged
+ * kernel), then 4 * snapshots per flush + (1 for the bulk-copy kernel), then
+ * the fused z blocking (0: split).  Overwrites the
  * context's field state and blocks until the timing is done.
  * Errors: INVALID_ARG, CUDA. */
 int csem_autotune(csem_ctx *ctx, int n_src, int *kz_out, void *stream);
@@ -216,7 +218,9 @@ int csem_autotune(csem_ctx *ctx, int n_src, int *kz_out, void *stream);
  * E blocks/SM, fused z blocking (0 = split kernels), flush kernel (0 register,
  * 1 bulk copy, FP32 only), snapshots per flush (16, or 32 when the context's
  * ring has 33 slots), H four-cells-per-thread (0/1, FP32, 4 or 6 blocks/SM),
- * E four-cells-per-thread (0/1)}.  Synchronises the device.
+ * E four-cells-per-thread (0/1), H bulk-copy-staged rows per block (0, or
+ * 1/2/4 for FP32 when the staged planes fit shared memory; z planes 2-16),
+ * E bulk-copy-staged rows per block}.  Synchronises the device.
  * Errors: INVALID_ARG. */
 int csem_set_launch(csem_ctx *ctx, const int *cfg);
 

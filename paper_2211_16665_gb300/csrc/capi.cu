@@ -90,6 +90,7 @@ struct csem_ctx {
     int MB_h = 4, MB_e = 4;             // min resident blocks per SM of the compiled variant (autotuned)
     int fused_kz = 0;                   // > 0: fused H+E step with this z blocking (autotuned)
     int VEC_h = 0, VEC_e = 0;           // 1: four-cells-per-thread FP32 kernels (autotuned)
+    int TMA_h = 0, TMA_e = 0;           // > 0: bulk-copy-staged FP32 kernels, rows per block (autotuned)
     long long psi_stride = 0, sx = 0, sy = 0, sz = 0;
     size_t rsize = 4;
     // device memory
@@ -296,6 +297,9 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
     p.MB_e = c->MB_e;
     p.VEC_h = c->VEC_h;
     p.VEC_e = c->VEC_e;
+    p.TMA_h = c->TMA_h;
+    p.TMA_e = c->TMA_e;
+    p.err = c->d_bad;
     p.colmap = nullptr;
     p.colmap_stride = 0;
     p.itaps = nullptr;
@@ -350,7 +354,8 @@ int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const 
     if (full > 0) {
         const int key[8] = {S, vol ? 1 : 0, kahan ? 1 : 0, q.n_itaps > 0 ? 1 : 0, q.n_rec > 0 ? 1 : 0,
                             (int)sizeof(R), ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
-                            ((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e};
+                            (((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e) * 25 +
+                                c->TMA_h * 5 + c->TMA_e};
         cudaGraph_t g = nullptr;
         const long long before = csem::g_launches.load();   // captured kernels are counted per replay
         CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
@@ -559,13 +564,20 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
     for (int which : {1, 4}) {
         double best = 1e30;
         int best_kz = 4, best_mb = 4, best_vec = 0;
-        const int ncand = (sizeof(R) == 4) ? 20 : 12;   // 12 scalar shapes, then 8 four-cell shapes
+        const int maxty = (sizeof(R) == 4) ? csem::tma_max_rows(c->pitch) : 0;
+        const int ntma = maxty >= 4 ? 12 : (maxty >= 2 ? 8 : (maxty >= 1 ? 4 : 0));
+        const int ncand = (sizeof(R) == 4) ? 20 + ntma : 12;   // 12 scalar, 8 four-cell, then staged shapes
+        int best_tma = 0;
         for (int cand = 0; cand < ncand; ++cand) {
-            const int vec = cand >= 12 ? 1 : 0;
-            const int kz = kzs[cand % 4], mb = vec ? mbs[(cand - 12) / 4] : mbs[cand / 4];
+            const int vec = (cand >= 12 && cand < 20) ? 1 : 0;
+            const int tma = cand >= 20 ? (1 << ((cand - 20) / 4)) : 0;          // rows per block 1, 2, 4
+            const int tkz[4] = {2, 4, 8, 16};
+            const int kz = tma ? tkz[(cand - 20) % 4] : kzs[cand % 4];
+            const int mb = tma ? 4 : (vec ? mbs[(cand - 12) / 4] : mbs[cand / 4]);
             p.KZ_h = p.KZ_e = kz;
             p.MB_h = p.MB_e = mb;
             p.VEC_h = p.VEC_e = vec;
+            p.TMA_h = p.TMA_e = tma;
             for (int j = 0; j < 3; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, which));
             CK(cudaEventRecord(e0, st));
             const int reps = 20;
@@ -574,15 +586,16 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
             CK(cudaEventSynchronize(e1));
             float t = 0.f;
             CK(cudaEventElapsedTime(&t, e0, e1));
-            if (t < best) { best = t; best_kz = kz; best_mb = mb; best_vec = vec; }
+            if (t < best) { best = t; best_kz = kz; best_mb = mb; best_vec = vec; best_tma = tma; }
         }
-        if (which == 1) { c->KZ_h = best_kz; c->MB_h = best_mb; c->VEC_h = best_vec; }
-        else { c->KZ_e = best_kz; c->MB_e = best_mb; c->VEC_e = best_vec; }
+        if (which == 1) { c->KZ_h = best_kz; c->MB_h = best_mb; c->VEC_h = best_vec; c->TMA_h = best_tma; }
+        else { c->KZ_e = best_kz; c->MB_e = best_mb; c->VEC_e = best_vec; c->TMA_e = best_tma; }
     }
     // fused H+E step (kz 4, 8, 16) against the best split pair
     {
         p.KZ_h = c->KZ_h; p.KZ_e = c->KZ_e; p.MB_h = c->MB_h; p.MB_e = c->MB_e;
         p.VEC_h = c->VEC_h; p.VEC_e = c->VEC_e;
+        p.TMA_h = c->TMA_h; p.TMA_e = c->TMA_e;
         double best = 1e30;
         int best_f = 0;
         for (int f : {0, 4, 8, 16}) {
@@ -791,10 +804,15 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     }
     rc = update_wavelet(c);
     if (rc != CSEM_OK) { free_ctx(c); return rc; }
-    if (csem::prepare_bulk_flush() != cudaSuccess || csem::prepare_fused_all() != cudaSuccess) {
-        cudaGetLastError();
-        free_ctx(c);
-        return fail(CSEM_ERR_CUDA, "cannot configure the bulk-copy flush kernel");
+    {
+        cudaError_t e1 = csem::prepare_bulk_flush(), e2 = csem::prepare_fused_all(), e3 = csem::prepare_tma();
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+            cudaGetLastError();
+            free_ctx(c);
+            return fail(CSEM_ERR_CUDA, std::string("cannot configure shared memory of the ") +
+                                           (e1 != cudaSuccess ? "bulk-copy flush" : e2 != cudaSuccess ? "fused step" : "staged step") +
+                                           " kernels");
+        }
     }
     *out = c;
     return CSEM_OK;
@@ -879,10 +897,18 @@ long long csem_launch_count(void) { return csem::g_launches.load(); }
 int csem_set_launch(csem_ctx *c, const int *cfg) {
     if (!c || !cfg) return fail(CSEM_ERR_INVALID_ARG, "NULL argument");
     const int kzh = cfg[0], mbh = cfg[1], kze = cfg[2], mbe = cfg[3], fkz = cfg[4], fm = cfg[5], M = cfg[6];
-    const int vh = cfg[7], ve = cfg[8];
+    const int vh = cfg[7], ve = cfg[8], th = cfg[9], te = cfg[10];
+    if (th || te) {
+        const int maxty = c->precision == 32 ? csem::tma_max_rows(c->pitch) : 0;
+        auto ok = [&](int ty, int kz) { return ty == 0 || ((ty == 1 || ty == 2 || ty == 4) && ty <= maxty &&
+                                                          (kz == 2 || kz == 4 || kz == 8 || kz == 16)); };
+        if (!ok(th, kzh) || !ok(te, kze)) return fail(CSEM_ERR_INVALID_ARG, "staged kernels: FP32, rows 1/2/4 that fit, 2-16 planes");
+    }
+    if (((kzh == 16 && !th) || (kze == 16 && !te)))
+        return fail(CSEM_ERR_INVALID_ARG, "16 planes per block only for the staged kernels");
     if ((vh || ve) && (c->precision != 32 || (vh && mbh == 8) || (ve && mbe == 8) || vh < 0 || vh > 1 || ve < 0 || ve > 1))
         return fail(CSEM_ERR_INVALID_ARG, "four-cell kernels: FP32 only, 4 or 6 blocks per SM");
-    auto kz_ok = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8; };
+    auto kz_ok = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16; };
     auto mb_ok = [](int v) { return v == 4 || v == 6 || v == 8; };
     if (!kz_ok(kzh) || !kz_ok(kze) || !mb_ok(mbh) || !mb_ok(mbe) || !(fkz == 0 || fkz == 4 || fkz == 8 || fkz == 16) ||
         !(fm == 0 || (fm == 1 && c->precision == 32)) || !(M == 16 || M == 32) || M + 1 > c->nslot)
@@ -891,6 +917,7 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
     c->KZ_h = kzh; c->MB_h = mbh; c->KZ_e = kze; c->MB_e = mbe;
     c->fused_kz = fkz; c->flush_mode = fm; c->M = M;
     c->VEC_h = vh; c->VEC_e = ve;
+    c->TMA_h = th; c->TMA_e = te;
     return CSEM_OK;
 }
 
@@ -899,8 +926,8 @@ int csem_autotune(csem_ctx *c, int n_src, int *kz_out, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     TRY(c->precision == 32 ? autotune_impl<float>(c, n_src, st) : autotune_impl<double>(c, n_src, st));
     if (kz_out) {
-        kz_out[0] = (c->KZ_h * 16 + c->MB_h) + 256 * c->VEC_h;
-        kz_out[1] = (c->KZ_e * 16 + c->MB_e) + 256 * c->VEC_e;
+        kz_out[0] = (c->KZ_h * 16 + c->MB_h) + 256 * c->VEC_h + 1024 * c->TMA_h;
+        kz_out[1] = (c->KZ_e * 16 + c->MB_e) + 256 * c->VEC_e + 1024 * c->TMA_e;
         kz_out[2] = c->M * 4 + c->flush_mode;
         kz_out[3] = c->fused_kz;
     }

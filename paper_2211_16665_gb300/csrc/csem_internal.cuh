@@ -75,6 +75,8 @@ struct StepParams {
     int KZ_h, KZ_e;                // z planes per thread of the H / E kernels (1, 2, 4 or 8)
     int MB_h, MB_e;                // minimum resident blocks per SM the kernels are compiled for (4, 6, 8)
     int VEC_h, VEC_e;              // 1: FP32 kernels with four cells per thread along x
+    int TMA_h, TMA_e;              // > 0: FP32 bulk-copy-staged kernels over this many rows per block
+    int *err;                      // device status word (bit 1: a bounded wait gave up)
     int nf;
     const typename C2<R>::T *w;    // [nt][nf] exp((-1+i) a_k n dt)
     typename C2<R>::T *acc;        // [S][3][nf][vol] or nullptr
@@ -136,6 +138,11 @@ cudaError_t launch_fused(const StepParams<R> &p, int S, int jstep, int kz, cudaS
 cudaError_t prepare_fused_all();
 // FP32 H / E kernels with four cells per thread (kern_vec.cu), kz in {1,2,4,8}, mb in {4,6}
 cudaError_t launch_field_vec(const StepParams<float> &p, int S, int jstep, cudaStream_t st, bool h, int kz, int mb);
+// FP32 bulk-copy-staged H / E kernels (kern_tma.cu): ty rows per block in {1,2,4}, kz planes per chunk
+cudaError_t launch_field_tma(const StepParams<float> &p, int S, int jstep, cudaStream_t st, bool h, int kz, int ty,
+                             int *err);
+cudaError_t prepare_tma();
+int tma_max_rows(int pitch);
 size_t fused_smem_bytes(int real_size);
 
 // ---- launchers (kern_aux.cu) ----

@@ -571,6 +571,8 @@ bool launch_kz(const StepParams<R> &p, dim3 grid, int jstep, cudaStream_t st, bo
 template <typename R>
 cudaError_t launch_field(const StepParams<R> &p, int S, int jstep, cudaStream_t st, bool h, int kz, int mb) {
     if constexpr (sizeof(R) == 4) {
+        const int ty = h ? p.TMA_h : p.TMA_e;
+        if (ty > 0) return launch_field_tma(p, S, jstep, st, h, kz, ty, p.err);
         if (h ? p.VEC_h : p.VEC_e) return launch_field_vec(p, S, jstep, st, h, kz, mb);
     }
     const long long plane_threads = (long long)p.NY * p.pitch;

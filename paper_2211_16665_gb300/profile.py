@@ -25,9 +25,13 @@ def main():
     ap.add_argument("--workload", default="thin_reservoir")
     ap.add_argument("--nt", type=int, default=256)
     ap.add_argument("--kahan", type=int, default=1)
+    ap.add_argument("--launch", default="", help="JSON keyword arguments of Engine.set_launch (skips autotuning)")
     args = ap.parse_args()
     wl = W.ALL[args.workload]()
-    eng = Engine.from_workload(wl, nt=args.nt, kahan=args.kahan)
+    eng = Engine.from_workload(wl, nt=args.nt, kahan=args.kahan, autotune=not args.launch)
+    if args.launch:
+        import json
+        eng.set_launch(**json.loads(args.launch))
     rho = eng.model_tensor(wl.rho)
     d, E = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)
     torch.cuda.synchronize()

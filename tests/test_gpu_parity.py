@@ -102,6 +102,9 @@ LAUNCH_VARIANTS = [
     dict(kz_h=2, mb_h=4, kz_e=1, mb_e=6, vec_h=1, vec_e=1, flush_mode=1, block=32),
     dict(kz_h=8, mb_h=6, kz_e=4, mb_e=4, vec_h=1, vec_e=0, flush_mode=1, block=16),
     dict(kz_h=4, mb_h=8, kz_e=8, mb_e=4, vec_h=0, vec_e=1, flush_mode=0, block=16),
+    dict(kz_h=4, mb_h=4, kz_e=2, mb_e=4, tma_h=4, tma_e=4, flush_mode=1, block=32),
+    dict(kz_h=16, mb_h=4, kz_e=8, mb_e=4, tma_h=1, tma_e=2, flush_mode=1, block=16),
+    dict(kz_h=2, mb_h=4, kz_e=16, mb_e=4, tma_h=2, tma_e=1, vec_h=0, flush_mode=0, block=16),
     dict(kz_h=8, mb_h=4, kz_e=2, mb_e=4, fused_kz=0, flush_mode=1, block=16),
     dict(fused_kz=4, flush_mode=1, block=32),
     dict(fused_kz=8, flush_mode=0, block=16),
