@@ -198,29 +198,39 @@ int csem_gradient(csem_ctx *ctx, const void *rho_dev, const void *Evol_dev, cons
 
 /* Picks the launch shape of the H and E stepping kernels -- z planes per
  * thread (1, 2, 4, 8), the register budget (4, 6 or 8 resident 256-thread
- * blocks per SM), and for FP32 one or four cells per thread along x or the
- * bulk-copy-staged kernels (1, 2 or 4 rows per block, 2-16 planes) -- by
+ * blocks per SM), and for FP32 one or four cells per thread along x, the
+ * bulk-copy-staged kernels (1, 2 or 4 rows per block, 2-16 planes) or the
+ * lean four-cell kernels (1, 2 or 4 planes; see csem_set_launch) -- by
  * timing each candidate on n_src sources of this grid;
- * later calls use the fastest; for FP32 it also picks the transform flush
- * (register kernel over 16 snapshots, or the bulk-copy kernel over 16 or 32).
- * It then times the fused H+E step kernel (z blocking 4, 8 or 16) against
- * the best split pair and keeps the faster.  kz_out (may be NULL, else 4
- * ints) receives, for H and E, 16 * planes + blocks (+ 256 for the FP32
- * four-cells-per-thread kernel, + 1024 * rows for the bulk-copy-staged
- * kernel), then 4 * snapshots per flush + (1 for the bulk-copy kernel), then
- * the fused z blocking (0: split).  Overwrites the
+ * later calls use the fastest.  It then times the fused H+E step kernel (z
+ * blocking 4, 8 or 16) against the best split pair and keeps the faster, and
+ * last, when nt >= 256, the transform flush over 128 steps: the register
+ * kernel or (FP32) the bulk-copy kernel, over 16 or 32 snapshots, run after
+ * its block or on a second stream overlapping the next block (needs a ring of
+ * 2 * snapshots + 1 slots; the results are the same bit for bit).  kz_out
+ * (may be NULL, else 4 ints) receives, for H and E, 16 * planes + blocks
+ * (+ 256 for the FP32 four-cells-per-thread kernel, + 1024 * rows for the
+ * bulk-copy-staged kernel, + 8192 * cells per thread for the lean kernel), then 4 * snapshots per flush + flush mode (as in
+ * csem_set_launch), then the fused z blocking (0: split).  Overwrites the
  * context's field state and blocks until the timing is done.
  * Errors: INVALID_ARG, CUDA. */
 int csem_autotune(csem_ctx *ctx, int n_src, int *kz_out, void *stream);
 
 /* Sets the launch configuration by hand instead of csem_autotune (tests run
  * every variant through it): cfg = {H z planes, H blocks/SM, E z planes,
- * E blocks/SM, fused z blocking (0 = split kernels), flush kernel (0 register,
- * 1 bulk copy, FP32 only), snapshots per flush (16, or 32 when the context's
- * ring has 33 slots), H four-cells-per-thread (0/1, FP32, 4 or 6 blocks/SM),
+ * E blocks/SM, fused z blocking (0 = split kernels), flush mode (bit 0: bulk
+ * copy, FP32 only, else register kernel; bit 1: overlapped with the next
+ * block on a second stream), snapshots per flush (16 or 32; the context's ring
+ * of 17, 33 or 65 slots must hold snapshots + 1, or 2 * snapshots + 1 when
+ * overlapped), H four-cells-per-thread (0/1, FP32, 4 or 6 blocks/SM),
  * E four-cells-per-thread (0/1), H bulk-copy-staged rows per block (0, or
  * 1/2/4 for FP32 when the staged planes fit shared memory; z planes 2-16),
- * E bulk-copy-staged rows per block}.  Synchronises the device.
+ * E bulk-copy-staged rows per block, H lean kernel (0 off, or 1 or 2 cells
+ * per thread: FP32 with nx a multiple of 4 and room for the CPML memory in 12
+ * volume arrays per source; 1, 2 or 4 planes, 4 or 6 blocks/SM), E lean
+ * kernel (0, 1 or 2)} -- 13 ints.  The
+ * lean kernel takes precedence over the staged and four-cell ones.
+ * Synchronises the device.
  * Errors: INVALID_ARG. */
 int csem_set_launch(csem_ctx *ctx, const int *cfg);
 

@@ -185,8 +185,10 @@ def autotune(ctx, n_src, stream):
     return int(out[0]), int(out[1]), int(out[2]), int(out[3])
 
 
-def set_launch(ctx, kz_h, mb_h, kz_e, mb_e, fused_kz, flush_mode, block, vec_h=0, vec_e=0, tma_h=0, tma_e=0):
-    cfg = (ctypes.c_int * 11)(kz_h, mb_h, kz_e, mb_e, fused_kz, flush_mode, block, vec_h, vec_e, tma_h, tma_e)
+def set_launch(ctx, kz_h, mb_h, kz_e, mb_e, fused_kz, flush_mode, block, vec_h=0, vec_e=0, tma_h=0, tma_e=0,
+               lean_h=0, lean_e=0):
+    cfg = (ctypes.c_int * 13)(kz_h, mb_h, kz_e, mb_e, fused_kz, flush_mode, block, vec_h, vec_e, tma_h, tma_e,
+                              lean_h, lean_e)
     _check(lib().csem_set_launch(ctx, cfg))
 
 

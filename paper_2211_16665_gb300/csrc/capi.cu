@@ -39,6 +39,7 @@ constexpr double kCpmlR = 1e-6;
 constexpr double kDecaySpan = 35.0;
 constexpr int kChunk = 64;        // time steps per captured graph
 constexpr int kBlockM = 32;        // largest snapshots per transform flush (divides kChunk)
+constexpr int kMaxSide = 4;       // event slots for overlapped flushes (at most two are in flight)
 
 struct Axis {
     int n = 0;
@@ -91,14 +92,19 @@ struct csem_ctx {
     int fused_kz = 0;                   // > 0: fused H+E step with this z blocking (autotuned)
     int VEC_h = 0, VEC_e = 0;           // 1: four-cells-per-thread FP32 kernels (autotuned)
     int TMA_h = 0, TMA_e = 0;           // > 0: bulk-copy-staged FP32 kernels, rows per block (autotuned)
+    int LEAN_h = 0, LEAN_e = 0;         // > 0: lean FP32 kernels, cells per thread (autotuned; needs d_psiL)
     long long psi_stride = 0, sx = 0, sy = 0, sz = 0;
     size_t rsize = 4;
     // device memory
     void *d_tab = nullptr;               // per-axis stepping tables (real)
     double *d_h = nullptr;               // primal widths (double) hx|hy|hz
+    void *d_tabL = nullptr;              // padded FP32 stepping tables (lean kernels)
+    float *d_psiL = nullptr, *d_cEm = nullptr;   // lean kernels: CPML memory in volume arrays, masked dt/eps
     void *d_cE = nullptr, *d_H = nullptr, *d_H2 = nullptr, *d_ering = nullptr, *d_psi = nullptr, *d_comp = nullptr, *d_edge = nullptr;
     int M = 16, nslot = 17;
-    int flush_mode = 0;                  // 0: register flush; 1: bulk-copy flush (FP32 only)
+    int flush_mode = 0;                  // bit 0: bulk-copy flush (FP32 only), else register flush;
+                                         // bit 1: flush on the side stream, overlapping the next block
+
     void *d_wR = nullptr;                // [nt][nf] complex real
     double2 *d_w64 = nullptr;            // [nt][nf]
     double2 *d_alpha = nullptr;          // [0..nf): forward, [nf..2nf): adjoint, [2nf..3nf): k_f
@@ -112,7 +118,8 @@ struct csem_ctx {
     double *d_trace = nullptr;
     int last_nrec = 0;
     long long bytes = 0;
-    cudaStream_t cap = nullptr;
+    cudaStream_t cap = nullptr, side = nullptr;
+    cudaEvent_t ev_fork[kMaxSide] = {}, ev_done[kMaxSide] = {};
     struct GraphSlot { int key[8]; cudaGraphExec_t exec; };
     std::vector<GraphSlot> graphs;
 };
@@ -149,6 +156,38 @@ void axis_tab(const csem_ctx *c, int a, csem::AxisTab<R> &t) {
     t.a_h = base + off + 3 * (n + 1);
     t.b_n = base + off + 4 * (n + 1);
     t.a_n = base + off + 5 * (n + 1);
+}
+
+// Lean-kernel tables: per axis ih_h, ih_n, b_h, a_h, b_n, a_n, each padded to
+// lean_len(n) floats (16-byte groups, zero past the axis); b_n, a_n are zero on
+// the outer nodes 0 and n, which carry no CPML update.
+int lean_len(int n) { return (n + 1 + 3 + 3) / 4 * 4; }
+void lean_tab(const csem_ctx *c, int a, csem::AxisTab<float> &t) {
+    const float *base = (const float *)c->d_tabL;
+    long long off = 0;
+    for (int b = 0; b < a; ++b) off += 6LL * lean_len(c->ax[b].n);
+    const int L = lean_len(c->ax[a].n);
+    t.ih_h = base + off; t.ih_n = base + off + L; t.b_h = base + off + 2 * L;
+    t.a_h = base + off + 3 * L; t.b_n = base + off + 4 * L; t.a_n = base + off + 5 * L;
+}
+int upload_lean_tables(csem_ctx *c) {
+    std::vector<float> tab;
+    for (int a = 0; a < 3; ++a) {
+        const Axis &A = c->ax[a];
+        const int n = A.n, L = lean_len(n);
+        std::vector<float> v(6 * (size_t)L, 0.f);
+        for (int i = 0; i < n; ++i) {
+            v[i] = (float)(1.0 / A.h[i]);
+            v[2 * L + i] = (float)A.bh[i];
+            v[3 * L + i] = (float)A.ah[i];
+        }
+        for (int i = 0; i <= n; ++i) v[L + i] = (float)(1.0 / A.ht[i]);
+        for (int i = 1; i < n; ++i) { v[4 * L + i] = (float)A.bn[i]; v[5 * L + i] = (float)A.an[i]; }
+        tab.insert(tab.end(), v.begin(), v.end());
+    }
+    TRY(dalloc(c, &c->d_tabL, tab.size() * sizeof(float)));
+    CK(cudaMemcpy(c->d_tabL, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return CSEM_OK;
 }
 
 template <typename R>
@@ -299,6 +338,16 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
     p.VEC_e = c->VEC_e;
     p.TMA_h = c->TMA_h;
     p.TMA_e = c->TMA_e;
+    p.LEAN_h = c->LEAN_h;
+    p.LEAN_e = c->LEAN_e;
+    p.lx = p.ly = p.lz = csem::AxisTab<R>{};
+    p.psiL = nullptr;
+    p.cEm = nullptr;
+    if constexpr (sizeof(R) == 4) {
+        if (c->d_tabL) { lean_tab(c, 0, p.lx); lean_tab(c, 1, p.ly); lean_tab(c, 2, p.lz); }
+        p.psiL = c->d_psiL;
+        p.cEm = c->d_cEm;
+    }
     p.err = c->d_bad;
     p.colmap = nullptr;
     p.colmap_stride = 0;
@@ -320,6 +369,7 @@ int reset_state(csem_ctx *c, int S, cudaStream_t st) {
     CK(cudaMemsetAsync(c->d_H2, 0, (size_t)S * 3 * c->vol * sizeof(R), st));
     CK(cudaMemsetAsync(c->d_ering, 0, (size_t)S * c->nslot * 3 * c->vol * sizeof(R), st));
     CK(cudaMemsetAsync(c->d_psi, 0, (size_t)S * c->psi_stride * sizeof(R), st));
+    if (c->d_psiL) CK(cudaMemsetAsync(c->d_psiL, 0, (size_t)S * 12 * c->vol * sizeof(float), st));
     CK(cudaMemsetAsync(c->d_step, 0, sizeof(int), st));
     return CSEM_OK;
 }
@@ -330,37 +380,83 @@ template <typename R>
 cudaError_t flush(csem_ctx *c, const csem::StepParams<R> &p, const csem::PointParams<R> &q, int S, int n0_off,
                   int cnt, bool vol, bool kahan, cudaStream_t st) {
     if constexpr (sizeof(R) == 4) {
-        if (c->flush_mode == 1 && vol && (cnt == 16 || cnt == 32))
+        if ((c->flush_mode & 1) && vol && (cnt == 16 || cnt == 32))
             return csem::launch_dft_bulk(p, q, S, n0_off, cnt, kahan, c->d_bad, st);
     }
     return csem::launch_dft<R>(p, q, S, n0_off, cnt, vol, kahan, st);
 }
 
+// Steps 0 .. n-1 (relative to the device step counter) with a transform flush
+// after every M steps.  Without overlap each flush follows its block on st.
+// With overlap (flush_mode bit 1) the flush of block b runs on the side stream
+// while block b+1 steps, and st waits for it before the first step of block b+2,
+// the first step that rewrites one of its ring slots (nslot >= 2M + 1).  lead:
+// first flush the block that ended just before step 0 (skipped on the device
+// when that block would start before step 0); trail: flush the last block here
+// too, else it is left for the next call's lead.  Flushes run one after another
+// on one stream in block order either way, so the results do not depend on the
+// overlap.
+template <typename R>
+cudaError_t emit_steps(csem_ctx *c, int S, bool vol, bool kahan, const csem::StepParams<R> &p,
+                       const csem::PointParams<R> &q, int n, bool lead, bool trail, cudaStream_t st) {
+    const int M = c->M;
+    const bool overlap = (c->flush_mode & 2) != 0;
+    // side flushes in flight: event slot k % kMaxSide, due before step join_at[k];
+    // at most two are in flight, so a slot is joined before it is recorded again
+    int nev = 0, njoined = 0;
+    int join_at[kMaxSide];
+    auto join = [&](int j) -> cudaError_t {   // every side flush due before step j, oldest first
+        while (njoined < nev && join_at[njoined % kMaxSide] <= j) {
+            cudaError_t e = cudaStreamWaitEvent(st, c->ev_done[njoined % kMaxSide], 0);
+            if (e != cudaSuccess) return e;
+            ++njoined;
+        }
+        return cudaSuccess;
+    };
+    auto side_flush = [&](int n0_off) -> cudaError_t {
+        if (nev - njoined >= kMaxSide) return cudaErrorInvalidValue;
+        const int k = nev % kMaxSide;
+        cudaError_t e = cudaEventRecord(c->ev_fork[k], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->side, c->ev_fork[k], 0);
+        if (e == cudaSuccess) e = flush<R>(c, p, q, S, n0_off, M, vol, kahan, c->side);
+        if (e == cudaSuccess) e = cudaEventRecord(c->ev_done[k], c->side);
+        join_at[k] = n0_off + 2 * M;
+        ++nev;
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    if (lead) e = overlap ? side_flush(-M) : flush<R>(c, p, q, S, -M, M, vol, kahan, st);
+    for (int j = 0; j < n && e == cudaSuccess; ++j) {
+        if (overlap) e = join(j);
+        if (e == cudaSuccess) e = csem::launch_step<R>(p, q, S, j, st);
+        if (e != cudaSuccess || (j + 1) % M != 0 || (j + 1 == n && !trail)) continue;
+        e = overlap ? side_flush(j + 1 - M) : flush<R>(c, p, q, S, j + 1 - M, M, vol, kahan, st);
+    }
+    if (e == cudaSuccess && overlap) e = join(1 << 30);
+    return e;
+}
+
 // nt steps of H, E and injection; after every M steps the finished snapshots are
 // transformed (and the receivers sampled).  Full chunks of kChunk steps replay
 // one captured graph; the remainder and the final partial block are launched
-// directly.
+// directly.  With overlapped flushes a chunk's last block is flushed at the start
+// of the next chunk (or of the remainder).
 template <typename R>
 int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const csem::PointParams<R> &q,
               cudaStream_t st) {
     const bool kahan = vol && c->kahan;
     const int M = c->M;
-    auto emit = [&](int j, cudaStream_t s2) -> cudaError_t {
-        cudaError_t e = csem::launch_step<R>(p, q, S, j, s2);
-        if (e == cudaSuccess && (j + 1) % M == 0) e = flush<R>(c, p, q, S, j + 1 - M, M, vol, kahan, s2);
-        return e;
-    };
+    const bool overlap = (c->flush_mode & 2) != 0;
     const int full = c->nt / kChunk, rem = c->nt % kChunk;
     if (full > 0) {
         const int key[8] = {S, vol ? 1 : 0, kahan ? 1 : 0, q.n_itaps > 0 ? 1 : 0, q.n_rec > 0 ? 1 : 0,
                             (int)sizeof(R), ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
-                            (((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e) * 25 +
-                                c->TMA_h * 5 + c->TMA_e};
+                            ((((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e) * 25 +
+                             c->TMA_h * 5 + c->TMA_e) * 4 + c->LEAN_h * 2 + c->LEAN_e};
         cudaGraph_t g = nullptr;
         const long long before = csem::g_launches.load();   // captured kernels are counted per replay
         CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-        cudaError_t le = cudaSuccess;
-        for (int j = 0; j < kChunk && le == cudaSuccess; ++j) le = emit(j, c->cap);
+        cudaError_t le = emit_steps<R>(c, S, vol, kahan, p, q, kChunk, overlap, !overlap, c->cap);
         if (le == cudaSuccess) le = csem::launch_advance(c->d_step, kChunk, c->cap);
         cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
         if (le != cudaSuccess) return fail(CSEM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(le));
@@ -393,7 +489,13 @@ int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const 
             CK(cudaGraphLaunch(exec, st));
             csem::g_launches += per_chunk;
         }
+        if (overlap) CK(flush<R>(c, p, q, S, -M, M, vol, kahan, st));
     }
+    auto emit = [&](int j, cudaStream_t s2) -> cudaError_t {
+        cudaError_t e = csem::launch_step<R>(p, q, S, j, s2);
+        if (e == cudaSuccess && (j + 1) % M == 0) e = flush<R>(c, p, q, S, j + 1 - M, M, vol, kahan, s2);
+        return e;
+    };
     for (int j = 0; j < rem; ++j) CK(emit(j, st));
     const int tail = c->nt % M;     // M divides kChunk, so this is also rem % M
     if (tail) CK(flush<R>(c, p, q, S, rem - tail, tail, vol, kahan, st));
@@ -406,6 +508,17 @@ csem::GeoD geo(const csem_ctx *c) {
     g.pitch = c->pitch; g.plane = c->plane; g.vol = c->vol;
     g.hx = c->d_h; g.hy = c->d_h + c->nx; g.hz = c->d_h + c->nx + c->ny;
     return g;
+}
+
+// dt/eps on every E edge from the model (and, for the lean kernels, its copy with
+// the PEC edges zeroed).
+template <typename R>
+int coef_init(csem_ctx *c, const void *rho, cudaStream_t st) {
+    CK(csem::launch_coef_init<R>(geo(c), (const R *)rho, (R *)c->d_cE, 2.0 * c->w0 * c->dt, c->d_bad, st));
+    if constexpr (sizeof(R) == 4) {
+        if (c->d_cEm) CK(csem::launch_mask_coef(step_params<float>(c, false, nullptr), (const float *)c->d_cE, c->d_cEm, st));
+    }
+    return CSEM_OK;
 }
 
 // Sorts each source's injection taps by lattice column (then index) and sets the
@@ -448,7 +561,7 @@ int fwd_impl(csem_ctx *c, const void *rho, const csem_points *src, const csem_po
         TRY(point_taps(c, rec->x[r], rec->y[r], rec->z[r], rec->comp[r], false, r, &rtaps[(size_t)r * 8]));
     TRY(upload_injection(c, itaps, S, 8, false, st));
     if (NR > 0) CK(cudaMemcpyAsync(c->d_rtaps, rtaps.data(), (size_t)NR * 8 * sizeof(Tap), cudaMemcpyHostToDevice, st));
-    CK(csem::launch_coef_init<R>(geo(c), (const R *)rho, (R *)c->d_cE, 2.0 * c->w0 * c->dt, c->d_bad, st));
+    TRY(coef_init<R>(c, rho, st));
     TRY(reset_state<R>(c, S, st));
     const bool dft = (Evol != nullptr);
     const size_t vbytes = (size_t)S * 3 * c->nf * c->vol * sizeof(typename C2<R>::T);
@@ -486,7 +599,7 @@ int adj_impl(csem_ctx *c, const void *rho, const csem_points *rec, int S, const 
         TRY(point_taps(c, rec->x[r], rec->y[r], rec->z[r], rec->comp[r], true, r, &itaps[(size_t)r * 8]));
     TRY(upload_injection(c, itaps, 1, NR * 8, true, st));
     CK(csem::launch_adjoint_coef(resid, c->d_coef, S, NR, c->nf, c->d_alpha + 2 * c->nf, 1.0 / c->dt, st));
-    CK(csem::launch_coef_init<R>(geo(c), (const R *)rho, (R *)c->d_cE, 2.0 * c->w0 * c->dt, c->d_bad, st));
+    TRY(coef_init<R>(c, rho, st));
     TRY(reset_state<R>(c, S, st));
     const size_t vbytes = (size_t)S * 3 * c->nf * c->vol * sizeof(typename C2<R>::T);
     CK(cudaMemsetAsync(Vvol, 0, vbytes, st));
@@ -566,18 +679,22 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
         int best_kz = 4, best_mb = 4, best_vec = 0;
         const int maxty = (sizeof(R) == 4) ? csem::tma_max_rows(c->pitch) : 0;
         const int ntma = maxty >= 4 ? 12 : (maxty >= 2 ? 8 : (maxty >= 1 ? 4 : 0));
-        const int ncand = (sizeof(R) == 4) ? 20 + ntma : 12;   // 12 scalar, 8 four-cell, then staged shapes
-        int best_tma = 0;
+        const int nlean = (sizeof(R) == 4 && c->d_psiL) ? 12 : 0;
+        const int ncand = (sizeof(R) == 4) ? 20 + ntma + nlean : 12;   // 12 scalar, 8 four-cell, staged, lean
+        int best_tma = 0, best_lean = 0;
         for (int cand = 0; cand < ncand; ++cand) {
+            const int lc = cand - 20 - ntma;
+            const int lean = (lc >= 0) ? 1 + lc / 6 : 0;                                   // cells per thread 1, 2
             const int vec = (cand >= 12 && cand < 20) ? 1 : 0;
-            const int tma = cand >= 20 ? (1 << ((cand - 20) / 4)) : 0;          // rows per block 1, 2, 4
-            const int tkz[4] = {2, 4, 8, 16};
-            const int kz = tma ? tkz[(cand - 20) % 4] : kzs[cand % 4];
-            const int mb = tma ? 4 : (vec ? mbs[(cand - 12) / 4] : mbs[cand / 4]);
+            const int tma = (cand >= 20 && !lean) ? (1 << ((cand - 20) / 4)) : 0;          // rows per block 1, 2, 4
+            const int tkz[4] = {2, 4, 8, 16}, lkz[3] = {1, 2, 4};
+            const int kz = lean ? lkz[lc % 3] : (tma ? tkz[(cand - 20) % 4] : kzs[cand % 4]);
+            const int mb = lean ? ((lc % 6) < 3 ? 4 : 6) : (tma ? 4 : (vec ? mbs[(cand - 12) / 4] : mbs[cand / 4]));
             p.KZ_h = p.KZ_e = kz;
             p.MB_h = p.MB_e = mb;
             p.VEC_h = p.VEC_e = vec;
             p.TMA_h = p.TMA_e = tma;
+            p.LEAN_h = p.LEAN_e = lean;
             for (int j = 0; j < 3; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, which));
             CK(cudaEventRecord(e0, st));
             const int reps = 20;
@@ -586,16 +703,17 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
             CK(cudaEventSynchronize(e1));
             float t = 0.f;
             CK(cudaEventElapsedTime(&t, e0, e1));
-            if (t < best) { best = t; best_kz = kz; best_mb = mb; best_vec = vec; best_tma = tma; }
+            if (t < best) { best = t; best_kz = kz; best_mb = mb; best_vec = vec; best_tma = tma; best_lean = lean; }
         }
-        if (which == 1) { c->KZ_h = best_kz; c->MB_h = best_mb; c->VEC_h = best_vec; c->TMA_h = best_tma; }
-        else { c->KZ_e = best_kz; c->MB_e = best_mb; c->VEC_e = best_vec; c->TMA_e = best_tma; }
+        if (which == 1) { c->KZ_h = best_kz; c->MB_h = best_mb; c->VEC_h = best_vec; c->TMA_h = best_tma; c->LEAN_h = best_lean; }
+        else { c->KZ_e = best_kz; c->MB_e = best_mb; c->VEC_e = best_vec; c->TMA_e = best_tma; c->LEAN_e = best_lean; }
     }
     // fused H+E step (kz 4, 8, 16) against the best split pair
     {
         p.KZ_h = c->KZ_h; p.KZ_e = c->KZ_e; p.MB_h = c->MB_h; p.MB_e = c->MB_e;
         p.VEC_h = c->VEC_h; p.VEC_e = c->VEC_e;
         p.TMA_h = c->TMA_h; p.TMA_e = c->TMA_e;
+        p.LEAN_h = c->LEAN_h; p.LEAN_e = c->LEAN_e;
         double best = 1e30;
         int best_f = 0;
         for (int f : {0, 4, 8, 16}) {
@@ -613,8 +731,10 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
         c->fused_kz = best_f;
         p.fused_kz = 0;
     }
-    // transform flush: register (16) vs bulk copy (16, 32 when the ring has room), per step
-    if (sizeof(R) == 4 && c->nt >= 64) {
+    // transform flush: register or bulk copy (FP32), 16 or 32 snapshots, after
+    // its block or overlapping the next one (when the ring has room); each
+    // candidate is timed over 2 kChunk steps with its flushes, from step kChunk on
+    if (c->nt >= 4 * kChunk) {
         typedef typename C2<R>::T R2;
         R2 *vol_tmp = nullptr;
         const size_t vb = (size_t)S * 3 * c->nf * c->vol * sizeof(R2);
@@ -622,25 +742,30 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
             CK(cudaMemsetAsync(vol_tmp, 0, vb, st));
             p.acc = vol_tmp;
             p.comp = c->kahan ? (R2 *)c->d_comp : nullptr;
-            struct Cand { int mode, m; } cands[3] = {{0, 16}, {1, 16}, {1, 32}};
+            p.fused_kz = c->fused_kz;
+            const bool kahan = c->kahan != 0;
             double best = 1e30;
             int bm = 0, bM = 16;
-            for (const Cand &cd : cands) {
-                if (cd.m + 1 > c->nslot) continue;
-                c->flush_mode = cd.mode;
-                for (int j = 0; j < 2; ++j) CK(flush<R>(c, p, q, S, 0, cd.m, true, c->kahan != 0, st));
-                CK(cudaEventRecord(e0, st));
-                const int reps = 8;
-                for (int j = 0; j < reps; ++j) CK(flush<R>(c, p, q, S, 0, cd.m, true, c->kahan != 0, st));
-                CK(cudaEventRecord(e1, st));
-                CK(cudaEventSynchronize(e1));
-                float t = 0.f;
-                CK(cudaEventElapsedTime(&t, e0, e1));
-                const double per_step = (double)t / reps / cd.m;
-                if (per_step < best) { best = per_step; bm = cd.mode; bM = cd.m; }
-            }
+            for (int mode = 0; mode < 4; ++mode)
+                for (int m : {16, 32}) {
+                    if ((mode & 1) && sizeof(R) != 4) continue;
+                    if (((mode & 2) ? 2 * m : m) + 1 > c->nslot) continue;
+                    c->flush_mode = mode;
+                    c->M = m;
+                    CK(cudaMemsetAsync(c->d_step, 0, sizeof(int), st));
+                    CK(csem::launch_advance(c->d_step, kChunk, st));
+                    CK(emit_steps<R>(c, S, true, kahan, p, q, kChunk, false, true, st));
+                    CK(cudaEventRecord(e0, st));
+                    CK(emit_steps<R>(c, S, true, kahan, p, q, 2 * kChunk, false, true, st));
+                    CK(cudaEventRecord(e1, st));
+                    CK(cudaEventSynchronize(e1));
+                    float t = 0.f;
+                    CK(cudaEventElapsedTime(&t, e0, e1));
+                    if (t < best) { best = t; bm = mode; bM = m; }
+                }
             c->flush_mode = bm;
             c->M = bM;
+            CK(cudaMemsetAsync(c->d_step, 0, sizeof(int), st));
             cudaFreeAsync(vol_tmp, st);
         } else {
             cudaGetLastError();
@@ -655,11 +780,16 @@ void free_ctx(csem_ctx *c) {
     if (!c) return;
     cudaDeviceSynchronize();
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
-    void *ptrs[] = {c->d_tab, c->d_h, c->d_cE, c->d_H, c->d_H2, c->d_ering, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
+    void *ptrs[] = {c->d_tabL, c->d_psiL, c->d_cEm, c->d_tab, c->d_h, c->d_cE, c->d_H, c->d_H2, c->d_ering, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
                     c->d_alpha, c->d_racc, c->d_coef, c->d_T, c->d_ones, c->d_rtaps, c->d_itaps, c->d_colmap, c->d_cpos, c->d_cval, c->d_step, c->d_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->side) cudaStreamDestroy(c->side);
+    for (int k = 0; k < kMaxSide; ++k) {
+        if (c->ev_fork[k]) cudaEventDestroy(c->ev_fork[k]);
+        if (c->ev_done[k]) cudaEventDestroy(c->ev_done[k]);
+    }
     delete c;
 }
 
@@ -756,13 +886,17 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     c->wavelet.assign(c->nt, 0.0);
     c->wavelet[0] = 1.0 / c->dt;
 
-    // E ring: 33 slots (room for 32-snapshot flushes) when it leaves room, else 17
+    // E ring: 65 slots (32-snapshot flushes overlapping the next block), 33
+    // (32-snapshot flushes, or overlapped 16-snapshot ones) or 17, the largest
+    // that leaves room
     {
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
-        const double ring33 = (double)c->max_src * 33 * 3 * c->vol * c->rsize;
+        const double slot = (double)c->max_src * 3 * c->vol * c->rsize;
         const double vols = (double)c->max_src * 3 * c->nf * c->vol * 2 * c->rsize * (c->kahan ? 3 : 2);
-        c->nslot = (ring33 + vols < 0.6 * (double)free_b) ? 33 : 17;
+        c->nslot = 17;
+        for (int ns : {65, 33})
+            if (ns * slot + vols < 0.6 * (double)free_b) { c->nslot = ns; break; }
         c->M = 16;
     }
     int rc = CSEM_OK;
@@ -790,6 +924,19 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     step(dalloc(c, &c->d_cval, (size_t)std::max(S, NR) * 8 * sizeof(int2)));
     step(dalloc(c, &c->d_step, sizeof(int)));
     step(dalloc(c, &c->d_bad, sizeof(int)));
+    // lean FP32 kernels: CPML memory as 12 volume arrays per source and the masked dt/eps
+    if (rc == CSEM_OK && c->precision == 32 && c->nx % 4 == 0) {
+        size_t free_b = 0, total_b = 0;
+        cudaMemGetInfo(&free_b, &total_b);
+        const double need = ((double)S * 12 + 3) * c->vol * sizeof(float);
+        if (need < 0.25 * (double)free_b) {
+            step(dalloc(c, &c->d_psiL, (size_t)S * 12 * c->vol * sizeof(float)));
+            step(dalloc(c, &c->d_cEm, 3 * (size_t)c->vol * sizeof(float)));
+            step(upload_lean_tables(c));
+            if (rc == CSEM_OK && cudaMemset(c->d_cEm, 0, 3 * (size_t)c->vol * sizeof(float)) != cudaSuccess)
+                rc = fail(CSEM_ERR_CUDA, "context initialisation failed");
+        }
+    }
     if (rc != CSEM_OK) { free_ctx(c); return rc; }
     std::vector<double> hcat;
     for (int a = 0; a < 3; ++a) hcat.insert(hcat.end(), c->ax[a].h.begin(), c->ax[a].h.end());
@@ -798,10 +945,17 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
         cudaMemcpy(c->d_ones, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(c->d_bad, 0, sizeof(int)) != cudaSuccess ||
         cudaMemset(c->d_cE, 0, 3 * (size_t)c->vol * c->rsize) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
         free_ctx(c);
         return fail(CSEM_ERR_CUDA, "context initialisation failed");
     }
+    for (int k = 0; k < kMaxSide; ++k)
+        if (cudaEventCreateWithFlags(&c->ev_fork[k], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_done[k], cudaEventDisableTiming) != cudaSuccess) {
+            free_ctx(c);
+            return fail(CSEM_ERR_CUDA, "context initialisation failed");
+        }
     rc = update_wavelet(c);
     if (rc != CSEM_OK) { free_ctx(c); return rc; }
     {
@@ -897,7 +1051,14 @@ long long csem_launch_count(void) { return csem::g_launches.load(); }
 int csem_set_launch(csem_ctx *c, const int *cfg) {
     if (!c || !cfg) return fail(CSEM_ERR_INVALID_ARG, "NULL argument");
     const int kzh = cfg[0], mbh = cfg[1], kze = cfg[2], mbe = cfg[3], fkz = cfg[4], fm = cfg[5], M = cfg[6];
-    const int vh = cfg[7], ve = cfg[8], th = cfg[9], te = cfg[10];
+    const int vh = cfg[7], ve = cfg[8], th = cfg[9], te = cfg[10], lh = cfg[11], le = cfg[12];
+    if (lh || le) {
+        auto ok = [&](int l, int kz, int mb) {
+            return l == 0 || ((l == 1 || l == 2) && (kz == 1 || kz == 2 || kz == 4) && (mb == 4 || mb == 6));
+        };
+        if (!c->d_psiL || !ok(lh, kzh, mbh) || !ok(le, kze, mbe))
+            return fail(CSEM_ERR_INVALID_ARG, "lean kernels: FP32, nx a multiple of 4, 1 or 2 cells, 1/2/4 planes, 4 or 6 blocks/SM");
+    }
     if (th || te) {
         const int maxty = c->precision == 32 ? csem::tma_max_rows(c->pitch) : 0;
         auto ok = [&](int ty, int kz) { return ty == 0 || ((ty == 1 || ty == 2 || ty == 4) && ty <= maxty &&
@@ -911,13 +1072,15 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
     auto kz_ok = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16; };
     auto mb_ok = [](int v) { return v == 4 || v == 6 || v == 8; };
     if (!kz_ok(kzh) || !kz_ok(kze) || !mb_ok(mbh) || !mb_ok(mbe) || !(fkz == 0 || fkz == 4 || fkz == 8 || fkz == 16) ||
-        !(fm == 0 || (fm == 1 && c->precision == 32)) || !(M == 16 || M == 32) || M + 1 > c->nslot)
+        fm < 0 || fm > 3 || ((fm & 1) && c->precision != 32) || !(M == 16 || M == 32) ||
+        ((fm & 2) ? 2 * M : M) + 1 > c->nslot)
         return fail(CSEM_ERR_INVALID_ARG, "launch configuration not supported by this context");
     CK(cudaDeviceSynchronize());
     c->KZ_h = kzh; c->MB_h = mbh; c->KZ_e = kze; c->MB_e = mbe;
     c->fused_kz = fkz; c->flush_mode = fm; c->M = M;
     c->VEC_h = vh; c->VEC_e = ve;
     c->TMA_h = th; c->TMA_e = te;
+    c->LEAN_h = lh; c->LEAN_e = le;
     return CSEM_OK;
 }
 
@@ -926,8 +1089,8 @@ int csem_autotune(csem_ctx *c, int n_src, int *kz_out, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     TRY(c->precision == 32 ? autotune_impl<float>(c, n_src, st) : autotune_impl<double>(c, n_src, st));
     if (kz_out) {
-        kz_out[0] = (c->KZ_h * 16 + c->MB_h) + 256 * c->VEC_h + 1024 * c->TMA_h;
-        kz_out[1] = (c->KZ_e * 16 + c->MB_e) + 256 * c->VEC_e + 1024 * c->TMA_e;
+        kz_out[0] = (c->KZ_h * 16 + c->MB_h) + 256 * c->VEC_h + 1024 * c->TMA_h + 8192 * c->LEAN_h;
+        kz_out[1] = (c->KZ_e * 16 + c->MB_e) + 256 * c->VEC_e + 1024 * c->TMA_e + 8192 * c->LEAN_e;
         kz_out[2] = c->M * 4 + c->flush_mode;
         kz_out[3] = c->fused_kz;
     }

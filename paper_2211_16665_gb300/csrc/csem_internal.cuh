@@ -76,6 +76,10 @@ struct StepParams {
     int MB_h, MB_e;                // minimum resident blocks per SM the kernels are compiled for (4, 6, 8)
     int VEC_h, VEC_e;              // 1: FP32 kernels with four cells per thread along x
     int TMA_h, TMA_e;              // > 0: FP32 bulk-copy-staged kernels over this many rows per block
+    int LEAN_h, LEAN_e;            // > 0: lean FP32 kernels with this many cells per thread (1 or 2)
+    AxisTab<R> lx, ly, lz;         // the stepping tables padded to 16-byte groups (lean kernels)
+    R *psiL;                       // [S][12][vol] CPML memory in the field layout (lean kernels)
+    const R *cEm;                  // [3][vol] dt/eps, zero on the PEC edges (lean kernels)
     int *err;                      // device status word (bit 1: a bounded wait gave up)
     int nf;
     const typename C2<R>::T *w;    // [nt][nf] exp((-1+i) a_k n dt)
@@ -137,6 +141,11 @@ template <typename R>
 cudaError_t launch_fused(const StepParams<R> &p, int S, int jstep, int kz, cudaStream_t st);
 cudaError_t prepare_fused_all();
 // FP32 H / E kernels with four cells per thread (kern_vec.cu), kz in {1,2,4,8}, mb in {4,6}
+// lean FP32 H / E kernels (kern_lean.cu), nx % 4 == 0, w (cells per thread) in {1,2}, kz in {1,2,4}, mb in {4,6}
+cudaError_t launch_field_lean(const StepParams<float> &p, int S, int jstep, cudaStream_t st, bool h, int w, int kz,
+                              int mb);
+// cEm = cE with the PEC edges zeroed
+cudaError_t launch_mask_coef(const StepParams<float> &p, const float *cE, float *cEm, cudaStream_t st);
 cudaError_t launch_field_vec(const StepParams<float> &p, int S, int jstep, cudaStream_t st, bool h, int kz, int mb);
 // FP32 bulk-copy-staged H / E kernels (kern_tma.cu): ty rows per block in {1,2,4}, kz planes per chunk
 cudaError_t launch_field_tma(const StepParams<float> &p, int S, int jstep, cudaStream_t st, bool h, int kz, int ty,

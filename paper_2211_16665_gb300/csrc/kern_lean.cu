@@ -1,0 +1,351 @@
+// Lean FP32 H and E step kernels (Sec. 2, Eq. 4 with the unsplit CPML): W
+// consecutive cells (W = 1 or 2; i a multiple of W) of one (j, k) row per
+// thread, the cell range [0,nx) x [0,ny) x [0,nz) (nx a multiple of 4), KZ
+// planes along z per thread.  They compute what the scalar kernels compute,
+// entry by entry, but keep each thread's memory operations independent of one
+// another so that all of a plane's loads are in flight together:
+//  * the CPML memory lives in volume arrays with the field layout (12 per
+//    source: 0-5 for H, 6-11 for E), so a slab entry is read and written with the
+//    same access as the field it corrects, issued with the field loads;
+//  * the coefficient tables are padded to whole 16-byte groups and the CPML
+//    coefficients are zero off the slabs and on the outer nodes, so a thread that
+//    touches a slab runs the recursion on all its cells without per-cell tests
+//    (psi stays zero where b = a = 0);
+//  * E is advanced with dt/eps set to zero on the PEC edges (tangential E on the
+//    outer faces), so all three components are written unconditionally and the
+//    PEC edges keep their zero;
+//  * the source taps of the thread's columns are read with its other loads and
+//    added to the new values in registers before the store.
+// W stays small so that a plane's loaded values fit the register budget.
+// The block is 32 x 8 threads (32 W cells of 8 rows); blockIdx.z runs over the
+// z blocks of every source.
+#include "csem_internal.cuh"
+
+namespace csem {
+
+namespace {
+
+constexpr int kLeanX = 32, kLeanRows = 8;
+
+template <int W> struct Vec { float v[W]; };
+template <int W> __device__ __forceinline__ Vec<W> ldc(const float *p) {
+    Vec<W> r;
+    if constexpr (W == 1) r.v[0] = __ldg(p);
+    else { const float2 t = __ldg(reinterpret_cast<const float2 *>(p)); r.v[0] = t.x; r.v[1] = t.y; }
+    return r;
+}
+template <int W> __device__ __forceinline__ Vec<W> ldw(const float *p) {
+    Vec<W> r;
+    if constexpr (W == 1) r.v[0] = *p;
+    else { const float2 t = *reinterpret_cast<const float2 *>(p); r.v[0] = t.x; r.v[1] = t.y; }
+    return r;
+}
+template <int W> __device__ __forceinline__ void stv(float *p, const Vec<W> &a) {
+    if constexpr (W == 1) *p = a.v[0];
+    else *reinterpret_cast<float2 *>(p) = make_float2(a.v[0], a.v[1]);
+}
+template <int W> __device__ __forceinline__ Vec<W> zv() {
+    Vec<W> r;
+#pragma unroll
+    for (int e = 0; e < W; ++e) r.v[e] = 0.f;
+    return r;
+}
+// (a - b) * s
+template <int W> __device__ __forceinline__ Vec<W> dsc(const Vec<W> &a, const Vec<W> &b, float s) {
+    Vec<W> r;
+#pragma unroll
+    for (int e = 0; e < W; ++e) r.v[e] = (a.v[e] - b.v[e]) * s;
+    return r;
+}
+template <int W> __device__ __forceinline__ Vec<W> dsc(const Vec<W> &a, const Vec<W> &b, const Vec<W> &s) {
+    Vec<W> r;
+#pragma unroll
+    for (int e = 0; e < W; ++e) r.v[e] = (a.v[e] - b.v[e]) * s.v[e];
+    return r;
+}
+// CPML recursion psi <- b psi + a d, then d += psi (shared or per-cell b, a)
+template <int W> __device__ __forceinline__ void cpml(Vec<W> &ps, Vec<W> &d, float b, float a) {
+#pragma unroll
+    for (int e = 0; e < W; ++e) { ps.v[e] = b * ps.v[e] + a * d.v[e]; d.v[e] += ps.v[e]; }
+}
+template <int W> __device__ __forceinline__ void cpml(Vec<W> &ps, Vec<W> &d, const Vec<W> &b, const Vec<W> &a) {
+#pragma unroll
+    for (int e = 0; e < W; ++e) { ps.v[e] = b.v[e] * ps.v[e] + a.v[e] * d.v[e]; d.v[e] += ps.v[e]; }
+}
+// h -= c (u - v)
+template <int W> __device__ __forceinline__ void hsub(Vec<W> &h, float c, const Vec<W> &u, const Vec<W> &v) {
+#pragma unroll
+    for (int e = 0; e < W; ++e) h.v[e] -= c * (u.v[e] - v.v[e]);
+}
+// eo + c (u - v)
+template <int W>
+__device__ __forceinline__ Vec<W> eadv(const Vec<W> &eo, const Vec<W> &c, const Vec<W> &u, const Vec<W> &v) {
+    Vec<W> r;
+#pragma unroll
+    for (int e = 0; e < W; ++e) r.v[e] = eo.v[e] + c.v[e] * (u.v[e] - v.v[e]);
+    return r;
+}
+// the W cells shifted by one: (prev, a0, .., a_{W-2}) and (a1, .., a_{W-1}, next)
+template <int W> __device__ __forceinline__ Vec<W> down(float prev, const Vec<W> &a) {
+    Vec<W> r;
+    r.v[0] = prev;
+#pragma unroll
+    for (int e = 1; e < W; ++e) r.v[e] = a.v[e - 1];
+    return r;
+}
+template <int W> __device__ __forceinline__ Vec<W> up(const Vec<W> &a, float next) {
+    Vec<W> r;
+#pragma unroll
+    for (int e = 0; e + 1 < W; ++e) r.v[e] = a.v[e + 1];
+    r.v[W - 1] = next;
+    return r;
+}
+
+// Source term E^{n+1} -= dt/eps J'^{n+1/2} for the taps in plane k of the
+// thread's column col (one cell; returns the three increments).
+__device__ __noinline__ float3 lean_taps(const StepParams<float> &p, int s, int n, int k, int col, int2 cm) {
+    const int plane = (int)p.plane, vol = (int)p.vol;
+    float3 r = make_float3(0.f, 0.f, 0.f);
+    for (int u = cm.x; u < cm.x + cm.y; ++u) {
+        const Tap tp = p.itaps[(long long)s * p.itap_stride + u];
+        if ((int)(tp.idx / plane) != k || (int)(tp.idx % plane) != col) continue;
+        const double *cf = p.coef + ((long long)s * p.n_emit + tp.emit) * p.J;
+        const double *T = p.T + (long long)n * p.J;
+        double amp = 0.0;
+        for (int jj = 0; jj < p.J; ++jj) amp += cf[jj] * T[jj];
+        const int o = tp.comp * vol + (int)tp.idx;
+        const double add = -(double)p.cE[o] * tp.w * amp;   // dt/eps at the tap's edge
+        if (add == 0.0) continue;
+        if (tp.comp == 0) r.x += (float)add;
+        else if (tp.comp == 1) r.y += (float)add;
+        else r.z += (float)add;
+    }
+    return r;
+}
+
+}  // namespace
+
+template <int W, int KZ, int MINB>
+__global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_h_lean(const StepParams<float> p, const int jstep) {
+    const int i = (blockIdx.x * kLeanX + threadIdx.x) * W;
+    const int j = blockIdx.y * kLeanRows + threadIdx.y;
+    const int nkb = (p.nz + KZ - 1) / KZ;
+    const int s = blockIdx.z / nkb;
+    const int k0 = (blockIdx.z - s * nkb) * KZ;
+    if (i >= p.nx || j >= p.ny) return;
+    const int k1 = min(k0 + KZ, p.nz);
+    const int n = *p.step + jstep;
+    const int vol = (int)p.vol, plane = (int)p.plane, pitch = p.pitch, npml = p.npml;
+    const float *__restrict__ E = p.ering + (long long)s * p.ering_stride + (long long)(n % p.nslot) * 3 * p.vol;
+    float *__restrict__ H = p.H + (long long)s * 3 * vol;
+    float *__restrict__ ps = p.psiL + (long long)s * 12 * vol;
+
+    const Vec<W> ihx = ldc<W>(p.lx.ih_h + i);
+    const bool xs = (i < npml) || (i + W > p.nx - npml);
+    Vec<W> bx = zv<W>(), ax = zv<W>();
+    if (xs) { bx = ldc<W>(p.lx.b_h + i); ax = ldc<W>(p.lx.a_h + i); }
+    const float ihy = __ldg(p.ly.ih_h + j);
+    const bool ys = (j < npml) || (j >= p.ny - npml);
+    float by = 0.f, ay = 0.f;
+    if (ys) { by = __ldg(p.ly.b_h + j); ay = __ldg(p.ly.a_h + j); }
+    const float cH = p.cH;
+
+    int idx = k0 * plane + j * pitch + i;
+    Vec<W> exc = ldc<W>(E + idx), eyc = ldc<W>(E + vol + idx);
+#pragma unroll
+    for (int kk = 0; kk < KZ; ++kk, idx += plane) {
+        const int k = k0 + kk;
+        if (k >= k1) break;
+        const Vec<W> ezc = ldc<W>(E + 2 * vol + idx);
+        const Vec<W> exk = ldc<W>(E + idx + plane), eyk = ldc<W>(E + vol + idx + plane);
+        const Vec<W> exj = ldc<W>(E + idx + pitch), ezj = ldc<W>(E + 2 * vol + idx + pitch);
+        const float eyn = __ldg(E + vol + idx + W), ezn = __ldg(E + 2 * vol + idx + W);
+        const float ihz = __ldg(p.lz.ih_h + k);
+        const bool zs = (k < npml) || (k >= p.nz - npml);
+        float bz = 0.f, az = 0.f;
+        if (zs) { bz = __ldg(p.lz.b_h + k); az = __ldg(p.lz.a_h + k); }
+        Vec<W> hx = ldw<W>(H + idx), hy = ldw<W>(H + vol + idx), hz = ldw<W>(H + 2 * vol + idx);
+        Vec<W> q0 = zv<W>(), q1 = zv<W>(), q2 = zv<W>(), q3 = zv<W>(), q4 = zv<W>(), q5 = zv<W>();
+        if (ys) { q0 = ldw<W>(ps + idx); q5 = ldw<W>(ps + 5 * vol + idx); }
+        if (zs) { q1 = ldw<W>(ps + vol + idx); q2 = ldw<W>(ps + 2 * vol + idx); }
+        if (xs) { q3 = ldw<W>(ps + 3 * vol + idx); q4 = ldw<W>(ps + 4 * vol + idx); }
+        const Vec<W> ezx = up<W>(ezc, ezn), eyx = up<W>(eyc, eyn);   // Ez, Ey at i+1 .. i+W
+
+        // Hx at (i, j+1/2, k+1/2)
+        Vec<W> dEz_dy = dsc<W>(ezj, ezc, ihy), dEy_dz = dsc<W>(eyk, eyc, ihz);
+        if (ys) { cpml<W>(q0, dEz_dy, by, ay); stv<W>(ps + idx, q0); }
+        if (zs) { cpml<W>(q1, dEy_dz, bz, az); stv<W>(ps + vol + idx, q1); }
+        hsub<W>(hx, cH, dEz_dy, dEy_dz);
+        // Hy at (i+1/2, j, k+1/2)
+        Vec<W> dEx_dz = dsc<W>(exk, exc, ihz), dEz_dx = dsc<W>(ezx, ezc, ihx);
+        if (zs) { cpml<W>(q2, dEx_dz, bz, az); stv<W>(ps + 2 * vol + idx, q2); }
+        if (xs) { cpml<W>(q3, dEz_dx, bx, ax); stv<W>(ps + 3 * vol + idx, q3); }
+        hsub<W>(hy, cH, dEx_dz, dEz_dx);
+        // Hz at (i+1/2, j+1/2, k)
+        Vec<W> dEy_dx = dsc<W>(eyx, eyc, ihx), dEx_dy = dsc<W>(exj, exc, ihy);
+        if (xs) { cpml<W>(q4, dEy_dx, bx, ax); stv<W>(ps + 4 * vol + idx, q4); }
+        if (ys) { cpml<W>(q5, dEx_dy, by, ay); stv<W>(ps + 5 * vol + idx, q5); }
+        hsub<W>(hz, cH, dEy_dx, dEx_dy);
+
+        stv<W>(H + idx, hx);
+        stv<W>(H + vol + idx, hy);
+        stv<W>(H + 2 * vol + idx, hz);
+        exc = exk;
+        eyc = eyk;
+    }
+}
+
+template <int W, int KZ, int MINB>
+__global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_e_lean(const StepParams<float> p, const int jstep) {
+    const int i = (blockIdx.x * kLeanX + threadIdx.x) * W;
+    const int j = blockIdx.y * kLeanRows + threadIdx.y;
+    const int nkb = (p.nz + KZ - 1) / KZ;
+    const int s = blockIdx.z / nkb;
+    const int k0 = (blockIdx.z - s * nkb) * KZ;
+    if (i >= p.nx || j >= p.ny) return;
+    const int k1 = min(k0 + KZ, p.nz);
+    const int n = *p.step + jstep;
+    const int vol = (int)p.vol, plane = (int)p.plane, pitch = p.pitch, npml = p.npml;
+    const float *__restrict__ ring = p.ering + (long long)s * p.ering_stride;
+    const float *__restrict__ Eo = ring + (long long)(n % p.nslot) * 3 * p.vol;
+    float *__restrict__ En = const_cast<float *>(ring) + (long long)((n + 1) % p.nslot) * 3 * p.vol;
+    const float *__restrict__ H = p.H + (long long)s * 3 * vol;
+    const float *__restrict__ cE = p.cEm;
+    float *__restrict__ ps = p.psiL + (long long)s * 12 * vol + 6LL * vol;
+
+    const Vec<W> ihx = ldc<W>(p.lx.ih_n + i);
+    const bool xs = (i < npml) || (i + W - 1 > p.nx - npml);
+    Vec<W> bx = zv<W>(), ax = zv<W>();
+    if (xs) { bx = ldc<W>(p.lx.b_n + i); ax = ldc<W>(p.lx.a_n + i); }
+    const float ihy = __ldg(p.ly.ih_n + j);
+    const bool ys = (j < npml) || (j > p.ny - npml);
+    float by = 0.f, ay = 0.f;
+    if (ys) { by = __ldg(p.ly.b_n + j); ay = __ldg(p.ly.a_n + j); }
+    int2 cm[W];
+#pragma unroll
+    for (int e = 0; e < W; ++e) cm[e] = make_int2(0, 0);
+    if (p.colmap) {
+        const int2 *c2 = p.colmap + (long long)s * p.colmap_stride + j * pitch + i;
+#pragma unroll
+        for (int e = 0; e < W; ++e) cm[e] = __ldg(c2 + e);
+    }
+    bool taps = false;
+#pragma unroll
+    for (int e = 0; e < W; ++e) taps |= (cm[e].y != 0);
+
+    int idx = k0 * plane + j * pitch + i;
+    Vec<W> hxm = (k0 > 0) ? ldc<W>(H + idx - plane) : zv<W>();
+    Vec<W> hym = (k0 > 0) ? ldc<W>(H + vol + idx - plane) : zv<W>();
+#pragma unroll
+    for (int kk = 0; kk < KZ; ++kk, idx += plane) {
+        const int k = k0 + kk;
+        if (k >= k1) break;
+        const Vec<W> hxc = ldc<W>(H + idx), hyc = ldc<W>(H + vol + idx), hzc = ldc<W>(H + 2 * vol + idx);
+        const Vec<W> hxj = (j > 0) ? ldc<W>(H + idx - pitch) : zv<W>();
+        const Vec<W> hzj = (j > 0) ? ldc<W>(H + 2 * vol + idx - pitch) : zv<W>();
+        const float hyp = (i > 0) ? __ldg(H + vol + idx - 1) : 0.f;
+        const float hzp = (i > 0) ? __ldg(H + 2 * vol + idx - 1) : 0.f;
+        const Vec<W> eo0 = ldc<W>(Eo + idx), eo1 = ldc<W>(Eo + vol + idx), eo2 = ldc<W>(Eo + 2 * vol + idx);
+        const Vec<W> c0 = ldc<W>(cE + idx), c1 = ldc<W>(cE + vol + idx), c2 = ldc<W>(cE + 2 * vol + idx);
+        const float ihz = __ldg(p.lz.ih_n + k);
+        const bool zs = (k < npml) || (k > p.nz - npml);
+        float bz = 0.f, az = 0.f;
+        if (zs) { bz = __ldg(p.lz.b_n + k); az = __ldg(p.lz.a_n + k); }
+        Vec<W> q0 = zv<W>(), q1 = zv<W>(), q2 = zv<W>(), q3 = zv<W>(), q4 = zv<W>(), q5 = zv<W>();
+        if (ys) { q0 = ldw<W>(ps + idx); q5 = ldw<W>(ps + 5 * vol + idx); }
+        if (zs) { q1 = ldw<W>(ps + vol + idx); q2 = ldw<W>(ps + 2 * vol + idx); }
+        if (xs) { q3 = ldw<W>(ps + 3 * vol + idx); q4 = ldw<W>(ps + 4 * vol + idx); }
+        const Vec<W> hzx = down<W>(hzp, hzc), hyx = down<W>(hyp, hyc);   // Hz, Hy at i-1 .. i+W-2
+
+        // Ex at (i+1/2, j, k)
+        Vec<W> dHz_dy = dsc<W>(hzc, hzj, ihy), dHy_dz = dsc<W>(hyc, hym, ihz);
+        if (ys) { cpml<W>(q0, dHz_dy, by, ay); stv<W>(ps + idx, q0); }
+        if (zs) { cpml<W>(q1, dHy_dz, bz, az); stv<W>(ps + vol + idx, q1); }
+        Vec<W> e0 = eadv<W>(eo0, c0, dHz_dy, dHy_dz);
+        // Ey at (i, j+1/2, k)
+        Vec<W> dHx_dz = dsc<W>(hxc, hxm, ihz), dHz_dx = dsc<W>(hzc, hzx, ihx);
+        if (zs) { cpml<W>(q2, dHx_dz, bz, az); stv<W>(ps + 2 * vol + idx, q2); }
+        if (xs) { cpml<W>(q3, dHz_dx, bx, ax); stv<W>(ps + 3 * vol + idx, q3); }
+        Vec<W> e1 = eadv<W>(eo1, c1, dHx_dz, dHz_dx);
+        // Ez at (i, j, k+1/2)
+        Vec<W> dHy_dx = dsc<W>(hyc, hyx, ihx), dHx_dy = dsc<W>(hxc, hxj, ihy);
+        if (xs) { cpml<W>(q4, dHy_dx, bx, ax); stv<W>(ps + 4 * vol + idx, q4); }
+        if (ys) { cpml<W>(q5, dHx_dy, by, ay); stv<W>(ps + 5 * vol + idx, q5); }
+        Vec<W> e2 = eadv<W>(eo2, c2, dHy_dx, dHx_dy);
+
+        if (taps) {
+#pragma unroll
+            for (int e = 0; e < W; ++e) {
+                if (cm[e].y == 0) continue;
+                const float3 a = lean_taps(p, s, n, k, j * pitch + i + e, cm[e]);
+                e0.v[e] += a.x; e1.v[e] += a.y; e2.v[e] += a.z;
+            }
+        }
+        stv<W>(En + idx, e0);
+        stv<W>(En + vol + idx, e1);
+        stv<W>(En + 2 * vol + idx, e2);
+        hxm = hxc;
+        hym = hyc;
+    }
+}
+
+// dt/eps with the PEC edges zeroed: Ex needs 1 <= j < ny, 1 <= k < nz, i < nx;
+// Ey 1 <= i < nx, 1 <= k < nz, j < ny; Ez 1 <= i < nx, 1 <= j < ny, k < nz.
+__global__ void k_mask_coef(const StepParams<float> p, const float *__restrict__ cE, float *__restrict__ cEm) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 3 * p.vol) return;
+    const int c = (int)(t / p.vol);
+    const int idx = (int)(t - (long long)c * p.vol);
+    const int k = idx / (int)p.plane;
+    const int r = idx - k * (int)p.plane;
+    const int j = r / p.pitch;
+    const int i = r - j * p.pitch;
+    const bool xi = (i >= 1 && i < p.nx), yi = (j >= 1 && j < p.ny), zi = (k >= 1 && k < p.nz);
+    bool ok;
+    if (c == 0) ok = (i < p.nx) && yi && zi;
+    else if (c == 1) ok = xi && (j < p.ny) && zi;
+    else ok = xi && yi && (k < p.nz);
+    cEm[t] = ok ? cE[t] : 0.f;
+}
+
+namespace {
+template <int W, int KZ, int MB>
+void lean_go(const StepParams<float> &p, int S, int jstep, cudaStream_t st, bool h) {
+    const dim3 block(kLeanX, kLeanRows);
+    const int nv = p.nx / W;
+    const dim3 grid((nv + kLeanX - 1) / kLeanX, (p.ny + kLeanRows - 1) / kLeanRows, ((p.nz + KZ - 1) / KZ) * S);
+    if (h) k_h_lean<W, KZ, MB><<<grid, block, 0, st>>>(p, jstep);
+    else k_e_lean<W, KZ, MB><<<grid, block, 0, st>>>(p, jstep);
+}
+template <int W, int MB>
+bool lean_kz(const StepParams<float> &p, int S, int jstep, cudaStream_t st, bool h, int kz) {
+    switch (kz) {
+        case 1: lean_go<W, 1, MB>(p, S, jstep, st, h); return true;
+        case 2: lean_go<W, 2, MB>(p, S, jstep, st, h); return true;
+        case 4: lean_go<W, 4, MB>(p, S, jstep, st, h); return true;
+        default: return false;
+    }
+}
+}  // namespace
+
+cudaError_t launch_field_lean(const StepParams<float> &p, int S, int jstep, cudaStream_t st, bool h, int w, int kz,
+                              int mb) {
+    if (p.nx % 4 != 0 || !p.psiL || !p.cEm || !p.lx.ih_n) return cudaErrorInvalidValue;
+    bool ok = false;
+    if (w == 1 && mb == 4) ok = lean_kz<1, 4>(p, S, jstep, st, h, kz);
+    else if (w == 1 && mb == 6) ok = lean_kz<1, 6>(p, S, jstep, st, h, kz);
+    else if (w == 2 && mb == 4) ok = lean_kz<2, 4>(p, S, jstep, st, h, kz);
+    else if (w == 2 && mb == 6) ok = lean_kz<2, 6>(p, S, jstep, st, h, kz);
+    if (!ok) return cudaErrorInvalidValue;
+    g_launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mask_coef(const StepParams<float> &p, const float *cE, float *cEm, cudaStream_t st) {
+    const long long n = 3 * p.vol;
+    k_mask_coef<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, cE, cEm);
+    g_launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace csem

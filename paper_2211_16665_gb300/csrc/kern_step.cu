@@ -2,8 +2,9 @@
 // on a stretched Yee grid with unsplit CPML, and the on-the-fly damped
 // transform of Eq. 6 into every frequency.
 //
-// E lives in a ring of nslot = M + 1 snapshots per source (E^n in slot n mod
-// nslot); H and the CPML memory are updated in place.  Per step:
+// E lives in a ring of nslot >= M + 1 snapshots per source (E^n in slot n mod
+// nslot; 2M + 1 when a block's transform overlaps the next block's steps); H and
+// the CPML memory are updated in place.  Per step:
 //   k_h       H^{n-1/2} -> H^{n+1/2} from E^n (slot n);
 //   k_e       E^{n+1} (slot n+1) = E^n + dt/eps (curl H^{n+1/2} - J'^{n+1/2}),
 //             the source term added by the thread that owns the tap's column.
@@ -265,6 +266,7 @@ __global__ void __launch_bounds__(kBlock) k_dft(const StepParams<R> p, const Poi
     typedef typename C2<R>::T R2;
     __shared__ R2 wsh[kMaxBlockSteps * kMaxFreq];
     const int n0 = *p.step + n0_off;
+    if (n0 < 0) return;               // a deferred flush before the first block: nothing to transform
     const int cnt = cnt_rt;
     const int nrec_blocks = q.n_rec > 0 ? S : 0;
     const int blk = blockIdx.x;
@@ -421,6 +423,7 @@ __global__ void __launch_bounds__(kBlock, 6) k_dft_bulk(const StepParams<float> 
     float2 *cmp_s = acc_s + p.nf * kBlock;                                  // [nf][256] (Kahan)
     float2 *w_s = cmp_s + (KAHAN ? p.nf * kBlock : 0);                      // [MS][nf]
     const int n0 = *p.step + n0_off;
+    if (n0 < 0) return;               // a deferred flush before the first block: nothing to transform
     const int nrec_blocks = q.n_rec > 0 ? S : 0;
     const int blk = blockIdx.x;
     if (blk < nrec_blocks) {          // receivers: same as the register flush
@@ -572,6 +575,7 @@ template <typename R>
 cudaError_t launch_field(const StepParams<R> &p, int S, int jstep, cudaStream_t st, bool h, int kz, int mb) {
     if constexpr (sizeof(R) == 4) {
         const int ty = h ? p.TMA_h : p.TMA_e;
+        if (h ? p.LEAN_h : p.LEAN_e) return launch_field_lean(p, S, jstep, st, h, h ? p.LEAN_h : p.LEAN_e, kz, mb);
         if (ty > 0) return launch_field_tma(p, S, jstep, st, h, kz, ty, p.err);
         if (h ? p.VEC_h : p.VEC_e) return launch_field_vec(p, S, jstep, st, h, kz, mb);
     }

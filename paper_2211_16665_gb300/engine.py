@@ -136,10 +136,12 @@ class Engine:
         _capi.check(self.ctx, _stream())
 
     def set_launch(self, kz_h=4, mb_h=4, kz_e=4, mb_e=4, fused_kz=0, flush_mode=0, block=16, vec_h=0, vec_e=0,
-                   tma_h=0, tma_e=0):
+                   tma_h=0, tma_e=0, lean_h=0, lean_e=0):
         """Pins a launch configuration (see csem_set_launch); launch_config() then reports it."""
-        _capi.set_launch(self.ctx, kz_h, mb_h, kz_e, mb_e, fused_kz, flush_mode, block, vec_h, vec_e, tma_h, tma_e)
-        self.kz = (kz_h * 16 + mb_h + 256 * vec_h + 1024 * tma_h, kz_e * 16 + mb_e + 256 * vec_e + 1024 * tma_e,
+        _capi.set_launch(self.ctx, kz_h, mb_h, kz_e, mb_e, fused_kz, flush_mode, block, vec_h, vec_e, tma_h, tma_e,
+                         lean_h, lean_e)
+        self.kz = (kz_h * 16 + mb_h + 256 * vec_h + 1024 * tma_h + 8192 * lean_h,
+                   kz_e * 16 + mb_e + 256 * vec_e + 1024 * tma_e + 8192 * lean_e,
                    block * 4 + flush_mode, fused_kz)
 
     def flush_block(self) -> int:
@@ -151,12 +153,16 @@ class Engine:
             return {}
         h, e, f, fz = self.kz
         def one(code):
+            if code >= 8192:
+                return {"kernel": "lean", "cells_per_thread": code // 8192, "z_planes": (code % 256) // 16,
+                        "blocks_per_sm": code % 16}
             if code >= 1024:
                 return {"kernel": "bulk-copy staged", "rows_per_block": code // 1024, "z_planes": (code % 1024) // 16}
             return {"kernel": "four cells per thread" if code >= 256 else "one cell per thread",
                     "z_planes": (code % 256) // 16, "blocks_per_sm": code % 16}
         step = ({"kernel": "fused H+E", "z_planes": fz} if fz else {"kernel": "split", "h": one(h), "e": one(e)})
-        return {"step": step, "flush": {"snapshots": f // 4, "kernel": "bulk-copy" if f % 4 == 1 else "register"}}
+        return {"step": step, "flush": {"snapshots": f // 4, "kernel": "bulk-copy" if f % 2 == 1 else "register",
+                                        "overlapped": f % 4 >= 2}}
 
 
 def misfit(d_obs: torch.Tensor, d_syn: torch.Tensor, weight: Optional[torch.Tensor] = None):

@@ -219,26 +219,32 @@ def heterogeneous_crop96() -> Workload:
 
 
 def small_box(n_core=24, h=100.0, npml=8, rho_bg=1.0, layered_model=True, n_freq=2,
-              nt=None, n_rec=6, ratio=1.0, n_st=0) -> Workload:
-    """Small seeded test problem spanning a few CUDA tiles with a ragged tail."""
+              nt=None, n_rec=6, ratio=1.0, n_st=0, n_core_y=None, n_core_z=None) -> Workload:
+    """Small seeded test problem spanning a few CUDA tiles with a ragged tail
+    (a cube unless n_core_y / n_core_z give other core sizes along y / z)."""
+    ncy = n_core if n_core_y is None else n_core_y
+    ncz = n_core if n_core_z is None else n_core_z
     xn = stretched_axis(h, n_core, n_st, n_st, npml, ratio, -h * n_core / 2)
-    zn = stretched_axis(h, n_core, n_st, n_st, npml, ratio, 0.0)
+    yn = stretched_axis(h, ncy, n_st, n_st, npml, ratio, -h * ncy / 2)
+    zn = stretched_axis(h, ncz, n_st, n_st, npml, ratio, 0.0)
     if layered_model:
-        seabed = h * (n_core // 3)
-        rho = layered(xn, xn, zn, 0.3, seabed, rho_bg)
-        rho_true = add_slab(rho, xn, xn, zn, half_x=h * n_core / 5, half_y=h * n_core / 5,
+        seabed = h * (ncz // 3)
+        rho = layered(xn, yn, zn, 0.3, seabed, rho_bg)
+        rho_true = add_slab(rho, xn, yn, zn, half_x=h * n_core / 5, half_y=h * ncy / 5,
                             top=seabed + 3 * h, bottom=seabed + 4 * h, value=20.0)
         zs = seabed - 0.5 * h
         zr = seabed
     else:
-        rho = np.full((zn.size - 1, xn.size - 1, xn.size - 1), rho_bg)
+        rho = np.full((zn.size - 1, yn.size - 1, xn.size - 1), rho_bg)
         rho_true = rho * 1.5
-        zs = zr = h * n_core / 2
+        zs = zr = h * ncz / 2
     src = Points.make([[0.3 * h, 0.0, zs]], 0)
     xr = np.linspace(-h * n_core / 3, h * n_core / 3, n_rec)
     rec = Points.make([[x, 0.2 * h, zr] for x in xr], 0)
     freqs = np.array([0.25, 0.75, 1.0, 0.5][:n_freq])
-    return Workload(f"small_box_{xn.size-1}c", xn, xn.copy(), zn, npml, rho, rho_true, src, rec, freqs,
+    name = f"small_box_{xn.size-1}c" if (ncy, ncz) == (n_core, n_core) else \
+        f"small_box_{xn.size-1}x{yn.size-1}x{zn.size-1}"
+    return Workload(name, xn, yn, zn, npml, rho, rho_true, src, rec, freqs,
                     rho_max=float(max(rho.max(), rho_true.max())), nt=nt, precision=32, kahan=1)
 
 

@@ -109,7 +109,77 @@ LAUNCH_VARIANTS = [
     dict(fused_kz=4, flush_mode=1, block=32),
     dict(fused_kz=8, flush_mode=0, block=16),
     dict(fused_kz=16, flush_mode=1, block=16),
+    dict(kz_h=1, mb_h=4, kz_e=4, mb_e=6, vec_h=1, flush_mode=3, block=32),
+    dict(kz_h=2, mb_h=6, kz_e=2, mb_e=4, vec_e=1, flush_mode=3, block=16),
+    dict(kz_h=4, mb_h=4, kz_e=4, mb_e=4, flush_mode=2, block=16),
+    dict(fused_kz=8, flush_mode=3, block=32),
+    dict(kz_h=1, mb_h=4, lean_h=1, kz_e=1, mb_e=4, lean_e=1, flush_mode=3, block=32),
+    dict(kz_h=2, mb_h=6, lean_h=2, kz_e=4, mb_e=4, lean_e=2, flush_mode=1, block=16),
 ]
+
+LEAN_VARIANTS = [
+    dict(kz_h=1, mb_h=4, lean_h=1, kz_e=1, mb_e=4, lean_e=1, flush_mode=3, block=32),
+    dict(kz_h=2, mb_h=4, lean_h=2, kz_e=4, mb_e=6, lean_e=2, flush_mode=1, block=16),
+    dict(kz_h=4, mb_h=6, lean_h=1, kz_e=2, mb_e=4, lean_e=2, flush_mode=0, block=16),
+    dict(kz_h=1, mb_h=6, lean_h=2, kz_e=4, mb_e=4, lean_e=1, flush_mode=2, block=16),
+    dict(kz_h=4, mb_h=4, lean_h=1, vec_e=1, kz_e=1, mb_e=4, flush_mode=3, block=16),
+]
+
+
+@pytest.fixture(scope="module")
+def ragged():
+    """52 x 45 x 43 cells: ragged for 1 or 2 cells per thread over 32-thread rows,
+    8-row blocks and 2- or 4-plane z blocks."""
+    wl = W.small_box(n_core=28, h=100.0, npml=8, ratio=1.08, n_st=4, n_rec=6, n_freq=2, n_core_y=21, n_core_z=19)
+    pb = fdtd.problem_from_workload(wl)
+    d_obs = fdtd.forward(pb, wl.rho_true, wl.src, wl.rec)
+    d, E, tr = fdtd.forward(pb, wl.rho, wl.src, wl.rec, keep_volume=True, return_trace=True)
+    phi, r = fdtd.misfit(d_obs, d)
+    Bp, fit = fdtd.adjoint_basis(pb, 1e-12)
+    V = fdtd.adjoint(pb, wl.rho, wl.rec, r, Bp)
+    g = fdtd.gradient(pb, wl.rho, E, V, wrt="lnrho")
+    return wl, dict(d_obs=d_obs, d=d, E=E, tr=tr, V=V, g=g)
+
+
+@pytest.mark.parametrize("variant", range(len(LEAN_VARIANTS)))
+def test_lean_kernels_match_oracle_on_a_ragged_box(ragged, variant):
+    wl, o = ragged
+    eng = Engine.from_workload(wl, precision=32, kahan=1, autotune=False)
+    eng.set_launch(**LEAN_VARIANTS[variant])
+    rho = eng.model_tensor(wl.rho)
+    d, E, tr = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True, trace=True)
+    assert rel_l2(tr.cpu().numpy(), o["tr"]) <= 1e-4
+    assert rel_l2(d.cpu().numpy(), o["d"]) <= 1e-5
+    Eg = gpu_volume(eng, E)
+    assert rel_l2(Eg, o["E"]) <= 1e-3
+    assert torch.count_nonzero(E[..., eng.nx + 1:]) == 0
+    basis, _, _ = eng.estimate_adjoint_basis()
+    d_obs = torch.as_tensor(o["d_obs"], device=eng.device)
+    phi, r = misfit(d_obs, d)
+    V = eng.adjoint_model(rho, wl.rec, r, basis)
+    assert rel_l2(gpu_volume(eng, V), o["V"]) <= 1e-3
+    assert rel_l2(eng.gradient(rho, E, V).cpu().numpy(), o["g"]) <= 1e-3
+    eng.check()
+    eng.close()
+
+
+def test_lean_kernels_refused_where_they_do_not_apply():
+    odd = W.small_box(n_core=20, h=100.0, npml=8, ratio=1.05, n_st=3, n_rec=6, n_freq=2)   # nx = 42
+    assert odd.nx % 4 != 0
+    eng = Engine.from_workload(odd, precision=32, autotune=False)
+    with pytest.raises(CsemError):
+        eng.set_launch(kz_h=1, mb_h=4, lean_h=1)
+    eng.close()
+    box = W.small_box(n_core=24, h=100.0, npml=8, ratio=1.08, n_st=4, n_rec=6, n_freq=2)
+    eng = Engine.from_workload(box, precision=64, autotune=False)
+    with pytest.raises(CsemError):
+        eng.set_launch(kz_e=1, mb_e=4, lean_e=2)
+    eng.close()
+    eng = Engine.from_workload(box, precision=32, autotune=False)
+    for bad in (dict(lean_h=3, kz_h=1), dict(lean_e=1, kz_e=8), dict(lean_h=1, kz_h=1, mb_h=8)):
+        with pytest.raises(CsemError):
+            eng.set_launch(**bad)
+    eng.close()
 
 
 @pytest.mark.parametrize("variant", range(len(LAUNCH_VARIANTS)))
@@ -132,6 +202,31 @@ def test_every_launch_variant_matches_oracle(box, box_oracle, variant):
     assert rel_l2(eng.gradient(rho, E, V).cpu().numpy(), o["g"]) <= 1e-3
     eng.check()
     eng.close()
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("nt", [40, 64, 200, 0])
+def test_overlapped_flush_is_bitwise_the_in_order_flush(box, precision, nt):
+    """The transform flush on the side stream (overlapping the next block) gives
+    the in-order flush's receivers, traces and volumes bit for bit: below one
+    captured chunk, exactly one chunk, chunks plus a ragged remainder, the full nt."""
+    wl, pb = box
+    modes = [(0, 16), (2, 16), (0, 32), (2, 32)]
+    if precision == 32:
+        modes += [(1, 16), (3, 16), (1, 32), (3, 32)]
+    out = {}
+    for fm, m in modes:
+        eng = Engine.from_workload(wl, precision=precision, kahan=1, autotune=False, nt=nt)
+        eng.set_launch(kz_h=4, mb_h=4, kz_e=4, mb_e=4, flush_mode=fm, block=m)
+        d, E, tr = eng.fwd_model(eng.model_tensor(wl.rho), wl.src, wl.rec, keep_volume=True, trace=True)
+        out[(fm, m)] = (d.clone(), E.clone(), tr.clone())
+        eng.check()
+        eng.close()
+    for (fm, m), got in out.items():
+        if fm & 2:
+            ref = out[(fm & 1, m)]
+            for a, b in zip(got, ref):
+                assert torch.equal(a, b), (fm, m)
 
 
 def test_fused_and_split_steps_agree_in_fp64(box):
