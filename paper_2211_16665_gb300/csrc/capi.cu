@@ -112,6 +112,8 @@ struct csem_ctx {
     double *d_coef = nullptr, *d_T = nullptr, *d_ones = nullptr;
     Tap *d_rtaps = nullptr, *d_itaps = nullptr;
     int2 *d_colmap = nullptr;            // [max_src][plane] injection taps per lattice column
+    unsigned char *d_tflag = nullptr;    // [max(max_src, max_rec)][ny][nseg] columns with taps, per 32 along x
+    int nseg = 1;
     long long *d_cpos = nullptr;         // scatter positions / values for the column map
     int2 *d_cval = nullptr;
     int *d_step = nullptr, *d_bad = nullptr;
@@ -185,6 +187,7 @@ int upload_lean_tables(csem_ctx *c) {
         for (int i = 1; i < n; ++i) { v[4 * L + i] = (float)A.bn[i]; v[5 * L + i] = (float)A.an[i]; }
         tab.insert(tab.end(), v.begin(), v.end());
     }
+    tab.insert(tab.end(), 4, 0.f);   // zeros read by lanes off the x slab
     TRY(dalloc(c, &c->d_tabL, tab.size() * sizeof(float)));
     CK(cudaMemcpy(c->d_tabL, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice));
     return CSEM_OK;
@@ -341,16 +344,25 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
     p.LEAN_h = c->LEAN_h;
     p.LEAN_e = c->LEAN_e;
     p.lx = p.ly = p.lz = csem::AxisTab<R>{};
+    p.lzero = nullptr;
     p.psiL = nullptr;
     p.cEm = nullptr;
     if constexpr (sizeof(R) == 4) {
-        if (c->d_tabL) { lean_tab(c, 0, p.lx); lean_tab(c, 1, p.ly); lean_tab(c, 2, p.lz); }
+        if (c->d_tabL) {
+            lean_tab(c, 0, p.lx); lean_tab(c, 1, p.ly); lean_tab(c, 2, p.lz);
+            long long off = 0;
+            for (int a = 0; a < 3; ++a) off += 6LL * lean_len(c->ax[a].n);
+            p.lzero = (const float *)c->d_tabL + off;
+        }
         p.psiL = c->d_psiL;
         p.cEm = c->d_cEm;
     }
     p.err = c->d_bad;
     p.colmap = nullptr;
     p.colmap_stride = 0;
+    p.tflag = nullptr;
+    p.tflag_stride = 0;
+    p.nseg = c->nseg;
     p.itaps = nullptr;
     p.itap_stride = 0;
     p.n_emit = p.J = 0;
@@ -547,6 +559,17 @@ int upload_injection(csem_ctx *c, std::vector<Tap> &taps, int n_lists, int per_l
     CK(cudaMemcpyAsync(c->d_cpos, pos.data(), pos.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_cval, val.data(), val.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
     CK(csem::launch_scatter_int2(c->d_colmap, c->d_cpos, c->d_cval, (int)pos.size(), st));
+    {   // tile flags: rows and 32-column segments of the cell range that hold a tap
+        const int nl = shared ? 1 : n_lists;
+        std::vector<unsigned char> fl((size_t)nl * c->ny * c->nseg, 0);
+        for (int s = 0; s < n_lists; ++s)
+            for (int u = 0; u < per_list; ++u) {
+                const long long col = taps[(size_t)s * per_list + u].idx % plane;
+                const int j = (int)(col / c->pitch), i = (int)(col % c->pitch);
+                if (j < c->ny && i < c->nx) fl[((size_t)(shared ? 0 : s) * c->ny + j) * c->nseg + i / 32] = 1;
+            }
+        CK(cudaMemcpyAsync(c->d_tflag, fl.data(), fl.size(), cudaMemcpyHostToDevice, st));
+    }
     return CSEM_OK;
 }
 
@@ -572,6 +595,7 @@ int fwd_impl(csem_ctx *c, const void *rho, const csem_points *src, const csem_po
 
     csem::StepParams<R> p = step_params<R>(c, dft, Evol);
     p.colmap = c->d_colmap; p.colmap_stride = c->plane;
+    p.tflag = c->d_tflag; p.tflag_stride = (long long)c->ny * c->nseg;
     p.itaps = c->d_itaps; p.itap_stride = 8;
     p.n_emit = 1; p.J = 1; p.coef = c->d_ones; p.T = c->d_T;   // unit moment for every source
     csem::PointParams<R> q;
@@ -606,6 +630,7 @@ int adj_impl(csem_ctx *c, const void *rho, const csem_points *rec, int S, const 
     if (c->kahan) CK(cudaMemsetAsync(c->d_comp, 0, vbytes, st));
     csem::StepParams<R> p = step_params<R>(c, true, Vvol);
     p.colmap = c->d_colmap; p.colmap_stride = 0;
+    p.tflag = c->d_tflag; p.tflag_stride = 0;
     p.itaps = c->d_itaps; p.itap_stride = 0;
     p.n_emit = NR; p.J = 2 * c->nf; p.coef = c->d_coef; p.T = basis;
     csem::PointParams<R> q;
@@ -636,6 +661,7 @@ int time_impl(csem_ctx *c, int S, void *vol, int launches, double *ms, cudaStrea
     CK(cudaEventCreate(&e1));
     const int cnt = std::min(c->M, c->nt);
     p.colmap = c->d_colmap; p.colmap_stride = c->plane;     // the last forward run's taps
+    p.tflag = c->d_tflag; p.tflag_stride = (long long)c->ny * c->nseg;
     p.itaps = c->d_itaps; p.itap_stride = 8;
     p.n_emit = 1; p.J = 1; p.coef = c->d_ones; p.T = c->d_T;
     const int fkz = p.fused_kz;
@@ -781,7 +807,7 @@ void free_ctx(csem_ctx *c) {
     cudaDeviceSynchronize();
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
     void *ptrs[] = {c->d_tabL, c->d_psiL, c->d_cEm, c->d_tab, c->d_h, c->d_cE, c->d_H, c->d_H2, c->d_ering, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
-                    c->d_alpha, c->d_racc, c->d_coef, c->d_T, c->d_ones, c->d_rtaps, c->d_itaps, c->d_colmap, c->d_cpos, c->d_cval, c->d_step, c->d_bad};
+                    c->d_alpha, c->d_racc, c->d_coef, c->d_T, c->d_ones, c->d_rtaps, c->d_itaps, c->d_colmap, c->d_tflag, c->d_cpos, c->d_cval, c->d_step, c->d_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->cap) cudaStreamDestroy(c->cap);
@@ -920,6 +946,8 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     step(dalloc(c, &c->d_rtaps, (size_t)NR * 8 * sizeof(Tap)));
     step(dalloc(c, &c->d_itaps, (size_t)std::max(S, NR) * 8 * sizeof(Tap)));
     step(dalloc(c, &c->d_colmap, (size_t)S * c->plane * sizeof(int2)));
+    c->nseg = (c->nx + 31) / 32;
+    step(dalloc(c, &c->d_tflag, (size_t)std::max(S, NR) * c->ny * c->nseg));
     step(dalloc(c, &c->d_cpos, (size_t)std::max(S, NR) * 8 * sizeof(long long)));
     step(dalloc(c, &c->d_cval, (size_t)std::max(S, NR) * 8 * sizeof(int2)));
     step(dalloc(c, &c->d_step, sizeof(int)));

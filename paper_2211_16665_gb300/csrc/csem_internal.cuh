@@ -78,6 +78,7 @@ struct StepParams {
     int TMA_h, TMA_e;              // > 0: FP32 bulk-copy-staged kernels over this many rows per block
     int LEAN_h, LEAN_e;            // > 0: lean FP32 kernels with this many cells per thread (1 or 2)
     AxisTab<R> lx, ly, lz;         // the stepping tables padded to 16-byte groups (lean kernels)
+    const R *lzero;                // 4 zeros, 16-byte aligned (lean kernels)
     R *psiL;                       // [S][12][vol] CPML memory in the field layout (lean kernels)
     const R *cEm;                  // [3][vol] dt/eps, zero on the PEC edges (lean kernels)
     int *err;                      // device status word (bit 1: a bounded wait gave up)
@@ -89,6 +90,11 @@ struct StepParams {
     // lattice column; colmap[s*colmap_stride + (j*pitch + i)] = (first tap, count)
     const int2 *colmap;            // nullptr: no injection
     long long colmap_stride;       // plane, or 0 when every source shares the taps
+    // tflag[s*tflag_stride + j*nseg + i/32] != 0: the 32 columns from i (rounded down) of row j
+    // hold a tap (lean kernels read the column map only there)
+    const unsigned char *tflag;
+    long long tflag_stride;        // ny*nseg, or 0 when every source shares the taps
+    int nseg;                      // ceil(nx / 32)
     const struct Tap *itaps;
     int itap_stride, n_emit, J;
     const double *coef;            // [S][n_emit][J]

@@ -2,20 +2,29 @@
 // consecutive cells (W = 1 or 2; i a multiple of W) of one (j, k) row per
 // thread, the cell range [0,nx) x [0,ny) x [0,nz) (nx a multiple of 4), KZ
 // planes along z per thread.  They compute what the scalar kernels compute,
-// entry by entry, but keep each thread's memory operations independent of one
-// another so that all of a plane's loads are in flight together:
-//  * the CPML memory lives in volume arrays with the field layout (12 per
-//    source: 0-5 for H, 6-11 for E), so a slab entry is read and written with the
-//    same access as the field it corrects, issued with the field loads;
-//  * the coefficient tables are padded to whole 16-byte groups and the CPML
-//    coefficients are zero off the slabs and on the outer nodes, so a thread that
-//    touches a slab runs the recursion on all its cells without per-cell tests
-//    (psi stays zero where b = a = 0);
+// entry by entry, with every load of a plane independent of the others, so that
+// a plane's loads are in flight together:
+//  * the CPML memory lives in arrays of its own (12 per source: 0-5 for H, 6-11
+//    for E).  The y- and z-slab arrays have the field layout.  The x-slab arrays
+//    (3, 4, 9, 10) are compact: row (k, j) holds the 2*nxs cells i < nxs and
+//    i >= nx - nxs (nxs = npml rounded up to even), so the slab entries of
+//    consecutive rows are contiguous;
+//  * the coefficient tables are padded to whole 16-byte groups, and the CPML
+//    coefficients are zero off the slabs and on the outer nodes.  A cell in the
+//    rounded-out slab but not in the CPML keeps psi = 0;
+//  * the x-slab recursion runs on every lane (lanes off the slab read zeros and
+//    have zero coefficients) and only slab lanes store, so warps do not diverge
+//    on it;
+//  * a block whose plane is off the z slabs and whose rows are off the y slabs
+//    takes a code path without the y/z recursion, with fewer live values;
 //  * E is advanced with dt/eps set to zero on the PEC edges (tangential E on the
-//    outer faces), so all three components are written unconditionally and the
-//    PEC edges keep their zero;
-//  * the source taps of the thread's columns are read with its other loads and
-//    added to the new values in registers before the store.
+//    outer faces), so all three components are written unconditionally, the PEC
+//    edges keep their zero, and the curl's lower neighbours are clamped to the
+//    cell itself on the outer faces (what they give there is multiplied by 0);
+//  * the source taps of the thread's columns are added to the new values in
+//    registers before the store; the column map is read only where a per-row,
+//    per-32-column flag marks a tap (a byte shared by a warp), inside that rare
+//    branch, so it holds no registers elsewhere.
 // W stays small so that a plane's loaded values fit the register budget.
 // The block is 32 x 8 threads (32 W cells of 8 rows); blockIdx.z runs over the
 // z blocks of every source.
@@ -101,9 +110,33 @@ template <int W> __device__ __forceinline__ Vec<W> up(const Vec<W> &a, float nex
     return r;
 }
 
+// Per-thread constants shared by the planes of a lean kernel.
+template <int W> struct LeanRow {
+    int i, j, nxs, ixs;
+    bool xs, ys;
+    Vec<W> ihx, bx, ax;
+    float ihy, by, ay;
+};
+template <int W>
+__device__ __forceinline__ void lean_row(const StepParams<float> &p, const AxisTab<float> &tx, const AxisTab<float> &ty,
+                                         bool half, int i, int j, LeanRow<W> &r) {
+    const int npml = p.npml;
+    r.i = i; r.j = j;
+    r.nxs = (npml + 1) & ~1;
+    r.xs = (i < r.nxs) || (i + W > p.nx - r.nxs);
+    r.ixs = (i < r.nxs) ? i : i - (p.nx - 2 * r.nxs);
+    r.ihx = ldc<W>((half ? tx.ih_h : tx.ih_n) + i);
+    r.bx = ldc<W>((half ? tx.b_h : tx.b_n) + i);
+    r.ax = ldc<W>((half ? tx.a_h : tx.a_n) + i);
+    r.ihy = __ldg((half ? ty.ih_h : ty.ih_n) + j);
+    r.ys = half ? ((j < npml) || (j >= p.ny - npml)) : ((j < npml) || (j > p.ny - npml));
+    r.by = r.ys ? __ldg((half ? ty.b_h : ty.b_n) + j) : 0.f;
+    r.ay = r.ys ? __ldg((half ? ty.a_h : ty.a_n) + j) : 0.f;
+}
+
 // Source term E^{n+1} -= dt/eps J'^{n+1/2} for the taps in plane k of the
 // thread's column col (one cell; returns the three increments).
-__device__ __noinline__ float3 lean_taps(const StepParams<float> &p, int s, int n, int k, int col, int2 cm) {
+__device__ __forceinline__ float3 lean_taps(const StepParams<float> &p, int s, int n, int k, int col, int2 cm) {
     const int plane = (int)p.plane, vol = (int)p.vol;
     float3 r = make_float3(0.f, 0.f, 0.f);
     for (int u = cm.x; u < cm.x + cm.y; ++u) {
@@ -125,6 +158,60 @@ __device__ __noinline__ float3 lean_taps(const StepParams<float> &p, int s, int 
 
 }  // namespace
 
+// One plane k of the H update for the thread's W cells; YZ: the y/z recursion
+// may apply (a block on a y or z slab).  exc, eyc: Ex, Ey of plane k (in), of
+// plane k+1 (out).
+template <int W, bool YZ>
+__device__ __forceinline__ void h_plane(const StepParams<float> &p, const float *__restrict__ E, float *__restrict__ H,
+                                        float *__restrict__ ps, const LeanRow<W> &r, int k, int idx, Vec<W> &exc,
+                                        Vec<W> &eyc) {
+    const int vol = (int)p.vol, plane = (int)p.plane, pitch = p.pitch, npml = p.npml;
+    const Vec<W> ezc = ldc<W>(E + 2 * vol + idx);
+    const Vec<W> exk = ldc<W>(E + idx + plane), eyk = ldc<W>(E + vol + idx + plane);
+    const Vec<W> exj = ldc<W>(E + idx + pitch), ezj = ldc<W>(E + 2 * vol + idx + pitch);
+    const float eyn = __ldg(E + vol + idx + W), ezn = __ldg(E + 2 * vol + idx + W);
+    const float ihz = __ldg(p.lz.ih_h + k);
+    Vec<W> hx = ldw<W>(H + idx), hy = ldw<W>(H + vol + idx), hz = ldw<W>(H + 2 * vol + idx);
+    const int xo = (k * p.ny + r.j) * (2 * r.nxs) + r.ixs;
+    float *px3 = ps + 3 * vol + xo, *px4 = ps + 4 * vol + xo;
+    Vec<W> q3 = ldw<W>(r.xs ? px3 : p.lzero), q4 = ldw<W>(r.xs ? px4 : p.lzero);
+    bool zs = false, ys = false;
+    float bz = 0.f, az = 0.f;
+    Vec<W> q0 = zv<W>(), q1 = zv<W>(), q2 = zv<W>(), q5 = zv<W>();
+    if constexpr (YZ) {
+        zs = (k < npml) || (k >= p.nz - npml);
+        ys = r.ys;
+        if (zs) { bz = __ldg(p.lz.b_h + k); az = __ldg(p.lz.a_h + k); }
+        if (ys) { q0 = ldw<W>(ps + idx); q5 = ldw<W>(ps + 5 * vol + idx); }
+        if (zs) { q1 = ldw<W>(ps + vol + idx); q2 = ldw<W>(ps + 2 * vol + idx); }
+    }
+    const Vec<W> ezx = up<W>(ezc, ezn), eyx = up<W>(eyc, eyn);   // Ez, Ey at i+1 .. i+W
+
+    // Hx at (i, j+1/2, k+1/2)
+    Vec<W> dEz_dy = dsc<W>(ezj, ezc, r.ihy), dEy_dz = dsc<W>(eyk, eyc, ihz);
+    if (YZ && ys) { cpml<W>(q0, dEz_dy, r.by, r.ay); stv<W>(ps + idx, q0); }
+    if (YZ && zs) { cpml<W>(q1, dEy_dz, bz, az); stv<W>(ps + vol + idx, q1); }
+    hsub<W>(hx, p.cH, dEz_dy, dEy_dz);
+    // Hy at (i+1/2, j, k+1/2)
+    Vec<W> dEx_dz = dsc<W>(exk, exc, ihz), dEz_dx = dsc<W>(ezx, ezc, r.ihx);
+    if (YZ && zs) { cpml<W>(q2, dEx_dz, bz, az); stv<W>(ps + 2 * vol + idx, q2); }
+    cpml<W>(q3, dEz_dx, r.bx, r.ax);
+    if (r.xs) stv<W>(px3, q3);
+    hsub<W>(hy, p.cH, dEx_dz, dEz_dx);
+    // Hz at (i+1/2, j+1/2, k)
+    Vec<W> dEy_dx = dsc<W>(eyx, eyc, r.ihx), dEx_dy = dsc<W>(exj, exc, r.ihy);
+    cpml<W>(q4, dEy_dx, r.bx, r.ax);
+    if (r.xs) stv<W>(px4, q4);
+    if (YZ && ys) { cpml<W>(q5, dEx_dy, r.by, r.ay); stv<W>(ps + 5 * vol + idx, q5); }
+    hsub<W>(hz, p.cH, dEy_dx, dEx_dy);
+
+    stv<W>(H + idx, hx);
+    stv<W>(H + vol + idx, hy);
+    stv<W>(H + 2 * vol + idx, hz);
+    exc = exk;
+    eyc = eyk;
+}
+
 template <int W, int KZ, int MINB>
 __global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_h_lean(const StepParams<float> p, const int jstep) {
     const int i = (blockIdx.x * kLeanX + threadIdx.x) * W;
@@ -135,64 +222,88 @@ __global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_h_lean(const StepPa
     if (i >= p.nx || j >= p.ny) return;
     const int k1 = min(k0 + KZ, p.nz);
     const int n = *p.step + jstep;
-    const int vol = (int)p.vol, plane = (int)p.plane, pitch = p.pitch, npml = p.npml;
+    const int vol = (int)p.vol, plane = (int)p.plane, npml = p.npml;
     const float *__restrict__ E = p.ering + (long long)s * p.ering_stride + (long long)(n % p.nslot) * 3 * p.vol;
     float *__restrict__ H = p.H + (long long)s * 3 * vol;
     float *__restrict__ ps = p.psiL + (long long)s * 12 * vol;
+    LeanRow<W> r;
+    lean_row<W>(p, p.lx, p.ly, true, i, j, r);
+    const int j0 = blockIdx.y * kLeanRows;
+    const bool yblk = (j0 < npml) || (j0 + kLeanRows > p.ny - npml);
 
-    const Vec<W> ihx = ldc<W>(p.lx.ih_h + i);
-    const bool xs = (i < npml) || (i + W > p.nx - npml);
-    Vec<W> bx = zv<W>(), ax = zv<W>();
-    if (xs) { bx = ldc<W>(p.lx.b_h + i); ax = ldc<W>(p.lx.a_h + i); }
-    const float ihy = __ldg(p.ly.ih_h + j);
-    const bool ys = (j < npml) || (j >= p.ny - npml);
-    float by = 0.f, ay = 0.f;
-    if (ys) { by = __ldg(p.ly.b_h + j); ay = __ldg(p.ly.a_h + j); }
-    const float cH = p.cH;
-
-    int idx = k0 * plane + j * pitch + i;
+    int idx = k0 * plane + j * p.pitch + i;
     Vec<W> exc = ldc<W>(E + idx), eyc = ldc<W>(E + vol + idx);
 #pragma unroll
     for (int kk = 0; kk < KZ; ++kk, idx += plane) {
         const int k = k0 + kk;
         if (k >= k1) break;
-        const Vec<W> ezc = ldc<W>(E + 2 * vol + idx);
-        const Vec<W> exk = ldc<W>(E + idx + plane), eyk = ldc<W>(E + vol + idx + plane);
-        const Vec<W> exj = ldc<W>(E + idx + pitch), ezj = ldc<W>(E + 2 * vol + idx + pitch);
-        const float eyn = __ldg(E + vol + idx + W), ezn = __ldg(E + 2 * vol + idx + W);
-        const float ihz = __ldg(p.lz.ih_h + k);
-        const bool zs = (k < npml) || (k >= p.nz - npml);
-        float bz = 0.f, az = 0.f;
-        if (zs) { bz = __ldg(p.lz.b_h + k); az = __ldg(p.lz.a_h + k); }
-        Vec<W> hx = ldw<W>(H + idx), hy = ldw<W>(H + vol + idx), hz = ldw<W>(H + 2 * vol + idx);
-        Vec<W> q0 = zv<W>(), q1 = zv<W>(), q2 = zv<W>(), q3 = zv<W>(), q4 = zv<W>(), q5 = zv<W>();
+        if (yblk || k < npml || k >= p.nz - npml) h_plane<W, true>(p, E, H, ps, r, k, idx, exc, eyc);
+        else h_plane<W, false>(p, E, H, ps, r, k, idx, exc, eyc);
+    }
+}
+
+// One plane k of the E update; hxm, hym: Hx, Hy of plane k-1 (in), of plane k (out).
+template <int W, bool YZ>
+__device__ __forceinline__ void e_plane(const StepParams<float> &p, const float *__restrict__ Eo, float *__restrict__ En,
+                                        const float *__restrict__ H, float *__restrict__ ps, const LeanRow<W> &r, int s,
+                                        int n, int k, int idx, bool taps, Vec<W> &hxm, Vec<W> &hym) {
+    const int vol = (int)p.vol, pitch = p.pitch, npml = p.npml;
+    const float *__restrict__ cE = p.cEm;
+    const int ij = (r.j > 0) ? idx - pitch : idx;    // lower neighbours, clamped on the outer faces
+    const int ii = (r.i > 0) ? idx - 1 : idx;
+    const Vec<W> hxc = ldc<W>(H + idx), hyc = ldc<W>(H + vol + idx), hzc = ldc<W>(H + 2 * vol + idx);
+    const Vec<W> hxj = ldc<W>(H + ij), hzj = ldc<W>(H + 2 * vol + ij);
+    const float hyp = __ldg(H + vol + ii), hzp = __ldg(H + 2 * vol + ii);
+    const Vec<W> eo0 = ldc<W>(Eo + idx), eo1 = ldc<W>(Eo + vol + idx), eo2 = ldc<W>(Eo + 2 * vol + idx);
+    const Vec<W> c0 = ldc<W>(cE + idx), c1 = ldc<W>(cE + vol + idx), c2 = ldc<W>(cE + 2 * vol + idx);
+    const float ihz = __ldg(p.lz.ih_n + k);
+    const int xo = (k * p.ny + r.j) * (2 * r.nxs) + r.ixs;
+    float *px3 = ps + 3 * vol + xo, *px4 = ps + 4 * vol + xo;
+    Vec<W> q3 = ldw<W>(r.xs ? px3 : p.lzero), q4 = ldw<W>(r.xs ? px4 : p.lzero);
+    bool zs = false, ys = false;
+    float bz = 0.f, az = 0.f;
+    Vec<W> q0 = zv<W>(), q1 = zv<W>(), q2 = zv<W>(), q5 = zv<W>();
+    if constexpr (YZ) {
+        zs = (k < npml) || (k > p.nz - npml);
+        ys = r.ys;
+        if (zs) { bz = __ldg(p.lz.b_n + k); az = __ldg(p.lz.a_n + k); }
         if (ys) { q0 = ldw<W>(ps + idx); q5 = ldw<W>(ps + 5 * vol + idx); }
         if (zs) { q1 = ldw<W>(ps + vol + idx); q2 = ldw<W>(ps + 2 * vol + idx); }
-        if (xs) { q3 = ldw<W>(ps + 3 * vol + idx); q4 = ldw<W>(ps + 4 * vol + idx); }
-        const Vec<W> ezx = up<W>(ezc, ezn), eyx = up<W>(eyc, eyn);   // Ez, Ey at i+1 .. i+W
-
-        // Hx at (i, j+1/2, k+1/2)
-        Vec<W> dEz_dy = dsc<W>(ezj, ezc, ihy), dEy_dz = dsc<W>(eyk, eyc, ihz);
-        if (ys) { cpml<W>(q0, dEz_dy, by, ay); stv<W>(ps + idx, q0); }
-        if (zs) { cpml<W>(q1, dEy_dz, bz, az); stv<W>(ps + vol + idx, q1); }
-        hsub<W>(hx, cH, dEz_dy, dEy_dz);
-        // Hy at (i+1/2, j, k+1/2)
-        Vec<W> dEx_dz = dsc<W>(exk, exc, ihz), dEz_dx = dsc<W>(ezx, ezc, ihx);
-        if (zs) { cpml<W>(q2, dEx_dz, bz, az); stv<W>(ps + 2 * vol + idx, q2); }
-        if (xs) { cpml<W>(q3, dEz_dx, bx, ax); stv<W>(ps + 3 * vol + idx, q3); }
-        hsub<W>(hy, cH, dEx_dz, dEz_dx);
-        // Hz at (i+1/2, j+1/2, k)
-        Vec<W> dEy_dx = dsc<W>(eyx, eyc, ihx), dEx_dy = dsc<W>(exj, exc, ihy);
-        if (xs) { cpml<W>(q4, dEy_dx, bx, ax); stv<W>(ps + 4 * vol + idx, q4); }
-        if (ys) { cpml<W>(q5, dEx_dy, by, ay); stv<W>(ps + 5 * vol + idx, q5); }
-        hsub<W>(hz, cH, dEy_dx, dEx_dy);
-
-        stv<W>(H + idx, hx);
-        stv<W>(H + vol + idx, hy);
-        stv<W>(H + 2 * vol + idx, hz);
-        exc = exk;
-        eyc = eyk;
     }
+    const Vec<W> hzx = down<W>(hzp, hzc), hyx = down<W>(hyp, hyc);   // Hz, Hy at i-1 .. i+W-2
+
+    // Ex at (i+1/2, j, k)
+    Vec<W> dHz_dy = dsc<W>(hzc, hzj, r.ihy), dHy_dz = dsc<W>(hyc, hym, ihz);
+    if (YZ && ys) { cpml<W>(q0, dHz_dy, r.by, r.ay); stv<W>(ps + idx, q0); }
+    if (YZ && zs) { cpml<W>(q1, dHy_dz, bz, az); stv<W>(ps + vol + idx, q1); }
+    Vec<W> e0 = eadv<W>(eo0, c0, dHz_dy, dHy_dz);
+    // Ey at (i, j+1/2, k)
+    Vec<W> dHx_dz = dsc<W>(hxc, hxm, ihz), dHz_dx = dsc<W>(hzc, hzx, r.ihx);
+    if (YZ && zs) { cpml<W>(q2, dHx_dz, bz, az); stv<W>(ps + 2 * vol + idx, q2); }
+    cpml<W>(q3, dHz_dx, r.bx, r.ax);
+    if (r.xs) stv<W>(px3, q3);
+    Vec<W> e1 = eadv<W>(eo1, c1, dHx_dz, dHz_dx);
+    // Ez at (i, j, k+1/2)
+    Vec<W> dHy_dx = dsc<W>(hyc, hyx, r.ihx), dHx_dy = dsc<W>(hxc, hxj, r.ihy);
+    cpml<W>(q4, dHy_dx, r.bx, r.ax);
+    if (r.xs) stv<W>(px4, q4);
+    if (YZ && ys) { cpml<W>(q5, dHx_dy, r.by, r.ay); stv<W>(ps + 5 * vol + idx, q5); }
+    Vec<W> e2 = eadv<W>(eo2, c2, dHy_dx, dHx_dy);
+
+    if (taps) {
+        const int2 *cm = p.colmap + (long long)s * p.colmap_stride + r.j * pitch + r.i;
+        for (int e = 0; e < W; ++e) {
+            const int2 c = __ldg(cm + e);
+            if (c.y == 0) continue;
+            const float3 a = lean_taps(p, s, n, k, r.j * pitch + r.i + e, c);
+            e0.v[e] += a.x; e1.v[e] += a.y; e2.v[e] += a.z;
+        }
+    }
+    stv<W>(En + idx, e0);
+    stv<W>(En + vol + idx, e1);
+    stv<W>(En + 2 * vol + idx, e2);
+    hxm = hxc;
+    hym = hyc;
 }
 
 template <int W, int KZ, int MINB>
@@ -210,82 +321,22 @@ __global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_e_lean(const StepPa
     const float *__restrict__ Eo = ring + (long long)(n % p.nslot) * 3 * p.vol;
     float *__restrict__ En = const_cast<float *>(ring) + (long long)((n + 1) % p.nslot) * 3 * p.vol;
     const float *__restrict__ H = p.H + (long long)s * 3 * vol;
-    const float *__restrict__ cE = p.cEm;
     float *__restrict__ ps = p.psiL + (long long)s * 12 * vol + 6LL * vol;
-
-    const Vec<W> ihx = ldc<W>(p.lx.ih_n + i);
-    const bool xs = (i < npml) || (i + W - 1 > p.nx - npml);
-    Vec<W> bx = zv<W>(), ax = zv<W>();
-    if (xs) { bx = ldc<W>(p.lx.b_n + i); ax = ldc<W>(p.lx.a_n + i); }
-    const float ihy = __ldg(p.ly.ih_n + j);
-    const bool ys = (j < npml) || (j > p.ny - npml);
-    float by = 0.f, ay = 0.f;
-    if (ys) { by = __ldg(p.ly.b_n + j); ay = __ldg(p.ly.a_n + j); }
-    int2 cm[W];
-#pragma unroll
-    for (int e = 0; e < W; ++e) cm[e] = make_int2(0, 0);
-    if (p.colmap) {
-        const int2 *c2 = p.colmap + (long long)s * p.colmap_stride + j * pitch + i;
-#pragma unroll
-        for (int e = 0; e < W; ++e) cm[e] = __ldg(c2 + e);
-    }
-    bool taps = false;
-#pragma unroll
-    for (int e = 0; e < W; ++e) taps |= (cm[e].y != 0);
+    LeanRow<W> r;
+    lean_row<W>(p, p.lx, p.ly, false, i, j, r);
+    const int j0 = blockIdx.y * kLeanRows;
+    const bool yblk = (j0 < npml) || (j0 + kLeanRows - 1 > p.ny - npml);
+    const bool taps = p.colmap && p.tflag[s * p.tflag_stride + j * p.nseg + (i >> 5)];
 
     int idx = k0 * plane + j * pitch + i;
-    Vec<W> hxm = (k0 > 0) ? ldc<W>(H + idx - plane) : zv<W>();
-    Vec<W> hym = (k0 > 0) ? ldc<W>(H + vol + idx - plane) : zv<W>();
+    const int im = (k0 > 0) ? idx - plane : idx;      // clamped on the bottom face
+    Vec<W> hxm = ldc<W>(H + im), hym = ldc<W>(H + vol + im);
 #pragma unroll
     for (int kk = 0; kk < KZ; ++kk, idx += plane) {
         const int k = k0 + kk;
         if (k >= k1) break;
-        const Vec<W> hxc = ldc<W>(H + idx), hyc = ldc<W>(H + vol + idx), hzc = ldc<W>(H + 2 * vol + idx);
-        const Vec<W> hxj = (j > 0) ? ldc<W>(H + idx - pitch) : zv<W>();
-        const Vec<W> hzj = (j > 0) ? ldc<W>(H + 2 * vol + idx - pitch) : zv<W>();
-        const float hyp = (i > 0) ? __ldg(H + vol + idx - 1) : 0.f;
-        const float hzp = (i > 0) ? __ldg(H + 2 * vol + idx - 1) : 0.f;
-        const Vec<W> eo0 = ldc<W>(Eo + idx), eo1 = ldc<W>(Eo + vol + idx), eo2 = ldc<W>(Eo + 2 * vol + idx);
-        const Vec<W> c0 = ldc<W>(cE + idx), c1 = ldc<W>(cE + vol + idx), c2 = ldc<W>(cE + 2 * vol + idx);
-        const float ihz = __ldg(p.lz.ih_n + k);
-        const bool zs = (k < npml) || (k > p.nz - npml);
-        float bz = 0.f, az = 0.f;
-        if (zs) { bz = __ldg(p.lz.b_n + k); az = __ldg(p.lz.a_n + k); }
-        Vec<W> q0 = zv<W>(), q1 = zv<W>(), q2 = zv<W>(), q3 = zv<W>(), q4 = zv<W>(), q5 = zv<W>();
-        if (ys) { q0 = ldw<W>(ps + idx); q5 = ldw<W>(ps + 5 * vol + idx); }
-        if (zs) { q1 = ldw<W>(ps + vol + idx); q2 = ldw<W>(ps + 2 * vol + idx); }
-        if (xs) { q3 = ldw<W>(ps + 3 * vol + idx); q4 = ldw<W>(ps + 4 * vol + idx); }
-        const Vec<W> hzx = down<W>(hzp, hzc), hyx = down<W>(hyp, hyc);   // Hz, Hy at i-1 .. i+W-2
-
-        // Ex at (i+1/2, j, k)
-        Vec<W> dHz_dy = dsc<W>(hzc, hzj, ihy), dHy_dz = dsc<W>(hyc, hym, ihz);
-        if (ys) { cpml<W>(q0, dHz_dy, by, ay); stv<W>(ps + idx, q0); }
-        if (zs) { cpml<W>(q1, dHy_dz, bz, az); stv<W>(ps + vol + idx, q1); }
-        Vec<W> e0 = eadv<W>(eo0, c0, dHz_dy, dHy_dz);
-        // Ey at (i, j+1/2, k)
-        Vec<W> dHx_dz = dsc<W>(hxc, hxm, ihz), dHz_dx = dsc<W>(hzc, hzx, ihx);
-        if (zs) { cpml<W>(q2, dHx_dz, bz, az); stv<W>(ps + 2 * vol + idx, q2); }
-        if (xs) { cpml<W>(q3, dHz_dx, bx, ax); stv<W>(ps + 3 * vol + idx, q3); }
-        Vec<W> e1 = eadv<W>(eo1, c1, dHx_dz, dHz_dx);
-        // Ez at (i, j, k+1/2)
-        Vec<W> dHy_dx = dsc<W>(hyc, hyx, ihx), dHx_dy = dsc<W>(hxc, hxj, ihy);
-        if (xs) { cpml<W>(q4, dHy_dx, bx, ax); stv<W>(ps + 4 * vol + idx, q4); }
-        if (ys) { cpml<W>(q5, dHx_dy, by, ay); stv<W>(ps + 5 * vol + idx, q5); }
-        Vec<W> e2 = eadv<W>(eo2, c2, dHy_dx, dHx_dy);
-
-        if (taps) {
-#pragma unroll
-            for (int e = 0; e < W; ++e) {
-                if (cm[e].y == 0) continue;
-                const float3 a = lean_taps(p, s, n, k, j * pitch + i + e, cm[e]);
-                e0.v[e] += a.x; e1.v[e] += a.y; e2.v[e] += a.z;
-            }
-        }
-        stv<W>(En + idx, e0);
-        stv<W>(En + vol + idx, e1);
-        stv<W>(En + 2 * vol + idx, e2);
-        hxm = hxc;
-        hym = hyc;
+        if (yblk || k < npml || k > p.nz - npml) e_plane<W, true>(p, Eo, En, H, ps, r, s, n, k, idx, taps, hxm, hym);
+        else e_plane<W, false>(p, Eo, En, H, ps, r, s, n, k, idx, taps, hxm, hym);
     }
 }
 
@@ -330,7 +381,7 @@ bool lean_kz(const StepParams<float> &p, int S, int jstep, cudaStream_t st, bool
 
 cudaError_t launch_field_lean(const StepParams<float> &p, int S, int jstep, cudaStream_t st, bool h, int w, int kz,
                               int mb) {
-    if (p.nx % 4 != 0 || !p.psiL || !p.cEm || !p.lx.ih_n) return cudaErrorInvalidValue;
+    if (p.nx % 4 != 0 || !p.psiL || !p.cEm || !p.lx.ih_n || !p.lzero) return cudaErrorInvalidValue;
     bool ok = false;
     if (w == 1 && mb == 4) ok = lean_kz<1, 4>(p, S, jstep, st, h, kz);
     else if (w == 1 && mb == 6) ok = lean_kz<1, 6>(p, S, jstep, st, h, kz);
