@@ -205,7 +205,7 @@ int csem_gradient(csem_ctx *ctx, const void *rho_dev, const void *Evol_dev, cons
  * later calls use the fastest.  It then times the fused H+E step kernel (z
  * blocking 4, 8 or 16) against the best split pair and keeps the faster, and
  * last, when nt >= 256, the transform flush over 128 steps: the register
- * kernel or (FP32) the bulk-copy kernel, over 16 or 32 snapshots, run after
+ * kernel or (FP32) the bulk-copy kernel, over 16, 32 or 64 snapshots, run after
  * its block or on a second stream overlapping the next block (needs a ring of
  * 2 * snapshots + 1 slots; the results are the same bit for bit).  kz_out
  * (may be NULL, else 4 ints) receives, for H and E, 16 * planes + blocks
@@ -220,9 +220,9 @@ int csem_autotune(csem_ctx *ctx, int n_src, int *kz_out, void *stream);
  * every variant through it): cfg = {H z planes, H blocks/SM, E z planes,
  * E blocks/SM, fused z blocking (0 = split kernels), flush mode (bit 0: bulk
  * copy, FP32 only, else register kernel; bit 1: overlapped with the next
- * block on a second stream), snapshots per flush (16 or 32; the context's ring
- * of 17, 33 or 65 slots must hold snapshots + 1, or 2 * snapshots + 1 when
- * overlapped), H four-cells-per-thread (0/1, FP32, 4 or 6 blocks/SM),
+ * block on a second stream), snapshots per flush (16, 32 or 64; the context's
+ * ring of 17, 33, 65 or 129 slots must hold snapshots + 1, or 2 * snapshots + 1
+ * when overlapped), H four-cells-per-thread (0/1, FP32, 4 or 6 blocks/SM),
  * E four-cells-per-thread (0/1), H bulk-copy-staged rows per block (0, or
  * 1/2/4 for FP32 when the staged planes fit shared memory; z planes 2-16),
  * E bulk-copy-staged rows per block, H lean kernel (0 off, or 1 or 2 cells

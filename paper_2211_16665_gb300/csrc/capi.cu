@@ -38,7 +38,7 @@ constexpr double kMu0 = 4e-7 * M_PI;
 constexpr double kCpmlR = 1e-6;
 constexpr double kDecaySpan = 35.0;
 constexpr int kChunk = 64;        // time steps per captured graph
-constexpr int kBlockM = 32;        // largest snapshots per transform flush (divides kChunk)
+constexpr int kBlockM = 64;        // largest snapshots per transform flush (divides kChunk)
 constexpr int kMaxSide = 4;       // event slots for overlapped flushes (at most two are in flight)
 
 struct Axis {
@@ -392,7 +392,7 @@ template <typename R>
 cudaError_t flush(csem_ctx *c, const csem::StepParams<R> &p, const csem::PointParams<R> &q, int S, int n0_off,
                   int cnt, bool vol, bool kahan, cudaStream_t st) {
     if constexpr (sizeof(R) == 4) {
-        if ((c->flush_mode & 1) && vol && (cnt == 16 || cnt == 32))
+        if ((c->flush_mode & 1) && vol && (cnt == 16 || cnt == 32 || cnt == 64))
             return csem::launch_dft_bulk(p, q, S, n0_off, cnt, kahan, c->d_bad, st);
     }
     return csem::launch_dft<R>(p, q, S, n0_off, cnt, vol, kahan, st);
@@ -773,7 +773,7 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
             double best = 1e30;
             int bm = 0, bM = 16;
             for (int mode = 0; mode < 4; ++mode)
-                for (int m : {16, 32}) {
+                for (int m : {16, 32, 64}) {
                     if ((mode & 1) && sizeof(R) != 4) continue;
                     if (((mode & 2) ? 2 * m : m) + 1 > c->nslot) continue;
                     c->flush_mode = mode;
@@ -912,8 +912,8 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     c->wavelet.assign(c->nt, 0.0);
     c->wavelet[0] = 1.0 / c->dt;
 
-    // E ring: 65 slots (32-snapshot flushes overlapping the next block), 33
-    // (32-snapshot flushes, or overlapped 16-snapshot ones) or 17, the largest
+    // E ring: 2M + 1 slots for an M-snapshot flush that overlaps the next block,
+    // M + 1 otherwise (M = 16, 32, 64): 129, 65, 33 or 17 slots, the largest
     // that leaves room
     {
         size_t free_b = 0, total_b = 0;
@@ -921,7 +921,7 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
         const double slot = (double)c->max_src * 3 * c->vol * c->rsize;
         const double vols = (double)c->max_src * 3 * c->nf * c->vol * 2 * c->rsize * (c->kahan ? 3 : 2);
         c->nslot = 17;
-        for (int ns : {65, 33})
+        for (int ns : {129, 65, 33})
             if (ns * slot + vols < 0.6 * (double)free_b) { c->nslot = ns; break; }
         c->M = 16;
     }
@@ -1100,7 +1100,7 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
     auto kz_ok = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16; };
     auto mb_ok = [](int v) { return v == 4 || v == 6 || v == 8; };
     if (!kz_ok(kzh) || !kz_ok(kze) || !mb_ok(mbh) || !mb_ok(mbe) || !(fkz == 0 || fkz == 4 || fkz == 8 || fkz == 16) ||
-        fm < 0 || fm > 3 || ((fm & 1) && c->precision != 32) || !(M == 16 || M == 32) ||
+        fm < 0 || fm > 3 || ((fm & 1) && c->precision != 32) || !(M == 16 || M == 32 || M == 64) ||
         ((fm & 2) ? 2 * M : M) + 1 > c->nslot)
         return fail(CSEM_ERR_INVALID_ARG, "launch configuration not supported by this context");
     CK(cudaDeviceSynchronize());

@@ -413,8 +413,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 
 constexpr int kWaitLimit = 1 << 22;   // try_wait rounds before a flush block gives up
 
+// resident blocks per SM that the shared memory allows (MS snapshots of 1 KB + accumulators)
+template <int MS> constexpr int bulk_minb() { return MS <= 16 ? 6 : (MS <= 32 ? 4 : 2); }
+
 template <bool KAHAN, int MS>
-__global__ void __launch_bounds__(kBlock, 6) k_dft_bulk(const StepParams<float> p, const PointParams<float> q,
+__global__ void __launch_bounds__(kBlock, bulk_minb<MS>()) k_dft_bulk(const StepParams<float> p, const PointParams<float> q,
                                                      const int n0_off, const int nvb, const int S, int *err) {
     __shared__ __align__(8) uint64_t bar;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -523,8 +526,12 @@ size_t bulk_smem_bytes(int ms, int nf, bool kahan) {
 }
 
 cudaError_t prepare_bulk_flush() {
-    const int big = (int)bulk_smem_bytes(32, kMaxFreq, true);
-    cudaError_t e = cudaFuncSetAttribute(k_dft_bulk<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    const int big = (int)bulk_smem_bytes(64, kMaxFreq, true);
+    cudaError_t e = cudaFuncSetAttribute(k_dft_bulk<true, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dft_bulk<false, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_dft_bulk<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_dft_bulk<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
     if (e == cudaSuccess)
@@ -539,7 +546,10 @@ cudaError_t launch_dft_bulk(const StepParams<float> &p, const PointParams<float>
     const int nvb = (int)((p.vol + kBlock - 1) / kBlock);
     const int nblk = nvb * 3 * S + (q.n_rec > 0 ? S : 0);
     const size_t sm = bulk_smem_bytes(cnt, p.nf, kahan);
-    if (cnt == 32) {
+    if (cnt == 64) {
+        if (kahan) k_dft_bulk<true, 64><<<nblk, kBlock, sm, st>>>(p, q, n0_off, nvb, S, err);
+        else k_dft_bulk<false, 64><<<nblk, kBlock, sm, st>>>(p, q, n0_off, nvb, S, err);
+    } else if (cnt == 32) {
         if (kahan) k_dft_bulk<true, 32><<<nblk, kBlock, sm, st>>>(p, q, n0_off, nvb, S, err);
         else k_dft_bulk<false, 32><<<nblk, kBlock, sm, st>>>(p, q, n0_off, nvb, S, err);
     } else if (cnt == 16) {

@@ -115,6 +115,9 @@ LAUNCH_VARIANTS = [
     dict(fused_kz=8, flush_mode=3, block=32),
     dict(kz_h=1, mb_h=4, lean_h=1, kz_e=1, mb_e=4, lean_e=1, flush_mode=3, block=32),
     dict(kz_h=2, mb_h=6, lean_h=2, kz_e=4, mb_e=4, lean_e=2, flush_mode=1, block=16),
+    dict(kz_h=2, mb_h=4, lean_h=2, kz_e=2, mb_e=4, lean_e=2, flush_mode=1, block=64),
+    dict(kz_h=2, mb_h=4, lean_h=2, kz_e=1, mb_e=4, lean_e=2, flush_mode=3, block=64),
+    dict(kz_h=4, mb_h=4, kz_e=4, mb_e=6, flush_mode=0, block=64),
 ]
 
 LEAN_VARIANTS = [
@@ -211,9 +214,9 @@ def test_overlapped_flush_is_bitwise_the_in_order_flush(box, precision, nt):
     the in-order flush's receivers, traces and volumes bit for bit: below one
     captured chunk, exactly one chunk, chunks plus a ragged remainder, the full nt."""
     wl, pb = box
-    modes = [(0, 16), (2, 16), (0, 32), (2, 32)]
+    modes = [(0, 16), (2, 16), (0, 32), (2, 32), (0, 64), (2, 64)]
     if precision == 32:
-        modes += [(1, 16), (3, 16), (1, 32), (3, 32)]
+        modes += [(1, 16), (3, 16), (1, 32), (3, 32), (1, 64), (3, 64)]
     out = {}
     for fm, m in modes:
         eng = Engine.from_workload(wl, precision=precision, kahan=1, autotune=False, nt=nt)
