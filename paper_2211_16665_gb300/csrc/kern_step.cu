@@ -415,16 +415,26 @@ constexpr int kWaitLimit = 1 << 22;   // try_wait rounds before a flush block gi
 
 // resident blocks per SM that the shared memory allows (MS snapshots of 1 KB + accumulators)
 template <int MS> constexpr int bulk_minb() { return MS <= 16 ? 6 : (MS <= 32 ? 4 : 2); }
+constexpr int kBulkThreads = 128;       // two lattice entries per thread, 256 per block
+__host__ __device__ constexpr int nf_pad(int nf) { return nf <= 2 ? 2 : (nf <= 4 ? 4 : 8); }
 
-template <bool KAHAN, int MS>
-__global__ void __launch_bounds__(kBlock, bulk_minb<MS>()) k_dft_bulk(const StepParams<float> p, const PointParams<float> q,
-                                                     const int n0_off, const int nvb, const int S, int *err) {
+// Each thread sums its two entries' MS snapshots into NF frequencies (NF a
+// compile-time bound, the weights of frequencies >= nf are zero and their sums
+// are dropped), reading each snapshot pair with one 8-byte load and each pair
+// of complex weights with one 16-byte broadcast.  One warp waits on the
+// barrier; the others wait at __syncthreads without issuing.
+template <bool KAHAN, int MS, int NF>
+__global__ void __launch_bounds__(kBulkThreads, bulk_minb<MS>()) k_dft_bulk(const StepParams<float> p,
+                                                                            const PointParams<float> q,
+                                                                            const int n0_off, const int nvb,
+                                                                            const int S, int *err) {
     __shared__ __align__(8) uint64_t bar;
+    __shared__ int bad;
     extern __shared__ __align__(128) unsigned char smem[];
     float *ring_s = reinterpret_cast<float *>(smem);                        // [MS][256]
     float2 *acc_s = reinterpret_cast<float2 *>(ring_s + MS * kBlock);       // [nf][256]
     float2 *cmp_s = acc_s + p.nf * kBlock;                                  // [nf][256] (Kahan)
-    float2 *w_s = cmp_s + (KAHAN ? p.nf * kBlock : 0);                      // [MS][nf]
+    float2 *w_s = cmp_s + (KAHAN ? p.nf * kBlock : 0);                      // [MS][NF], zero past nf
     const int n0 = *p.step + n0_off;
     if (n0 < 0) return;               // a deferred flush before the first block: nothing to transform
     const int nrec_blocks = q.n_rec > 0 ? S : 0;
@@ -463,7 +473,10 @@ __global__ void __launch_bounds__(kBlock, bulk_minb<MS>()) k_dft_bulk(const Step
     float2 *A = p.acc + ((long long)s * 3 + c) * p.nf * p.vol + i0;
     float2 *C = KAHAN ? p.comp + ((long long)s * 3 + c) * p.nf * p.vol + i0 : nullptr;
     const float *ring = p.ering + (long long)s * p.ering_stride + (long long)c * p.vol + i0;
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        bad = 0;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t rb = (uint32_t)rows * sizeof(float), cb = (uint32_t)rows * sizeof(float2);
@@ -478,66 +491,99 @@ __global__ void __launch_bounds__(kBlock, bulk_minb<MS>()) k_dft_bulk(const Step
             if (KAHAN) bulk_g2s(cmp_s + f * kBlock, C + (long long)f * p.vol, cb, &bar);
         }
     }
-    for (int u = threadIdx.x; u < MS * p.nf; u += blockDim.x) w_s[u] = p.w[(long long)n0 * p.nf + u];
-    __syncthreads();
-    bool ok = false;
-    for (int it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(&bar, 0);
-    if (!ok) {
-        if (threadIdx.x == 0) atomicOr(err, 2);
+    for (int u = threadIdx.x; u < MS * NF; u += blockDim.x) {
+        const int m = u / NF, f = u - m * NF;
+        w_s[u] = (f < p.nf) ? p.w[(long long)(n0 + m) * p.nf + f] : make_float2(0.f, 0.f);
+    }
+    if (threadIdx.x < 32) {
+        bool ok = false;
         for (int it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(&bar, 0);
-        return;
-    }
-    const int t = threadIdx.x;
-    if (t >= rows) return;
-    float2 bs[kMaxFreq];
-#pragma unroll
-    for (int f = 0; f < kMaxFreq; ++f) bs[f].x = bs[f].y = 0.f;
-#pragma unroll 8
-    for (int m = 0; m < MS; ++m) {
-        const float e = ring_s[m * kBlock + t];
-#pragma unroll
-        for (int f = 0; f < kMaxFreq; ++f)
-            if (f < p.nf) {
-                const float2 w = w_s[m * p.nf + f];
-                bs[f].x = fmaf(e, w.x, bs[f].x);
-                bs[f].y = fmaf(e, w.y, bs[f].y);
+        if (!ok) {
+            if (threadIdx.x == 0) {
+                atomicOr(err, 2);
+                bad = 1;
             }
-    }
-#pragma unroll
-    for (int f = 0; f < kMaxFreq; ++f)
-        if (f < p.nf) {
-            float2 a = acc_s[f * kBlock + t];
-            if (KAHAN) {
-                float2 cc = cmp_s[f * kBlock + t];
-                kahan_add(a.x, cc.x, bs[f].x);
-                kahan_add(a.y, cc.y, bs[f].y);
-                C[(long long)f * p.vol + t] = cc;
-            } else {
-                a.x += bs[f].x;
-                a.y += bs[f].y;
-            }
-            A[(long long)f * p.vol + t] = a;
+            for (int it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(&bar, 0);
         }
+    }
+    __syncthreads();
+    if (bad) return;
+    const int t2 = 2 * threadIdx.x;
+    if (t2 >= rows) return;
+    float2 b0[NF], b1[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) b0[f] = b1[f] = make_float2(0.f, 0.f);
+    const float4 *w4 = reinterpret_cast<const float4 *>(w_s);
+#pragma unroll 4
+    for (int m = 0; m < MS; ++m) {
+        const float2 e = *reinterpret_cast<const float2 *>(ring_s + m * kBlock + t2);
+#pragma unroll
+        for (int g = 0; g < NF / 2; ++g) {
+            const float4 w = w4[m * (NF / 2) + g];       // frequencies 2g and 2g+1
+            b0[2 * g].x = fmaf(e.x, w.x, b0[2 * g].x);
+            b0[2 * g].y = fmaf(e.x, w.y, b0[2 * g].y);
+            b0[2 * g + 1].x = fmaf(e.x, w.z, b0[2 * g + 1].x);
+            b0[2 * g + 1].y = fmaf(e.x, w.w, b0[2 * g + 1].y);
+            b1[2 * g].x = fmaf(e.y, w.x, b1[2 * g].x);
+            b1[2 * g].y = fmaf(e.y, w.y, b1[2 * g].y);
+            b1[2 * g + 1].x = fmaf(e.y, w.z, b1[2 * g + 1].x);
+            b1[2 * g + 1].y = fmaf(e.y, w.w, b1[2 * g + 1].y);
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        if (f >= p.nf) break;
+        float4 a = *reinterpret_cast<const float4 *>(acc_s + f * kBlock + t2);   // entries t2, t2+1
+        if (KAHAN) {
+            float4 cc = *reinterpret_cast<const float4 *>(cmp_s + f * kBlock + t2);
+            kahan_add(a.x, cc.x, b0[f].x);
+            kahan_add(a.y, cc.y, b0[f].y);
+            kahan_add(a.z, cc.z, b1[f].x);
+            kahan_add(a.w, cc.w, b1[f].y);
+            *reinterpret_cast<float4 *>(C + (long long)f * p.vol + t2) = cc;
+        } else {
+            a.x += b0[f].x;
+            a.y += b0[f].y;
+            a.z += b1[f].x;
+            a.w += b1[f].y;
+        }
+        *reinterpret_cast<float4 *>(A + (long long)f * p.vol + t2) = a;
+    }
 }
 
 size_t bulk_smem_bytes(int ms, int nf, bool kahan) {
     return (size_t)ms * kBlock * sizeof(float) + (size_t)nf * kBlock * sizeof(float2) * (kahan ? 2 : 1) +
-           (size_t)ms * nf * sizeof(float2);
+           (size_t)ms * nf_pad(nf) * sizeof(float2);
 }
+
+namespace {
+template <bool KAHAN, int MS, int NF>
+cudaError_t bulk_attr(int bytes) {
+    return cudaFuncSetAttribute(k_dft_bulk<KAHAN, MS, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+template <int MS>
+cudaError_t bulk_attr_ms(int bytes) {
+    cudaError_t e = cudaSuccess;
+    for (cudaError_t r : {bulk_attr<true, MS, 2>(bytes), bulk_attr<true, MS, 4>(bytes), bulk_attr<true, MS, 8>(bytes),
+                          bulk_attr<false, MS, 2>(bytes), bulk_attr<false, MS, 4>(bytes), bulk_attr<false, MS, 8>(bytes)})
+        if (r != cudaSuccess) e = r;
+    return e;
+}
+template <bool KAHAN, int MS>
+void bulk_go(const StepParams<float> &p, const PointParams<float> &q, int S, int n0_off, int nvb, int nblk, size_t sm,
+             int *err, cudaStream_t st) {
+    const int np = nf_pad(p.nf);
+    if (np == 2) k_dft_bulk<KAHAN, MS, 2><<<nblk, kBulkThreads, sm, st>>>(p, q, n0_off, nvb, S, err);
+    else if (np == 4) k_dft_bulk<KAHAN, MS, 4><<<nblk, kBulkThreads, sm, st>>>(p, q, n0_off, nvb, S, err);
+    else k_dft_bulk<KAHAN, MS, 8><<<nblk, kBulkThreads, sm, st>>>(p, q, n0_off, nvb, S, err);
+}
+}  // namespace
 
 cudaError_t prepare_bulk_flush() {
     const int big = (int)bulk_smem_bytes(64, kMaxFreq, true);
-    cudaError_t e = cudaFuncSetAttribute(k_dft_bulk<true, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_dft_bulk<false, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_dft_bulk<true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_dft_bulk<false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_dft_bulk<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_dft_bulk<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, big);
+    cudaError_t e = bulk_attr_ms<64>(big);
+    if (e == cudaSuccess) e = bulk_attr_ms<32>(big);
+    if (e == cudaSuccess) e = bulk_attr_ms<16>(big);
     return e;
 }
 
@@ -547,14 +593,14 @@ cudaError_t launch_dft_bulk(const StepParams<float> &p, const PointParams<float>
     const int nblk = nvb * 3 * S + (q.n_rec > 0 ? S : 0);
     const size_t sm = bulk_smem_bytes(cnt, p.nf, kahan);
     if (cnt == 64) {
-        if (kahan) k_dft_bulk<true, 64><<<nblk, kBlock, sm, st>>>(p, q, n0_off, nvb, S, err);
-        else k_dft_bulk<false, 64><<<nblk, kBlock, sm, st>>>(p, q, n0_off, nvb, S, err);
+        if (kahan) bulk_go<true, 64>(p, q, S, n0_off, nvb, nblk, sm, err, st);
+        else bulk_go<false, 64>(p, q, S, n0_off, nvb, nblk, sm, err, st);
     } else if (cnt == 32) {
-        if (kahan) k_dft_bulk<true, 32><<<nblk, kBlock, sm, st>>>(p, q, n0_off, nvb, S, err);
-        else k_dft_bulk<false, 32><<<nblk, kBlock, sm, st>>>(p, q, n0_off, nvb, S, err);
+        if (kahan) bulk_go<true, 32>(p, q, S, n0_off, nvb, nblk, sm, err, st);
+        else bulk_go<false, 32>(p, q, S, n0_off, nvb, nblk, sm, err, st);
     } else if (cnt == 16) {
-        if (kahan) k_dft_bulk<true, 16><<<nblk, kBlock, sm, st>>>(p, q, n0_off, nvb, S, err);
-        else k_dft_bulk<false, 16><<<nblk, kBlock, sm, st>>>(p, q, n0_off, nvb, S, err);
+        if (kahan) bulk_go<true, 16>(p, q, S, n0_off, nvb, nblk, sm, err, st);
+        else bulk_go<false, 16>(p, q, S, n0_off, nvb, nblk, sm, err, st);
     } else {
         return cudaErrorInvalidValue;
     }
