@@ -705,17 +705,18 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
         int best_kz = 4, best_mb = 4, best_vec = 0;
         const int maxty = (sizeof(R) == 4) ? csem::tma_max_rows(c->pitch) : 0;
         const int ntma = maxty >= 4 ? 12 : (maxty >= 2 ? 8 : (maxty >= 1 ? 4 : 0));
-        const int nlean = (sizeof(R) == 4 && c->d_psiL) ? 12 : 0;
+        const int nlean = (sizeof(R) == 4 && c->d_psiL) ? 15 : 0;
         const int ncand = (sizeof(R) == 4) ? 20 + ntma + nlean : 12;   // 12 scalar, 8 four-cell, staged, lean
         int best_tma = 0, best_lean = 0;
         for (int cand = 0; cand < ncand; ++cand) {
             const int lc = cand - 20 - ntma;
-            const int lean = (lc >= 0) ? 1 + lc / 6 : 0;                                   // cells per thread 1, 2
+            const int lean = (lc >= 0) ? (lc < 6 ? 1 : 2) : 0;                            // cells per thread 1, 2
             const int vec = (cand >= 12 && cand < 20) ? 1 : 0;
             const int tma = (cand >= 20 && !lean) ? (1 << ((cand - 20) / 4)) : 0;          // rows per block 1, 2, 4
             const int tkz[4] = {2, 4, 8, 16}, lkz[3] = {1, 2, 4};
             const int kz = lean ? lkz[lc % 3] : (tma ? tkz[(cand - 20) % 4] : kzs[cand % 4]);
-            const int mb = lean ? ((lc % 6) < 3 ? 4 : 6) : (tma ? 4 : (vec ? mbs[(cand - 12) / 4] : mbs[cand / 4]));
+            const int lmb[3] = {4, 6, 3};
+            const int mb = lean ? lmb[(lc % (lc < 6 ? 6 : 9)) / 3] : (tma ? 4 : (vec ? mbs[(cand - 12) / 4] : mbs[cand / 4]));
             p.KZ_h = p.KZ_e = kz;
             p.MB_h = p.MB_e = mb;
             p.VEC_h = p.VEC_e = vec;
@@ -1082,7 +1083,8 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
     const int vh = cfg[7], ve = cfg[8], th = cfg[9], te = cfg[10], lh = cfg[11], le = cfg[12];
     if (lh || le) {
         auto ok = [&](int l, int kz, int mb) {
-            return l == 0 || ((l == 1 || l == 2) && (kz == 1 || kz == 2 || kz == 4) && (mb == 4 || mb == 6));
+            return l == 0 || ((l == 1 || l == 2) && (kz == 1 || kz == 2 || kz == 4) &&
+                              (mb == 4 || mb == 6 || (mb == 3 && l == 2)));
         };
         if (!c->d_psiL || !ok(lh, kzh, mbh) || !ok(le, kze, mbe))
             return fail(CSEM_ERR_INVALID_ARG, "lean kernels: FP32, nx a multiple of 4, 1 or 2 cells, 1/2/4 planes, 4 or 6 blocks/SM");
@@ -1099,7 +1101,7 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
         return fail(CSEM_ERR_INVALID_ARG, "four-cell kernels: FP32 only, 4 or 6 blocks per SM");
     auto kz_ok = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16; };
     auto mb_ok = [](int v) { return v == 4 || v == 6 || v == 8; };
-    if (!kz_ok(kzh) || !kz_ok(kze) || !mb_ok(mbh) || !mb_ok(mbe) || !(fkz == 0 || fkz == 4 || fkz == 8 || fkz == 16) ||
+    if (!kz_ok(kzh) || !kz_ok(kze) || !(mb_ok(mbh) || (mbh == 3 && lh == 2)) || !(mb_ok(mbe) || (mbe == 3 && le == 2)) || !(fkz == 0 || fkz == 4 || fkz == 8 || fkz == 16) ||
         fm < 0 || fm > 3 || ((fm & 1) && c->precision != 32) || !(M == 16 || M == 32 || M == 64) ||
         ((fm & 2) ? 2 * M : M) + 1 > c->nslot)
         return fail(CSEM_ERR_INVALID_ARG, "launch configuration not supported by this context");

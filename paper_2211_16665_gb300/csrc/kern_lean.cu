@@ -387,6 +387,7 @@ cudaError_t launch_field_lean(const StepParams<float> &p, int S, int jstep, cuda
     else if (w == 1 && mb == 6) ok = lean_kz<1, 6>(p, S, jstep, st, h, kz);
     else if (w == 2 && mb == 4) ok = lean_kz<2, 4>(p, S, jstep, st, h, kz);
     else if (w == 2 && mb == 6) ok = lean_kz<2, 6>(p, S, jstep, st, h, kz);
+    else if (w == 2 && mb == 3) ok = lean_kz<2, 3>(p, S, jstep, st, h, kz);
     if (!ok) return cudaErrorInvalidValue;
     g_launches++;
     return cudaGetLastError();
