@@ -256,7 +256,9 @@ int csem_check(csem_ctx *ctx, void *stream);
  * each stepping kernel `launches` times for n_src sources and returns the mean
  * duration of one launch in milliseconds, from CUDA events on stream:
  * ms_out[0] = split H half-step, ms_out[1] = fused H+E step when the
- * autotuner selected it (else 0), ms_out[2] = split E step (with injection),
+ * autotuner selected it (else 0), ms_out[2] = split E step (with the source
+ * injection of the last forward run; without injection when the last run was
+ * an adjoint run),
  * ms_out[3] = one damped-transform flush of transform_block snapshots
  * into vol_dev ([n_src][3][n_freq][vol] complex(real), overwritten).  Field
  * values are overwritten. */

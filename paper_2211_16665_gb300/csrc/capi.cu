@@ -114,6 +114,10 @@ struct csem_ctx {
     int2 *d_colmap = nullptr;            // [max_src][plane] injection taps per lattice column
     unsigned char *d_tflag = nullptr;    // [max(max_src, max_rec)][ny][nseg] columns with taps, per 32 along x
     int nseg = 1;
+    float *d_inc = nullptr;              // lean kernels: [kChunk][max_src][ntl] tap increments of a chunk
+    int *d_tapk = nullptr;               // [max(max_src, max_rec) * 8] plane * 4 + component of each tap
+    int last_ntl = 8;                    // taps per list of the last run (8 forward, 8 * receivers adjoint)
+    bool last_shared = false;            // the uploaded taps are an adjoint run's (one list, receiver emitters)
     long long *d_cpos = nullptr;         // scatter positions / values for the column map
     int2 *d_cval = nullptr;
     int *d_step = nullptr, *d_bad = nullptr;
@@ -345,6 +349,8 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
     p.LEAN_e = c->LEAN_e;
     p.lx = p.ly = p.lz = csem::AxisTab<R>{};
     p.lzero = nullptr;
+    p.inc = nullptr;
+    p.tapk = nullptr;
     p.psiL = nullptr;
     p.cEm = nullptr;
     if constexpr (sizeof(R) == 4) {
@@ -356,6 +362,8 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
         }
         p.psiL = c->d_psiL;
         p.cEm = c->d_cEm;
+        p.inc = c->d_inc;
+        p.tapk = c->d_tapk;
     }
     p.err = c->d_bad;
     p.colmap = nullptr;
@@ -363,6 +371,7 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
     p.tflag = nullptr;
     p.tflag_stride = 0;
     p.nseg = c->nseg;
+    p.inc_ntl = 0;
     p.itaps = nullptr;
     p.itap_stride = 0;
     p.n_emit = p.J = 0;
@@ -396,6 +405,15 @@ cudaError_t flush(csem_ctx *c, const csem::StepParams<R> &p, const csem::PointPa
             return csem::launch_dft_bulk(p, q, S, n0_off, cnt, kahan, c->d_bad, st);
     }
     return csem::launch_dft<R>(p, q, S, n0_off, cnt, vol, kahan, st);
+}
+
+// Tap increments of the next nsteps steps for the lean E kernel (FP32 runs with injection).
+template <typename R>
+cudaError_t tap_prep(csem_ctx *c, const csem::StepParams<R> &p, int S, int nsteps, cudaStream_t st) {
+    if constexpr (sizeof(R) == 4) {
+        if (p.inc && p.colmap && p.LEAN_e) return csem::launch_tap_inc(p, S, nsteps, c->nt, st);
+    }
+    return cudaSuccess;
 }
 
 // Steps 0 .. n-1 (relative to the device step counter) with a transform flush
@@ -468,7 +486,8 @@ int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const 
         cudaGraph_t g = nullptr;
         const long long before = csem::g_launches.load();   // captured kernels are counted per replay
         CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-        cudaError_t le = emit_steps<R>(c, S, vol, kahan, p, q, kChunk, overlap, !overlap, c->cap);
+        cudaError_t le = tap_prep<R>(c, p, S, kChunk, c->cap);
+        if (le == cudaSuccess) le = emit_steps<R>(c, S, vol, kahan, p, q, kChunk, overlap, !overlap, c->cap);
         if (le == cudaSuccess) le = csem::launch_advance(c->d_step, kChunk, c->cap);
         cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
         if (le != cudaSuccess) return fail(CSEM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(le));
@@ -508,6 +527,7 @@ int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const 
         if (e == cudaSuccess && (j + 1) % M == 0) e = flush<R>(c, p, q, S, j + 1 - M, M, vol, kahan, s2);
         return e;
     };
+    if (rem > 0) CK(tap_prep<R>(c, p, S, rem, st));
     for (int j = 0; j < rem; ++j) CK(emit(j, st));
     const int tail = c->nt % M;     // M divides kChunk, so this is also rem % M
     if (tail) CK(flush<R>(c, p, q, S, rem - tail, tail, vol, kahan, st));
@@ -570,6 +590,13 @@ int upload_injection(csem_ctx *c, std::vector<Tap> &taps, int n_lists, int per_l
             }
         CK(cudaMemcpyAsync(c->d_tflag, fl.data(), fl.size(), cudaMemcpyHostToDevice, st));
     }
+    if (c->d_tapk) {   // plane and component of each tap, for the lean E kernel
+        std::vector<int> tk(taps.size());
+        for (size_t u = 0; u < taps.size(); ++u) tk[u] = (int)(taps[u].idx / plane) * 4 + taps[u].comp;
+        CK(cudaMemcpyAsync(c->d_tapk, tk.data(), tk.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    }
+    c->last_ntl = per_list;
+    c->last_shared = shared;
     return CSEM_OK;
 }
 
@@ -596,6 +623,7 @@ int fwd_impl(csem_ctx *c, const void *rho, const csem_points *src, const csem_po
     csem::StepParams<R> p = step_params<R>(c, dft, Evol);
     p.colmap = c->d_colmap; p.colmap_stride = c->plane;
     p.tflag = c->d_tflag; p.tflag_stride = (long long)c->ny * c->nseg;
+    p.inc_ntl = 8;
     p.itaps = c->d_itaps; p.itap_stride = 8;
     p.n_emit = 1; p.J = 1; p.coef = c->d_ones; p.T = c->d_T;   // unit moment for every source
     csem::PointParams<R> q;
@@ -631,6 +659,7 @@ int adj_impl(csem_ctx *c, const void *rho, const csem_points *rec, int S, const 
     csem::StepParams<R> p = step_params<R>(c, true, Vvol);
     p.colmap = c->d_colmap; p.colmap_stride = 0;
     p.tflag = c->d_tflag; p.tflag_stride = 0;
+    p.inc_ntl = NR * 8;
     p.itaps = c->d_itaps; p.itap_stride = 0;
     p.n_emit = NR; p.J = 2 * c->nf; p.coef = c->d_coef; p.T = basis;
     csem::PointParams<R> q;
@@ -660,18 +689,23 @@ int time_impl(csem_ctx *c, int S, void *vol, int launches, double *ms, cudaStrea
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const int cnt = std::min(c->M, c->nt);
-    p.colmap = c->d_colmap; p.colmap_stride = c->plane;     // the last forward run's taps
+    // the last forward run's taps (unit moments); after an adjoint run the uploaded taps
+    // belong to receivers with basis-series amplitudes, so the E step is timed without them
+    p.colmap = c->last_shared ? nullptr : c->d_colmap; p.colmap_stride = c->plane;
     p.tflag = c->d_tflag; p.tflag_stride = (long long)c->ny * c->nseg;
+    p.inc_ntl = c->last_ntl;
     p.itaps = c->d_itaps; p.itap_stride = 8;
     p.n_emit = 1; p.J = 1; p.coef = c->d_ones; p.T = c->d_T;
     const int fkz = p.fused_kz;
+    const int jmod = std::max(1, std::min(kChunk, c->nt - 1));   // steps within one chunk's tap increments
+    if constexpr (sizeof(R) == 4) CK(csem::launch_tap_inc(p, S, kChunk, c->nt, st));
     for (int w : {0, 1, 2, 3}) {
         if (w == 1 && fkz == 0) { ms[1] = 0.0; continue; }
         auto go = [&](int j) -> cudaError_t {
             if (w == 3) return flush<R>(c, p, q, S, 0, cnt, true, c->kahan != 0, st);
             csem::StepParams<R> pp = p;
             pp.fused_kz = (w == 1) ? fkz : 0;
-            return csem::launch_step<R>(pp, q, S, j % (c->nt - 1), st, w == 1 ? 5 : (w == 0 ? 1 : 4));
+            return csem::launch_step<R>(pp, q, S, j % jmod, st, w == 1 ? 5 : (w == 0 ? 1 : 4));
         };
         for (int j = 0; j < 2; ++j) CK(go(j));
         CK(cudaEventRecord(e0, st));
@@ -807,7 +841,7 @@ void free_ctx(csem_ctx *c) {
     if (!c) return;
     cudaDeviceSynchronize();
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
-    void *ptrs[] = {c->d_tabL, c->d_psiL, c->d_cEm, c->d_tab, c->d_h, c->d_cE, c->d_H, c->d_H2, c->d_ering, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
+    void *ptrs[] = {c->d_tabL, c->d_psiL, c->d_cEm, c->d_inc, c->d_tapk, c->d_tab, c->d_h, c->d_cE, c->d_H, c->d_H2, c->d_ering, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
                     c->d_alpha, c->d_racc, c->d_coef, c->d_T, c->d_ones, c->d_rtaps, c->d_itaps, c->d_colmap, c->d_tflag, c->d_cpos, c->d_cval, c->d_step, c->d_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -961,6 +995,8 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
         if (need < 0.25 * (double)free_b) {
             step(dalloc(c, &c->d_psiL, (size_t)S * 12 * c->vol * sizeof(float)));
             step(dalloc(c, &c->d_cEm, 3 * (size_t)c->vol * sizeof(float)));
+            step(dalloc(c, &c->d_inc, (size_t)kChunk * S * std::max(8, NR * 8) * sizeof(float)));
+            step(dalloc(c, &c->d_tapk, (size_t)std::max(S, NR) * 8 * sizeof(int)));
             step(upload_lean_tables(c));
             if (rc == CSEM_OK && cudaMemset(c->d_cEm, 0, 3 * (size_t)c->vol * sizeof(float)) != cudaSuccess)
                 rc = fail(CSEM_ERR_CUDA, "context initialisation failed");

@@ -95,6 +95,12 @@ struct StepParams {
     const unsigned char *tflag;
     long long tflag_stride;        // ny*nseg, or 0 when every source shares the taps
     int nseg;                      // ceil(nx / 32)
+    // lean E kernel: the increment -dt/eps J'^{n+1/2} of tap u of source s at step jstep of the
+    // current graph chunk, inc[(jstep*S + s)*inc_ntl + u] (FP32, rounded once from FP64), and
+    // tapk[s*itap_stride + u] = (plane k of the tap) * 4 + component
+    float *inc;
+    const int *tapk;
+    int inc_ntl;
     const struct Tap *itaps;
     int itap_stride, n_emit, J;
     const double *coef;            // [S][n_emit][J]
@@ -152,6 +158,8 @@ cudaError_t launch_field_lean(const StepParams<float> &p, int S, int jstep, cuda
                               int mb);
 // cEm = cE with the PEC edges zeroed
 cudaError_t launch_mask_coef(const StepParams<float> &p, const float *cE, float *cEm, cudaStream_t st);
+// p.inc for the steps jstep in [0, nsteps) after *p.step (zero past nt)
+cudaError_t launch_tap_inc(const StepParams<float> &p, int S, int nsteps, int nt, cudaStream_t st);
 cudaError_t launch_field_vec(const StepParams<float> &p, int S, int jstep, cudaStream_t st, bool h, int kz, int mb);
 // FP32 bulk-copy-staged H / E kernels (kern_tma.cu): ty rows per block in {1,2,4}, kz planes per chunk
 cudaError_t launch_field_tma(const StepParams<float> &p, int S, int jstep, cudaStream_t st, bool h, int kz, int ty,

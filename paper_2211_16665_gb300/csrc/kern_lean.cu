@@ -134,24 +134,18 @@ __device__ __forceinline__ void lean_row(const StepParams<float> &p, const AxisT
     r.ay = r.ys ? __ldg((half ? ty.a_h : ty.a_n) + j) : 0.f;
 }
 
-// Source term E^{n+1} -= dt/eps J'^{n+1/2} for the taps in plane k of the
-// thread's column col (one cell; returns the three increments).
-__device__ __forceinline__ float3 lean_taps(const StepParams<float> &p, int s, int n, int k, int col, int2 cm) {
-    const int plane = (int)p.plane, vol = (int)p.vol;
+// Source term E^{n+1} -= dt/eps J'^{n+1/2} for the taps in plane k of one
+// column (first tap, count in cm): the increments were computed for the chunk's
+// steps by k_tap_inc, so each tap costs two independent loads.
+__device__ __forceinline__ float3 lean_taps(const int *__restrict__ tk, const float *__restrict__ inc, int k, int2 cm) {
     float3 r = make_float3(0.f, 0.f, 0.f);
     for (int u = cm.x; u < cm.x + cm.y; ++u) {
-        const Tap tp = p.itaps[(long long)s * p.itap_stride + u];
-        if ((int)(tp.idx / plane) != k || (int)(tp.idx % plane) != col) continue;
-        const double *cf = p.coef + ((long long)s * p.n_emit + tp.emit) * p.J;
-        const double *T = p.T + (long long)n * p.J;
-        double amp = 0.0;
-        for (int jj = 0; jj < p.J; ++jj) amp += cf[jj] * T[jj];
-        const int o = tp.comp * vol + (int)tp.idx;
-        const double add = -(double)p.cE[o] * tp.w * amp;   // dt/eps at the tap's edge
-        if (add == 0.0) continue;
-        if (tp.comp == 0) r.x += (float)add;
-        else if (tp.comp == 1) r.y += (float)add;
-        else r.z += (float)add;
+        const int code = __ldg(tk + u);
+        const float v = __ldg(inc + u);
+        if ((code >> 2) != k) continue;
+        if ((code & 3) == 0) r.x += v;
+        else if ((code & 3) == 1) r.y += v;
+        else r.z += v;
     }
     return r;
 }
@@ -246,7 +240,7 @@ __global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_h_lean(const StepPa
 template <int W, bool YZ>
 __device__ __forceinline__ void e_plane(const StepParams<float> &p, const float *__restrict__ Eo, float *__restrict__ En,
                                         const float *__restrict__ H, float *__restrict__ ps, const LeanRow<W> &r, int s,
-                                        int n, int k, int idx, bool taps, Vec<W> &hxm, Vec<W> &hym) {
+                                        int S, int jstep, int k, int idx, bool taps, Vec<W> &hxm, Vec<W> &hym) {
     const int vol = (int)p.vol, pitch = p.pitch, npml = p.npml;
     const float *__restrict__ cE = p.cEm;
     const int ij = (r.j > 0) ? idx - pitch : idx;    // lower neighbours, clamped on the outer faces
@@ -292,10 +286,12 @@ __device__ __forceinline__ void e_plane(const StepParams<float> &p, const float 
 
     if (taps) {
         const int2 *cm = p.colmap + (long long)s * p.colmap_stride + r.j * pitch + r.i;
+        const int *tk = p.tapk + (long long)s * p.itap_stride;
+        const float *inc = p.inc + ((long long)jstep * S + s) * p.inc_ntl;
         for (int e = 0; e < W; ++e) {
             const int2 c = __ldg(cm + e);
             if (c.y == 0) continue;
-            const float3 a = lean_taps(p, s, n, k, r.j * pitch + r.i + e, c);
+            const float3 a = lean_taps(tk, inc, k, c);
             e0.v[e] += a.x; e1.v[e] += a.y; e2.v[e] += a.z;
         }
     }
@@ -326,7 +322,8 @@ __global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_e_lean(const StepPa
     lean_row<W>(p, p.lx, p.ly, false, i, j, r);
     const int j0 = blockIdx.y * kLeanRows;
     const bool yblk = (j0 < npml) || (j0 + kLeanRows - 1 > p.ny - npml);
-    const bool taps = p.colmap && p.tflag[s * p.tflag_stride + j * p.nseg + (i >> 5)];
+    const bool taps = p.colmap && p.inc && p.tflag[s * p.tflag_stride + j * p.nseg + (i >> 5)];
+    const int S = gridDim.z / nkb;
 
     int idx = k0 * plane + j * pitch + i;
     const int im = (k0 > 0) ? idx - plane : idx;      // clamped on the bottom face
@@ -335,9 +332,34 @@ __global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_e_lean(const StepPa
     for (int kk = 0; kk < KZ; ++kk, idx += plane) {
         const int k = k0 + kk;
         if (k >= k1) break;
-        if (yblk || k < npml || k > p.nz - npml) e_plane<W, true>(p, Eo, En, H, ps, r, s, n, k, idx, taps, hxm, hym);
-        else e_plane<W, false>(p, Eo, En, H, ps, r, s, n, k, idx, taps, hxm, hym);
+        if (yblk || k < npml || k > p.nz - npml) e_plane<W, true>(p, Eo, En, H, ps, r, s, S, jstep, k, idx, taps, hxm, hym);
+        else e_plane<W, false>(p, Eo, En, H, ps, r, s, S, jstep, k, idx, taps, hxm, hym);
     }
+}
+
+// Increment -dt/eps J'^{n+1/2} of every injection tap (Sec. 2, Eq. 4 source
+// term; the amplitude sum_j coef_j T_j(n) in FP64, one rounding to FP32, the same
+// value the other step kernels add) for the steps jstep in [0, nsteps) after the
+// device step counter: inc[(jstep*S + s)*inc_ntl + u].
+__global__ void k_tap_inc(const StepParams<float> p, const int S, const int nsteps, const int nt) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ntl = p.inc_ntl;
+    if (t >= (long long)nsteps * S * ntl) return;
+    const int u = (int)(t % ntl);
+    const int s = (int)((t / ntl) % S);
+    const int jstep = (int)(t / ((long long)ntl * S));
+    const int n = *p.step + jstep;
+    float v = 0.f;
+    if (n < nt) {
+        const Tap tp = p.itaps[(long long)s * p.itap_stride + u];
+        const double *cf = p.coef + ((long long)s * p.n_emit + tp.emit) * p.J;
+        const double *T = p.T + (long long)n * p.J;
+        double amp = 0.0;
+        for (int jj = 0; jj < p.J; ++jj) amp += cf[jj] * T[jj];
+        const int o = tp.comp * (int)p.vol + (int)tp.idx;
+        v = (float)(-(double)p.cE[o] * tp.w * amp);
+    }
+    p.inc[t] = v;
 }
 
 // dt/eps with the PEC edges zeroed: Ex needs 1 <= j < ny, 1 <= k < nz, i < nx;
@@ -389,6 +411,14 @@ cudaError_t launch_field_lean(const StepParams<float> &p, int S, int jstep, cuda
     else if (w == 2 && mb == 6) ok = lean_kz<2, 6>(p, S, jstep, st, h, kz);
     else if (w == 2 && mb == 3) ok = lean_kz<2, 3>(p, S, jstep, st, h, kz);
     if (!ok) return cudaErrorInvalidValue;
+    g_launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tap_inc(const StepParams<float> &p, int S, int nsteps, int nt, cudaStream_t st) {
+    const long long n = (long long)nsteps * S * p.inc_ntl;
+    if (n <= 0 || !p.inc || !p.itaps) return cudaSuccess;
+    k_tap_inc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, S, nsteps, nt);
     g_launches++;
     return cudaGetLastError();
 }
