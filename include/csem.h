@@ -227,8 +227,9 @@ int csem_autotune(csem_ctx *ctx, int n_src, int *kz_out, void *stream);
  * 1/2/4 for FP32 when the staged planes fit shared memory; z planes 2-16),
  * E bulk-copy-staged rows per block, H lean kernel (0 off, or 1 or 2 cells
  * per thread: FP32 with nx a multiple of 4 and room for the CPML memory in 12
- * volume arrays per source; 1, 2 or 4 planes, 4 or 6 blocks/SM), E lean
- * kernel (0, 1 or 2)} -- 13 ints.  The
+ * volume arrays per source; 1, 2 or 4 planes; blocks of 128 threads, 6 or 8
+ * resident per SM, or 4, 6 or 8 with 2 cells), E lean kernel (0, 1 or 2)}
+ * -- 13 ints.  The
  * lean kernel takes precedence over the staged and four-cell ones.
  * Synchronises the device.
  * Errors: INVALID_ARG. */

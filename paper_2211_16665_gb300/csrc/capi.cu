@@ -749,7 +749,7 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
             const int tma = (cand >= 20 && !lean) ? (1 << ((cand - 20) / 4)) : 0;          // rows per block 1, 2, 4
             const int tkz[4] = {2, 4, 8, 16}, lkz[3] = {1, 2, 4};
             const int kz = lean ? lkz[lc % 3] : (tma ? tkz[(cand - 20) % 4] : kzs[cand % 4]);
-            const int lmb[3] = {4, 6, 3};
+            const int lmb[3] = {6, 8, 4};   // 1 cell: 6, 8; 2 cells: 6, 8, 4 blocks of 128 threads per SM
             const int mb = lean ? lmb[(lc % (lc < 6 ? 6 : 9)) / 3] : (tma ? 4 : (vec ? mbs[(cand - 12) / 4] : mbs[cand / 4]));
             p.KZ_h = p.KZ_e = kz;
             p.MB_h = p.MB_e = mb;
@@ -1120,10 +1120,10 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
     if (lh || le) {
         auto ok = [&](int l, int kz, int mb) {
             return l == 0 || ((l == 1 || l == 2) && (kz == 1 || kz == 2 || kz == 4) &&
-                              (mb == 4 || mb == 6 || (mb == 3 && l == 2)));
+                              (mb == 6 || mb == 8 || (mb == 4 && l == 2)));
         };
         if (!c->d_psiL || !ok(lh, kzh, mbh) || !ok(le, kze, mbe))
-            return fail(CSEM_ERR_INVALID_ARG, "lean kernels: FP32, nx a multiple of 4, 1 or 2 cells, 1/2/4 planes, 4 or 6 blocks/SM");
+            return fail(CSEM_ERR_INVALID_ARG, "lean kernels: FP32, nx a multiple of 4, 1 or 2 cells, 1/2/4 planes, 6 or 8 (2 cells: 4, 6 or 8) blocks/SM");
     }
     if (th || te) {
         const int maxty = c->precision == 32 ? csem::tma_max_rows(c->pitch) : 0;
@@ -1137,7 +1137,7 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
         return fail(CSEM_ERR_INVALID_ARG, "four-cell kernels: FP32 only, 4 or 6 blocks per SM");
     auto kz_ok = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16; };
     auto mb_ok = [](int v) { return v == 4 || v == 6 || v == 8; };
-    if (!kz_ok(kzh) || !kz_ok(kze) || !(mb_ok(mbh) || (mbh == 3 && lh == 2)) || !(mb_ok(mbe) || (mbe == 3 && le == 2)) || !(fkz == 0 || fkz == 4 || fkz == 8 || fkz == 16) ||
+    if (!kz_ok(kzh) || !kz_ok(kze) || !mb_ok(mbh) || !mb_ok(mbe) || !(fkz == 0 || fkz == 4 || fkz == 8 || fkz == 16) ||
         fm < 0 || fm > 3 || ((fm & 1) && c->precision != 32) || !(M == 16 || M == 32 || M == 64) ||
         ((fm & 2) ? 2 * M : M) + 1 > c->nslot)
         return fail(CSEM_ERR_INVALID_ARG, "launch configuration not supported by this context");

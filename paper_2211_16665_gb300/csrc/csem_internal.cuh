@@ -153,7 +153,8 @@ template <typename R>
 cudaError_t launch_fused(const StepParams<R> &p, int S, int jstep, int kz, cudaStream_t st);
 cudaError_t prepare_fused_all();
 // FP32 H / E kernels with four cells per thread (kern_vec.cu), kz in {1,2,4,8}, mb in {4,6}
-// lean FP32 H / E kernels (kern_lean.cu), nx % 4 == 0, w (cells per thread) in {1,2}, kz in {1,2,4}, mb in {4,6}
+// lean FP32 H / E kernels (kern_lean.cu), nx % 4 == 0, w (cells per thread) in {1,2}, kz in {1,2,4},
+// mb (resident 128-thread blocks per SM) in {6,8} for w = 1 and {4,6,8} for w = 2
 cudaError_t launch_field_lean(const StepParams<float> &p, int S, int jstep, cudaStream_t st, bool h, int w, int kz,
                               int mb);
 // cEm = cE with the PEC edges zeroed

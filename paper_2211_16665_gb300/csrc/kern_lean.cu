@@ -26,15 +26,16 @@
 //    per-32-column flag marks a tap (a byte shared by a warp), inside that rare
 //    branch, so it holds no registers elsewhere.
 // W stays small so that a plane's loaded values fit the register budget.
-// The block is 32 x 8 threads (32 W cells of 8 rows); blockIdx.z runs over the
-// z blocks of every source.
+// The block is 32 x 4 threads (32 W cells of 4 rows; 128 threads, so 4, 6 or 8
+// resident blocks per SM give 128, 85 or 64 registers per thread); blockIdx.z
+// runs over the z blocks of every source.
 #include "csem_internal.cuh"
 
 namespace csem {
 
 namespace {
 
-constexpr int kLeanX = 32, kLeanRows = 8;
+constexpr int kLeanX = 32, kLeanRows = 4;
 
 template <int W> struct Vec { float v[W]; };
 template <int W> __device__ __forceinline__ Vec<W> ldc(const float *p) {
@@ -405,11 +406,11 @@ cudaError_t launch_field_lean(const StepParams<float> &p, int S, int jstep, cuda
                               int mb) {
     if (p.nx % 4 != 0 || !p.psiL || !p.cEm || !p.lx.ih_n || !p.lzero) return cudaErrorInvalidValue;
     bool ok = false;
-    if (w == 1 && mb == 4) ok = lean_kz<1, 4>(p, S, jstep, st, h, kz);
-    else if (w == 1 && mb == 6) ok = lean_kz<1, 6>(p, S, jstep, st, h, kz);
+    if (w == 1 && mb == 6) ok = lean_kz<1, 6>(p, S, jstep, st, h, kz);
+    else if (w == 1 && mb == 8) ok = lean_kz<1, 8>(p, S, jstep, st, h, kz);
     else if (w == 2 && mb == 4) ok = lean_kz<2, 4>(p, S, jstep, st, h, kz);
     else if (w == 2 && mb == 6) ok = lean_kz<2, 6>(p, S, jstep, st, h, kz);
-    else if (w == 2 && mb == 3) ok = lean_kz<2, 3>(p, S, jstep, st, h, kz);
+    else if (w == 2 && mb == 8) ok = lean_kz<2, 8>(p, S, jstep, st, h, kz);
     if (!ok) return cudaErrorInvalidValue;
     g_launches++;
     return cudaGetLastError();

@@ -113,19 +113,19 @@ LAUNCH_VARIANTS = [
     dict(kz_h=2, mb_h=6, kz_e=2, mb_e=4, vec_e=1, flush_mode=3, block=16),
     dict(kz_h=4, mb_h=4, kz_e=4, mb_e=4, flush_mode=2, block=16),
     dict(fused_kz=8, flush_mode=3, block=32),
-    dict(kz_h=1, mb_h=4, lean_h=1, kz_e=1, mb_e=4, lean_e=1, flush_mode=3, block=32),
+    dict(kz_h=1, mb_h=8, lean_h=1, kz_e=1, mb_e=6, lean_e=1, flush_mode=3, block=32),
     dict(kz_h=2, mb_h=6, lean_h=2, kz_e=4, mb_e=4, lean_e=2, flush_mode=1, block=16),
-    dict(kz_h=2, mb_h=4, lean_h=2, kz_e=2, mb_e=4, lean_e=2, flush_mode=1, block=64),
+    dict(kz_h=2, mb_h=8, lean_h=2, kz_e=2, mb_e=6, lean_e=2, flush_mode=1, block=64),
     dict(kz_h=2, mb_h=4, lean_h=2, kz_e=1, mb_e=4, lean_e=2, flush_mode=3, block=64),
     dict(kz_h=4, mb_h=4, kz_e=4, mb_e=6, flush_mode=0, block=64),
 ]
 
 LEAN_VARIANTS = [
-    dict(kz_h=1, mb_h=4, lean_h=1, kz_e=1, mb_e=4, lean_e=1, flush_mode=3, block=32),
+    dict(kz_h=1, mb_h=6, lean_h=1, kz_e=1, mb_e=8, lean_e=1, flush_mode=3, block=32),
     dict(kz_h=2, mb_h=4, lean_h=2, kz_e=4, mb_e=6, lean_e=2, flush_mode=1, block=16),
-    dict(kz_h=4, mb_h=6, lean_h=1, kz_e=2, mb_e=4, lean_e=2, flush_mode=0, block=16),
-    dict(kz_h=1, mb_h=6, lean_h=2, kz_e=4, mb_e=4, lean_e=1, flush_mode=2, block=16),
-    dict(kz_h=4, mb_h=4, lean_h=1, vec_e=1, kz_e=1, mb_e=4, flush_mode=3, block=16),
+    dict(kz_h=4, mb_h=6, lean_h=1, kz_e=2, mb_e=8, lean_e=2, flush_mode=0, block=16),
+    dict(kz_h=1, mb_h=6, lean_h=2, kz_e=4, mb_e=8, lean_e=1, flush_mode=2, block=16),
+    dict(kz_h=4, mb_h=8, lean_h=1, vec_e=1, kz_e=1, mb_e=4, flush_mode=3, block=16),
 ]
 
 
@@ -171,7 +171,7 @@ def test_lean_kernels_refused_where_they_do_not_apply():
     assert odd.nx % 4 != 0
     eng = Engine.from_workload(odd, precision=32, autotune=False)
     with pytest.raises(CsemError):
-        eng.set_launch(kz_h=1, mb_h=4, lean_h=1)
+        eng.set_launch(kz_h=1, mb_h=8, lean_h=1)
     eng.close()
     box = W.small_box(n_core=24, h=100.0, npml=8, ratio=1.08, n_st=4, n_rec=6, n_freq=2)
     eng = Engine.from_workload(box, precision=64, autotune=False)
@@ -179,7 +179,8 @@ def test_lean_kernels_refused_where_they_do_not_apply():
         eng.set_launch(kz_e=1, mb_e=4, lean_e=2)
     eng.close()
     eng = Engine.from_workload(box, precision=32, autotune=False)
-    for bad in (dict(lean_h=3, kz_h=1), dict(lean_e=1, kz_e=8), dict(lean_h=1, kz_h=1, mb_h=8)):
+    for bad in (dict(lean_h=3, kz_h=1), dict(lean_e=1, kz_e=8), dict(lean_h=1, kz_h=1, mb_h=4),
+                dict(lean_e=2, kz_e=1, mb_e=3)):
         with pytest.raises(CsemError):
             eng.set_launch(**bad)
     eng.close()
