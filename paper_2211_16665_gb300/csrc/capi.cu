@@ -948,16 +948,21 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     c->wavelet[0] = 1.0 / c->dt;
 
     // E ring: 2M + 1 slots for an M-snapshot flush that overlaps the next block,
-    // M + 1 otherwise (M = 16, 32, 64): 129, 65, 33 or 17 slots, the largest
-    // that leaves room
+    // M + 1 otherwise (M = 16, 32, 64): 129, 65, 33 or 17 slots, the largest that
+    // fits in 85 % of the free memory beside the rest of the per-source state and
+    // the transform volumes a gradient holds (forward and adjoint, and the Kahan
+    // terms)
     {
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
-        const double slot = (double)c->max_src * 3 * c->vol * c->rsize;
-        const double vols = (double)c->max_src * 3 * c->nf * c->vol * 2 * c->rsize * (c->kahan ? 3 : 2);
+        const double S = c->max_src, V = (double)c->vol, r = (double)c->rsize;
+        const double slot = S * 3 * V * r;
+        const double vols = S * 3 * c->nf * V * 2 * r * (c->kahan ? 3 : 2);
+        const double rest = S * (6 * V * r + (double)c->psi_stride * r + (c->precision == 32 ? 12 * V * 4 : 0)) +
+                            6 * V * r;
         c->nslot = 17;
         for (int ns : {129, 65, 33})
-            if (ns * slot + vols < 0.6 * (double)free_b) { c->nslot = ns; break; }
+            if (ns * slot + vols + rest < 0.85 * (double)free_b) { c->nslot = ns; break; }
         c->M = 16;
     }
     int rc = CSEM_OK;
