@@ -7,7 +7,12 @@
   the misfit computed with the FP64 engine on 20 seeded cells;
 * batched_towline (256x256x128, 32 sources): one batched launch equals
   single-source launches bit for bit (a property that holds at any size);
-* source chunks recomputed in backward give the unchunked gradient.
+* source chunks recomputed in backward give the unchunked gradient;
+* large_gradient (400x400x200, 8 frequencies): the source-chunked autograd path
+  with recomputation gives the chunked path that keeps the forward volumes, bit
+  for bit, at the full grid size (nt shortened; a property that holds at any nt);
+* heterogeneous (512x512x256, Gaussian random field model): a two-source batch
+  equals single-source runs bit for bit, receivers and volumes, at the full grid.
 """
 import json
 import os
@@ -132,4 +137,41 @@ def test_chunked_recompute_gives_the_unchunked_gradient():
         grads.append(ln_rho.grad.cpu().numpy())
     for g in grads[1:]:
         assert rel_l2(g, grads[0]) <= 1e-6
+    eng.close()
+
+
+def test_large_gradient_chunked_recompute_at_full_size():
+    wl = W.large_gradient()
+    src = wl.src.subset([0, 21, 40, 63])
+    eng = Engine.from_workload(wl, max_src=2, nt=192)
+    basis, _, _ = eng.estimate_adjoint_basis()
+    ln_true = torch.tensor(np.log(wl.rho_true), dtype=torch.float64, device="cuda")
+    with torch.no_grad():
+        d_obs = 0.9 * forward_data(ln_true, eng, src, wl.rec, basis, chunk=2, recompute=True)
+    grads = []
+    for recompute in (False, True):
+        ln_rho = ln_true.clone().requires_grad_(True)
+        d = forward_data(ln_rho, eng, src, wl.rec, basis, chunk=2, recompute=recompute)
+        (0.5 * (d_obs - d).abs().pow(2).sum()).backward()
+        grads.append(ln_rho.grad)
+    eng.check()
+    eng.close()
+    g = grads[0]
+    assert torch.isfinite(g).all() and g.abs().max() > 0
+    assert torch.equal(grads[1], g)
+
+
+def test_heterogeneous_full_grid_batched_equals_single_source():
+    wl = W.heterogeneous()
+    src = wl.src.subset([0, 9])
+    eng = Engine.from_workload(wl, max_src=2, nt=128)
+    rho = eng.model_tensor(wl.rho)
+    d2, E2 = eng.fwd_model(rho, src, wl.rec, keep_volume=True)
+    assert torch.isfinite(E2).all() and E2.abs().max() > 0
+    for s in (0, 1):
+        d1, E1 = eng.fwd_model(rho, src.subset([s]), wl.rec, keep_volume=True)
+        assert torch.equal(d1[0], d2[s])
+        assert torch.equal(E1[0], E2[s])
+        del E1
+    eng.check()
     eng.close()
