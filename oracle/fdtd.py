@@ -12,6 +12,9 @@ adjoint source estimation"):
   Sec. 3.2, Eq. 14 conj(v) from the same engine with conjugated residual sources
   Sec. 3.3         adjoint time series from the basis functions
   Sec. 3.5         m = ln(rho): dphi/dm = -(1/rho) dphi/dsigma
+  Sec. 2, Sec. 3.1 Eq. 15  VTI medium: sigma_h = sigma_xx = sigma_yy on the x and y edges,
+                   sigma_v = sigma_zz on the z edges; dphi/dsigma_h collects the x and y
+                   edges, dphi/dsigma_v the z edges
 
 Readings where the paper is silent (each listed in the design notes):
   * second-order Yee stencil; tangential E = 0 on the outer boundary;
@@ -106,10 +109,25 @@ def _edge_sums(A):
     return np.stack([sx, sy, sz])
 
 
+def is_vti(rho) -> bool:
+    """A model of shape (2, nz, ny, nx) holds (rho_h, rho_v) of a VTI medium."""
+    return np.ndim(rho) == 4 and np.shape(rho)[0] == 2
+
+
 def edge_conductivity(rho, xn, yn, zn):
-    """sigma_e = sum_c V_c sigma_c / sum_c V_c over the cells sharing edge e."""
+    """sigma_e = sum_c V_c sigma_c / sum_c V_c over the cells sharing edge e.
+
+    rho is (nz, ny, nx) for an isotropic medium or (2, nz, ny, nx) = (rho_h, rho_v)
+    for a VTI medium (Sec. 2): the x and y edges average sigma_h = 1/rho_h, the z
+    edges sigma_v = 1/rho_v.
+    """
     V = cell_volumes(xn, yn, zn)
-    num = _edge_sums(V / rho)
+    rho = np.asarray(rho, float)
+    if is_vti(rho):
+        num = _edge_sums(V / rho[0])
+        num[2] = _edge_sums(V / rho[1])[2]
+    else:
+        num = _edge_sums(V / rho)
     den = _edge_sums(V)
     out = np.zeros_like(num)
     np.divide(num, den, out=out, where=den > 0)
@@ -481,6 +499,8 @@ def gradient(pb: Problem, rho, Evol, Vvol, wrt="lnrho"):
     Edge form (Sec. 3.1, isotropic): dphi/dsigma_e = -Re sum_s sum_k conj(v)_e E_e dV_e.
     Cell form: dphi/dsigma_c = sum_{e touching c} dphi/dsigma_e * V_c / sum_{c' at e} V_c'.
     ln rho (Sec. 3.5): dphi/dln(rho_c) = -sigma_c dphi/dsigma_c.
+    VTI (Sec. 3.1, Eq. 15): dphi/dsigma_h collects the x and y edges of the cell,
+    dphi/dsigma_v its z edges; the result is (2, nz, ny, nx) = (h, v).
     """
     xn, yn, zn = pb.xn, pb.yn, pb.zn
     dV = edge_dual_volumes(xn, yn, zn)
@@ -494,17 +514,22 @@ def gradient(pb: Problem, rho, Evol, Vvol, wrt="lnrho"):
     gx = ratio[0]
     gy = ratio[1]
     gz = ratio[2]
-    acc = np.zeros((nz, ny, nx))
+    acc_h = np.zeros((nz, ny, nx))
+    acc_v = np.zeros((nz, ny, nx))
     for dk in (0, 1):
         for dj in (0, 1):
-            acc += gx[dk:dk + nz, dj:dj + ny, 0:nx]                # Ex(i, j+dj, k+dk)
+            acc_h += gx[dk:dk + nz, dj:dj + ny, 0:nx]              # Ex(i, j+dj, k+dk)
     for dk in (0, 1):
         for di in (0, 1):
-            acc += gy[dk:dk + nz, 0:ny, di:di + nx]                # Ey(i+di, j, k+dk)
+            acc_h += gy[dk:dk + nz, 0:ny, di:di + nx]              # Ey(i+di, j, k+dk)
     for dj in (0, 1):
         for di in (0, 1):
-            acc += gz[0:nz, dj:dj + ny, di:di + nx]                # Ez(i+di, j+dj, k)
-    g_sigma = acc * V
+            acc_v += gz[0:nz, dj:dj + ny, di:di + nx]              # Ez(i+di, j+dj, k)
+    rho = np.asarray(rho, float)
+    if is_vti(rho):
+        g_sigma = np.stack([acc_h * V, acc_v * V])
+    else:
+        g_sigma = (acc_h + acc_v) * V
     if wrt == "sigma":
         return g_sigma
-    return -g_sigma / np.asarray(rho, float)
+    return -g_sigma / rho
