@@ -80,6 +80,10 @@ typedef struct {
     const double *freqs;/* [n_freq] frequencies [Hz] */
     int max_src;        /* largest source batch any call will pass */
     int max_rec;        /* largest receiver (or adjoint-source) count */
+    int anisotropy;     /* 0: isotropic, models and gradients [cells]; 1: VTI (Sec. 2:
+                           sigma_h = sigma_xx = sigma_yy on the x and y edges, sigma_v =
+                           sigma_zz on the z edges), models [2][cells] = (rho_h, rho_v)
+                           and gradients [2][cells] = (h, v) (Sec. 3.1, Eq. 15) */
 } csem_opts;
 
 typedef struct {
@@ -90,7 +94,8 @@ typedef struct {
     int nt;                       /* steps per run */
     int precision, kahan, n_freq, max_src, max_rec;
     long long workspace_bytes;    /* device memory the context holds */
-    int transform_block;          /* E snapshots per damped-transform flush (16 or 32) */
+    int transform_block;          /* E snapshots per damped-transform flush (16, 32 or 64) */
+    int anisotropy;               /* as in csem_opts */
 } csem_info;
 
 /* Creates a context on the current device: validates the grid and options,
@@ -106,7 +111,8 @@ void csem_destroy(csem_ctx *ctx);
 int csem_get_info(const csem_ctx *ctx, csem_info *info);
 
 /* Forward modelling (Sec. 2, Eq. 2-6; data d_syn = R u, Sec. 3.1).
- *  rho_dev   [nz][ny][nx] real resistivity [ohm-m], > 0.
+ *  rho_dev   [nz][ny][nx] real resistivity [ohm-m], > 0; for a VTI context
+ *            (anisotropy = 1) [2][nz][ny][nx] = (rho_h, rho_v).
  *  src       src->n unit x/y/z electric dipoles (1 A m), one per batch entry
  *            (1 <= src->n <= max_src); each is injected trilinearly on its
  *            component's lattice at t_{n+1/2}.
@@ -188,10 +194,14 @@ int csem_adjoint_model(csem_ctx *ctx, const void *rho_dev, const csem_points *re
 /* Resistivity gradient (Sec. 3.1 isotropic form, scaled by the cell volume;
  * Sec. 3.5 chain rule).  Edge form -Re sum_s sum_k conj(v)_e E_e dV_e mapped
  * to cells by the transpose of the edge conductivity average
- * sigma_e = sum_c V_c sigma_c / sum_c V_c.
+ * sigma_e = sum_c V_c sigma_c / sum_c V_c.  For a VTI context (Sec. 3.1,
+ * Eq. 15) the x and y edges of a cell give its sigma_h gradient and the z
+ * edges its sigma_v gradient.
  *  Evol_dev, Vvol_dev  [n_src][3][n_freq][vol] from the two runs.
- *  wrt        0: d phi / d sigma_c;  1: d phi / d ln(rho_c) = -sigma_c d phi / d sigma_c.
- *  grad_dev   [nz][ny][nx] real, ACCUMULATED (+=) so batches can be summed.
+ *  wrt        0: d phi / d sigma_c;  1: d phi / d ln(rho_c) = -sigma_c d phi / d sigma_c
+ *             (per part for VTI: -sigma_h d phi / d sigma_h, -sigma_v d phi / d sigma_v).
+ *  grad_dev   [nz][ny][nx] real ([2][nz][ny][nx] = (h, v) for VTI),
+ *             ACCUMULATED (+=) so batches can be summed.
  * Errors: INVALID_ARG, CUDA. */
 int csem_gradient(csem_ctx *ctx, const void *rho_dev, const void *Evol_dev, const void *Vvol_dev,
                   int n_src, int wrt, void *grad_dev, void *stream);

@@ -47,7 +47,7 @@ class CsemForward(torch.autograd.Function):
         (rho,) = ctx.saved_tensors
         eng = ctx.engine
         S = ctx.src.n
-        g = torch.zeros((eng.nz, eng.ny, eng.nx), dtype=eng.real, device=rho.device)
+        g = torch.zeros(eng.model_shape, dtype=eng.real, device=rho.device)
         resid = (-grad_d).to(torch.complex128).contiguous()
         for ci, s0 in enumerate(range(0, S, ctx.chunk)):
             idx = list(range(s0, min(S, s0 + ctx.chunk)))

@@ -84,6 +84,7 @@ struct csem_ctx {
     Axis ax[3];
     double f0, w0, rho_max, dt, safety;
     int nt, precision, kahan, nf, max_src, max_rec;
+    int vti = 0;                         // 1: models [2][cells] = (rho_h, rho_v), gradients (h, v)
     std::vector<double> freqs, a;        // a_k = sqrt(w_k w0)
     std::vector<std::complex<double>> kf, alpha_fwd;
     std::vector<double> wavelet;         // J'(t_{n+1/2})
@@ -546,7 +547,9 @@ csem::GeoD geo(const csem_ctx *c) {
 // the PEC edges zeroed).
 template <typename R>
 int coef_init(csem_ctx *c, const void *rho, cudaStream_t st) {
-    CK(csem::launch_coef_init<R>(geo(c), (const R *)rho, (R *)c->d_cE, 2.0 * c->w0 * c->dt, c->d_bad, st));
+    const long long cells = (long long)c->nx * c->ny * c->nz;
+    const R *rho_h = (const R *)rho, *rho_z = rho_h + (c->vti ? cells : 0);
+    CK(csem::launch_coef_init<R>(geo(c), rho_h, rho_z, (R *)c->d_cE, 2.0 * c->w0 * c->dt, c->d_bad, st));
     if constexpr (sizeof(R) == 4) {
         if (c->d_cEm) CK(csem::launch_mask_coef(step_params<float>(c, false, nullptr), (const float *)c->d_cE, c->d_cEm, st));
     }
@@ -870,6 +873,7 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     if (o->n_freq < 1 || o->n_freq > csem::kMaxFreq || !o->freqs)
         return fail(CSEM_ERR_INVALID_ARG, "n_freq must be in 1..8");
     if (!(o->f0 > 0.0) || !(o->rho_max > 0.0)) return fail(CSEM_ERR_INVALID_ARG, "f0 and rho_max must be > 0");
+    if (o->anisotropy != 0 && o->anisotropy != 1) return fail(CSEM_ERR_INVALID_ARG, "anisotropy must be 0 or 1");
     if (o->max_src < 1 || o->max_rec < 0 || o->max_src > 65535)
         return fail(CSEM_ERR_INVALID_ARG, "max_src must be >= 1, max_rec >= 0");
     for (int f = 0; f < o->n_freq; ++f)
@@ -936,6 +940,7 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     c->kahan = (o->precision == 32 && o->kahan) ? 1 : 0;
     c->max_src = o->max_src;
     c->max_rec = o->max_rec;
+    c->vti = o->anisotropy;
     c->rsize = (c->precision == 32) ? 4 : 8;
     for (int a = 0; a < 3; ++a) cpml_axis(c->ax[a], c->npml, c->dt, vmax, c->f0);
     const int np2 = 2 * c->npml;
@@ -1051,6 +1056,7 @@ int csem_get_info(const csem_ctx *c, csem_info *info) {
     info->precision = c->precision; info->kahan = c->kahan; info->n_freq = c->nf;
     info->max_src = c->max_src; info->max_rec = c->max_rec; info->workspace_bytes = c->bytes;
     info->transform_block = c->M;
+    info->anisotropy = c->vti;
     return CSEM_OK;
 }
 
@@ -1107,11 +1113,11 @@ int csem_gradient(csem_ctx *c, const void *rho_dev, const void *Evol_dev, const 
     cudaStream_t st = (cudaStream_t)stream;
     if (c->precision == 32)
         CK(csem::launch_gradient<float>(geo(c), (const float *)rho_dev, (const float2 *)Evol_dev,
-                                        (const float2 *)Vvol_dev, n_src, c->nf, wrt, (float *)c->d_edge,
+                                        (const float2 *)Vvol_dev, n_src, c->nf, wrt, c->vti != 0, (float *)c->d_edge,
                                         (float *)grad_dev, st));
     else
         CK(csem::launch_gradient<double>(geo(c), (const double *)rho_dev, (const double2 *)Evol_dev,
-                                         (const double2 *)Vvol_dev, n_src, c->nf, wrt, (double *)c->d_edge,
+                                         (const double2 *)Vvol_dev, n_src, c->nf, wrt, c->vti != 0, (double *)c->d_edge,
                                          (double *)grad_dev, st));
     return CSEM_OK;
 }

@@ -176,7 +176,9 @@ struct GeoD {                      // double-precision geometry for set-up and g
     const double *hx, *hy, *hz;    // primal widths [n]
 };
 template <typename R>
-cudaError_t launch_coef_init(const GeoD &g, const R *rho, R *cE, double two_w0_dt, int *bad_flag, cudaStream_t st);
+// dt/eps on every edge from the cell resistivity (rho_z on the z edges: rho_v of a VTI medium, else rho)
+cudaError_t launch_coef_init(const GeoD &g, const R *rho, const R *rho_z, R *cE, double two_w0_dt, int *bad_flag,
+                             cudaStream_t st);
 template <typename R>
 cudaError_t launch_finalize_volume(typename C2<R>::T *acc, const typename C2<R>::T *comp, long long vol, int S,
                                    int nf, const double2 *alpha, cudaStream_t st);
@@ -186,7 +188,7 @@ cudaError_t launch_adjoint_coef(const double *resid, double *coef, int S, int n_
                                 const double2 *kf, double inv_dt, cudaStream_t st);
 template <typename R>
 cudaError_t launch_gradient(const GeoD &g, const R *rho, const typename C2<R>::T *E, const typename C2<R>::T *V,
-                            int S, int nf, int wrt, R *edge_scratch, R *grad, cudaStream_t st);
+                            int S, int nf, int wrt, bool vti, R *edge_scratch, R *grad, cudaStream_t st);
 cudaError_t launch_scatter_int2(int2 *dst, const long long *pos, const int2 *val, int n, cudaStream_t st);
 cudaError_t launch_misfit(int n, const double *d_obs, const double *d_syn, const double *w, double *resid,
                           double *phi, cudaStream_t st);

@@ -8,8 +8,8 @@ namespace csem {
 // sigma_e = sum_c V_c / rho_c / sum_c V_c over the (up to four) cells sharing e.
 // ---------------------------------------------------------------------------
 template <typename R>
-__global__ void k_coef_init(const GeoD g, const R *__restrict__ rho, R *__restrict__ cE, double two_w0_dt,
-                            int *bad) {
+__global__ void k_coef_init(const GeoD g, const R *__restrict__ rho, const R *__restrict__ rho_z,
+                            R *__restrict__ cE, double two_w0_dt, int *bad) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
     if (t >= g.vol) return;
@@ -31,7 +31,7 @@ __global__ void k_coef_init(const GeoD g, const R *__restrict__ rho, R *__restri
                 for (int ii = i0; ii <= i1; ++ii) {
                     if (ii < 0 || jj < 0 || kk < 0 || ii >= g.nx || jj >= g.ny || kk >= g.nz) continue;
                     const double V = g.hx[ii] * g.hy[jj] * g.hz[kk];
-                    const double rc = (double)rho[((long long)kk * g.ny + jj) * g.nx + ii];
+                    const double rc = (double)(c == 2 ? rho_z : rho)[((long long)kk * g.ny + jj) * g.nx + ii];
                     if (!(rc > 0.0) || !isfinite(rc)) atomicOr(bad, 1);
                     num += V / rc;
                     den += V;
@@ -42,9 +42,10 @@ __global__ void k_coef_init(const GeoD g, const R *__restrict__ rho, R *__restri
 }
 
 template <typename R>
-cudaError_t launch_coef_init(const GeoD &g, const R *rho, R *cE, double two_w0_dt, int *bad, cudaStream_t st) {
+cudaError_t launch_coef_init(const GeoD &g, const R *rho, const R *rho_z, R *cE, double two_w0_dt, int *bad,
+                             cudaStream_t st) {
     dim3 grid((unsigned)((g.vol + 255) / 256), 3);
-    k_coef_init<R><<<grid, 256, 0, st>>>(g, rho, cE, two_w0_dt, bad);
+    k_coef_init<R><<<grid, 256, 0, st>>>(g, rho, rho_z, cE, two_w0_dt, bad);
     g_launches++;
     return cudaGetLastError();
 }
@@ -141,8 +142,9 @@ __global__ void k_grad_edge(const typename C2<R>::T *E, const typename C2<R>::T 
     pe[(long long)c * vol + t] = (R)(-acc);
 }
 
+// rho_v, grad_v non-null: VTI, the x and y edges feed grad (sigma_h), the z edges grad_v (sigma_v)
 template <typename R>
-__global__ void k_grad_cell(const GeoD g, const R *pe, const R *rho, int wrt, R *grad) {
+__global__ void k_grad_cell(const GeoD g, const R *pe, const R *rho, const R *rho_v, int wrt, R *grad, R *grad_v) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long cells = (long long)g.nx * g.ny * g.nz;
     if (t >= cells) return;
@@ -152,26 +154,34 @@ __global__ void k_grad_cell(const GeoD g, const R *pe, const R *rho, int wrt, R 
     const int k = (int)(r / g.ny);
     const R *px = pe, *py = pe + g.vol, *pz = pe + 2 * g.vol;
     auto at = [&](int ii, int jj, int kk) { return ((long long)kk * g.NY + jj) * g.pitch + ii; };
-    double sum = 0.0;
+    double sh = 0.0, sv = 0.0;
     for (int d1 = 0; d1 < 2; ++d1)
         for (int d0 = 0; d0 < 2; ++d0) {
-            sum += (double)px[at(i, j + d0, k + d1)];
-            sum += (double)py[at(i + d0, j, k + d1)];
-            sum += (double)pz[at(i + d0, j + d1, k)];
+            sh += (double)px[at(i, j + d0, k + d1)];
+            sh += (double)py[at(i + d0, j, k + d1)];
+            sv += (double)pz[at(i + d0, j + d1, k)];
         }
     const double V = g.hx[i] * g.hy[j] * g.hz[k];
-    double gs = 0.25 * V * sum;                 // d phi / d sigma_c
+    if (grad_v) {
+        double gh = 0.25 * V * sh, gv = 0.25 * V * sv;   // d phi / d sigma_h, d phi / d sigma_v
+        if (wrt == 1) { gh = -gh / (double)rho[t]; gv = -gv / (double)rho_v[t]; }
+        grad[t] += (R)gh;
+        grad_v[t] += (R)gv;
+        return;
+    }
+    double gs = 0.25 * V * (sh + sv);           // d phi / d sigma_c
     if (wrt == 1) gs = -gs / (double)rho[t];    // d phi / d ln rho_c = -sigma_c d phi / d sigma_c
     grad[t] += (R)gs;
 }
 
 template <typename R>
 cudaError_t launch_gradient(const GeoD &g, const R *rho, const typename C2<R>::T *E, const typename C2<R>::T *V,
-                            int S, int nf, int wrt, R *edge_scratch, R *grad, cudaStream_t st) {
+                            int S, int nf, int wrt, bool vti, R *edge_scratch, R *grad, cudaStream_t st) {
     dim3 ge((unsigned)((g.vol + 255) / 256), 3);
     k_grad_edge<R><<<ge, 256, 0, st>>>(E, V, g.vol, S, nf, edge_scratch);
     const long long cells = (long long)g.nx * g.ny * g.nz;
-    k_grad_cell<R><<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(g, edge_scratch, rho, wrt, grad);
+    k_grad_cell<R><<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(g, edge_scratch, rho, vti ? rho + cells : nullptr,
+                                                                      wrt, grad, vti ? grad + cells : nullptr);
     g_launches += 2;
     return cudaGetLastError();
 }
@@ -437,15 +447,17 @@ cudaError_t launch_scatter_int2(int2 *dst, const long long *pos, const int2 *val
     return cudaGetLastError();
 }
 
-template cudaError_t launch_coef_init<float>(const GeoD &, const float *, float *, double, int *, cudaStream_t);
-template cudaError_t launch_coef_init<double>(const GeoD &, const double *, double *, double, int *, cudaStream_t);
+template cudaError_t launch_coef_init<float>(const GeoD &, const float *, const float *, float *, double, int *,
+                                             cudaStream_t);
+template cudaError_t launch_coef_init<double>(const GeoD &, const double *, const double *, double *, double, int *,
+                                              cudaStream_t);
 template cudaError_t launch_finalize_volume<float>(float2 *, const float2 *, long long, int, int, const double2 *,
                                                    cudaStream_t);
 template cudaError_t launch_finalize_volume<double>(double2 *, const double2 *, long long, int, int,
                                                     const double2 *, cudaStream_t);
 template cudaError_t launch_gradient<float>(const GeoD &, const float *, const float2 *, const float2 *, int, int,
-                                            int, float *, float *, cudaStream_t);
+                                            int, bool, float *, float *, cudaStream_t);
 template cudaError_t launch_gradient<double>(const GeoD &, const double *, const double2 *, const double2 *, int,
-                                             int, int, double *, double *, cudaStream_t);
+                                             int, int, bool, double *, double *, cudaStream_t);
 
 }  // namespace csem

@@ -38,22 +38,27 @@ def _ptr(t: Optional[torch.Tensor]):
 
 
 class Engine:
-    """One context: grid, frequencies, dt/nt, precision, batch capacity."""
+    """One context: grid, frequencies, dt/nt, precision, batch capacity.
+
+    vti=True: a VTI medium (Sec. 2); models are (2, nz, ny, nx) = (rho_h, rho_v) and
+    gradients (2, nz, ny, nx) = (h, v) (Sec. 3.1, Eq. 15)."""
 
     def __init__(self, xn, yn, zn, npml, freqs, f0=1.0, rho_max=1.0, precision=32, kahan=1,
-                 max_src=1, max_rec=0, nt=0, dt=0.0, device=None, autotune=True):
+                 max_src=1, max_rec=0, nt=0, dt=0.0, device=None, autotune=True, vti=False):
         if not torch.cuda.is_available():
             raise RuntimeError("the CSEM engine needs a CUDA device")
         self.device = torch.device(device or "cuda")
         with torch.cuda.device(self.device):
             self.ctx = _capi.create(xn, yn, zn, npml, freqs, f0=f0, rho_max=rho_max, dt=dt, nt=nt,
-                                    precision=precision, kahan=kahan, max_src=max_src, max_rec=max_rec)
+                                    precision=precision, kahan=kahan, max_src=max_src, max_rec=max_rec,
+                                    anisotropy=1 if vti else 0)
         info = _capi.get_info(self.ctx)
         self.info = info
         self.nx, self.ny, self.nz = info.nx, info.ny, info.nz
         self.pitch, self.vol = info.pitch, info.vol_elems
         self.dt, self.nt = info.dt, info.nt
         self.precision = precision
+        self.vti = bool(vti)
         self.freqs = np.asarray(freqs, np.float64)
         self.nf = self.freqs.size
         self.f0 = f0
@@ -84,8 +89,24 @@ class Engine:
     def volume_shape(self, n_src):
         return (n_src, 3, self.nf, self.nz + 1, self.ny + 1, self.pitch)
 
+    @property
+    def model_shape(self):
+        """Shape of a model or gradient: (nz, ny, nx), or (2, nz, ny, nx) for VTI."""
+        return ((2,) if self.vti else ()) + (self.nz, self.ny, self.nx)
+
+    def _model(self, rho):
+        """The model a call passes to the library: on this device, contiguous, of model_shape."""
+        same_device = torch.is_tensor(rho) and rho.is_cuda and \
+            (self.device.index is None or rho.device.index == self.device.index)
+        if not same_device or tuple(rho.shape) != self.model_shape or rho.dtype != self.real \
+                or not rho.is_contiguous():
+            raise ValueError(f"expected a contiguous {self.real} model of shape {self.model_shape} on {self.device}")
+        return rho
+
     def model_tensor(self, rho) -> torch.Tensor:
         t = torch.as_tensor(np.asarray(rho), dtype=self.real) if not torch.is_tensor(rho) else rho.to(self.real)
+        if tuple(t.shape) != self.model_shape:
+            raise ValueError(f"model of shape {tuple(t.shape)}, expected {self.model_shape}")
         return t.to(self.device).contiguous()
 
     # -- C-ABI calls ---------------------------------------------------------
@@ -98,7 +119,8 @@ class Engine:
             tr = torch.zeros((S, rec.n, self.nt), dtype=torch.float64, device=self.device)
             _capi.set_trace(self.ctx, _ptr(tr))
         try:
-            _capi.fwd_model(self.ctx, _ptr(rho), src, rec, _ptr(d) if rec.n else None, _ptr(vol), _stream())
+            _capi.fwd_model(self.ctx, _ptr(self._model(rho)), src, rec, _ptr(d) if rec.n else None, _ptr(vol),
+                            _stream())
         finally:
             if trace:
                 _capi.set_trace(self.ctx, None)
@@ -122,14 +144,19 @@ class Engine:
         S = resid.shape[0]
         assert resid.dtype == torch.complex128 and resid.shape[1:] == (rec.n, self.nf)
         vol = torch.empty(self.volume_shape(S), dtype=self.cplx, device=self.device)
-        _capi.adjoint_model(self.ctx, _ptr(rho), rec, S, _ptr(resid.contiguous()), _ptr(basis), _ptr(vol), _stream())
+        _capi.adjoint_model(self.ctx, _ptr(self._model(rho)), rec, S, _ptr(resid.contiguous()), _ptr(basis),
+                            _ptr(vol), _stream())
         return vol
 
     def gradient(self, rho, Evol, Vvol, wrt="lnrho", out=None):
         if out is None:
-            out = torch.zeros((self.nz, self.ny, self.nx), dtype=self.real, device=self.device)
-        _capi.gradient(self.ctx, _ptr(rho), _ptr(Evol), _ptr(Vvol), Evol.shape[0], 1 if wrt == "lnrho" else 0,
-                       _ptr(out), _stream())
+            out = torch.zeros(self.model_shape, dtype=self.real, device=self.device)
+        self._model(out)
+        vs = self.volume_shape(Evol.shape[0])
+        if tuple(Evol.shape) != vs or tuple(Vvol.shape) != vs:
+            raise ValueError(f"volumes of shape {vs} expected")
+        _capi.gradient(self.ctx, _ptr(self._model(rho)), _ptr(Evol), _ptr(Vvol), Evol.shape[0],
+                       1 if wrt == "lnrho" else 0, _ptr(out), _stream())
         return out
 
     def check(self):

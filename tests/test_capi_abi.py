@@ -52,3 +52,4 @@ def test_struct_layouts_match_header_sizes():
     assert ctypes.sizeof(_capi.Grid) == 48
     assert ctypes.sizeof(_capi.PointsC) == 40
     assert ctypes.sizeof(_capi.Info) == 80
+    assert ctypes.sizeof(_capi.Opts) == 80
