@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="thin_reservoir")
+    ap.add_argument("--vti", action="store_true", help="VTI medium: models (rho_h, rho_v), split gradient")
     ap.add_argument("--cpu-steps", type=int, default=2000, help="time steps in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -111,10 +112,17 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
-def make_workload(name, rank, world):
+def make_workload(name, rank, world, vti=False):
     from paper_2211_16665_gb300 import dist as D
     from paper_2211_16665_gb300 import workloads as W
     wl = W.ALL[name]()
+    if vti:
+        # VTI medium (Sec. 2): rho_v = 2 rho_h below the water, capped at the CFL resistivity
+        water = wl.rho.min()
+        def split(r):
+            rv = np.where(r > water, np.minimum(2.0 * r, wl.rho_max), r)
+            return np.stack([r, rv])
+        wl.rho, wl.rho_true = split(wl.rho), split(wl.rho_true)
     if world > 1:
         # weak scaling: a towline of `world` sources on the same model, one share per rank
         line = D.towline(wl.src, world * wl.src.n)
@@ -214,8 +222,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    wl = make_workload(args.workload, rank, world)
-    eng = Engine.from_workload(wl)
+    wl = make_workload(args.workload, rank, world, vti=args.vti)
+    eng = Engine.from_workload(wl, vti=args.vti)
     S = wl.src.n
     rho = eng.model_tensor(wl.rho)
     rho_true = eng.model_tensor(wl.rho_true)
@@ -323,7 +331,8 @@ def run_ours(args):
                           "dt": eng.dt, "n_src_per_gpu": S, "n_rec": wl.rec.n, "freqs_hz": list(map(float, wl.freqs)),
                           "kahan": bool(eng.info.kahan), "launch": eng.launch_config(), "l2": "inputs larger than L2 (each step streams "
                           f"{2 * 3 * eng.nf * eng.vol * 8 * S * (2 if eng.info.kahan else 1) / 2**20:.0f} MiB of "
-                          "transform volumes)", "parallelism": f"sources sharded, dp{world}"},
+                          "transform volumes)", "parallelism": f"sources sharded, dp{world}",
+                          "medium": "vti" if args.vti else "isotropic"},
                "grad_s_per_source": round(ms / 1e3 / S, 4),
                "basis_fit": fit,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
@@ -341,7 +350,7 @@ def run_reference(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return
     from oracle import fdtd
-    wl = make_workload(args.workload, 0, 1)
+    wl = make_workload(args.workload, 0, 1, vti=args.vti)
     pb = fdtd.problem_from_workload(wl)
     src = wl.src.subset([0])
     # calibrate: size each step so that warmup + steps take ~2.5 minutes
@@ -361,7 +370,7 @@ def run_reference(args):
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * t, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": wl.name, "cells": wl.cells, "grid": [wl.nx, wl.ny, wl.nz], "nt": pb.nt,
-                      "nt_sample": nt_s},
+                      "nt_sample": nt_s, "medium": "vti" if args.vti else "isotropic"},
            "cpu_baseline": {"value": round(value, 5), "unit": "Gcell-updates/s", "cores": cores, "kind": "oracle",
                             "sample": f"{nt_s} of {pb.nt} steps of one forward run with the volumetric transform"},
            "e2e": {"value": round(value, 5), "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0,
