@@ -58,6 +58,7 @@ class Engine:
         self.pitch, self.vol = info.pitch, info.vol_elems
         self.dt, self.nt = info.dt, info.nt
         self.precision = precision
+        self.rho_max = float(rho_max)
         self.vti = bool(vti)
         self.freqs = np.asarray(freqs, np.float64)
         self.nf = self.freqs.size
