@@ -12,6 +12,9 @@ adjoint source estimation"):
   Sec. 3.2, Eq. 14 conj(v) from the same engine with conjugated residual sources
   Sec. 3.3         adjoint time series from the basis functions
   Sec. 3.5         m = ln(rho): dphi/dm = -(1/rho) dphi/dsigma
+  Appendix          time-domain adjoint: the same scheme run in reversed time,
+                   driven at the receivers by the transpose of the data functional,
+                   and the gradient as the time correlation of the two fields
   Sec. 2, Sec. 3.1 Eq. 15  VTI medium: sigma_h = sigma_xx = sigma_yy on the x and y edges,
                    sigma_v = sigma_zz on the z edges; dphi/dsigma_h collects the x and y
                    edges, dphi/dsigma_v the z edges
@@ -502,9 +505,14 @@ def gradient(pb: Problem, rho, Evol, Vvol, wrt="lnrho"):
     VTI (Sec. 3.1, Eq. 15): dphi/dsigma_h collects the x and y edges of the cell,
     dphi/dsigma_v its z edges; the result is (2, nz, ny, nx) = (h, v).
     """
-    xn, yn, zn = pb.xn, pb.yn, pb.zn
-    dV = edge_dual_volumes(xn, yn, zn)
+    dV = edge_dual_volumes(pb.xn, pb.yn, pb.zn)
     g_edge = -np.real(np.sum(Vvol * Evol, axis=(0, 2))) * dV         # [3, nodes]
+    return _edge_to_cells(pb, np.asarray(rho, float), g_edge, wrt)
+
+
+def _edge_to_cells(pb: Problem, rho, g_edge, wrt):
+    """dphi/dsigma per edge [3, nodes] -> per cell (h, v parts for VTI), in sigma or ln rho."""
+    xn, yn, zn = pb.xn, pb.yn, pb.zn
     V = cell_volumes(xn, yn, zn)
     den = _edge_sums(V)
     ratio = np.zeros_like(g_edge)
@@ -525,7 +533,6 @@ def gradient(pb: Problem, rho, Evol, Vvol, wrt="lnrho"):
     for dj in (0, 1):
         for di in (0, 1):
             acc_v += gz[0:nz, dj:dj + ny, di:di + nx]              # Ez(i+di, j+dj, k)
-    rho = np.asarray(rho, float)
     if is_vti(rho):
         g_sigma = np.stack([acc_h * V, acc_v * V])
     else:
@@ -533,3 +540,45 @@ def gradient(pb: Problem, rho, Evol, Vvol, wrt="lnrho"):
     if wrt == "sigma":
         return g_sigma
     return -g_sigma / rho
+
+def gradient_time_domain(pb: Problem, rho, src, rec, resid, wrt="lnrho", wavelet=None):
+    """Cell gradient by the appendix's time-domain adjoint (full storage; small grids).
+
+    With d_k = norm_k sum_n w_{k,n} tr^n (tr^n: E^n sampled at the receivers,
+    norm_k = k_k / What_k) the data functional's derivative is
+    d phi / d tr^n = -q^n, q^n = Re sum_k conj(r_k) norm_k w_{k,n}.  The adjoint of
+    the leap-frog scheme is the same scheme run in reversed time, m = nt - 1 - n,
+    driven by q^{nt-1-m} injected at the receivers like a source; with its field
+    Et^m the gradient on each edge is
+        dphi/dsigma_e = -1 / (2 w0 dt) sum_n dV_e Et_e^{nt-1-n} (E_e^{n+1} - E_e^n)
+    (Appendix: dphi/dsigma = -(1 / 2 w0) int Et . d_t E dt', sigma = 2 w0 eps),
+    mapped to cells like the frequency-domain gradient.  resid: r [n_src, n_rec, n_freq].
+    """
+    st = Stepper(pb, rho)
+    N, nt = pb.N, pb.nt
+    wav = pb.impulse() if wavelet is None else np.asarray(wavelet, float)
+    norm = pb.k / pb.wavelet_spectrum(wav)
+    W = pb.dft_weights()
+    dV = edge_dual_volumes(pb.xn, pb.yn, pb.zn).reshape(-1)
+    rinj = []
+    for r in range(rec.n):
+        rinj += point_taps(pb, rec, r, scale_by_dV=st.dV, tag=r)
+    corr = np.zeros(3 * N)
+    for s in range(src.n):
+        fields, psi = st.new_state()
+        inj = point_taps(pb, src, s, scale_by_dV=st.dV, tag=0)
+        E = np.zeros((nt + 1, 3 * N))
+        for n in range(nt):
+            st.run(fields, psi, n, n + 1, inj=inj, series=wav[None, :])
+            E[n + 1] = fields[:3 * N]
+        q = np.real((np.conj(resid[s]) * norm[None, :]) @ W.T)          # [n_rec, nt]
+        series = np.ascontiguousarray(q[:, ::-1])
+        fa, pa = st.new_state()
+        Et = np.zeros(3 * N)
+        for m in range(nt):
+            n = nt - 1 - m
+            corr += Et * (E[n + 1] - E[n])                               # Et = adjoint field after m steps
+            st.run(fa, pa, m, m + 1, inj=rinj, series=series)
+            Et = fa[:3 * N].copy()
+    g_edge = (-(1.0 / (2 * omega0(pb.f0) * pb.dt)) * corr * dV).reshape((3,) + pb.shape_nodes)
+    return _edge_to_cells(pb, np.asarray(rho, float), g_edge, wrt)
