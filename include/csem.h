@@ -206,6 +206,47 @@ int csem_adjoint_model(csem_ctx *ctx, const void *rho_dev, const csem_points *re
 int csem_gradient(csem_ctx *ctx, const void *rho_dev, const void *Evol_dev, const void *Vvol_dev,
                   int n_src, int wrt, void *grad_dev, void *stream);
 
+/* Time-domain adjoint gradient (the paper's appendix): the exact gradient of
+ * the discrete scheme, a second route to the one above that needs no basis
+ * estimate.  The adjoint of the leap-frog scheme is the same scheme run in
+ * reversed fictitious time, m = nt - 1 - n, driven at the receivers like a
+ * source by q^{nt-1-m}, q^n = Re sum_k conj(r_k) alpha_k w_{k,n}
+ * (alpha_k = k_k / What_k the forward normalisation, w_{k,n} the transform
+ * weights exp((-1+i) a_k n dt)); with E^n the forward E after n steps and
+ * Et^m the adjoint E after m steps,
+ *     dphi/dsigma_e = -1 / (2 w0 dt) sum_{m<nt} dV_e Et_e^m (E_e^{nt-m} - E_e^{nt-1-m})
+ * (appendix: dphi/dsigma = -(1 / 2 w0) int Et . dE/dt' dt'), mapped to cells
+ * and to ln rho as in csem_gradient.  Because the forward field is consumed
+ * backwards in time, the forward run is replayed in segments of `segment`
+ * steps from checkpoints of its state (H, the E snapshot, the CPML memory)
+ * kept by a first pass; each replayed segment's E snapshots sit in a ring in
+ * the workspace while the adjoint run advances through them.  Forward steps:
+ * (ceil(nt / segment) - 1) * segment + nt; adjoint steps: nt.
+ *
+ * csem_td_plan: workspace for n_src sources and n_rec receivers.  In:
+ *  *segment_out > 0 asks for that segment length (even); else the call picks
+ *  the length with the least replayed steps whose workspace fits budget_bytes
+ *  (budget_bytes <= 0: the smallest workspace).  Out: *segment_out, and
+ *  *bytes_out the workspace size.  The size depends on the launch
+ *  configuration in force (csem_autotune, csem_set_launch): plan after it.
+ *  Errors: INVALID_ARG, OOM (no plan fits the budget).
+ * csem_gradient_td:
+ *  rho_dev    as in csem_fwd_model.
+ *  src, rec   sources (1..max_src) and receivers (1..max_rec) of the residual.
+ *  resid_dev  [src->n][rec->n][n_freq] complex128 weighted residual, as for
+ *             csem_adjoint_model (the data of the same model and sources).
+ *  segment    from csem_td_plan (even, >= 2).
+ *  wrt, grad_dev  as in csem_gradient (ACCUMULATED, += ; summed over sources).
+ *  work_dev   device workspace of work_bytes >= the plan's bytes, 256-byte
+ *             aligned, owned by the caller; its contents are scratch.
+ * Overwrites the context's field state.
+ * Errors: INVALID_ARG (also a workspace too small), OUT_OF_DOMAIN, CUDA. */
+int csem_td_plan(const csem_ctx *ctx, int n_src, int n_rec, long long budget_bytes, int *segment_out,
+                 long long *bytes_out);
+int csem_gradient_td(csem_ctx *ctx, const void *rho_dev, const csem_points *src, const csem_points *rec,
+                     const double *resid_dev, int segment, int wrt, void *grad_dev, void *work_dev,
+                     long long work_bytes, void *stream);
+
 /* Picks the launch shape of the H and E stepping kernels -- z planes per
  * thread (1, 2, 4, 8), the register budget (4, 6 or 8 resident 256-thread
  * blocks per SM), and for FP32 one or four cells per thread along x, the

@@ -65,6 +65,10 @@ SIGNATURES = {
     "csem_misfit": (ctypes.c_int, [ctypes.c_int, _V, _V, _V, _V, _V, _V]),
     "csem_adjoint_model": (ctypes.c_int, [_V, _V, ctypes.POINTER(PointsC), ctypes.c_int, _V, _V, _V, _V]),
     "csem_gradient": (ctypes.c_int, [_V, _V, _V, _V, ctypes.c_int, ctypes.c_int, _V, _V]),
+    "csem_td_plan": (ctypes.c_int, [_V, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _I,
+                                    ctypes.POINTER(ctypes.c_longlong)]),
+    "csem_gradient_td": (ctypes.c_int, [_V, _V, ctypes.POINTER(PointsC), ctypes.POINTER(PointsC), _V, ctypes.c_int,
+                                        ctypes.c_int, _V, _V, ctypes.c_longlong, _V]),
     "csem_autotune": (ctypes.c_int, [_V, ctypes.c_int, _I, _V]),
     "csem_set_launch": (ctypes.c_int, [_V, _I]),
     "csem_set_wavelet": (ctypes.c_int, [_V, _D]),
@@ -177,6 +181,21 @@ def adjoint_model(ctx, rho_ptr, rec, n_src, resid_ptr, basis_ptr, vvol_ptr, stre
 
 def gradient(ctx, rho_ptr, evol_ptr, vvol_ptr, n_src, wrt, grad_ptr, stream):
     _check(lib().csem_gradient(ctx, rho_ptr, evol_ptr, vvol_ptr, int(n_src), int(wrt), grad_ptr, stream))
+
+
+def td_plan(ctx, n_src, n_rec, budget_bytes=0, segment=0):
+    """(segment, workspace bytes) of the time-domain adjoint gradient."""
+    seg = ctypes.c_int(int(segment))
+    nb = ctypes.c_longlong(0)
+    _check(lib().csem_td_plan(ctx, int(n_src), int(n_rec), int(budget_bytes), ctypes.byref(seg), ctypes.byref(nb)))
+    return seg.value, nb.value
+
+
+def gradient_td(ctx, rho_ptr, src, rec, resid_ptr, segment, wrt, grad_ptr, work_ptr, work_bytes, stream):
+    keep = []
+    _check(lib().csem_gradient_td(ctx, rho_ptr, ctypes.byref(make_points(src, keep)),
+                                  ctypes.byref(make_points(rec, keep)), resid_ptr, int(segment), int(wrt), grad_ptr,
+                                  work_ptr, int(work_bytes), stream))
 
 
 def autotune(ctx, n_src, stream):

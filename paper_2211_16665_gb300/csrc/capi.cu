@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -13,6 +14,7 @@
 
 #include "../../include/csem.h"
 #include "csem_internal.cuh"
+#include "csem_td.cuh"
 
 using csem::C2;
 using csem::Tap;
@@ -467,6 +469,46 @@ cudaError_t emit_steps(csem_ctx *c, int S, bool vol, bool kahan, const csem::Ste
     return e;
 }
 
+// Captures one chunk of launches (emit on the capture stream) into a graph and
+// returns the executable kept for key (updated in place when only parameters
+// changed) and the number of kernels one replay launches.
+template <typename Emit>
+int chunk_graph(csem_ctx *c, const int key[8], Emit &&emit, cudaGraphExec_t *out, long long *per_chunk) {
+    cudaGraph_t g = nullptr;
+    const long long before = csem::g_launches.load();   // captured kernels are counted per replay
+    CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = emit(c->cap);
+    cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
+    if (le != cudaSuccess) return fail(CSEM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(le));
+    CK(ee);
+    cudaGraphExec_t exec = nullptr;
+    for (auto &slot : c->graphs)
+        if (std::equal(key, key + 8, slot.key)) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(slot.exec, g, &info) == cudaSuccess) exec = slot.exec;
+            else {
+                cudaGetLastError();
+                CK(cudaDeviceSynchronize());
+                cudaGraphExecDestroy(slot.exec);
+                CK(cudaGraphInstantiate(&slot.exec, g, 0));
+                exec = slot.exec;
+            }
+            break;
+        }
+    if (!exec) {
+        csem_ctx::GraphSlot slot;
+        std::copy(key, key + 8, slot.key);
+        CK(cudaGraphInstantiate(&slot.exec, g, 0));
+        c->graphs.push_back(slot);
+        exec = slot.exec;
+    }
+    cudaGraphDestroy(g);
+    *per_chunk = csem::g_launches.load() - before;
+    csem::g_launches -= *per_chunk;
+    *out = exec;
+    return CSEM_OK;
+}
+
 // nt steps of H, E and injection; after every M steps the finished snapshots are
 // transformed (and the receivers sampled).  Full chunks of kChunk steps replay
 // one captured graph; the remainder and the final partial block are launched
@@ -484,39 +526,14 @@ int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const 
                             (int)sizeof(R), ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
                             ((((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e) * 25 +
                              c->TMA_h * 5 + c->TMA_e) * 4 + c->LEAN_h * 2 + c->LEAN_e};
-        cudaGraph_t g = nullptr;
-        const long long before = csem::g_launches.load();   // captured kernels are counted per replay
-        CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-        cudaError_t le = tap_prep<R>(c, p, S, kChunk, c->cap);
-        if (le == cudaSuccess) le = emit_steps<R>(c, S, vol, kahan, p, q, kChunk, overlap, !overlap, c->cap);
-        if (le == cudaSuccess) le = csem::launch_advance(c->d_step, kChunk, c->cap);
-        cudaError_t ee = cudaStreamEndCapture(c->cap, &g);
-        if (le != cudaSuccess) return fail(CSEM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(le));
-        CK(ee);
         cudaGraphExec_t exec = nullptr;
-        for (auto &slot : c->graphs)
-            if (std::equal(key, key + 8, slot.key)) {
-                cudaGraphExecUpdateResultInfo info;
-                if (cudaGraphExecUpdate(slot.exec, g, &info) == cudaSuccess) exec = slot.exec;
-                else {
-                    cudaGetLastError();
-                    CK(cudaDeviceSynchronize());
-                    cudaGraphExecDestroy(slot.exec);
-                    CK(cudaGraphInstantiate(&slot.exec, g, 0));
-                    exec = slot.exec;
-                }
-                break;
-            }
-        if (!exec) {
-            csem_ctx::GraphSlot slot;
-            std::copy(key, key + 8, slot.key);
-            CK(cudaGraphInstantiate(&slot.exec, g, 0));
-            c->graphs.push_back(slot);
-            exec = slot.exec;
-        }
-        cudaGraphDestroy(g);
-        const long long per_chunk = csem::g_launches.load() - before;
-        csem::g_launches -= per_chunk;
+        long long per_chunk = 0;
+        TRY(chunk_graph(c, key, [&](cudaStream_t cs) {
+            cudaError_t le = tap_prep<R>(c, p, S, kChunk, cs);
+            if (le == cudaSuccess) le = emit_steps<R>(c, S, vol, kahan, p, q, kChunk, overlap, !overlap, cs);
+            if (le == cudaSuccess) le = csem::launch_advance(c->d_step, kChunk, cs);
+            return le;
+        }, &exec, &per_chunk));
         for (int ch = 0; ch < full; ++ch) {
             CK(cudaGraphLaunch(exec, st));
             csem::g_launches += per_chunk;
@@ -556,9 +573,21 @@ int coef_init(csem_ctx *c, const void *rho, cudaStream_t st) {
     return CSEM_OK;
 }
 
+// Device arrays that describe one injection (the context's own, or a second set).
+struct InjDst {
+    Tap *itaps;
+    int2 *colmap;
+    unsigned char *tflag;
+    int *tapk;
+};
+
 // Sorts each source's injection taps by lattice column (then index) and sets the
 // device column map: colmap[s*stride + col] = (first tap, count), zero elsewhere.
-int upload_injection(csem_ctx *c, std::vector<Tap> &taps, int n_lists, int per_list, bool shared, cudaStream_t st) {
+// dst: where to put the taps, column map, tile flags and tap planes (NULL: the context's).
+int upload_injection(csem_ctx *c, std::vector<Tap> &taps, int n_lists, int per_list, bool shared, cudaStream_t st,
+                     const InjDst *dst = nullptr) {
+    const InjDst own{c->d_itaps, c->d_colmap, c->d_tflag, c->d_tapk};
+    const InjDst &d = dst ? *dst : own;
     const long long plane = c->plane;
     std::vector<long long> pos;
     std::vector<int2> val;
@@ -577,11 +606,11 @@ int upload_injection(csem_ctx *c, std::vector<Tap> &taps, int n_lists, int per_l
             val.back().y += 1;
         }
     }
-    CK(cudaMemcpyAsync(c->d_itaps, taps.data(), taps.size() * sizeof(Tap), cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(c->d_colmap, 0, (size_t)(shared ? 1 : n_lists) * plane * sizeof(int2), st));
+    CK(cudaMemcpyAsync(d.itaps, taps.data(), taps.size() * sizeof(Tap), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(d.colmap, 0, (size_t)(shared ? 1 : n_lists) * plane * sizeof(int2), st));
     CK(cudaMemcpyAsync(c->d_cpos, pos.data(), pos.size() * sizeof(long long), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(c->d_cval, val.data(), val.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
-    CK(csem::launch_scatter_int2(c->d_colmap, c->d_cpos, c->d_cval, (int)pos.size(), st));
+    CK(csem::launch_scatter_int2(d.colmap, c->d_cpos, c->d_cval, (int)pos.size(), st));
     {   // tile flags: rows and 32-column segments of the cell range that hold a tap
         const int nl = shared ? 1 : n_lists;
         std::vector<unsigned char> fl((size_t)nl * c->ny * c->nseg, 0);
@@ -591,15 +620,17 @@ int upload_injection(csem_ctx *c, std::vector<Tap> &taps, int n_lists, int per_l
                 const int j = (int)(col / c->pitch), i = (int)(col % c->pitch);
                 if (j < c->ny && i < c->nx) fl[((size_t)(shared ? 0 : s) * c->ny + j) * c->nseg + i / 32] = 1;
             }
-        CK(cudaMemcpyAsync(c->d_tflag, fl.data(), fl.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d.tflag, fl.data(), fl.size(), cudaMemcpyHostToDevice, st));
     }
-    if (c->d_tapk) {   // plane and component of each tap, for the lean E kernel
+    if (d.tapk) {   // plane and component of each tap, for the lean E kernel
         std::vector<int> tk(taps.size());
         for (size_t u = 0; u < taps.size(); ++u) tk[u] = (int)(taps[u].idx / plane) * 4 + taps[u].comp;
-        CK(cudaMemcpyAsync(c->d_tapk, tk.data(), tk.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d.tapk, tk.data(), tk.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     }
-    c->last_ntl = per_list;
-    c->last_shared = shared;
+    if (!dst) {
+        c->last_ntl = per_list;
+        c->last_shared = shared;
+    }
     return CSEM_OK;
 }
 
@@ -675,6 +706,262 @@ int adj_impl(csem_ctx *c, const void *rho, const csem_points *rec, int S, const 
     CK(csem::launch_finalize_volume<R>((typename C2<R>::T *)Vvol,
                                        c->kahan ? (const typename C2<R>::T *)c->d_comp : nullptr, c->vol, S, c->nf,
                                        c->d_alpha + c->nf, st));
+    return CSEM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Time-domain adjoint gradient (appendix).  The forward run is cut into
+// segments of C steps.  A first pass steps segments 0 .. K-2 and keeps the
+// state at each segment start 1 .. K-2 (checkpoints).  The sweep then takes the
+// segments last to first: it steps the forward segment again from its start
+// (the last one continues from the first pass, the first one from zero), so that
+// E^{n_a} .. E^{n_b} sit in a ring of C + 1 snapshots, and advances the adjoint
+// run (reversed time) over the matching m range in sub-blocks of up to B steps,
+// each followed by the correlation of its B snapshots with the forward ring.
+// Forward steps: (K - 1) C + nt; adjoint steps: nt.
+// ---------------------------------------------------------------------------
+struct TdPlan {
+    int C = 0, K = 0, B = kChunk, nck = 0;
+    bool lean = false, fused = false;
+    size_t o_seg = 0, o_aH = 0, o_aH2 = 0, o_aring = 0, o_apsi = 0, o_apsiL = 0, o_T = 0, o_coef = 0, o_acc = 0;
+    size_t o_itaps = 0, o_colmap = 0, o_tflag = 0, o_tapk = 0, o_ck = 0;
+    size_t ck_H = 0, ck_E = 0, ck_psi = 0, ck_psiL = 0, ck_bytes = 0, total = 0;
+    long long recompute = 0;             // forward steps beyond nt
+};
+
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+TdPlan td_layout(const csem_ctx *c, int S, int NR, int C) {
+    TdPlan P;
+    P.C = C;
+    P.K = (c->nt + C - 1) / C;
+    P.nck = std::max(P.K - 2, 0);
+    P.recompute = (long long)(P.K - 1) * C;
+    P.lean = c->d_psiL && (c->LEAN_h || c->LEAN_e);
+    P.fused = c->fused_kz > 0;
+    const size_t R = c->rsize, v3 = 3 * (size_t)c->vol, Ss = (size_t)S;
+    const size_t psi = Ss * (size_t)c->psi_stride * R, psiL = P.lean ? Ss * 12 * (size_t)c->vol * sizeof(float) : 0;
+    size_t o = 0;
+    auto take = [&](size_t bytes) { const size_t at = o; o += al256(bytes); return at; };
+    P.o_seg = take(Ss * (size_t)(C + 1) * v3 * R);
+    P.o_aH = take(Ss * v3 * R);
+    P.o_aH2 = take(P.fused ? Ss * v3 * R : 0);
+    P.o_aring = take(Ss * (size_t)(P.B + 1) * v3 * R);
+    P.o_apsi = take(psi);
+    P.o_apsiL = take(psiL);
+    P.o_T = take((size_t)c->nt * 2 * c->nf * sizeof(double));
+    P.o_coef = take(Ss * NR * 2 * c->nf * sizeof(double));
+    P.o_acc = take(v3 * sizeof(double));
+    P.o_itaps = take((size_t)NR * 8 * sizeof(Tap));
+    P.o_colmap = take((size_t)c->plane * sizeof(int2));
+    P.o_tflag = take((size_t)c->ny * c->nseg);
+    P.o_tapk = take(c->d_tapk ? (size_t)NR * 8 * sizeof(int) : 0);
+    P.o_ck = o;
+    size_t q = 0;
+    auto ck = [&](size_t bytes) { const size_t at = q; q += al256(bytes); return at; };
+    P.ck_H = ck(Ss * v3 * R);
+    P.ck_E = ck(Ss * v3 * R);
+    P.ck_psi = ck(psi);
+    P.ck_psiL = ck(psiL);
+    P.ck_bytes = q;
+    P.total = o + (size_t)P.nck * P.ck_bytes;
+    return P;
+}
+
+// segment > 0: that length (even); else the candidate with the least forward
+// recomputation whose workspace fits budget (budget <= 0: the least workspace).
+int td_plan(const csem_ctx *c, int S, int NR, int segment, long long budget, TdPlan *out) {
+    if (segment > 0) {
+        if (segment % 2) return fail(CSEM_ERR_INVALID_ARG, "segment length must be even");
+        *out = td_layout(c, S, NR, segment);
+        return CSEM_OK;
+    }
+    std::vector<TdPlan> cand;
+    cand.push_back(td_layout(c, S, NR, (c->nt + 1) / 2 * 2));              // whole run, no recomputation
+    for (int K = 2; K <= (c->nt + kChunk - 1) / kChunk; ++K) {
+        const int C = ((c->nt + K - 1) / K + kChunk - 1) / kChunk * kChunk;
+        if ((c->nt + C - 1) / C == K) cand.push_back(td_layout(c, S, NR, C));
+    }
+    const TdPlan *best = nullptr;
+    for (const auto &P : cand) {
+        if (budget > 0) {
+            if ((long long)P.total > budget) continue;
+            if (!best || P.recompute < best->recompute || (P.recompute == best->recompute && P.total < best->total))
+                best = &P;
+        } else if (!best || P.total < best->total) {
+            best = &P;
+        }
+    }
+    if (!best) return fail(CSEM_ERR_OOM, "no checkpoint plan fits the workspace budget");
+    *out = *best;
+    return CSEM_OK;
+}
+
+// Steps n0 .. n0+L-1 of one run without transforms: whole chunks of kChunk steps
+// replay a graph captured per role (2: forward, 3: adjoint) on first use, the
+// rest is launched directly.
+struct RoleGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long per_chunk = 0;
+};
+
+template <typename R>
+int run_range(csem_ctx *c, int S, int role, RoleGraph &g, const csem::StepParams<R> &p,
+              const csem::PointParams<R> &q, int n0, int L, cudaStream_t st) {
+    CK(csem::launch_set_step(c->d_step, n0, st));
+    const int full = L / kChunk, rem = L % kChunk;
+    if (full > 0 && !g.exec) {
+        const int key[8] = {S, role, 0, q.n_itaps, q.n_emit, (int)sizeof(R),
+                            ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
+                            (((c->fused_kz * 4 + c->VEC_h * 2 + c->VEC_e) * 25 + c->TMA_h * 5 + c->TMA_e) * 4 +
+                             c->LEAN_h * 2 + c->LEAN_e)};
+        TRY(chunk_graph(c, key, [&](cudaStream_t cs) {
+            cudaError_t e = tap_prep<R>(c, p, S, kChunk, cs);
+            for (int j = 0; j < kChunk && e == cudaSuccess; ++j) e = csem::launch_step<R>(p, q, S, j, cs);
+            if (e == cudaSuccess) e = csem::launch_advance(c->d_step, kChunk, cs);
+            return e;
+        }, &g.exec, &g.per_chunk));
+    }
+    for (int ch = 0; ch < full; ++ch) {
+        CK(cudaGraphLaunch(g.exec, st));
+        csem::g_launches += g.per_chunk;
+    }
+    if (rem > 0) {
+        CK(tap_prep<R>(c, p, S, rem, st));
+        for (int j = 0; j < rem; ++j) CK(csem::launch_step<R>(p, q, S, j, st));
+    }
+    return CSEM_OK;
+}
+
+template <typename R>
+int td_impl(csem_ctx *c, const void *rho, const csem_points *src, const csem_points *rec, const double *resid,
+            int segment, int wrt, void *grad, void *work, long long work_bytes, cudaStream_t st) {
+    const int S = src->n, NR = rec->n, nt = c->nt;
+    TdPlan P;
+    TRY(td_plan(c, S, NR, segment, 0, &P));
+    if (work_bytes < (long long)P.total)
+        return fail(CSEM_ERR_INVALID_ARG, "workspace of " + std::to_string(work_bytes) + " bytes, the plan needs " +
+                                              std::to_string((long long)P.total));
+    if ((uintptr_t)work % 256) return fail(CSEM_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+    char *w = (char *)work;
+    const size_t v3 = 3 * (size_t)c->vol, R_ = sizeof(R);
+    const int C = P.C, B = P.B;
+
+    // injection: the sources into the forward run (the context's arrays), the
+    // receivers as emitters of the adjoint run (the workspace's)
+    std::vector<Tap> itaps((size_t)S * 8), rtaps((size_t)NR * 8);
+    for (int s = 0; s < S; ++s)
+        TRY(point_taps(c, src->x[s], src->y[s], src->z[s], src->comp[s], true, 0, &itaps[(size_t)s * 8]));
+    for (int r = 0; r < NR; ++r)
+        TRY(point_taps(c, rec->x[r], rec->y[r], rec->z[r], rec->comp[r], true, r, &rtaps[(size_t)r * 8]));
+    TRY(upload_injection(c, itaps, S, 8, false, st));
+    const InjDst adst{(Tap *)(w + P.o_itaps), (int2 *)(w + P.o_colmap), (unsigned char *)(w + P.o_tflag),
+                      c->d_tapk ? (int *)(w + P.o_tapk) : nullptr};
+    TRY(upload_injection(c, rtaps, 1, NR * 8, true, st, &adst));
+    TRY(coef_init<R>(c, rho, st));
+    double *T = (double *)(w + P.o_T), *coef = (double *)(w + P.o_coef), *acc = (double *)(w + P.o_acc);
+    CK(csem::launch_td_series(c->d_w64, T, nt, c->nf, st));
+    CK(csem::launch_td_coef(resid, c->d_alpha, coef, S, NR, c->nf, st));
+
+    // zero state: forward (context arrays; its E lives in the segment ring), adjoint, accumulator
+    R *seg = (R *)(w + P.o_seg), *aring = (R *)(w + P.o_aring);
+    const long long seg_stride = (long long)(C + 1) * v3, a_stride = (long long)(B + 1) * v3;
+    const size_t psi_b = (size_t)S * c->psi_stride * R_, psiL_b = P.lean ? (size_t)S * 12 * c->vol * sizeof(float) : 0;
+    auto zero_forward = [&]() -> int {
+        CK(cudaMemsetAsync(c->d_H, 0, (size_t)S * v3 * R_, st));
+        if (psi_b) CK(cudaMemsetAsync(c->d_psi, 0, psi_b, st));
+        if (psiL_b) CK(cudaMemsetAsync(c->d_psiL, 0, psiL_b, st));
+        CK(cudaMemset2DAsync(seg, seg_stride * R_, 0, v3 * R_, S, st));      // E^0 in slot 0
+        return CSEM_OK;
+    };
+    TRY(zero_forward());
+    // the kernels never write the row padding and the PEC boundary edges, so every slot starts at zero
+    CK(cudaMemsetAsync(seg, 0, (size_t)S * seg_stride * R_, st));
+    CK(cudaMemsetAsync(w + P.o_aH, 0, (size_t)S * v3 * R_, st));
+    if (P.fused) CK(cudaMemsetAsync(w + P.o_aH2, 0, (size_t)S * v3 * R_, st));
+    CK(cudaMemsetAsync(aring, 0, (size_t)S * a_stride * R_, st));
+    if (psi_b) CK(cudaMemsetAsync(w + P.o_apsi, 0, psi_b, st));
+    if (psiL_b) CK(cudaMemsetAsync(w + P.o_apsiL, 0, psiL_b, st));
+    CK(cudaMemsetAsync(acc, 0, v3 * sizeof(double), st));
+
+    csem::StepParams<R> pf = step_params<R>(c, false, nullptr);
+    pf.ering = seg; pf.ering_stride = seg_stride; pf.nslot = C + 1;
+    pf.colmap = c->d_colmap; pf.colmap_stride = c->plane;
+    pf.tflag = c->d_tflag; pf.tflag_stride = (long long)c->ny * c->nseg;
+    pf.inc_ntl = 8;
+    pf.itaps = c->d_itaps; pf.itap_stride = 8;
+    pf.n_emit = 1; pf.J = 1; pf.coef = c->d_ones; pf.T = c->d_T;
+    csem::PointParams<R> qf;
+    qf.cE = (const R *)c->d_cE; qf.step = c->d_step;
+    qf.nt = nt; qf.nf = c->nf;
+    qf.n_rec = 0; qf.rtaps = nullptr; qf.racc = nullptr; qf.w64 = c->d_w64; qf.trace = nullptr;
+    qf.n_itaps = 8; qf.itaps = c->d_itaps; qf.itap_stride = 8;
+    qf.n_emit = 1; qf.J = 1; qf.coef = c->d_ones; qf.T = c->d_T;
+
+    csem::StepParams<R> pa = step_params<R>(c, false, nullptr);
+    pa.H = (R *)(w + P.o_aH); pa.H2 = P.fused ? (R *)(w + P.o_aH2) : pa.H;
+    pa.ering = aring; pa.ering_stride = a_stride; pa.nslot = B + 1;
+    pa.psi = (R *)(w + P.o_apsi);
+    if constexpr (sizeof(R) == 4) pa.psiL = P.lean ? (float *)(w + P.o_apsiL) : nullptr;
+    pa.colmap = adst.colmap; pa.colmap_stride = 0;
+    pa.tflag = adst.tflag; pa.tflag_stride = 0;
+    pa.inc_ntl = NR * 8;
+    if constexpr (sizeof(R) == 4) pa.tapk = adst.tapk;
+    pa.itaps = adst.itaps; pa.itap_stride = 0;
+    pa.n_emit = NR; pa.J = 2 * c->nf; pa.coef = coef; pa.T = T;
+    csem::PointParams<R> qa = qf;
+    qa.n_itaps = NR * 8; qa.itaps = adst.itaps; qa.itap_stride = 0;
+    qa.n_emit = NR; qa.J = 2 * c->nf; qa.coef = coef; qa.T = T;
+
+    // checkpoint j (1 .. K-2) holds the forward state at n = j C
+    auto ck_at = [&](int j) { return w + P.o_ck + (size_t)(j - 1) * P.ck_bytes; };
+    auto save = [&](int j) -> int {
+        char *d = ck_at(j);
+        const int sl = (j * C) % (C + 1);
+        CK(cudaMemcpyAsync(d + P.ck_H, c->d_H, (size_t)S * v3 * R_, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpy2DAsync(d + P.ck_E, v3 * R_, seg + (size_t)sl * v3, seg_stride * R_, v3 * R_, S,
+                             cudaMemcpyDeviceToDevice, st));
+        if (psi_b) CK(cudaMemcpyAsync(d + P.ck_psi, c->d_psi, psi_b, cudaMemcpyDeviceToDevice, st));
+        if (psiL_b) CK(cudaMemcpyAsync(d + P.ck_psiL, c->d_psiL, psiL_b, cudaMemcpyDeviceToDevice, st));
+        return CSEM_OK;
+    };
+    auto restore = [&](int j) -> int {
+        const char *d = ck_at(j);
+        const int sl = (j * C) % (C + 1);
+        CK(cudaMemcpyAsync(c->d_H, d + P.ck_H, (size_t)S * v3 * R_, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpy2DAsync(seg + (size_t)sl * v3, seg_stride * R_, d + P.ck_E, v3 * R_, v3 * R_, S,
+                             cudaMemcpyDeviceToDevice, st));
+        if (psi_b) CK(cudaMemcpyAsync(c->d_psi, d + P.ck_psi, psi_b, cudaMemcpyDeviceToDevice, st));
+        if (psiL_b) CK(cudaMemcpyAsync(c->d_psiL, d + P.ck_psiL, psiL_b, cudaMemcpyDeviceToDevice, st));
+        return CSEM_OK;
+    };
+
+    // first pass: segments 0 .. K-2, keeping the starts of segments 1 .. K-2
+    RoleGraph gf, ga;
+    for (int k = 0; k + 1 < P.K; ++k) {
+        TRY(run_range<R>(c, S, 2, gf, pf, qf, k * C, C, st));
+        if (k + 1 <= P.K - 2) TRY(save(k + 1));
+    }
+    // sweep: last segment first; the adjoint advances through m = 0 .. nt-1 in order
+    for (int k = P.K - 1; k >= 0; --k) {
+        const int na = k * C, L = std::min(C, nt - na);
+        if (k < P.K - 1) {
+            if (k == 0) TRY(zero_forward());
+            else TRY(restore(k));
+        }
+        TRY(run_range<R>(c, S, 2, gf, pf, qf, na, L, st));
+        const int ma = nt - na - L;
+        for (int b0 = 0; b0 < L; b0 += B) {
+            const int b = std::min(B, L - b0);
+            TRY(run_range<R>(c, S, 3, ga, pa, qa, ma + b0, b, st));
+            CK(csem::launch_td_corr<R>(seg, seg_stride, C + 1, aring, a_stride, B + 1, S, (long long)v3, nt, ma + b0, b,
+                                       acc, st));
+        }
+    }
+    // per-edge gradient divided by dV_e, then the cell mapping of csem_gradient
+    CK(csem::launch_td_edges<R>(acc, -1.0 / (2.0 * c->w0 * c->dt), (long long)v3, (R *)c->d_edge, st));
+    CK(csem::launch_grad_cells<R>(geo(c), (const R *)rho, (const R *)c->d_edge, wrt, c->vti != 0, (R *)grad, st));
+    c->last_nrec = 0;
     return CSEM_OK;
 }
 
@@ -1120,6 +1407,31 @@ int csem_gradient(csem_ctx *c, const void *rho_dev, const void *Evol_dev, const 
                                          (const double2 *)Vvol_dev, n_src, c->nf, wrt, c->vti != 0, (double *)c->d_edge,
                                          (double *)grad_dev, st));
     return CSEM_OK;
+}
+
+int csem_td_plan(const csem_ctx *c, int n_src, int n_rec, long long budget_bytes, int *segment_out,
+                 long long *bytes_out) {
+    if (!c || !segment_out || !bytes_out) return fail(CSEM_ERR_INVALID_ARG, "NULL argument");
+    if (n_src < 1 || n_src > c->max_src || n_rec < 1 || n_rec > c->max_rec)
+        return fail(CSEM_ERR_INVALID_ARG, "n_src or n_rec out of range");
+    TdPlan P;
+    TRY(td_plan(c, n_src, n_rec, *segment_out > 0 ? *segment_out : 0, budget_bytes, &P));
+    *segment_out = P.C;
+    *bytes_out = (long long)P.total;
+    return CSEM_OK;
+}
+
+int csem_gradient_td(csem_ctx *c, const void *rho_dev, const csem_points *src, const csem_points *rec,
+                     const double *resid_dev, int segment, int wrt, void *grad_dev, void *work_dev,
+                     long long work_bytes, void *stream) {
+    if (!c || !rho_dev || !resid_dev || !grad_dev || !work_dev) return fail(CSEM_ERR_INVALID_ARG, "NULL argument");
+    TRY(check_points(src, c->max_src, "sources", false));
+    TRY(check_points(rec, c->max_rec, "receivers", false));
+    if (segment < 2 || (wrt != 0 && wrt != 1)) return fail(CSEM_ERR_INVALID_ARG, "bad segment or wrt");
+    cudaStream_t st = (cudaStream_t)stream;
+    return c->precision == 32
+               ? td_impl<float>(c, rho_dev, src, rec, resid_dev, segment, wrt, grad_dev, work_dev, work_bytes, st)
+               : td_impl<double>(c, rho_dev, src, rec, resid_dev, segment, wrt, grad_dev, work_dev, work_bytes, st);
 }
 
 long long csem_launch_count(void) { return csem::g_launches.load(); }

@@ -1,5 +1,6 @@
 // Set-up, normalisation, misfit, gradient and adjoint-basis kernels.
 #include "csem_internal.cuh"
+#include "csem_td.cuh"
 
 namespace csem {
 
@@ -183,6 +184,15 @@ cudaError_t launch_gradient(const GeoD &g, const R *rho, const typename C2<R>::T
     k_grad_cell<R><<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(g, edge_scratch, rho, vti ? rho + cells : nullptr,
                                                                       wrt, grad, vti ? grad + cells : nullptr);
     g_launches += 2;
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_grad_cells(const GeoD &g, const R *rho, const R *pe, int wrt, bool vti, R *grad, cudaStream_t st) {
+    const long long cells = (long long)g.nx * g.ny * g.nz;
+    k_grad_cell<R><<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(g, pe, rho, vti ? rho + cells : nullptr, wrt,
+                                                                      grad, vti ? grad + cells : nullptr);
+    g_launches++;
     return cudaGetLastError();
 }
 
@@ -459,5 +469,9 @@ template cudaError_t launch_gradient<float>(const GeoD &, const float *, const f
                                             int, bool, float *, float *, cudaStream_t);
 template cudaError_t launch_gradient<double>(const GeoD &, const double *, const double2 *, const double2 *, int,
                                              int, int, bool, double *, double *, cudaStream_t);
+template cudaError_t launch_grad_cells<float>(const GeoD &, const float *, const float *, int, bool, float *,
+                                              cudaStream_t);
+template cudaError_t launch_grad_cells<double>(const GeoD &, const double *, const double *, int, bool, double *,
+                                               cudaStream_t);
 
 }  // namespace csem

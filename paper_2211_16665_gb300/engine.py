@@ -6,6 +6,7 @@ PyTorch, every computation from the CUDA library (no fallback path).
   .estimate_adjoint_basis()   -> B+ [nt, 2F] float64 (device), fit residual
   .adjoint_model(rho, rec, resid, basis) -> conj(v) volumes
   .gradient(rho, E, V, wrt)   -> [nz, ny, nx]
+  .gradient_td(rho, src, rec, resid, wrt) -> [nz, ny, nx] by the time-domain adjoint
   misfit(d_obs, d_syn, w)     -> phi (0-d tensor), resid
 """
 from __future__ import annotations
@@ -158,6 +159,37 @@ class Engine:
             raise ValueError(f"volumes of shape {vs} expected")
         _capi.gradient(self.ctx, _ptr(self._model(rho)), _ptr(Evol), _ptr(Vvol), Evol.shape[0],
                        1 if wrt == "lnrho" else 0, _ptr(out), _stream())
+        return out
+
+    def td_plan(self, n_src, n_rec, budget_bytes=0, segment=0):
+        """(segment length, workspace bytes) of gradient_td; budget_bytes > 0 picks the
+        segment with the fewest replayed forward steps that fits it."""
+        return _capi.td_plan(self.ctx, n_src, n_rec, budget_bytes, segment)
+
+    def gradient_td(self, rho, src, rec, resid: torch.Tensor, wrt="lnrho", segment=0, budget_bytes=None, out=None,
+                    work=None):
+        """Gradient by the time-domain adjoint (appendix): the reversed-time run of the
+        scheme driven by the residual, correlated with the forward field replayed from
+        checkpoints.  budget_bytes: workspace limit (default: 80% of the free memory);
+        work: a uint8 device tensor to use as the workspace (else one is allocated)."""
+        S = src.n
+        if resid.dtype != torch.complex128 or tuple(resid.shape) != (S, rec.n, self.nf):
+            raise ValueError(f"resid of shape {(S, rec.n, self.nf)} complex128 expected")
+        if out is None:
+            out = torch.zeros(self.model_shape, dtype=self.real, device=self.device)
+        self._model(out)
+        if budget_bytes is None:
+            budget_bytes = int(0.8 * torch.cuda.mem_get_info(self.device)[0])
+        seg, nbytes = _capi.td_plan(self.ctx, S, rec.n, budget_bytes if segment <= 0 else 0, segment)
+        if work is None:
+            work = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        off = (-work.data_ptr()) % 256
+        if work.dtype != torch.uint8 or not work.is_cuda or work.numel() < nbytes + off:
+            raise ValueError(f"workspace of at least {nbytes + off} bytes (uint8, on the device) expected")
+        _capi.gradient_td(self.ctx, _ptr(self._model(rho)), src, rec, _ptr(resid.contiguous()), seg,
+                          1 if wrt == "lnrho" else 0, _ptr(out), ctypes_void(work.data_ptr() + off), nbytes,
+                          _stream())
+        self.last_td = dict(segment=seg, workspace_bytes=nbytes)
         return out
 
     def check(self):
