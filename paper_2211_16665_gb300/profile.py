@@ -1,6 +1,8 @@
-"""One forward run with the volumetric transform on a workload, for profiler captures.
+"""One forward run with the volumetric transform on a workload, for profiler captures
+(or, with --td, one time-domain adjoint gradient).
 
     python -m paper_2211_16665_gb300.profile --workload thin_reservoir --nt 256
+    python -m paper_2211_16665_gb300.profile --workload thin_reservoir --nt 256 --td --segment 128
 
 Runs the same kernels as a gradient's runs (H half-step with the fused
 damped transform, point operators, E step), with nt limited so that a
@@ -26,6 +28,8 @@ def main():
     ap.add_argument("--nt", type=int, default=256)
     ap.add_argument("--kahan", type=int, default=1)
     ap.add_argument("--launch", default="", help="JSON keyword arguments of Engine.set_launch (skips autotuning)")
+    ap.add_argument("--td", action="store_true", help="run a time-domain adjoint gradient instead")
+    ap.add_argument("--segment", type=int, default=0, help="segment length of --td (0: the plan's)")
     args = ap.parse_args()
     wl = W.ALL[args.workload]()
     eng = Engine.from_workload(wl, nt=args.nt, kahan=args.kahan, autotune=not args.launch)
@@ -33,6 +37,14 @@ def main():
         import json
         eng.set_launch(**json.loads(args.launch))
     rho = eng.model_tensor(wl.rho)
+    if args.td:
+        d = eng.fwd_model(rho, wl.src, wl.rec)
+        g = eng.gradient_td(rho, wl.src, wl.rec, d, segment=args.segment)
+        torch.cuda.synchronize()
+        print(f"profile run ok: {wl.name}, time-domain adjoint, nt={eng.nt}, segment={eng.last_td['segment']}, "
+              f"|g|max={g.abs().max().item():.3e}")
+        eng.close()
+        return
     d, E = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)
     torch.cuda.synchronize()
     print(f"profile run ok: {wl.name}, nt={eng.nt}, |d|max={d.abs().max().item():.3e}")
