@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="thin_reservoir")
     ap.add_argument("--vti", action="store_true", help="VTI medium: models (rho_h, rho_v), split gradient")
+    ap.add_argument("--order", type=int, default=2, choices=[2, 4],
+                    help="spatial order of the staggered differences (4: four-point kernels)")
     ap.add_argument("--inversion", type=int, default=0, help="run this many iterations of the outer inversion loop")
     ap.add_argument("--td", type=int, default=0,
                     help="time this many time-domain adjoint gradients against the basis route")
@@ -192,9 +194,9 @@ def ncu_traffic(wl, eng, kernel):
     return NCU_TRAFFIC.get((wl.name, kernel, code, sha(src)))
 
 
-def cpu_baseline(wl, nt_sample):
+def cpu_baseline(wl, nt_sample, order=2):
     from oracle import fdtd
-    pb = fdtd.problem_from_workload(wl)
+    pb = fdtd.problem_from_workload(wl, order=order)
     nt_sample = min(nt_sample, pb.nt)
     t0 = time.perf_counter()
     fdtd.forward(pb, wl.rho, wl.src.subset([0]), wl.rec, keep_volume=True, nt_run=nt_sample)
@@ -226,7 +228,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     wl = make_workload(args.workload, rank, world, vti=args.vti)
-    eng = Engine.from_workload(wl, vti=args.vti)
+    eng = Engine.from_workload(wl, vti=args.vti, order=args.order)
     S = wl.src.n
     rho = eng.model_tensor(wl.rho)
     rho_true = eng.model_tensor(wl.rho_true)
@@ -323,7 +325,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl, args.cpu_steps)
+        cpu = cpu_baseline(wl, args.cpu_steps, args.order)
 
     if rank == 0:
         out = {"metric": METRIC, "value": round(value, 3), "unit": "Gcell-updates/s", "n_gpus": world,
@@ -335,7 +337,7 @@ def run_ours(args):
                           "kahan": bool(eng.info.kahan), "launch": eng.launch_config(), "l2": "inputs larger than L2 (each step streams "
                           f"{2 * 3 * eng.nf * eng.vol * 8 * S * (2 if eng.info.kahan else 1) / 2**20:.0f} MiB of "
                           "transform volumes)", "parallelism": f"sources sharded, dp{world}",
-                          "medium": "vti" if args.vti else "isotropic"},
+                          "medium": "vti" if args.vti else "isotropic", "order": eng.order},
                "grad_s_per_source": round(ms / 1e3 / S, 4),
                "basis_fit": fit,
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),

@@ -84,6 +84,15 @@ typedef struct {
                            sigma_h = sigma_xx = sigma_yy on the x and y edges, sigma_v =
                            sigma_zz on the z edges), models [2][cells] = (rho_h, rho_v)
                            and gradients [2][cells] = (h, v) (Sec. 3.1, Eq. 15) */
+    int order;          /* spatial order of the staggered differences (Sec. 2: high-order
+                           differences on the non-uniform grid): 0 or 2 = Yee; 4 = four-point
+                           differences, at each half node from the nodes p-1..p+2 and at each
+                           node from the half nodes q-2..q+1, the derivative of the cubic
+                           through the four points (exact for cubics on any spacing), the
+                           two-point difference where four points do not fit (next to the
+                           outer boundary); dt <= 0 then gives 2 s / (v(rho_max) sqrt(sum over
+                           axes of the largest absolute weight-row sum squared)).  Order 4 runs
+                           its own H and E kernels (csem_set_launch accepts no other family) */
 } csem_opts;
 
 typedef struct {
@@ -96,6 +105,7 @@ typedef struct {
     long long workspace_bytes;    /* device memory the context holds */
     int transform_block;          /* E snapshots per damped-transform flush (16, 32 or 64) */
     int anisotropy;               /* as in csem_opts */
+    int order;                    /* 2 or 4, as in csem_opts */
 } csem_info;
 
 /* Creates a context on the current device: validates the grid and options,

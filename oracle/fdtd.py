@@ -20,7 +20,9 @@ adjoint source estimation"):
                    edges, dphi/dsigma_v the z edges
 
 Readings where the paper is silent (each listed in the design notes):
-  * second-order Yee stencil; tangential E = 0 on the outer boundary;
+  * second-order Yee stencil (order 2), or four-point staggered differences exact
+    for cubics on the non-uniform nodes, two-point rows next to the outer boundary
+    (order 4); tangential E = 0 on the outer boundary;
   * cell-centred rho; edge conductivity = volume-weighted mean of the (up to
     four) cells sharing the edge; gradient mapped back by the transpose;
   * CFL step dt = s / (v_max sqrt(max_cells sum 1/h^2)), v = sqrt(2 w0 rho / mu0),
@@ -82,6 +84,62 @@ def cfl_dt(xn, yn, zn, rho_max: float, f0: float, safety: float = CFL_SAFETY) ->
     hx, hy, hz = np.diff(xn), np.diff(yn), np.diff(zn)
     s = 1 / hz[:, None, None] ** 2 + 1 / hy[None, :, None] ** 2 + 1 / hx[None, None, :] ** 2
     return float(safety / (wave_speed(rho_max, f0) * np.sqrt(s.max())))
+
+
+def fd_weights(x0: float, xs) -> np.ndarray:
+    """Weights w with sum_i w_i f(xs_i) = f'(x0) for every polynomial f of degree < len(xs):
+    the derivative of the Lagrange interpolant through the points (moment conditions
+    sum_i w_i (xs_i - x0)^m = [m == 1], m = 0 .. len(xs) - 1)."""
+    d = np.asarray(xs, float) - x0
+    A = np.vander(d, d.size, increasing=True).T          # A[m, i] = d_i^m
+    rhs = np.zeros(d.size)
+    rhs[1] = 1.0
+    return np.linalg.solve(A, rhs)
+
+
+def staggered_weights(xn):
+    """Fourth-order staggered difference weights on one non-uniform axis (Sec. 2: high-order
+    differences on the non-uniform grid; the paper prints no coefficients).
+
+    H rows (derivative at the half node p from the nodes p-1 .. p+2) and E rows (derivative
+    at the node q from the half nodes q-2 .. q+1) are each the weights of fd_weights at
+    their own point, so both are exact for cubics on any node spacing.  Rows whose four
+    points would leave the lattice (the first and last half node, the nodes 1 and n-1)
+    keep the two-point difference of the second-order scheme.
+    Returns wh [n][4] (nodes p-1 .. p+2) and wn [n+1][4] (half nodes q-2 .. q+1).
+    """
+    xn = np.asarray(xn, float)
+    n = xn.size - 1
+    h, ht = spacings(xn)
+    xh = 0.5 * (xn[1:] + xn[:-1])
+    wh = np.zeros((n, 4))
+    for p in range(n):
+        if 1 <= p <= n - 2:
+            wh[p] = fd_weights(xh[p], xn[p - 1:p + 3])
+        else:
+            wh[p, 1], wh[p, 2] = -1.0 / h[p], 1.0 / h[p]
+    wn = np.zeros((n + 1, 4))
+    for q in range(1, n):
+        if 2 <= q <= n - 2:
+            wn[q] = fd_weights(xn[q], xh[q - 2:q + 2])
+        else:
+            wn[q, 1], wn[q, 2] = -1.0 / ht[q], 1.0 / ht[q]
+    return wh, wn
+
+
+def cfl_dt_order4(xn, yn, zn, rho_max: float, f0: float, safety: float = CFL_SAFETY) -> float:
+    """Leap-frog limit for the four-point scheme: dt = 2 s / (v sqrt(max_cells sum_a S_a^2)),
+    S_a the largest absolute row sum of the weights touching the cell along axis a (the
+    largest symbol of the staggered difference; two-point rows give 2/h, the Yee limit)."""
+    S = []
+    for g in (xn, yn, zn):
+        wh, wn = staggered_weights(g)
+        rh = np.abs(wh).sum(axis=1)
+        rn = np.abs(wn).sum(axis=1)
+        S.append(np.maximum(rh, np.maximum(rn[:-1], rn[1:])))
+    sx, sy, sz = S
+    tot = sz[:, None, None] ** 2 + sy[None, :, None] ** 2 + sx[None, None, :] ** 2
+    return float(2.0 * safety / (wave_speed(rho_max, f0) * np.sqrt(tot.max())))
 
 
 def default_nt(dt: float, freqs, f0: float) -> int:
@@ -225,7 +283,8 @@ class _Model(ctypes.Structure):
         [(n, _D) for n in ("ihx_h", "ihx_n", "ihy_h", "ihy_n", "ihz_h", "ihz_n",
                            "bx_h", "ax_h", "bx_n", "ax_n", "by_h", "ay_h", "by_n", "ay_n",
                            "bz_h", "az_h", "bz_n", "az_n")] + \
-        [("cH", ctypes.c_double), ("cE", _D)]
+        [("cH", ctypes.c_double), ("cE", _D), ("order", ctypes.c_int)] + \
+        [(n, _D) for n in ("wx_h", "wx_n", "wy_h", "wy_n", "wz_h", "wz_n")]
 
 
 class _IO(ctypes.Structure):
@@ -273,6 +332,7 @@ class Problem:
     nt: int
     rho_max: float
     v_pml: float
+    order: int = 2
 
     @property
     def shape_nodes(self):
@@ -307,20 +367,24 @@ class Problem:
         return w
 
 
-def make_problem(xn, yn, zn, npml, freqs, f0=1.0, rho_max=1.0, nt=None, dt=None, v_pml=None) -> Problem:
+def make_problem(xn, yn, zn, npml, freqs, f0=1.0, rho_max=1.0, nt=None, dt=None, v_pml=None,
+                 order=2) -> Problem:
+    if order not in (2, 4):
+        raise ValueError("spatial order 2 or 4")
     if dt is None:
-        dt = cfl_dt(xn, yn, zn, rho_max, f0)
+        dt = cfl_dt(xn, yn, zn, rho_max, f0) if order == 2 else cfl_dt_order4(xn, yn, zn, rho_max, f0)
     if nt is None:
         nt = default_nt(dt, freqs, f0)
     if v_pml is None:
         v_pml = float(wave_speed(rho_max, f0))
     return Problem(np.asarray(xn, float), np.asarray(yn, float), np.asarray(zn, float), int(npml),
-                   np.asarray(freqs, float), float(f0), float(dt), int(nt), float(rho_max), float(v_pml))
+                   np.asarray(freqs, float), float(f0), float(dt), int(nt), float(rho_max), float(v_pml),
+                   int(order))
 
 
-def problem_from_workload(wl, nt=None) -> Problem:
+def problem_from_workload(wl, nt=None, order=2) -> Problem:
     return make_problem(wl.xn, wl.yn, wl.zn, wl.npml, wl.freqs, wl.f0, wl.rho_max,
-                        nt if nt is not None else wl.nt)
+                        nt if nt is not None else wl.nt, order=order)
 
 
 class Stepper:
@@ -354,6 +418,14 @@ class Stepper:
             setattr(m, name, _dp(arr))
         m.cH = pb.dt / MU0
         m.cE = _dp(self.cE)
+        m.order = pb.order
+        if pb.order == 4:
+            ws = []
+            for g in (xn, yn, zn):
+                ws += [np.ascontiguousarray(w) for w in staggered_weights(g)]
+            self._keep += ws
+            for name, arr in zip(("wx_h", "wx_n", "wy_h", "wy_n", "wz_h", "wz_n"), ws):
+                setattr(m, name, _dp(arr))
         self._model = m
 
     def new_state(self):

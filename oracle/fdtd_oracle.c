@@ -22,6 +22,13 @@
  *
  * Every array is full-size and every loop visits every point: slow on
  * purpose, so that each line can be checked against the equations.
+ *
+ * Spatial order (Sec. 2 uses high-order differences on the non-uniform grid):
+ * order 2 is the two-point Yee difference.  Order 4 takes, at each half node
+ * p, the four-point weights wh[p][0..3] on the nodes p-1 .. p+2 (H update),
+ * and at each node q the weights wn[q][0..3] on the half nodes q-2 .. q+1
+ * (E update); the tables come from the caller, terms outside the lattice are
+ * skipped (their weights are zero).
  */
 #include <stddef.h>
 #include <stdlib.h>
@@ -36,7 +43,37 @@ typedef struct {
     const double *bz_h, *az_h, *bz_n, *az_n;
     double cH;          /* dt / mu0 */
     const double *cE;   /* [3][N] dt / eps on each E edge */
+    int order;          /* 2 or 4 */
+    /* order 4: weights at half nodes [n][4] and at nodes [n+1][4], per axis */
+    const double *wx_h, *wx_n, *wy_h, *wy_n, *wz_h, *wz_n;
 } orc_model;
+
+/* d/da of a node-located field at half node p along an axis of n cells;
+ * F + at is the field at node p, s the stride along the axis. */
+static double d_half(const double *F, size_t at, size_t s, int p, int n, int order, const double *ih,
+                     const double *wh)
+{
+    if (order != 4) return (F[at + s] - F[at]) * ih[p];
+    double d = 0.0;
+    for (int o = 0; o < 4; ++o) {
+        const int q = p - 1 + o;
+        if (q >= 0 && q <= n) d += wh[4 * p + o] * F[at + (size_t)(o - 1) * s];
+    }
+    return d;
+}
+
+/* d/da of a half-node-located field at node p; F + at is the field at half node p. */
+static double d_node(const double *F, size_t at, size_t s, int p, int n, int order, const double *ih,
+                     const double *wn)
+{
+    if (order != 4) return (F[at] - F[at - s]) * ih[p];
+    double d = 0.0;
+    for (int o = 0; o < 4; ++o) {
+        const int q = p - 2 + o;
+        if (q >= 0 && q <= n - 1) d += wn[4 * p + o] * F[at + (size_t)(o - 2) * s];
+    }
+    return d;
+}
 
 typedef struct {
     /* point injection: J'_edge(t_{n+1/2}) = w * series[e][n] (w already holds 1/dV) */
@@ -57,6 +94,7 @@ typedef struct {
 } orc_io;
 
 #define AT(a, i, j, k) (a)[((size_t)(k) * (size_t)(ny + 1) + (size_t)(j)) * (size_t)(nx + 1) + (size_t)(i)]
+#define IX(i, j, k) (((size_t)(k) * (size_t)(ny + 1) + (size_t)(j)) * (size_t)(nx + 1) + (size_t)(i))
 
 /* fields: [6][N] = Ex,Ey,Ez,Hx,Hy,Hz.  psi: [12][N]. Runs steps n0..n1-1. */
 int orc_run(const orc_model *m, const orc_io *io, double *fields, double *psi, int n0, int n1)
@@ -72,6 +110,8 @@ int orc_run(const orc_model *m, const orc_io *io, double *fields, double *psi, i
     double *p_ey_x = psi + 9 * N, *p_ez_x = psi + 10 * N, *p_ez_y = psi + 11 * N;
     const double *cEx = m->cE, *cEy = m->cE + N, *cEz = m->cE + 2 * N;
     const double cH = m->cH;
+    const int od = m->order;
+    const size_t sx = 1, sy = (size_t)(nx + 1), sz = (size_t)(nx + 1) * (size_t)(ny + 1);
 
     for (int n = n0; n < n1; ++n) {
         /* ---- sample E^n at the receivers ---- */
@@ -105,22 +145,22 @@ int orc_run(const orc_model *m, const orc_io *io, double *fields, double *psi, i
             for (int j = 0; j <= ny; ++j)
                 for (int i = 0; i <= nx; ++i) {
                     if (j < ny && k < nz) {             /* Hx at (i, j+1/2, k+1/2) */
-                        double dEz_dy = (AT(Ez, i, j + 1, k) - AT(Ez, i, j, k)) * m->ihy_h[j];
-                        double dEy_dz = (AT(Ey, i, j, k + 1) - AT(Ey, i, j, k)) * m->ihz_h[k];
+                        double dEz_dy = d_half(Ez, IX(i, j, k), sy, j, ny, od, m->ihy_h, m->wy_h);
+                        double dEy_dz = d_half(Ey, IX(i, j, k), sz, k, nz, od, m->ihz_h, m->wz_h);
                         AT(p_hx_y, i, j, k) = m->by_h[j] * AT(p_hx_y, i, j, k) + m->ay_h[j] * dEz_dy;
                         AT(p_hx_z, i, j, k) = m->bz_h[k] * AT(p_hx_z, i, j, k) + m->az_h[k] * dEy_dz;
                         AT(Hx, i, j, k) -= cH * ((dEz_dy + AT(p_hx_y, i, j, k)) - (dEy_dz + AT(p_hx_z, i, j, k)));
                     }
                     if (i < nx && k < nz) {             /* Hy at (i+1/2, j, k+1/2) */
-                        double dEx_dz = (AT(Ex, i, j, k + 1) - AT(Ex, i, j, k)) * m->ihz_h[k];
-                        double dEz_dx = (AT(Ez, i + 1, j, k) - AT(Ez, i, j, k)) * m->ihx_h[i];
+                        double dEx_dz = d_half(Ex, IX(i, j, k), sz, k, nz, od, m->ihz_h, m->wz_h);
+                        double dEz_dx = d_half(Ez, IX(i, j, k), sx, i, nx, od, m->ihx_h, m->wx_h);
                         AT(p_hy_z, i, j, k) = m->bz_h[k] * AT(p_hy_z, i, j, k) + m->az_h[k] * dEx_dz;
                         AT(p_hy_x, i, j, k) = m->bx_h[i] * AT(p_hy_x, i, j, k) + m->ax_h[i] * dEz_dx;
                         AT(Hy, i, j, k) -= cH * ((dEx_dz + AT(p_hy_z, i, j, k)) - (dEz_dx + AT(p_hy_x, i, j, k)));
                     }
                     if (i < nx && j < ny) {             /* Hz at (i+1/2, j+1/2, k) */
-                        double dEy_dx = (AT(Ey, i + 1, j, k) - AT(Ey, i, j, k)) * m->ihx_h[i];
-                        double dEx_dy = (AT(Ex, i, j + 1, k) - AT(Ex, i, j, k)) * m->ihy_h[j];
+                        double dEy_dx = d_half(Ey, IX(i, j, k), sx, i, nx, od, m->ihx_h, m->wx_h);
+                        double dEx_dy = d_half(Ex, IX(i, j, k), sy, j, ny, od, m->ihy_h, m->wy_h);
                         AT(p_hz_x, i, j, k) = m->bx_h[i] * AT(p_hz_x, i, j, k) + m->ax_h[i] * dEy_dx;
                         AT(p_hz_y, i, j, k) = m->by_h[j] * AT(p_hz_y, i, j, k) + m->ay_h[j] * dEx_dy;
                         AT(Hz, i, j, k) -= cH * ((dEy_dx + AT(p_hz_x, i, j, k)) - (dEx_dy + AT(p_hz_y, i, j, k)));
@@ -133,22 +173,22 @@ int orc_run(const orc_model *m, const orc_io *io, double *fields, double *psi, i
             for (int j = 0; j <= ny; ++j)
                 for (int i = 0; i <= nx; ++i) {
                     if (i < nx && j >= 1 && j < ny && k >= 1 && k < nz) {   /* Ex */
-                        double dHz_dy = (AT(Hz, i, j, k) - AT(Hz, i, j - 1, k)) * m->ihy_n[j];
-                        double dHy_dz = (AT(Hy, i, j, k) - AT(Hy, i, j, k - 1)) * m->ihz_n[k];
+                        double dHz_dy = d_node(Hz, IX(i, j, k), sy, j, ny, od, m->ihy_n, m->wy_n);
+                        double dHy_dz = d_node(Hy, IX(i, j, k), sz, k, nz, od, m->ihz_n, m->wz_n);
                         AT(p_ex_y, i, j, k) = m->by_n[j] * AT(p_ex_y, i, j, k) + m->ay_n[j] * dHz_dy;
                         AT(p_ex_z, i, j, k) = m->bz_n[k] * AT(p_ex_z, i, j, k) + m->az_n[k] * dHy_dz;
                         AT(Ex, i, j, k) += AT(cEx, i, j, k) * ((dHz_dy + AT(p_ex_y, i, j, k)) - (dHy_dz + AT(p_ex_z, i, j, k)));
                     }
                     if (j < ny && i >= 1 && i < nx && k >= 1 && k < nz) {   /* Ey */
-                        double dHx_dz = (AT(Hx, i, j, k) - AT(Hx, i, j, k - 1)) * m->ihz_n[k];
-                        double dHz_dx = (AT(Hz, i, j, k) - AT(Hz, i - 1, j, k)) * m->ihx_n[i];
+                        double dHx_dz = d_node(Hx, IX(i, j, k), sz, k, nz, od, m->ihz_n, m->wz_n);
+                        double dHz_dx = d_node(Hz, IX(i, j, k), sx, i, nx, od, m->ihx_n, m->wx_n);
                         AT(p_ey_z, i, j, k) = m->bz_n[k] * AT(p_ey_z, i, j, k) + m->az_n[k] * dHx_dz;
                         AT(p_ey_x, i, j, k) = m->bx_n[i] * AT(p_ey_x, i, j, k) + m->ax_n[i] * dHz_dx;
                         AT(Ey, i, j, k) += AT(cEy, i, j, k) * ((dHx_dz + AT(p_ey_z, i, j, k)) - (dHz_dx + AT(p_ey_x, i, j, k)));
                     }
                     if (k < nz && i >= 1 && i < nx && j >= 1 && j < ny) {   /* Ez */
-                        double dHy_dx = (AT(Hy, i, j, k) - AT(Hy, i - 1, j, k)) * m->ihx_n[i];
-                        double dHx_dy = (AT(Hx, i, j, k) - AT(Hx, i, j - 1, k)) * m->ihy_n[j];
+                        double dHy_dx = d_node(Hy, IX(i, j, k), sx, i, nx, od, m->ihx_n, m->wx_n);
+                        double dHx_dy = d_node(Hx, IX(i, j, k), sy, j, ny, od, m->ihy_n, m->wy_n);
                         AT(p_ez_x, i, j, k) = m->bx_n[i] * AT(p_ez_x, i, j, k) + m->ax_n[i] * dHy_dx;
                         AT(p_ez_y, i, j, k) = m->by_n[j] * AT(p_ez_y, i, j, k) + m->ay_n[j] * dHx_dy;
                         AT(Ez, i, j, k) += AT(cEz, i, j, k) * ((dHy_dx + AT(p_ez_x, i, j, k)) - (dHx_dy + AT(p_ez_y, i, j, k)));

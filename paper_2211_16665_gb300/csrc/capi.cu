@@ -15,6 +15,7 @@
 #include "../../include/csem.h"
 #include "csem_internal.cuh"
 #include "csem_td.cuh"
+#include "csem_ho.cuh"
 
 using csem::C2;
 using csem::Tap;
@@ -47,7 +48,50 @@ struct Axis {
     int n = 0;
     std::vector<double> x, h, ht;   // nodes, primal widths (n), dual widths (n+1)
     std::vector<double> bh, ah, bn, an;
+    std::vector<double> wh, wn;     // fourth order: [n][4] at half nodes, [n+1][4] at nodes
 };
+
+// Derivative at x0 of the Lagrange interpolant through the four points x[0..3]:
+// w_i = L_i'(x0) = sum_{m != i} 1/(x_i - x_m) prod_{l != i, m} (x0 - x_l)/(x_i - x_l).
+void lagrange_d1(double x0, const double *x, double *w) {
+    for (int i = 0; i < 4; ++i) {
+        double sum = 0.0;
+        for (int m = 0; m < 4; ++m) {
+            if (m == i) continue;
+            double prod = 1.0 / (x[i] - x[m]);
+            for (int l = 0; l < 4; ++l)
+                if (l != i && l != m) prod *= (x0 - x[l]) / (x[i] - x[l]);
+            sum += prod;
+        }
+        w[i] = sum;
+    }
+}
+
+// Fourth-order staggered weights of one axis (Sec. 2, high-order differences on the
+// non-uniform grid): the half node p from the nodes p-1 .. p+2 and the node q from
+// the half nodes q-2 .. q+1, each exact for cubics; two-point rows where four points
+// do not fit (half nodes 0 and n-1, nodes 1 and n-1).  Returns the largest absolute
+// row sum touching a cell (the bound of the difference's symbol, for the CFL step).
+double ho_axis(Axis &A) {
+    const int n = A.n;
+    A.wh.assign(4 * (size_t)n, 0.0);
+    A.wn.assign(4 * (size_t)(n + 1), 0.0);
+    std::vector<double> xh(n);
+    for (int i = 0; i < n; ++i) xh[i] = 0.5 * (A.x[i] + A.x[i + 1]);
+    for (int p = 0; p < n; ++p) {
+        if (p >= 1 && p <= n - 2) lagrange_d1(xh[p], &A.x[p - 1], &A.wh[4 * p]);
+        else { A.wh[4 * p + 1] = -1.0 / A.h[p]; A.wh[4 * p + 2] = 1.0 / A.h[p]; }
+    }
+    for (int q = 1; q < n; ++q) {
+        if (q >= 2 && q <= n - 2) lagrange_d1(A.x[q], &xh[q - 2], &A.wn[4 * q]);
+        else { A.wn[4 * q + 1] = -1.0 / A.ht[q]; A.wn[4 * q + 2] = 1.0 / A.ht[q]; }
+    }
+    auto rs = [](const double *w) { return std::fabs(w[0]) + std::fabs(w[1]) + std::fabs(w[2]) + std::fabs(w[3]); };
+    double smax = 0.0;
+    for (int i = 0; i < n; ++i)
+        smax = std::max(smax, std::max(rs(&A.wh[4 * i]), std::max(rs(&A.wn[4 * i]), rs(&A.wn[4 * (i + 1)]))));
+    return smax;
+}
 
 // CPML recursion coefficients psi <- b psi + a du (Komatitsch & Martin 2007 with
 // kappa = 1): d = d0 (xi/L)^2, d0 = -3 v ln(R) / (2 L), alpha = pi f0 (1 - xi/L),
@@ -87,6 +131,8 @@ struct csem_ctx {
     double f0, w0, rho_max, dt, safety;
     int nt, precision, kahan, nf, max_src, max_rec;
     int vti = 0;                         // 1: models [2][cells] = (rho_h, rho_v), gradients (h, v)
+    int order = 2;                       // spatial order of the differences: 2 (Yee) or 4
+    void *d_ho = nullptr;                // fourth order: weight tables (real) wxh|wxn|wyh|wyn|wzh|wzn
     std::vector<double> freqs, a;        // a_k = sqrt(w_k w0)
     std::vector<std::complex<double>> kf, alpha_fwd;
     std::vector<double> wavelet;         // J'(t_{n+1/2})
@@ -410,6 +456,25 @@ cudaError_t flush(csem_ctx *c, const csem::StepParams<R> &p, const csem::PointPa
     return csem::launch_dft<R>(p, q, S, n0_off, cnt, vol, kahan, st);
 }
 
+template <typename R>
+csem::HoTab<R> ho_tab(const csem_ctx *c) {
+    const R *t = (const R *)c->d_ho;
+    csem::HoTab<R> w;
+    const int nx = c->nx, ny = c->ny, nz = c->nz;
+    w.wxh = t; w.wxn = w.wxh + 4 * nx;
+    w.wyh = w.wxn + 4 * (nx + 1); w.wyn = w.wyh + 4 * ny;
+    w.wzh = w.wyn + 4 * (ny + 1); w.wzn = w.wzh + 4 * nz;
+    return w;
+}
+
+// One step (or its H / E half, which: bit 0 H, bit 2 E) with the kernels of the context's order.
+template <typename R>
+cudaError_t launch_any(const csem_ctx *c, const csem::StepParams<R> &p, const csem::PointParams<R> &q, int S,
+                       int jstep, cudaStream_t st, int which = 5) {
+    if (c->order == 4) return csem::launch_ho<R>(p, ho_tab<R>(c), S, jstep, st, which);
+    return csem::launch_step<R>(p, q, S, jstep, st, which);
+}
+
 // Tap increments of the next nsteps steps for the lean E kernel (FP32 runs with injection).
 template <typename R>
 cudaError_t tap_prep(csem_ctx *c, const csem::StepParams<R> &p, int S, int nsteps, cudaStream_t st) {
@@ -461,7 +526,7 @@ cudaError_t emit_steps(csem_ctx *c, int S, bool vol, bool kahan, const csem::Ste
     if (lead) e = overlap ? side_flush(-M) : flush<R>(c, p, q, S, -M, M, vol, kahan, st);
     for (int j = 0; j < n && e == cudaSuccess; ++j) {
         if (overlap) e = join(j);
-        if (e == cudaSuccess) e = csem::launch_step<R>(p, q, S, j, st);
+        if (e == cudaSuccess) e = launch_any<R>(c, p, q, S, j, st);
         if (e != cudaSuccess || (j + 1) % M != 0 || (j + 1 == n && !trail)) continue;
         e = overlap ? side_flush(j + 1 - M) : flush<R>(c, p, q, S, j + 1 - M, M, vol, kahan, st);
     }
@@ -541,7 +606,7 @@ int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const 
         if (overlap) CK(flush<R>(c, p, q, S, -M, M, vol, kahan, st));
     }
     auto emit = [&](int j, cudaStream_t s2) -> cudaError_t {
-        cudaError_t e = csem::launch_step<R>(p, q, S, j, s2);
+        cudaError_t e = launch_any<R>(c, p, q, S, j, s2);
         if (e == cudaSuccess && (j + 1) % M == 0) e = flush<R>(c, p, q, S, j + 1 - M, M, vol, kahan, s2);
         return e;
     };
@@ -817,7 +882,7 @@ int run_range(csem_ctx *c, int S, int role, RoleGraph &g, const csem::StepParams
                              c->LEAN_h * 2 + c->LEAN_e)};
         TRY(chunk_graph(c, key, [&](cudaStream_t cs) {
             cudaError_t e = tap_prep<R>(c, p, S, kChunk, cs);
-            for (int j = 0; j < kChunk && e == cudaSuccess; ++j) e = csem::launch_step<R>(p, q, S, j, cs);
+            for (int j = 0; j < kChunk && e == cudaSuccess; ++j) e = launch_any<R>(c, p, q, S, j, cs);
             if (e == cudaSuccess) e = csem::launch_advance(c->d_step, kChunk, cs);
             return e;
         }, &g.exec, &g.per_chunk));
@@ -828,7 +893,7 @@ int run_range(csem_ctx *c, int S, int role, RoleGraph &g, const csem::StepParams
     }
     if (rem > 0) {
         CK(tap_prep<R>(c, p, S, rem, st));
-        for (int j = 0; j < rem; ++j) CK(csem::launch_step<R>(p, q, S, j, st));
+        for (int j = 0; j < rem; ++j) CK(launch_any<R>(c, p, q, S, j, st));
     }
     return CSEM_OK;
 }
@@ -995,7 +1060,7 @@ int time_impl(csem_ctx *c, int S, void *vol, int launches, double *ms, cudaStrea
             if (w == 3) return flush<R>(c, p, q, S, 0, cnt, true, c->kahan != 0, st);
             csem::StepParams<R> pp = p;
             pp.fused_kz = (w == 1) ? fkz : 0;
-            return csem::launch_step<R>(pp, q, S, j % jmod, st, w == 1 ? 5 : (w == 0 ? 1 : 4));
+            return launch_any<R>(c, pp, q, S, j % jmod, st, w == 1 ? 5 : (w == 0 ? 1 : 4));
         };
         for (int j = 0; j < 2; ++j) CK(go(j));
         CK(cudaEventRecord(e0, st));
@@ -1022,65 +1087,67 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const int kzs[4] = {1, 2, 4, 8};
-    const int mbs[3] = {4, 6, 8};
-    for (int which : {1, 4}) {
-        double best = 1e30;
-        int best_kz = 4, best_mb = 4, best_vec = 0;
-        const int maxty = (sizeof(R) == 4) ? csem::tma_max_rows(c->pitch) : 0;
-        const int ntma = maxty >= 4 ? 12 : (maxty >= 2 ? 8 : (maxty >= 1 ? 4 : 0));
-        const int nlean = (sizeof(R) == 4 && c->d_psiL) ? 15 : 0;
-        const int ncand = (sizeof(R) == 4) ? 20 + ntma + nlean : 12;   // 12 scalar, 8 four-cell, staged, lean
-        int best_tma = 0, best_lean = 0;
-        for (int cand = 0; cand < ncand; ++cand) {
-            const int lc = cand - 20 - ntma;
-            const int lean = (lc >= 0) ? (lc < 6 ? 1 : 2) : 0;                            // cells per thread 1, 2
-            const int vec = (cand >= 12 && cand < 20) ? 1 : 0;
-            const int tma = (cand >= 20 && !lean) ? (1 << ((cand - 20) / 4)) : 0;          // rows per block 1, 2, 4
-            const int tkz[4] = {2, 4, 8, 16}, lkz[3] = {1, 2, 4};
-            const int kz = lean ? lkz[lc % 3] : (tma ? tkz[(cand - 20) % 4] : kzs[cand % 4]);
-            const int lmb[3] = {6, 8, 4};   // 1 cell: 6, 8; 2 cells: 6, 8, 4 blocks of 128 threads per SM
-            const int mb = lean ? lmb[(lc % (lc < 6 ? 6 : 9)) / 3] : (tma ? 4 : (vec ? mbs[(cand - 12) / 4] : mbs[cand / 4]));
-            p.KZ_h = p.KZ_e = kz;
-            p.MB_h = p.MB_e = mb;
-            p.VEC_h = p.VEC_e = vec;
-            p.TMA_h = p.TMA_e = tma;
-            p.LEAN_h = p.LEAN_e = lean;
-            for (int j = 0; j < 3; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, which));
-            CK(cudaEventRecord(e0, st));
-            const int reps = 20;
-            for (int j = 0; j < reps; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, which));
-            CK(cudaEventRecord(e1, st));
-            CK(cudaEventSynchronize(e1));
-            float t = 0.f;
-            CK(cudaEventElapsedTime(&t, e0, e1));
-            if (t < best) { best = t; best_kz = kz; best_mb = mb; best_vec = vec; best_tma = tma; best_lean = lean; }
+    if (c->order == 2) {   // the fourth-order kernels have one launch shape
+        const int kzs[4] = {1, 2, 4, 8};
+        const int mbs[3] = {4, 6, 8};
+        for (int which : {1, 4}) {
+            double best = 1e30;
+            int best_kz = 4, best_mb = 4, best_vec = 0;
+            const int maxty = (sizeof(R) == 4) ? csem::tma_max_rows(c->pitch) : 0;
+            const int ntma = maxty >= 4 ? 12 : (maxty >= 2 ? 8 : (maxty >= 1 ? 4 : 0));
+            const int nlean = (sizeof(R) == 4 && c->d_psiL) ? 15 : 0;
+            const int ncand = (sizeof(R) == 4) ? 20 + ntma + nlean : 12;   // 12 scalar, 8 four-cell, staged, lean
+            int best_tma = 0, best_lean = 0;
+            for (int cand = 0; cand < ncand; ++cand) {
+                const int lc = cand - 20 - ntma;
+                const int lean = (lc >= 0) ? (lc < 6 ? 1 : 2) : 0;                            // cells per thread 1, 2
+                const int vec = (cand >= 12 && cand < 20) ? 1 : 0;
+                const int tma = (cand >= 20 && !lean) ? (1 << ((cand - 20) / 4)) : 0;          // rows per block 1, 2, 4
+                const int tkz[4] = {2, 4, 8, 16}, lkz[3] = {1, 2, 4};
+                const int kz = lean ? lkz[lc % 3] : (tma ? tkz[(cand - 20) % 4] : kzs[cand % 4]);
+                const int lmb[3] = {6, 8, 4};   // 1 cell: 6, 8; 2 cells: 6, 8, 4 blocks of 128 threads per SM
+                const int mb = lean ? lmb[(lc % (lc < 6 ? 6 : 9)) / 3] : (tma ? 4 : (vec ? mbs[(cand - 12) / 4] : mbs[cand / 4]));
+                p.KZ_h = p.KZ_e = kz;
+                p.MB_h = p.MB_e = mb;
+                p.VEC_h = p.VEC_e = vec;
+                p.TMA_h = p.TMA_e = tma;
+                p.LEAN_h = p.LEAN_e = lean;
+                for (int j = 0; j < 3; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, which));
+                CK(cudaEventRecord(e0, st));
+                const int reps = 20;
+                for (int j = 0; j < reps; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, which));
+                CK(cudaEventRecord(e1, st));
+                CK(cudaEventSynchronize(e1));
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, e0, e1));
+                if (t < best) { best = t; best_kz = kz; best_mb = mb; best_vec = vec; best_tma = tma; best_lean = lean; }
+            }
+            if (which == 1) { c->KZ_h = best_kz; c->MB_h = best_mb; c->VEC_h = best_vec; c->TMA_h = best_tma; c->LEAN_h = best_lean; }
+            else { c->KZ_e = best_kz; c->MB_e = best_mb; c->VEC_e = best_vec; c->TMA_e = best_tma; c->LEAN_e = best_lean; }
         }
-        if (which == 1) { c->KZ_h = best_kz; c->MB_h = best_mb; c->VEC_h = best_vec; c->TMA_h = best_tma; c->LEAN_h = best_lean; }
-        else { c->KZ_e = best_kz; c->MB_e = best_mb; c->VEC_e = best_vec; c->TMA_e = best_tma; c->LEAN_e = best_lean; }
-    }
-    // fused H+E step (kz 4, 8, 16) against the best split pair
-    {
-        p.KZ_h = c->KZ_h; p.KZ_e = c->KZ_e; p.MB_h = c->MB_h; p.MB_e = c->MB_e;
-        p.VEC_h = c->VEC_h; p.VEC_e = c->VEC_e;
-        p.TMA_h = c->TMA_h; p.TMA_e = c->TMA_e;
-        p.LEAN_h = c->LEAN_h; p.LEAN_e = c->LEAN_e;
-        double best = 1e30;
-        int best_f = 0;
-        for (int f : {0, 4, 8, 16}) {
-            p.fused_kz = f;
-            for (int j = 0; j < 3; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, 5));
-            CK(cudaEventRecord(e0, st));
-            const int reps = 20;
-            for (int j = 0; j < reps; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, 5));
-            CK(cudaEventRecord(e1, st));
-            CK(cudaEventSynchronize(e1));
-            float t = 0.f;
-            CK(cudaEventElapsedTime(&t, e0, e1));
-            if (t < best) { best = t; best_f = f; }
+        // fused H+E step (kz 4, 8, 16) against the best split pair
+        {
+            p.KZ_h = c->KZ_h; p.KZ_e = c->KZ_e; p.MB_h = c->MB_h; p.MB_e = c->MB_e;
+            p.VEC_h = c->VEC_h; p.VEC_e = c->VEC_e;
+            p.TMA_h = c->TMA_h; p.TMA_e = c->TMA_e;
+            p.LEAN_h = c->LEAN_h; p.LEAN_e = c->LEAN_e;
+            double best = 1e30;
+            int best_f = 0;
+            for (int f : {0, 4, 8, 16}) {
+                p.fused_kz = f;
+                for (int j = 0; j < 3; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, 5));
+                CK(cudaEventRecord(e0, st));
+                const int reps = 20;
+                for (int j = 0; j < reps; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, 5));
+                CK(cudaEventRecord(e1, st));
+                CK(cudaEventSynchronize(e1));
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, e0, e1));
+                if (t < best) { best = t; best_f = f; }
+            }
+            c->fused_kz = best_f;
+            p.fused_kz = 0;
         }
-        c->fused_kz = best_f;
-        p.fused_kz = 0;
     }
     // transform flush: register or bulk copy (FP32), 16 or 32 snapshots, after
     // its block or overlapping the next one (when the ring has room); each
@@ -1131,7 +1198,7 @@ void free_ctx(csem_ctx *c) {
     if (!c) return;
     cudaDeviceSynchronize();
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
-    void *ptrs[] = {c->d_tabL, c->d_psiL, c->d_cEm, c->d_inc, c->d_tapk, c->d_tab, c->d_h, c->d_cE, c->d_H, c->d_H2, c->d_ering, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
+    void *ptrs[] = {c->d_ho, c->d_tabL, c->d_psiL, c->d_cEm, c->d_inc, c->d_tapk, c->d_tab, c->d_h, c->d_cE, c->d_H, c->d_H2, c->d_ering, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
                     c->d_alpha, c->d_racc, c->d_coef, c->d_T, c->d_ones, c->d_rtaps, c->d_itaps, c->d_colmap, c->d_tflag, c->d_cpos, c->d_cval, c->d_step, c->d_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -1161,6 +1228,7 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
         return fail(CSEM_ERR_INVALID_ARG, "n_freq must be in 1..8");
     if (!(o->f0 > 0.0) || !(o->rho_max > 0.0)) return fail(CSEM_ERR_INVALID_ARG, "f0 and rho_max must be > 0");
     if (o->anisotropy != 0 && o->anisotropy != 1) return fail(CSEM_ERR_INVALID_ARG, "anisotropy must be 0 or 1");
+    if (o->order != 0 && o->order != 2 && o->order != 4) return fail(CSEM_ERR_INVALID_ARG, "order must be 2 or 4");
     if (o->max_src < 1 || o->max_rec < 0 || o->max_src > 65535)
         return fail(CSEM_ERR_INVALID_ARG, "max_src must be >= 1, max_rec >= 0");
     for (int f = 0; f < o->n_freq; ++f)
@@ -1200,7 +1268,15 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     c->safety = o->cfl_safety > 0.0 ? o->cfl_safety : 0.99;
     // fictitious speed v = 1/sqrt(mu0 eps), eps = sigma/(2 w0)  (Eq. 2)
     const double vmax = std::sqrt(2.0 * c->w0 * c->rho_max / kMu0);
-    const double dt_lim = 1.0 / (vmax * std::sqrt(inv2max[0] + inv2max[1] + inv2max[2]));
+    c->order = o->order == 4 ? 4 : 2;
+    double dt_lim = 1.0 / (vmax * std::sqrt(inv2max[0] + inv2max[1] + inv2max[2]));
+    if (c->order == 4) {
+        // leap-frog limit 2 / (v sqrt(sum over axes of the largest symbol squared)); the
+        // cells form a tensor product, so the largest sum is the sum of the per-axis maxima
+        double s2 = 0.0;
+        for (int a = 0; a < 3; ++a) { const double sm = ho_axis(c->ax[a]); s2 += sm * sm; }
+        dt_lim = 2.0 / (vmax * std::sqrt(s2));
+    }
     if (o->dt > 0.0) {
         if (o->dt > dt_lim * (1.0 + 1e-12)) {
             delete c;
@@ -1235,7 +1311,7 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     c->sx = pad8((long long)c->NZ * c->NY * np2);
     c->sy = pad8((long long)c->NZ * np2 * c->pitch);
     c->sz = pad8((long long)np2 * c->NY * c->pitch);
-    c->psi_stride = 6 * (c->sx + c->sy + c->sz);
+    c->psi_stride = c->order == 4 ? 12 * c->vol : 6 * (c->sx + c->sy + c->sz);
     c->wavelet.assign(c->nt, 0.0);
     c->wavelet[0] = 1.0 / c->dt;
 
@@ -1285,7 +1361,24 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
     step(dalloc(c, &c->d_step, sizeof(int)));
     step(dalloc(c, &c->d_bad, sizeof(int)));
     // lean FP32 kernels: CPML memory as 12 volume arrays per source and the masked dt/eps
-    if (rc == CSEM_OK && c->precision == 32 && c->nx % 4 == 0) {
+    if (rc == CSEM_OK && c->order == 4) {
+        std::vector<double> t;
+        for (int a = 0; a < 3; ++a) {
+            t.insert(t.end(), c->ax[a].wh.begin(), c->ax[a].wh.end());
+            t.insert(t.end(), c->ax[a].wn.begin(), c->ax[a].wn.end());
+        }
+        if (c->precision == 32) {
+            std::vector<float> tf(t.begin(), t.end());
+            step(dalloc(c, (float **)&c->d_ho, tf.size() * sizeof(float)));
+            if (rc == CSEM_OK && cudaMemcpy(c->d_ho, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+                rc = fail(CSEM_ERR_CUDA, "context initialisation failed");
+        } else {
+            step(dalloc(c, (double **)&c->d_ho, t.size() * sizeof(double)));
+            if (rc == CSEM_OK && cudaMemcpy(c->d_ho, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+                rc = fail(CSEM_ERR_CUDA, "context initialisation failed");
+        }
+    }
+    if (rc == CSEM_OK && c->order == 2 && c->precision == 32 && c->nx % 4 == 0) {
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
         const double need = ((double)S * 12 + 3) * c->vol * sizeof(float);
@@ -1340,6 +1433,7 @@ int csem_get_info(const csem_ctx *c, csem_info *info) {
     if (!c || !info) return fail(CSEM_ERR_INVALID_ARG, "NULL argument");
     info->nx = c->nx; info->ny = c->ny; info->nz = c->nz; info->npml = c->npml;
     info->pitch = c->pitch; info->vol_elems = c->vol; info->dt = c->dt; info->nt = c->nt;
+    info->order = c->order;
     info->precision = c->precision; info->kahan = c->kahan; info->n_freq = c->nf;
     info->max_src = c->max_src; info->max_rec = c->max_rec; info->workspace_bytes = c->bytes;
     info->transform_block = c->M;
@@ -1464,6 +1558,8 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
         fm < 0 || fm > 3 || ((fm & 1) && c->precision != 32) || !(M == 16 || M == 32 || M == 64) ||
         ((fm & 2) ? 2 * M : M) + 1 > c->nslot)
         return fail(CSEM_ERR_INVALID_ARG, "launch configuration not supported by this context");
+    if (c->order == 4 && (fkz || vh || ve || th || te || lh || le))
+        return fail(CSEM_ERR_INVALID_ARG, "a fourth-order context runs its own H and E kernels only");
     CK(cudaDeviceSynchronize());
     c->KZ_h = kzh; c->MB_h = mbh; c->KZ_e = kze; c->MB_e = mbe;
     c->fused_kz = fkz; c->flush_mode = fm; c->M = M;

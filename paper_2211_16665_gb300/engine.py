@@ -42,17 +42,18 @@ class Engine:
     """One context: grid, frequencies, dt/nt, precision, batch capacity.
 
     vti=True: a VTI medium (Sec. 2); models are (2, nz, ny, nx) = (rho_h, rho_v) and
-    gradients (2, nz, ny, nx) = (h, v) (Sec. 3.1, Eq. 15)."""
+    gradients (2, nz, ny, nx) = (h, v) (Sec. 3.1, Eq. 15).  order=4: four-point staggered
+    differences on the non-uniform grid instead of the two-point Yee ones."""
 
     def __init__(self, xn, yn, zn, npml, freqs, f0=1.0, rho_max=1.0, precision=32, kahan=1,
-                 max_src=1, max_rec=0, nt=0, dt=0.0, device=None, autotune=True, vti=False):
+                 max_src=1, max_rec=0, nt=0, dt=0.0, device=None, autotune=True, vti=False, order=2):
         if not torch.cuda.is_available():
             raise RuntimeError("the CSEM engine needs a CUDA device")
         self.device = torch.device(device or "cuda")
         with torch.cuda.device(self.device):
             self.ctx = _capi.create(xn, yn, zn, npml, freqs, f0=f0, rho_max=rho_max, dt=dt, nt=nt,
                                     precision=precision, kahan=kahan, max_src=max_src, max_rec=max_rec,
-                                    anisotropy=1 if vti else 0)
+                                    anisotropy=1 if vti else 0, order=order)
         info = _capi.get_info(self.ctx)
         self.info = info
         self.nx, self.ny, self.nz = info.nx, info.ny, info.nz
@@ -61,6 +62,7 @@ class Engine:
         self.precision = precision
         self.rho_max = float(rho_max)
         self.vti = bool(vti)
+        self.order = info.order
         self.freqs = np.asarray(freqs, np.float64)
         self.nf = self.freqs.size
         self.f0 = f0

@@ -51,5 +51,5 @@ def test_struct_layouts_match_header_sizes():
     # pointer-sized fields on LP64: grid = 3 ints (+pad) + 3 ptrs + int (+pad)
     assert ctypes.sizeof(_capi.Grid) == 48
     assert ctypes.sizeof(_capi.PointsC) == 40
-    assert ctypes.sizeof(_capi.Info) == 80
+    assert ctypes.sizeof(_capi.Info) == 88
     assert ctypes.sizeof(_capi.Opts) == 80
