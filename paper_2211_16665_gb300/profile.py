@@ -30,9 +30,10 @@ def main():
     ap.add_argument("--launch", default="", help="JSON keyword arguments of Engine.set_launch (skips autotuning)")
     ap.add_argument("--td", action="store_true", help="run a time-domain adjoint gradient instead")
     ap.add_argument("--segment", type=int, default=0, help="segment length of --td (0: the plan's)")
+    ap.add_argument("--order", type=int, default=2, choices=[2, 4], help="spatial order of the differences")
     args = ap.parse_args()
     wl = W.ALL[args.workload]()
-    eng = Engine.from_workload(wl, nt=args.nt, kahan=args.kahan, autotune=not args.launch)
+    eng = Engine.from_workload(wl, nt=args.nt, kahan=args.kahan, autotune=not args.launch, order=args.order)
     if args.launch:
         import json
         eng.set_launch(**json.loads(args.launch))
