@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--order", type=int, default=2, choices=[2, 4],
                     help="spatial order of the staggered differences (4: four-point kernels)")
     ap.add_argument("--inversion", type=int, default=0, help="run this many iterations of the outer inversion loop")
+    ap.add_argument("--early-stop", type=float, default=0.0,
+                    help="time forward data runs with the early end at this tolerance against full runs")
     ap.add_argument("--td", type=int, default=0,
                     help="time this many time-domain adjoint gradients against the basis route")
     ap.add_argument("--cpu-steps", type=int, default=2000, help="time steps in the oracle sample")
@@ -469,6 +471,8 @@ def run_inversion(args):
     wl = make_workload(args.workload, 0, 1)
     eng = Engine.from_workload(wl)
     d_true = eng.fwd_model(eng.model_tensor(wl.rho_true), wl.src, wl.rec).cpu().numpy()
+    if args.early_stop > 0:
+        eng.set_early_stop(args.early_stop)    # the line-search forwards keep no volumes
     d_obs = W.add_noise(d_true, wl.noise, wl.noise_seed)
     dx = wl.rec.x[None, :] - wl.src.x[:, None]
     dy = wl.rec.y[None, :] - wl.src.y[:, None]
@@ -502,7 +506,8 @@ def run_inversion(args):
                                   "end": float(np.exp(m.cpu().numpy()[slab].mean())),
                                   "true": float(wl.rho_true[slab].mean())},
            "largest_update": {"ln_rho": float(upd.max()), "depth_m": float(0.5 * (wl.zn[kz] + wl.zn[kz + 1]))},
-           "basis_fit": fit, "data": "synthetic, 1 % noise (seed 42), 600 m mute, 3 % relative-error weights"}
+           "basis_fit": fit, "early_stop_tol": args.early_stop,
+           "data": "synthetic, 1 % noise (seed 42), 600 m mute, 3 % relative-error weights"}
     print(json.dumps(out))
 
 
@@ -553,16 +558,49 @@ def run_td(args):
     print(json.dumps(out))
 
 
+def run_early_stop(args):
+    """Forward data runs (receivers only) on the thin reservoir with the early end of Sec. 2
+    at the given tolerance against full runs: ms per run, steps, relative L2 change of the data."""
+    import torch
+    from paper_2211_16665_gb300.engine import Engine
+    torch.cuda.set_device(0)
+    wl = make_workload(args.workload, 0, 1)
+    eng = Engine.from_workload(wl)
+    rho = eng.model_tensor(wl.rho)
+    out = {"mode": "early_stop", "workload": wl.name, "nt": eng.nt, "tol": args.early_stop}
+    data = {}
+    for name, tol in (("full", 0.0), ("early", args.early_stop)):
+        eng.set_early_stop(tol)
+        for _ in range(args.warmup):
+            d = eng.fwd_model(rho, wl.src, wl.rec)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            d = eng.fwd_model(rho, wl.src, wl.rec)
+        ev1.record()
+        torch.cuda.synchronize()
+        out[f"ms_per_run_{name}"] = round(ev0.elapsed_time(ev1) / args.steps, 3)
+        out[f"steps_{name}"] = eng.last_run_steps()
+        data[name] = d.cpu().numpy()
+    out["speedup"] = round(out["ms_per_run_full"] / out["ms_per_run_early"], 3)
+    out["rel_l2_data_change"] = float(np.linalg.norm(data["early"] - data["full"]) / np.linalg.norm(data["full"]))
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
+    if args.inversion:
+        run_inversion(args)
+        return
+    if args.early_stop > 0:
+        run_early_stop(args)
+        return
     if args.td:
         run_td(args)
         return
     if args.batched_vs_plain:
         run_batched_vs_plain(args)
-        return
-    if args.inversion:
-        run_inversion(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -257,6 +257,22 @@ int csem_gradient_td(csem_ctx *ctx, const void *rho_dev, const csem_points *src,
                      const double *resid_dev, int segment, int wrt, void *grad_dev, void *work_dev,
                      long long work_bytes, void *stream);
 
+/* Early end of forward data runs (Sec. 2: the stepping can stop once the
+ * frequency-domain field has reached its steady state, checked regularly during
+ * the run).  tol > 0: csem_fwd_model calls that keep no volumes (Evol_dev NULL,
+ * at least one receiver) check, after every 64 steps, the running transform
+ * R_c[s][r][k] = sum_{n < 64 (c+1)} w_{k,n} E^n(x_r) and end after the first
+ * chunk c >= 1 with |R_c - R_{c-1}| <= tol |R_c| for every source, receiver and
+ * frequency; the data are then alpha_k R_c.  The transform is flushed after each
+ * block (never overlapped) in these runs.  tol = 0 turns the check off (the
+ * default).  Runs that keep volumes, adjoint runs and csem_gradient_td always
+ * take nt steps.  The first call with tol > 0 allocates the check's buffers.
+ * csem_last_run_steps: the steps whose snapshots the last csem_fwd_model data
+ * include (nt unless that run ended early); synchronises stream.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int csem_set_early_stop(csem_ctx *ctx, double tol);
+int csem_last_run_steps(csem_ctx *ctx, void *stream, int *steps);
+
 /* Picks the launch shape of the H and E stepping kernels -- z planes per
  * thread (1, 2, 4, 8), the register budget (4, 6 or 8 resident 256-thread
  * blocks per SM), and for FP32 one or four cells per thread along x, the

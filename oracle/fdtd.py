@@ -7,6 +7,7 @@ adjoint source estimation"):
   Sec. 2, Eq. 2-3  sigma = 2 w0 eps, J' = k J, E' = E, k = sqrt(-i w / 2 w0)
   Sec. 2, Eq. 4    fictitious-time Maxwell system, leap-frog on a staggered grid
   Sec. 2, Eq. 6    on-the-fly damped transform, no dt factor, n = 0..nt-1
+  Sec. 2           early end of a forward run once the receiver spectra stop changing
   Sec. 3.1, Eq. 7  misfit 1/2 ||W (d - R u)||^2
   Sec. 3.1         gradient -Re sum_s sum_w conj(v_E) . E, scaled by cell volume
   Sec. 3.2, Eq. 14 conj(v) from the same engine with conjugated residual sources
@@ -524,6 +525,43 @@ def forward(pb: Problem, rho, src, rec, keep_volume=False, wavelet=None, nt_run=
     if return_trace:
         out.append(traces)
     return out[0] if len(out) == 1 else tuple(out)
+
+
+def forward_early_stop(pb: Problem, rho, src, rec, tol: float, chunk: int = 64, wavelet=None):
+    """Receiver spectra with the early end of Sec. 2 (stepping ends once the frequency-domain
+    field has reached its steady state, checked regularly during the run).
+
+    All sources advance together in chunks of `chunk` steps.  After chunk c the running
+    transform R_c[s, r, k] = sum_{n < chunk (c+1)} w_{k,n} E^n(x_r) is compared with R_{c-1};
+    the run ends after the first chunk c >= 1 with |R_c - R_{c-1}| <= tol |R_c| for every
+    source, receiver and frequency, or at nt.  Returns (d = alpha_k R, steps run).
+    """
+    st = Stepper(pb, rho)
+    nt = pb.nt
+    wav = pb.impulse() if wavelet is None else np.asarray(wavelet, float)
+    norm = pb.k / pb.wavelet_spectrum(wav)
+    W = pb.dft_weights()
+    taps = []
+    for r in range(rec.n):
+        taps += point_taps(pb, rec, r)
+    states = [st.new_state() for _ in range(src.n)]
+    injs = [point_taps(pb, src, s, scale_by_dV=st.dV, tag=0) for s in range(src.n)]
+    traces = [np.zeros(rec.n * nt) for _ in range(src.n)]
+    prev = None
+    n1 = 0
+    for c in range((nt + chunk - 1) // chunk):
+        n0, n1 = c * chunk, min(nt, (c + 1) * chunk)
+        for s in range(src.n):
+            fields, psi = states[s]
+            st.run(fields, psi, n0, n1, inj=injs[s], series=wav[None, :], taps=taps, n_rec=rec.n,
+                   trace=traces[s])
+        R = np.stack([tr.reshape(rec.n, nt)[:, :n1] @ W[:n1] for tr in traces])
+        if n1 == nt:
+            break
+        if prev is not None and np.all(np.abs(R - prev) <= tol * np.abs(R)):
+            break
+        prev = R
+    return R * norm[None, None, :], n1
 
 
 def misfit(d_obs, d_syn, weights=None):

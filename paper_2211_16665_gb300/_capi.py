@@ -70,6 +70,8 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_longlong)]),
     "csem_gradient_td": (ctypes.c_int, [_V, _V, ctypes.POINTER(PointsC), ctypes.POINTER(PointsC), _V, ctypes.c_int,
                                         ctypes.c_int, _V, _V, ctypes.c_longlong, _V]),
+    "csem_set_early_stop": (ctypes.c_int, [_V, ctypes.c_double]),
+    "csem_last_run_steps": (ctypes.c_int, [_V, _V, _I]),
     "csem_autotune": (ctypes.c_int, [_V, ctypes.c_int, _I, _V]),
     "csem_set_launch": (ctypes.c_int, [_V, _I]),
     "csem_set_wavelet": (ctypes.c_int, [_V, _D]),
@@ -197,6 +199,16 @@ def gradient_td(ctx, rho_ptr, src, rec, resid_ptr, segment, wrt, grad_ptr, work_
     _check(lib().csem_gradient_td(ctx, rho_ptr, ctypes.byref(make_points(src, keep)),
                                   ctypes.byref(make_points(rec, keep)), resid_ptr, int(segment), int(wrt), grad_ptr,
                                   work_ptr, int(work_bytes), stream))
+
+
+def set_early_stop(ctx, tol):
+    _check(lib().csem_set_early_stop(ctx, float(tol)))
+
+
+def last_run_steps(ctx, stream) -> int:
+    v = ctypes.c_int(0)
+    _check(lib().csem_last_run_steps(ctx, stream, ctypes.byref(v)))
+    return v.value
 
 
 def autotune(ctx, n_src, stream):

@@ -62,5 +62,13 @@ class CsemForward(torch.autograd.Function):
 
 
 def forward_data(ln_rho, engine, src, rec, basis, chunk=None, recompute=False):
-    """d_syn = F(ln rho) with the adjoint-state gradient attached."""
+    """d_syn = F(ln rho) with the adjoint-state gradient attached.  Without a gradient to
+    attach (grad mode off, or ln_rho not requiring one) the runs keep no volumes, so the
+    engine's early end of data runs (Engine.set_early_stop) applies."""
+    if not (torch.is_grad_enabled() and ln_rho.requires_grad):
+        rho = torch.exp(ln_rho).to(engine.real).contiguous()
+        S = src.n
+        chunk = chunk or S
+        return torch.cat([engine.fwd_model(rho, src.subset(list(range(s0, min(S, s0 + chunk)))), rec)
+                          for s0 in range(0, S, chunk)], dim=0)
     return CsemForward.apply(ln_rho, engine, src, rec, basis, chunk, recompute)

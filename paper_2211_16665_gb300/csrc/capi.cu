@@ -16,6 +16,7 @@
 #include "csem_internal.cuh"
 #include "csem_td.cuh"
 #include "csem_ho.cuh"
+#include "csem_es.cuh"
 
 using csem::C2;
 using csem::Tap;
@@ -43,6 +44,7 @@ constexpr double kDecaySpan = 35.0;
 constexpr int kChunk = 64;        // time steps per captured graph
 constexpr int kBlockM = 64;        // largest snapshots per transform flush (divides kChunk)
 constexpr int kMaxSide = 4;       // event slots for overlapped flushes (at most two are in flight)
+constexpr int kEsDepth = 4;       // early end: chunks in flight before the host reads a convergence flag
 
 struct Axis {
     int n = 0;
@@ -175,6 +177,13 @@ struct csem_ctx {
     long long bytes = 0;
     cudaStream_t cap = nullptr, side = nullptr;
     cudaEvent_t ev_fork[kMaxSide] = {}, ev_done[kMaxSide] = {};
+    // early end of forward data runs (tol > 0): previous and kept receiver transforms,
+    // device state {ended, steps}, host copies of the ended flag per chunk slot
+    double es_tol = 0.0;
+    double2 *d_rprev = nullptr, *d_rfin = nullptr;
+    int *d_es = nullptr, *h_es = nullptr;
+    cudaEvent_t es_ev[kEsDepth] = {};
+    bool last_es = false;                // the last forward run used the early end
     struct GraphSlot { int key[8]; cudaGraphExec_t exec; };
     std::vector<GraphSlot> graphs;
 };
@@ -699,6 +708,63 @@ int upload_injection(csem_ctx *c, std::vector<Tap> &taps, int n_lists, int per_l
     return CSEM_OK;
 }
 
+// Forward data run with the early end (Sec. 2): whole chunks replay the captured
+// graph (block flushes in order, no overlap), each followed by the convergence
+// check; the host keeps at most kEsDepth chunks in flight and stops issuing once a
+// check it has read says the run has ended (chunks already issued then run, but
+// the kept spectra are those of the ending chunk).  Without an end the remainder
+// runs as in run_steps and the last check keeps the full transform.
+template <typename R>
+int run_steps_es(csem_ctx *c, int S, int NR, const csem::StepParams<R> &p, const csem::PointParams<R> &q,
+                 cudaStream_t st) {
+    const int saved = c->flush_mode;
+    c->flush_mode &= 1;
+    struct Restore { csem_ctx *c; int m; ~Restore() { c->flush_mode = m; } } restore{c, saved};
+    const int M = c->M, nt = c->nt, n = S * NR * c->nf;
+    const int full = nt / kChunk, rem = nt % kChunk;
+    CK(cudaMemsetAsync(c->d_es, 0, 2 * sizeof(int), st));
+    bool ended = false;
+    if (full > 0) {
+        const int key[8] = {S, 4, 0, q.n_itaps > 0 ? 1 : 0, 1, (int)sizeof(R),
+                            ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
+                            ((((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e) * 25 +
+                             c->TMA_h * 5 + c->TMA_e) * 4 + c->LEAN_h * 2 + c->LEAN_e};
+        cudaGraphExec_t exec = nullptr;
+        long long per_chunk = 0;
+        TRY(chunk_graph(c, key, [&](cudaStream_t cs) {
+            cudaError_t le = tap_prep<R>(c, p, S, kChunk, cs);
+            if (le == cudaSuccess) le = emit_steps<R>(c, S, false, false, p, q, kChunk, false, true, cs);
+            if (le == cudaSuccess) le = csem::launch_advance(c->d_step, kChunk, cs);
+            return le;
+        }, &exec, &per_chunk));
+        for (int ch = 0; ch < full; ++ch) {
+            const int slot = ch % kEsDepth;
+            if (ch >= kEsDepth) {
+                CK(cudaEventSynchronize(c->es_ev[slot]));
+                if (c->h_es[slot]) { ended = true; break; }
+            }
+            CK(cudaGraphLaunch(exec, st));
+            csem::g_launches += per_chunk;
+            const bool last = (ch == full - 1 && rem == 0);
+            CK(csem::launch_es_check(c->d_racc, c->d_rprev, c->d_rfin, n, c->es_tol, ch, last ? 1 : 0,
+                                     (ch + 1) * kChunk, c->d_es, st));
+            CK(cudaMemcpyAsync(&c->h_es[slot], c->d_es, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaEventRecord(c->es_ev[slot], st));
+        }
+    }
+    if (!ended && rem > 0) {
+        CK(tap_prep<R>(c, p, S, rem, st));
+        for (int j = 0; j < rem; ++j) {
+            CK(launch_any<R>(c, p, q, S, j, st));
+            if ((j + 1) % M == 0) CK(flush<R>(c, p, q, S, j + 1 - M, M, false, false, st));
+        }
+        const int tail = rem % M;
+        if (tail) CK(flush<R>(c, p, q, S, rem - tail, tail, false, false, st));
+        CK(csem::launch_es_check(c->d_racc, c->d_rprev, c->d_rfin, n, c->es_tol, full, 1, nt, c->d_es, st));
+    }
+    return CSEM_OK;
+}
+
 template <typename R>
 int fwd_impl(csem_ctx *c, const void *rho, const csem_points *src, const csem_points *rec, double *d_syn,
              void *Evol, cudaStream_t st) {
@@ -731,9 +797,13 @@ int fwd_impl(csem_ctx *c, const void *rho, const csem_points *src, const csem_po
     q.n_rec = NR; q.rtaps = c->d_rtaps; q.racc = c->d_racc; q.w64 = c->d_w64; q.trace = c->d_trace;
     q.n_itaps = 8; q.itaps = c->d_itaps; q.itap_stride = 8;
     q.n_emit = 1; q.J = 1; q.coef = c->d_ones; q.T = c->d_T;
-    TRY(run_steps<R>(c, S, dft, p, q, st));
+    const bool es = c->es_tol > 0.0 && NR > 0 && !dft;
+    if (es) TRY(run_steps_es<R>(c, S, NR, p, q, st));
+    else TRY(run_steps<R>(c, S, dft, p, q, st));
+    c->last_es = es;
     c->last_nrec = NR;
-    if (NR > 0) CK(csem::launch_finalize_receivers(c->d_racc, d_syn, S, NR, c->nf, c->d_alpha, st));
+    if (NR > 0)
+        CK(csem::launch_finalize_receivers(es ? c->d_rfin : c->d_racc, d_syn, S, NR, c->nf, c->d_alpha, st));
     if (dft)
         CK(csem::launch_finalize_volume<R>((typename C2<R>::T *)Evol,
                                            c->kahan ? (const typename C2<R>::T *)c->d_comp : nullptr, c->vol, S,
@@ -1202,6 +1272,11 @@ void free_ctx(csem_ctx *c) {
                     c->d_alpha, c->d_racc, c->d_coef, c->d_T, c->d_ones, c->d_rtaps, c->d_itaps, c->d_colmap, c->d_tflag, c->d_cpos, c->d_cval, c->d_step, c->d_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (void *p : {(void *)c->d_rprev, (void *)c->d_rfin, (void *)c->d_es})
+        if (p) cudaFree(p);
+    if (c->h_es) cudaFreeHost(c->h_es);
+    for (int k = 0; k < kEsDepth; ++k)
+        if (c->es_ev[k]) cudaEventDestroy(c->es_ev[k]);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->side) cudaStreamDestroy(c->side);
     for (int k = 0; k < kMaxSide; ++k) {
@@ -1526,6 +1601,30 @@ int csem_gradient_td(csem_ctx *c, const void *rho_dev, const csem_points *src, c
     return c->precision == 32
                ? td_impl<float>(c, rho_dev, src, rec, resid_dev, segment, wrt, grad_dev, work_dev, work_bytes, st)
                : td_impl<double>(c, rho_dev, src, rec, resid_dev, segment, wrt, grad_dev, work_dev, work_bytes, st);
+}
+
+int csem_set_early_stop(csem_ctx *c, double tol) {
+    if (!c || !(tol >= 0.0) || !std::isfinite(tol)) return fail(CSEM_ERR_INVALID_ARG, "tol must be finite and >= 0");
+    if (tol > 0.0 && !c->d_es) {
+        const size_t nb = (size_t)c->max_src * std::max(c->max_rec, 1) * c->nf * sizeof(double2);
+        TRY(dalloc(c, &c->d_rprev, nb));
+        TRY(dalloc(c, &c->d_rfin, nb));
+        TRY(dalloc(c, &c->d_es, 2 * sizeof(int)));
+        CK(cudaHostAlloc((void **)&c->h_es, kEsDepth * sizeof(int), cudaHostAllocDefault));
+        for (int k = 0; k < kEsDepth; ++k) CK(cudaEventCreateWithFlags(&c->es_ev[k], cudaEventDisableTiming));
+    }
+    c->es_tol = tol;
+    return CSEM_OK;
+}
+
+int csem_last_run_steps(csem_ctx *c, void *stream, int *steps) {
+    if (!c || !steps) return fail(CSEM_ERR_INVALID_ARG, "NULL argument");
+    if (!c->last_es) { *steps = c->nt; return CSEM_OK; }
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    int st[2] = {0, 0};
+    CK(cudaMemcpy(st, c->d_es, sizeof(st), cudaMemcpyDeviceToHost));
+    *steps = st[0] ? st[1] : c->nt;
+    return CSEM_OK;
 }
 
 long long csem_launch_count(void) { return csem::g_launches.load(); }

@@ -1,6 +1,7 @@
 // Set-up, normalisation, misfit, gradient and adjoint-basis kernels.
 #include "csem_internal.cuh"
 #include "csem_td.cuh"
+#include "csem_es.cuh"
 
 namespace csem {
 
@@ -192,6 +193,40 @@ cudaError_t launch_grad_cells(const GeoD &g, const R *rho, const R *pe, int wrt,
     const long long cells = (long long)g.nx * g.ny * g.nz;
     k_grad_cell<R><<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(g, pe, rho, vti ? rho + cells : nullptr, wrt,
                                                                       grad, vti ? grad + cells : nullptr);
+    g_launches++;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// early end of a forward data run: convergence of the running receiver transform
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_es_check(const double2 *racc, double2 *prev, double2 *fin, int n,
+                                                  double tol, int chunk, int last, int steps_at, int *state) {
+    __shared__ int moved;
+    if (state[0]) return;                      // already ended: the kept spectra stay
+    if (threadIdx.x == 0) moved = (chunk == 0) ? 1 : 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const double2 a = racc[t], b = prev[t];
+        const double dr = a.x - b.x, di = a.y - b.y;
+        if (sqrt(dr * dr + di * di) > tol * sqrt(a.x * a.x + a.y * a.y)) moved = 1;
+    }
+    __syncthreads();
+    const bool done = !moved || last;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const double2 a = racc[t];
+        prev[t] = a;
+        if (done) fin[t] = a;
+    }
+    if (done && threadIdx.x == 0) {
+        state[1] = steps_at;
+        state[0] = 1;
+    }
+}
+
+cudaError_t launch_es_check(const double2 *racc, double2 *prev, double2 *fin, int n, double tol, int chunk,
+                            int last, int steps_at, int *state, cudaStream_t st) {
+    k_es_check<<<1, 256, 0, st>>>(racc, prev, fin, n, tol, chunk, last, steps_at, state);
     g_launches++;
     return cudaGetLastError();
 }

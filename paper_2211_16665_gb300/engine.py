@@ -135,6 +135,15 @@ class Engine:
             out.append(tr)
         return out[0] if len(out) == 1 else tuple(out)
 
+    def set_early_stop(self, tol=0.0):
+        """Forward data runs (no volumes) end once the receiver spectra change by at most
+        tol (relative) over 64 steps (Sec. 2); 0 turns it off."""
+        _capi.set_early_stop(self.ctx, tol)
+
+    def last_run_steps(self) -> int:
+        """Steps the last fwd_model data include (synchronises the current stream)."""
+        return _capi.last_run_steps(self.ctx, _stream())
+
     def set_wavelet(self, wavelet=None):
         _capi.set_wavelet(self.ctx, wavelet)
 

@@ -1,0 +1,54 @@
+"""Pins of the early end of a forward run (Sec. 2: stepping can end once the
+frequency-domain field has reached its steady state):
+
+  S1  with tol = 0 no chunk qualifies (the late increments are never exactly zero):
+      all nt steps run and the spectra equal the plain forward run;
+  S2  the chunked run reproduces the plain run's traces, so the stop chunk is the
+      first chunk whose 64-step increment of the running transform, computed from
+      the plain run's traces, is within tol of the running value everywhere;
+  S3  the spectra after the early end differ from the full run by no more than a
+      small multiple of tol (the damped weights shrink the later increments), and a
+      smaller tol runs more steps.
+"""
+import numpy as np
+
+from oracle import fdtd
+from paper_2211_16665_gb300.workloads import small_box
+
+
+def case():
+    wl = small_box(n_core=10, h=100.0, npml=5, ratio=1.0, n_st=0, n_rec=4, n_freq=2)
+    return wl, fdtd.problem_from_workload(wl)
+
+
+def test_zero_tolerance_runs_everything():
+    wl, pb = case()
+    d_full = fdtd.forward(pb, wl.rho, wl.src, wl.rec)
+    d, steps = fdtd.forward_early_stop(pb, wl.rho, wl.src, wl.rec, 0.0)
+    assert steps == pb.nt
+    np.testing.assert_allclose(d, d_full, rtol=1e-13, atol=0)
+
+
+def test_stop_chunk_from_the_plain_run_and_error_bound():
+    wl, pb = case()
+    d_full, _, tr = fdtd.forward(pb, wl.rho, wl.src, wl.rec, keep_volume=True, return_trace=True)
+    W = pb.dft_weights()
+    norm = pb.k / pb.wavelet_spectrum(pb.impulse())
+    prev_steps = 0
+    for tol in (1e-4, 1e-6, 1e-8):
+        d, steps = fdtd.forward_early_stop(pb, wl.rho, wl.src, wl.rec, tol)
+        # first qualifying chunk from the plain run's traces
+        expect = pb.nt
+        prev = None
+        for c in range((pb.nt + 63) // 64):
+            n1 = min(pb.nt, 64 * (c + 1))
+            R = tr[:, :, :n1] @ W[:n1]
+            if n1 < pb.nt and prev is not None and np.all(np.abs(R - prev) <= tol * np.abs(R)):
+                expect = n1
+                break
+            prev = R
+        assert steps == expect < pb.nt
+        assert steps > prev_steps
+        prev_steps = steps
+        assert np.abs(d - d_full).max() <= 20 * tol * np.abs(d_full).max()
+        np.testing.assert_allclose(d, (tr[:, :, :steps] @ W[:steps]) * norm, rtol=1e-12)
