@@ -170,17 +170,24 @@ def kernel_bytes(wl, eng):
     return {k: v * units[k] for k, v in per.items()}, per
 
 
-# DRAM bytes (read + write) per launch of a kernel from one ncu capture (--set full,
-# cold cache, 128x128x96 thin reservoir, nt = 256 through the profile driver with the
-# launch configuration below), valid only for the source it was taken on: keyed by
-# workload, kernel, launch code (Engine.kz entry) and the SHA-1 of the kernel's source
-# file followed by the shared header.  Any other kernel reports null.
+# DRAM bytes (read + write) per launch of a kernel from ncu captures of
+# dram__bytes_read.sum and dram__bytes_write.sum (cold cache, 128x128x96 thin reservoir,
+# nt = 256 through the profile driver with the launch configurations of
+# profiles/traffic_lean_thin_reservoir.md; the mean over the captured launches), valid only
+# for the source they were taken on: keyed by workload, kernel, launch code (Engine.kz
+# entry) and the SHA-1 of the kernel's source file, with the shared header's SHA-1
+# checked separately.  Any other kernel reports null.
+_LEAN = "78b60ad8187d51577bc248ded4ea5cffa931c7e7"
+_STEP = "2b13003dc0a546c8de35f6b3b533bac6c5297935"
 NCU_TRAFFIC = {
-    ("thin_reservoir_128x128x96_fp32", "k_e", 16422, "78b60ad8187d51577bc248ded4ea5cffa931c7e7"): 66.876e6 + 3.342e6,
-    ("thin_reservoir_128x128x96_fp32", "k_h", 16422, "78b60ad8187d51577bc248ded4ea5cffa931c7e7"): 47.267e6 + 0.023e6,
-    ("thin_reservoir_128x128x96_fp32", "k_dft", 129, "2b13003dc0a546c8de35f6b3b533bac6c5297935"): 980.352e6 + 291.750e6,
+    ("thin_reservoir_128x128x96_fp32", "k_e", 16422, _LEAN): 66.875e6 + 1.251e6,
+    ("thin_reservoir_128x128x96_fp32", "k_h", 16422, _LEAN): 47.268e6 + 0.002e6,
+    ("thin_reservoir_128x128x96_fp32", "k_e", 16424, _LEAN): 66.885e6 + 1.476e6,
+    ("thin_reservoir_128x128x96_fp32", "k_h", 16424, _LEAN): 47.270e6 + 0.001e6,
+    ("thin_reservoir_128x128x96_fp32", "k_dft", 129, _STEP): 980.377e6 + 288.796e6,
+    ("thin_reservoir_128x128x96_fp32", "k_dft", 131, _STEP): 980.487e6 + 288.802e6,
 }
-_HEADER_SHA = "7bdadc91a6034eb56f238494459cf396db90aca6"
+_HEADER_SHA = "d4d538b5843a1f7202e9ae15e2c39d39f857e817"
 
 
 def ncu_traffic(wl, eng, kernel):
