@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--order", type=int, default=2, choices=[2, 4],
                     help="spatial order of the staggered differences (4: four-point kernels)")
     ap.add_argument("--inversion", type=int, default=0, help="run this many iterations of the outer inversion loop")
+    ap.add_argument("--oracle-timings", action="store_true",
+                    help="time the FP64 oracle (1 thread and all cores) beside the device on three workloads")
     ap.add_argument("--early-stop", type=float, default=0.0,
                     help="time forward data runs with the early end at this tolerance against full runs")
     ap.add_argument("--td", type=int, default=0,
@@ -565,6 +567,56 @@ def run_td(args):
     print(json.dumps(out))
 
 
+def run_oracle_timings(args):
+    """The FP64 oracle timed on the host cores, single-threaded and on all cores, on bounded
+    samples of the tiny FP64 box, the thin reservoir and the 116^3 crop of the heterogeneous
+    model (one source, forward run with the volumetric transform), beside the device's
+    gradient on the same workloads (Gcell-updates/s over both runs of all sources)."""
+    import torch
+    from oracle import fdtd
+    from paper_2211_16665_gb300 import workloads as W
+    from paper_2211_16665_gb300.engine import Engine, misfit
+    torch.cuda.set_device(0)
+    all_threads = os.cpu_count() or 1
+    out = {"mode": "oracle_timings", "host_cores": all_threads, "rows": []}
+    for name, nt_sample in (("plain_tiny", 300), ("thin_reservoir", 200), ("heterogeneous_crop96", 200)):
+        wl = W.ALL[name]()
+        row = {"workload": wl.name, "cells": wl.cells, "precision": wl.precision}
+        pb = fdtd.problem_from_workload(wl)
+        n = min(nt_sample, pb.nt)
+        for threads in (1, all_threads):
+            fdtd.set_threads(threads)
+            t0 = time.perf_counter()
+            fdtd.forward(pb, wl.rho, wl.src.subset([0]), wl.rec, keep_volume=True, nt_run=n)
+            t = time.perf_counter() - t0
+            row[f"oracle_gcell_s_{threads}_threads"] = round(wl.cells * n / t / 1e9, 5)
+        row["oracle_sample"] = f"{n} of {pb.nt} steps, one source, volumetric transform"
+        fdtd.set_threads(all_threads)
+        eng = Engine.from_workload(wl)
+        rho = eng.model_tensor(wl.rho)
+        d_obs = eng.fwd_model(eng.model_tensor(wl.rho_true), wl.src, wl.rec)
+        basis, _, _ = eng.estimate_adjoint_basis()
+
+        def grad():
+            d, E = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)
+            _, r = misfit(d_obs, d)
+            V = eng.adjoint_model(rho, wl.rec, r, basis)
+            return eng.gradient(rho, E, V)
+        grad()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        grad()
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        row["gpu_gcell_s"] = round(2.0 * wl.cells * eng.nt * wl.src.n / t / 1e9, 3)
+        row["gpu_s_per_gradient_per_source"] = round(t / wl.src.n, 4)
+        row["n_src"] = wl.src.n
+        row["gpu_over_oracle_all_cores"] = round(row["gpu_gcell_s"] / row[f"oracle_gcell_s_{all_threads}_threads"], 1)
+        eng.close()
+        out["rows"].append(row)
+    print(json.dumps(out))
+
+
 def run_early_stop(args):
     """Forward data runs (receivers only) on the thin reservoir with the early end of Sec. 2
     at the given tolerance against full runs: ms per run, steps, relative L2 change of the data."""
@@ -597,6 +649,9 @@ def run_early_stop(args):
 
 def main():
     args = parse()
+    if args.oracle_timings:
+        run_oracle_timings(args)
+        return
     if args.inversion:
         run_inversion(args)
         return

@@ -306,7 +306,20 @@ def _lib():
         _LIB = ctypes.CDLL(build_oracle())
         _LIB.orc_run.argtypes = [ctypes.POINTER(_Model), ctypes.POINTER(_IO), _D, _D, ctypes.c_int, ctypes.c_int]
         _LIB.orc_run.restype = ctypes.c_int
+        _LIB.orc_set_threads.argtypes = [ctypes.c_int]
+        _LIB.orc_set_threads.restype = None
+        _LIB.orc_get_threads.argtypes = []
+        _LIB.orc_get_threads.restype = ctypes.c_int
     return _LIB
+
+
+def set_threads(n: int):
+    """OpenMP threads of the C stepper (timing only)."""
+    _lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(_lib().orc_get_threads())
 
 
 def _dp(a):
