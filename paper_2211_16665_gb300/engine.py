@@ -147,10 +147,18 @@ class Engine:
     def set_wavelet(self, wavelet=None):
         _capi.set_wavelet(self.ctx, wavelet)
 
-    def estimate_adjoint_basis(self, gamma=1e-12, relative=True, max_iter=200, tol=1e-14):
+    def estimate_adjoint_basis(self, gamma=1e-12, relative=True, max_iter=200, tol=1e-14, fit_target=None):
+        """B+ (Sec. 3.3).  fit_target: with a relative gamma, divide gamma by 100 (down to 1e-16)
+        until the fit residual max |B B+ - I| is at most fit_target (the Gram matrix of many
+        widely spaced frequencies is ill-conditioned and needs less regularisation)."""
         basis = torch.empty((self.nt, 2 * self.nf), dtype=torch.float64, device=self.device)
-        fit, its = _capi.estimate_adjoint_basis(self.dt, self.nt, self.freqs, self.f0, gamma, int(relative),
-                                                max_iter, tol, _ptr(basis), _stream())
+        while True:
+            fit, its = _capi.estimate_adjoint_basis(self.dt, self.nt, self.freqs, self.f0, gamma, int(relative),
+                                                    max_iter, tol, _ptr(basis), _stream())
+            if fit_target is None or not relative or fit <= fit_target or gamma <= 1e-16 * 1.0001:
+                break
+            gamma = max(gamma / 100.0, 1e-16)
+        self.basis_gamma = gamma
         return basis, fit, its
 
     def adjoint_model(self, rho, rec, resid: torch.Tensor, basis: torch.Tensor):

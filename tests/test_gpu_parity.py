@@ -334,3 +334,22 @@ def test_error_statuses(box):
     with pytest.raises(CsemError) as e:
         Engine(wl.xn, wl.yn, wl.zn, wl.npml, wl.freqs, rho_max=wl.rho_max, dt=1.0)
     assert e.value.code == -3
+
+
+def test_basis_fit_target_on_eight_widely_spaced_frequencies():
+    """The Gram matrix of 8 log-spaced frequencies 0.1-1.5 Hz over 19 492 steps has a
+    condition number near 1e12: gamma = 1e-12 relative leaves a fit residual of 0.19, and
+    the fit target lowers gamma until the device basis fits the oracle's B to 1e-3."""
+    from oracle import basis as OB
+    wl = W.large_gradient()
+    pb = fdtd.problem_from_workload(wl)
+    M = OB.basis_matrix(pb.dt, pb.nt, pb.freqs, pb.f0)
+    small = W.small_box(n_core=10, h=100.0, npml=4, n_freq=2)
+    eng = Engine.from_workload(small, autotune=False)
+    eng.dt, eng.nt, eng.freqs, eng.nf = pb.dt, pb.nt, np.asarray(pb.freqs), pb.freqs.size
+    b12, fit12, _ = eng.estimate_adjoint_basis(gamma=1e-12, relative=True)
+    assert fit12 > 0.1 and abs(fit12 - OB.fit_residual(M, b12.cpu().numpy())) <= 1e-6
+    b, fit, _ = eng.estimate_adjoint_basis(gamma=1e-12, relative=True, fit_target=1e-3)
+    assert eng.basis_gamma < 1e-12 and fit <= 1e-3
+    assert OB.fit_residual(M, b.cpu().numpy()) <= 1e-3
+    eng.close()
