@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--order", type=int, default=2, choices=[2, 4],
                     help="spatial order of the staggered differences (4: four-point kernels)")
     ap.add_argument("--inversion", type=int, default=0, help="run this many iterations of the outer inversion loop")
+    ap.add_argument("--route", default="basis", choices=["basis", "td"],
+                    help="gradient route of --inversion: basis-function adjoint or time-domain adjoint")
     ap.add_argument("--max-src", type=int, default=0,
                     help="use only the first K sources of the workload (side measurements of large configs)")
     ap.add_argument("--oracle-timings", action="store_true",
@@ -494,7 +496,7 @@ def run_inversion(args):
     free = wl.rho > wl.rho.min()
     basis, fit, _ = eng.estimate_adjoint_basis(gamma=1e-12, relative=True)
     inv = Inversion(eng, wl.src, wl.rec, torch.as_tensor(d_obs), wl.rho, free, basis, weights=w,
-                    xn=wl.xn, yn=wl.yn, zn=wl.zn, m_max=math.log(wl.rho_max))
+                    xn=wl.xn, yn=wl.yn, zn=wl.zn, m_max=math.log(wl.rho_max), route=args.route)
     runs = {"fwd": 0}
     calls = eng.fwd_model
 
@@ -519,7 +521,7 @@ def run_inversion(args):
                                   "end": float(np.exp(m.cpu().numpy()[slab].mean())),
                                   "true": float(wl.rho_true[slab].mean())},
            "largest_update": {"ln_rho": float(upd.max()), "depth_m": float(0.5 * (wl.zn[kz] + wl.zn[kz + 1]))},
-           "basis_fit": fit, "early_stop_tol": args.early_stop,
+           "basis_fit": fit, "early_stop_tol": args.early_stop, "gradient_route": args.route,
            "data": "synthetic, 1 % noise (seed 42), 600 m mute, 3 % relative-error weights"}
     print(json.dumps(out))
 

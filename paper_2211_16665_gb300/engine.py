@@ -69,6 +69,7 @@ class Engine:
         self.real = torch.float32 if precision == 32 else torch.float64
         self.cplx = torch.complex64 if precision == 32 else torch.complex128
         self._wavelet = None
+        self.early_stop_tol = 0.0
         self.kz = _capi.autotune(self.ctx, max_src, _stream()) if autotune else None
 
     @classmethod
@@ -139,6 +140,7 @@ class Engine:
         """Forward data runs (no volumes) end once the receiver spectra change by at most
         tol (relative) over 64 steps (Sec. 2); 0 turns it off."""
         _capi.set_early_stop(self.ctx, tol)
+        self.early_stop_tol = float(tol)
 
     def last_run_steps(self) -> int:
         """Steps the last fwd_model data include (synchronises the current stream)."""

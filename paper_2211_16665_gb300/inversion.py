@@ -61,12 +61,13 @@ class Tikhonov:
 
 class Inversion:
     """Minimises phi over m = ln(rho) on the free cells with the engine's forward
-    and adjoint runs (one gradient per iteration, one forward per trial step)."""
+    and adjoint runs (one gradient per iteration, one forward per trial step).
+    route: "basis" (Sec. 3.2-3.3) or "td" (the appendix's time-domain adjoint)."""
 
     def __init__(self, engine, src, rec, d_obs: torch.Tensor, rho_fixed, free, basis: torch.Tensor,
                  weights: Optional[torch.Tensor] = None, m_ref=None, alpha=(1.0, 1.0, 0.1), xn=None, yn=None,
                  zn=None, beta0=0.01, cool=0.7, m_min=math.log(0.1), m_max=math.log(1e3), memory=5, step0=0.5,
-                 max_backtracks=6, chunk=None, recompute=False):
+                 max_backtracks=6, chunk=None, recompute=False, route="basis"):
         dev = engine.device
         self.eng, self.src, self.rec, self.basis = engine, src, rec, basis
         self.d_obs = d_obs.to(dev)
@@ -80,12 +81,12 @@ class Inversion:
         self.m_min = m_min
         self.m_max = min(m_max, math.log(engine.rho_max))
         self.memory, self.step0, self.max_backtracks = memory, step0, max_backtracks
-        self.chunk, self.recompute = chunk, recompute
+        self.chunk, self.recompute, self.route = chunk, recompute, route
 
     def _phi_d(self, m: torch.Tensor) -> torch.Tensor:
         ln_rho = torch.where(self.free, m, self.ln_fixed)
         d = forward_data(ln_rho, self.eng, self.src, self.rec, self.basis, chunk=self.chunk,
-                         recompute=self.recompute)
+                         recompute=self.recompute, route=self.route)
         res = self.d_obs - d
         if self.w is not None:
             res = res * self.w
