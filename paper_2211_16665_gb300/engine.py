@@ -80,6 +80,7 @@ class Engine:
                    nt=nt if nt is not None else (wl.nt or 0), **kw)
 
     def close(self):
+        self._td_work = None
         if getattr(self, "ctx", None):
             _capi.destroy(self.ctx)
             self.ctx = None
@@ -199,11 +200,18 @@ class Engine:
         if out is None:
             out = torch.zeros(self.model_shape, dtype=self.real, device=self.device)
         self._model(out)
-        if budget_bytes is None:
-            budget_bytes = int(0.8 * torch.cuda.mem_get_info(self.device)[0])
+        cached = getattr(self, "_td_work", None)
+        if budget_bytes is None:     # the engine's own cached workspace counts as free
+            held = cached.numel() if (cached is not None and work is None) else 0
+            budget_bytes = int(0.8 * (torch.cuda.mem_get_info(self.device)[0] + held))
         seg, nbytes = _capi.td_plan(self.ctx, S, rec.n, budget_bytes if segment <= 0 else 0, segment)
         if work is None:
-            work = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+            if cached is not None and cached.numel() >= nbytes + 256:
+                work = cached
+            else:
+                self._td_work = cached = None
+                work = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+                self._td_work = work     # kept for the next call (released by close())
         off = (-work.data_ptr()) % 256
         if work.dtype != torch.uint8 or not work.is_cuda or work.numel() < nbytes + off:
             raise ValueError(f"workspace of at least {nbytes + off} bytes (uint8, on the device) expected")
