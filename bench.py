@@ -55,6 +55,8 @@ def parse():
                     help="use only the first K sources of the workload (side measurements of large configs)")
     ap.add_argument("--oracle-timings", action="store_true",
                     help="time the FP64 oracle (1 thread and all cores) beside the device on three workloads")
+    ap.add_argument("--early-stop-volumes", type=float, default=0.0,
+                    help="time gradients with the early end of the forward and adjoint volume runs")
     ap.add_argument("--early-stop", type=float, default=0.0,
                     help="time forward data runs with the early end at this tolerance against full runs")
     ap.add_argument("--td", type=int, default=0,
@@ -630,6 +632,48 @@ def run_oracle_timings(args):
     print(json.dumps(out))
 
 
+def run_early_stop_volumes(args):
+    """Gradients on the thin reservoir with the early end applied to the volumetric
+    transforms of the forward and adjoint runs (Sec. 2) against full gradients: seconds per
+    gradient, the steps each run took, and the relative L2 change of the gradient."""
+    import torch
+    from paper_2211_16665_gb300 import workloads as W
+    from paper_2211_16665_gb300.engine import Engine, misfit
+    torch.cuda.set_device(0)
+    wl = make_workload(args.workload, 0, 1)
+    eng = Engine.from_workload(wl)
+    rho = eng.model_tensor(wl.rho)
+    d_obs = torch.as_tensor(W.add_noise(eng.fwd_model(eng.model_tensor(wl.rho_true), wl.src, wl.rec).cpu().numpy(),
+                                        wl.noise, wl.noise_seed), device=eng.device)
+    basis, _, _ = eng.estimate_adjoint_basis(gamma=1e-12, relative=True, fit_target=1e-3)
+    out = {"mode": "early_stop_volumes", "workload": wl.name, "nt": eng.nt, "tol": args.early_stop_volumes}
+    grads = {}
+    for name, tol in (("full", 0.0), ("early", args.early_stop_volumes)):
+        eng.set_early_stop_volumes(tol)
+
+        def grad():
+            d, E = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)
+            sf = eng.last_run_steps()
+            _, r = misfit(d_obs, d)
+            V = eng.adjoint_model(rho, wl.rec, r, basis)
+            sa = eng.last_run_steps()
+            return eng.gradient(rho, E, V), sf, sa
+        for _ in range(max(1, args.warmup)):
+            grad()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            g, sf, sa = grad()
+        torch.cuda.synchronize()
+        out[f"s_per_gradient_{name}"] = round((time.perf_counter() - t0) / args.steps, 4)
+        out[f"steps_{name}"] = {"forward": sf, "adjoint": sa}
+        grads[name] = g.double().cpu().numpy()
+    out["speedup"] = round(out["s_per_gradient_full"] / out["s_per_gradient_early"], 3)
+    out["rel_l2_gradient_change"] = float(np.linalg.norm(grads["early"] - grads["full"]) /
+                                          np.linalg.norm(grads["full"]))
+    print(json.dumps(out))
+
+
 def run_early_stop(args):
     """Forward data runs (receivers only) on the thin reservoir with the early end of Sec. 2
     at the given tolerance against full runs: ms per run, steps, relative L2 change of the data."""
@@ -667,6 +711,9 @@ def main():
         return
     if args.inversion:
         run_inversion(args)
+        return
+    if args.early_stop_volumes > 0:
+        run_early_stop_volumes(args)
         return
     if args.early_stop > 0:
         run_early_stop(args)

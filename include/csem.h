@@ -267,11 +267,25 @@ int csem_gradient_td(csem_ctx *ctx, const void *rho_dev, const csem_points *src,
  * block (never overlapped) in these runs.  tol = 0 turns the check off (the
  * default).  Runs that keep volumes, adjoint runs and csem_gradient_td always
  * take nt steps.  The first call with tol > 0 allocates the check's buffers.
- * csem_last_run_steps: the steps whose snapshots the last csem_fwd_model data
- * include (nt unless that run ended early); synchronises stream.
+ * csem_last_run_steps: the steps whose snapshots the last csem_fwd_model or
+ * csem_adjoint_model run includes (nt unless it ended early, here or through
+ * csem_set_early_stop_volumes); synchronises stream.
  * Errors: INVALID_ARG, OOM, CUDA. */
 int csem_set_early_stop(csem_ctx *ctx, double tol);
 int csem_last_run_steps(csem_ctx *ctx, void *stream, int *steps);
+
+/* Early end of runs that keep volumes (csem_fwd_model with Evol_dev, csem_adjoint_model;
+ * the same reading of Sec. 2 on the volumetric transform).  tol > 0: after every 64
+ * steps one pass over the accumulators gives, per frequency k, A_k = max |acc| and
+ * D_k = max |acc - acc at the previous check| over every source, component and entry;
+ * the run ends after the first chunk c >= 1 with D_k <= tol A_k for every k (the
+ * decision taken in FP32).  The volumes (and the receivers of a forward run) then hold
+ * the transform of the steps up to that chunk; csem_last_run_steps reports them.  The
+ * host waits for each chunk's verdict before issuing the next, so nothing runs past the
+ * end.  tol = 0 turns it off (the default); the first call with tol > 0 allocates a
+ * copy of max_src volumes.  The time-domain gradient always takes nt steps.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int csem_set_early_stop_volumes(csem_ctx *ctx, double tol);
 
 /* Picks the launch shape of the H and E stepping kernels -- z planes per
  * thread (1, 2, 4, 8), the register budget (4, 6 or 8 resident 256-thread

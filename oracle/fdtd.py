@@ -577,6 +577,77 @@ def forward_early_stop(pb: Problem, rho, src, rec, tol: float, chunk: int = 64, 
     return R * norm[None, None, :], n1
 
 
+def _volume_converged(V, prev, tol):
+    """The early end of runs with volumes: per frequency, the largest change since the
+    previous check within tol of the largest magnitude, over every source, component
+    and entry.  V, prev: [n_src][3][n_freq][N] complex."""
+    a = np.abs(V).max(axis=(0, 1, 3))
+    d = np.abs(V - prev).max(axis=(0, 1, 3))
+    return bool(np.all(d <= tol * a))
+
+
+def _volumes_in_chunks(pb, st, runs, tol, chunk):
+    """Steps every source's run (fields, psi, inj, series) together in chunks, with the
+    volumetric transform; ends after the first chunk c >= 1 that passes _volume_converged,
+    or at nt.  Returns the raw transforms [n_src][3][n_freq][N] and the steps run."""
+    nt, nf, N = pb.nt, pb.freqs.size, pb.N
+    W = pb.dft_weights()
+    vre = [np.zeros(3 * nf * N) for _ in runs]
+    vim = [np.zeros(3 * nf * N) for _ in runs]
+    prev = None
+    n1 = 0
+    for c in range((nt + chunk - 1) // chunk):
+        n0, n1 = c * chunk, min(nt, (c + 1) * chunk)
+        for s, (fields, psi, inj, series, extra) in enumerate(runs):
+            st.run(fields, psi, n0, n1, inj=inj, series=series, dft=W, vol_re=vre[s], vol_im=vim[s], **extra)
+        V = np.stack([(vre[s] + 1j * vim[s]).reshape(3, nf, N) for s in range(len(runs))])
+        if n1 == nt:
+            break
+        if prev is not None and tol > 0 and _volume_converged(V, prev, tol):
+            break
+        prev = V
+    return V, n1
+
+
+def forward_volumes_early_stop(pb: Problem, rho, src, rec, tol: float, chunk: int = 64):
+    """Forward run with volumes and the early end of Sec. 2 applied to the volumetric
+    transform (all sources together, checked every `chunk` steps).  Returns (d, volumes,
+    steps) with d and the volumes normalised as in forward()."""
+    st = Stepper(pb, rho)
+    wav = pb.impulse()
+    norm = pb.k / pb.wavelet_spectrum(wav)
+    W = pb.dft_weights()
+    taps = []
+    for r in range(rec.n):
+        taps += point_taps(pb, rec, r)
+    traces = [np.zeros(rec.n * pb.nt) for _ in range(src.n)]
+    runs = []
+    for s in range(src.n):
+        fields, psi = st.new_state()
+        runs.append((fields, psi, point_taps(pb, src, s, scale_by_dV=st.dV, tag=0), wav[None, :],
+                     dict(taps=taps, n_rec=rec.n, trace=traces[s])))
+    V, steps = _volumes_in_chunks(pb, st, runs, tol, chunk)
+    d = np.stack([(tr.reshape(rec.n, pb.nt)[:, :steps] @ W[:steps]) * norm[None, :] for tr in traces])
+    vols = V.reshape((src.n, 3, pb.freqs.size) + pb.shape_nodes) * norm[None, None, :, None, None, None]
+    return d, vols, steps
+
+
+def adjoint_early_stop(pb: Problem, rho, rec, resid, Bp, tol: float, chunk: int = 64):
+    """adjoint() with the early end of Sec. 2 applied to the volumetric transform.
+    Returns (conj(v) volumes, steps)."""
+    st = Stepper(pb, rho)
+    inj = []
+    for r in range(rec.n):
+        inj += point_taps(pb, rec, r, scale_by_dV=st.dV, tag=r)
+    runs = []
+    for s in range(resid.shape[0]):
+        coef = pb.k[None, :] * np.conj(resid[s]) / pb.dt
+        fields, psi = st.new_state()
+        runs.append((fields, psi, inj, _basis.synthesize(Bp, coef), {}))
+    V, steps = _volumes_in_chunks(pb, st, runs, tol, chunk)
+    return pb.dt * V.reshape((resid.shape[0], 3, pb.freqs.size) + pb.shape_nodes), steps
+
+
 def misfit(d_obs, d_syn, weights=None):
     """phi = 1/2 sum |W (d_obs - d_syn)|^2 and the weighted residual r = W^T W (d_obs - d_syn)  (Eq. 7)."""
     w = 1.0 if weights is None else weights
@@ -592,7 +663,7 @@ def adjoint_basis(pb: Problem, gamma_rel=1e-12):
     return Bp, _basis.fit_residual(B, Bp)
 
 
-def adjoint(pb: Problem, rho, rec, resid, Bp):
+def adjoint(pb: Problem, rho, rec, resid, Bp, nt_run=None):
     """conj(v) volumes [n_src, 3, n_freq, nodes] for E residuals r at the receivers.
 
     The adjoint system (Eq. 14) is the forward system with an electric
@@ -614,7 +685,8 @@ def adjoint(pb: Problem, rho, rec, resid, Bp):
         fields, psi = st.new_state()
         vre = np.zeros(3 * pb.freqs.size * pb.N)
         vim = np.zeros_like(vre)
-        st.run(fields, psi, 0, pb.nt, inj=inj, series=series, dft=W, vol_re=vre, vol_im=vim)
+        st.run(fields, psi, 0, pb.nt if nt_run is None else nt_run, inj=inj, series=series, dft=W, vol_re=vre,
+               vol_im=vim)
         out[s] = pb.dt * (vre + 1j * vim).reshape((3, pb.freqs.size) + pb.shape_nodes)
     return out
 

@@ -183,7 +183,11 @@ struct csem_ctx {
     double2 *d_rprev = nullptr, *d_rfin = nullptr;
     int *d_es = nullptr, *h_es = nullptr;
     cudaEvent_t es_ev[kEsDepth] = {};
-    bool last_es = false;                // the last forward run used the early end
+    bool last_es = false;                // the last forward or adjoint run used an early end
+    // early end of runs that keep volumes (tol > 0): previous accumulators, per-frequency stats
+    double es_vol_tol = 0.0;
+    void *d_vprev = nullptr;             // [max_src][3][nf][vol] complex (real)
+    unsigned *d_vstats = nullptr;        // [2 nf]
     struct GraphSlot { int key[8]; cudaGraphExec_t exec; };
     std::vector<GraphSlot> graphs;
 };
@@ -765,6 +769,65 @@ int run_steps_es(csem_ctx *c, int S, int NR, const csem::StepParams<R> &p, const
     return CSEM_OK;
 }
 
+// A run that keeps volumes, with the early end (Sec. 2): after every chunk of
+// kChunk steps (graph replay, block flushes in order) one pass over the transform
+// accumulators gives, per frequency, the largest magnitude and the largest change
+// since the previous check; the run ends after the first chunk c >= 1 whose changes
+// are all within tol of the magnitudes.  The host reads each chunk's verdict before
+// issuing the next chunk, so no step after the end touches the volumes or the
+// receivers.  Without an end the remainder runs as in run_steps.
+template <typename R>
+int run_steps_vol_es(csem_ctx *c, int S, const csem::StepParams<R> &p, const csem::PointParams<R> &q,
+                     cudaStream_t st) {
+    typedef typename C2<R>::T R2;
+    const int saved = c->flush_mode;
+    c->flush_mode &= 1;
+    struct Restore { csem_ctx *c; int m; ~Restore() { c->flush_mode = m; } } restore{c, saved};
+    const bool kahan = c->kahan != 0;
+    const int M = c->M, nt = c->nt, nf = c->nf;
+    const int full = nt / kChunk, rem = nt % kChunk;
+    CK(cudaMemsetAsync(c->d_es, 0, 2 * sizeof(int), st));
+    bool ended = false;
+    if (full > 0) {
+        const int key[8] = {S, 5, kahan ? 1 : 0, q.n_itaps, q.n_rec > 0 ? 1 : 0, (int)sizeof(R),
+                            ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
+                            ((((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e) * 25 +
+                             c->TMA_h * 5 + c->TMA_e) * 4 + c->LEAN_h * 2 + c->LEAN_e};
+        cudaGraphExec_t exec = nullptr;
+        long long per_chunk = 0;
+        TRY(chunk_graph(c, key, [&](cudaStream_t cs) {
+            cudaError_t le = tap_prep<R>(c, p, S, kChunk, cs);
+            if (le == cudaSuccess) le = emit_steps<R>(c, S, true, kahan, p, q, kChunk, false, true, cs);
+            if (le == cudaSuccess) le = csem::launch_advance(c->d_step, kChunk, cs);
+            return le;
+        }, &exec, &per_chunk));
+        for (int ch = 0; ch < full; ++ch) {
+            CK(cudaGraphLaunch(exec, st));
+            csem::g_launches += per_chunk;
+            const bool last = (ch == full - 1 && rem == 0);
+            CK(cudaMemsetAsync(c->d_vstats, 0, 2 * nf * sizeof(unsigned), st));
+            CK(csem::launch_es_vol_stats<R>((const R2 *)p.acc, (R2 *)c->d_vprev, c->vol, S, nf, c->d_vstats, st));
+            CK(csem::launch_es_vol_decide(c->d_vstats, nf, c->es_vol_tol, ch, last ? 1 : 0, (ch + 1) * kChunk,
+                                          c->d_es, st));
+            CK(cudaMemcpyAsync(&c->h_es[0], c->d_es, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaEventRecord(c->es_ev[0], st));
+            CK(cudaEventSynchronize(c->es_ev[0]));
+            if (c->h_es[0]) { ended = true; break; }
+        }
+    }
+    if (!ended && rem > 0) {
+        CK(tap_prep<R>(c, p, S, rem, st));
+        for (int j = 0; j < rem; ++j) {
+            CK(launch_any<R>(c, p, q, S, j, st));
+            if ((j + 1) % M == 0) CK(flush<R>(c, p, q, S, j + 1 - M, M, true, kahan, st));
+        }
+        const int tail = rem % M;
+        if (tail) CK(flush<R>(c, p, q, S, rem - tail, tail, true, kahan, st));
+        CK(csem::launch_es_vol_decide(c->d_vstats, nf, c->es_vol_tol, full, 1, nt, c->d_es, st));
+    }
+    return CSEM_OK;
+}
+
 template <typename R>
 int fwd_impl(csem_ctx *c, const void *rho, const csem_points *src, const csem_points *rec, double *d_syn,
              void *Evol, cudaStream_t st) {
@@ -798,9 +861,11 @@ int fwd_impl(csem_ctx *c, const void *rho, const csem_points *src, const csem_po
     q.n_itaps = 8; q.itaps = c->d_itaps; q.itap_stride = 8;
     q.n_emit = 1; q.J = 1; q.coef = c->d_ones; q.T = c->d_T;
     const bool es = c->es_tol > 0.0 && NR > 0 && !dft;
+    const bool es_vol = c->es_vol_tol > 0.0 && dft;
     if (es) TRY(run_steps_es<R>(c, S, NR, p, q, st));
+    else if (es_vol) TRY(run_steps_vol_es<R>(c, S, p, q, st));
     else TRY(run_steps<R>(c, S, dft, p, q, st));
-    c->last_es = es;
+    c->last_es = es || es_vol;
     c->last_nrec = NR;
     if (NR > 0)
         CK(csem::launch_finalize_receivers(es ? c->d_rfin : c->d_racc, d_syn, S, NR, c->nf, c->d_alpha, st));
@@ -837,7 +902,10 @@ int adj_impl(csem_ctx *c, const void *rho, const csem_points *rec, int S, const 
     q.n_rec = 0; q.rtaps = nullptr; q.racc = nullptr; q.w64 = c->d_w64; q.trace = nullptr;
     q.n_itaps = NR * 8; q.itaps = c->d_itaps; q.itap_stride = 0;
     q.n_emit = NR; q.J = 2 * c->nf; q.coef = c->d_coef; q.T = basis;
-    TRY(run_steps<R>(c, S, true, p, q, st));
+    const bool es_vol = c->es_vol_tol > 0.0;
+    if (es_vol) TRY(run_steps_vol_es<R>(c, S, p, q, st));
+    else TRY(run_steps<R>(c, S, true, p, q, st));
+    c->last_es = es_vol;
     CK(csem::launch_finalize_volume<R>((typename C2<R>::T *)Vvol,
                                        c->kahan ? (const typename C2<R>::T *)c->d_comp : nullptr, c->vol, S, c->nf,
                                        c->d_alpha + c->nf, st));
@@ -1272,7 +1340,7 @@ void free_ctx(csem_ctx *c) {
                     c->d_alpha, c->d_racc, c->d_coef, c->d_T, c->d_ones, c->d_rtaps, c->d_itaps, c->d_colmap, c->d_tflag, c->d_cpos, c->d_cval, c->d_step, c->d_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    for (void *p : {(void *)c->d_rprev, (void *)c->d_rfin, (void *)c->d_es})
+    for (void *p : {(void *)c->d_rprev, (void *)c->d_rfin, (void *)c->d_es, c->d_vprev, (void *)c->d_vstats})
         if (p) cudaFree(p);
     if (c->h_es) cudaFreeHost(c->h_es);
     for (int k = 0; k < kEsDepth; ++k)
@@ -1603,17 +1671,41 @@ int csem_gradient_td(csem_ctx *c, const void *rho_dev, const csem_points *src, c
                : td_impl<double>(c, rho_dev, src, rec, resid_dev, segment, wrt, grad_dev, work_dev, work_bytes, st);
 }
 
+namespace {
+// The device state {ended, steps}, its pinned host copies and events, shared by both early ends.
+int es_state(csem_ctx *c) {
+    if (!c->d_es) TRY(dalloc(c, &c->d_es, 2 * sizeof(int)));
+    if (!c->h_es) CK(cudaHostAlloc((void **)&c->h_es, kEsDepth * sizeof(int), cudaHostAllocDefault));
+    for (int k = 0; k < kEsDepth; ++k)
+        if (!c->es_ev[k]) CK(cudaEventCreateWithFlags(&c->es_ev[k], cudaEventDisableTiming));
+    return CSEM_OK;
+}
+}  // namespace
+
 int csem_set_early_stop(csem_ctx *c, double tol) {
     if (!c || !(tol >= 0.0) || !std::isfinite(tol)) return fail(CSEM_ERR_INVALID_ARG, "tol must be finite and >= 0");
-    if (tol > 0.0 && !c->d_es) {
-        const size_t nb = (size_t)c->max_src * std::max(c->max_rec, 1) * c->nf * sizeof(double2);
-        TRY(dalloc(c, &c->d_rprev, nb));
-        TRY(dalloc(c, &c->d_rfin, nb));
-        TRY(dalloc(c, &c->d_es, 2 * sizeof(int)));
-        CK(cudaHostAlloc((void **)&c->h_es, kEsDepth * sizeof(int), cudaHostAllocDefault));
-        for (int k = 0; k < kEsDepth; ++k) CK(cudaEventCreateWithFlags(&c->es_ev[k], cudaEventDisableTiming));
+    if (tol > 0.0) {
+        TRY(es_state(c));
+        if (!c->d_rprev) {
+            const size_t nb = (size_t)c->max_src * std::max(c->max_rec, 1) * c->nf * sizeof(double2);
+            TRY(dalloc(c, &c->d_rprev, nb));
+            TRY(dalloc(c, &c->d_rfin, nb));
+        }
     }
     c->es_tol = tol;
+    return CSEM_OK;
+}
+
+int csem_set_early_stop_volumes(csem_ctx *c, double tol) {
+    if (!c || !(tol >= 0.0) || !std::isfinite(tol)) return fail(CSEM_ERR_INVALID_ARG, "tol must be finite and >= 0");
+    if (tol > 0.0) {
+        TRY(es_state(c));
+        if (!c->d_vprev) {
+            TRY(dalloc(c, (char **)&c->d_vprev, (size_t)c->max_src * 3 * c->nf * c->vol * 2 * c->rsize));
+            TRY(dalloc(c, &c->d_vstats, 2 * (size_t)c->nf * sizeof(unsigned)));
+        }
+    }
+    c->es_vol_tol = tol;
     return CSEM_OK;
 }
 

@@ -13,4 +13,15 @@ namespace csem {
 cudaError_t launch_es_check(const double2 *racc, double2 *prev, double2 *fin, int n, double tol, int chunk,
                             int last, int steps_at, int *state, cudaStream_t st);
 
+// Runs that keep volumes.  Per frequency f, over every source, component and
+// entry of the accumulators acc [S][3][nf][vol]: stats[f] = max |acc| and
+// stats[nf + f] = max |acc - prev| (bit patterns of non-negative floats, combined by
+// atomicMax, cleared by the caller); prev takes acc.
+template <typename R>
+cudaError_t launch_es_vol_stats(const typename C2<R>::T *acc, typename C2<R>::T *prev, long long vol, int S, int nf,
+                                unsigned *stats, cudaStream_t st);
+// state = {1, steps_at} when chunk >= 1 and stats[nf + f] <= tol stats[f] for every f, or when last.
+cudaError_t launch_es_vol_decide(const unsigned *stats, int nf, double tol, int chunk, int last, int steps_at,
+                                 int *state, cudaStream_t st);
+
 }  // namespace csem

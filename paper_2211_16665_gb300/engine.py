@@ -143,8 +143,13 @@ class Engine:
         _capi.set_early_stop(self.ctx, tol)
         self.early_stop_tol = float(tol)
 
+    def set_early_stop_volumes(self, tol=0.0):
+        """Forward runs with volumes and adjoint runs end once every frequency's volumetric
+        transform changes by at most tol of its largest magnitude over 64 steps (Sec. 2)."""
+        _capi.set_early_stop_volumes(self.ctx, tol)
+
     def last_run_steps(self) -> int:
-        """Steps the last fwd_model data include (synchronises the current stream)."""
+        """Steps the last fwd_model or adjoint_model run included (synchronises the current stream)."""
         return _capi.last_run_steps(self.ctx, _stream())
 
     def set_wavelet(self, wavelet=None):

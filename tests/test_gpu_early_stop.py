@@ -78,3 +78,49 @@ def test_forward_data_without_gradient_uses_the_early_end(case):
     d2 = forward_data(m.clone().requires_grad_(True), eng, wl.src, wl.rec, basis)
     assert eng.last_run_steps() == pb.nt and d2.requires_grad
     eng.close()
+
+
+def gpu_volume(eng, v):
+    return v.cpu().numpy()[..., : eng.nx + 1].astype(np.complex128)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_volume_early_end_matches_oracle(case, precision):
+    """Forward (with volumes) and adjoint runs ending on the volumetric transform: the same
+    stop steps as the oracle in FP64 (within a chunk in FP32); volumes and gradient equal to
+    the oracle's truncated at the device's steps; the gradient within 1e-5 of the full one."""
+    wl, pb, partial, ref = case
+    tol = 1e-6
+    d_obs = fdtd.forward(pb, wl.rho_true, wl.src, wl.rec)
+    d_full, E_full = fdtd.forward(pb, wl.rho, wl.src, wl.rec, keep_volume=True)
+    _, r = fdtd.misfit(d_obs, d_full)
+    Bp, _ = fdtd.adjoint_basis(pb, 1e-12)
+    _, _, steps_ref = fdtd.forward_volumes_early_stop(pb, wl.rho, wl.src, wl.rec, tol)
+    _, sa_ref = fdtd.adjoint_early_stop(pb, wl.rho, wl.rec, r, Bp, tol)
+    assert steps_ref < pb.nt and sa_ref < pb.nt
+
+    eng = Engine.from_workload(wl, precision=precision, kahan=1)
+    rho = eng.model_tensor(wl.rho)
+    basis, _, _ = eng.estimate_adjoint_basis(gamma=1e-12, relative=True)
+    rg = torch.as_tensor(r, dtype=torch.complex128, device=eng.device)
+    E_all, V_all = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)[1], eng.adjoint_model(rho, wl.rec, rg, basis)
+    g_all = eng.gradient(rho, E_all, V_all).double().cpu().numpy()
+    eng.set_early_stop_volumes(tol)
+    d, E = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)
+    steps = eng.last_run_steps()
+    V = eng.adjoint_model(rho, wl.rec, rg, basis)
+    sa = eng.last_run_steps()
+    g = eng.gradient(rho, E, V).double().cpu().numpy()
+    if precision == 64:
+        assert (steps, sa) == (steps_ref, sa_ref)
+    else:
+        assert abs(steps - steps_ref) <= 64 and abs(sa - sa_ref) <= 64
+    tol_v = 1e-10 if precision == 64 else 1e-3
+    d_t, E_t = fdtd.forward(pb, wl.rho, wl.src, wl.rec, keep_volume=True, nt_run=steps)
+    V_t = fdtd.adjoint(pb, wl.rho, wl.rec, r, Bp, nt_run=sa)
+    assert rel_l2(d.cpu().numpy(), d_t) <= (1e-10 if precision == 64 else 1e-5)
+    assert rel_l2(gpu_volume(eng, E), E_t) <= tol_v
+    assert rel_l2(gpu_volume(eng, V), V_t) <= (1e-9 if precision == 64 else 1e-3)
+    assert rel_l2(g, fdtd.gradient(pb, wl.rho, E_t, V_t)) <= (1e-9 if precision == 64 else 1e-3)
+    assert rel_l2(g, g_all) <= 1e-5
+    eng.close()

@@ -52,3 +52,48 @@ def test_stop_chunk_from_the_plain_run_and_error_bound():
         prev_steps = steps
         assert np.abs(d - d_full).max() <= 20 * tol * np.abs(d_full).max()
         np.testing.assert_allclose(d, (tr[:, :, :steps] @ W[:steps]) * norm, rtol=1e-12)
+
+
+def test_volume_early_end():
+    """V1 tol = 0 reproduces forward() and adjoint(); V2 the stop chunk is the first one
+    whose per-frequency volume change, from a plain run's chunked transforms, is within tol
+    of the largest magnitude; V3 the truncated gradient stays close to the full one."""
+    wl, pb = case()
+    d_full, E_full = fdtd.forward(pb, wl.rho, wl.src, wl.rec, keep_volume=True)
+    d0, E0, steps0 = fdtd.forward_volumes_early_stop(pb, wl.rho, wl.src, wl.rec, 0.0)
+    assert steps0 == pb.nt
+    np.testing.assert_allclose(d0, d_full, rtol=1e-13)
+    np.testing.assert_allclose(E0, E_full, rtol=1e-12, atol=1e-12 * np.abs(E_full).max())
+    d_obs = fdtd.forward(pb, wl.rho_true, wl.src, wl.rec)
+    _, r = fdtd.misfit(d_obs, d_full)
+    Bp, _ = fdtd.adjoint_basis(pb, 1e-12)
+    V_full = fdtd.adjoint(pb, wl.rho, wl.rec, r, Bp)
+    V0, sa0 = fdtd.adjoint_early_stop(pb, wl.rho, wl.rec, r, Bp, 0.0)
+    assert sa0 == pb.nt
+    np.testing.assert_allclose(V0, V_full, rtol=1e-12, atol=1e-12 * np.abs(V_full).max())
+    g_full = fdtd.gradient(pb, wl.rho, E_full, V_full)
+    tol = 1e-6
+    d, E, steps = fdtd.forward_volumes_early_stop(pb, wl.rho, wl.src, wl.rec, tol)
+    V, sa = fdtd.adjoint_early_stop(pb, wl.rho, wl.rec, r, Bp, tol)
+    assert steps < pb.nt and sa < pb.nt
+    # the stop chunk from plain chunked transforms (brute force on the running sum)
+    st = fdtd.Stepper(pb, wl.rho)
+    W = pb.dft_weights()
+    fields, psi = st.new_state()
+    inj = fdtd.point_taps(pb, wl.src, 0, scale_by_dV=st.dV, tag=0)
+    vre, vim = np.zeros(3 * 2 * pb.N), np.zeros(3 * 2 * pb.N)
+    prev, expect = None, pb.nt
+    for c in range((pb.nt + 63) // 64):
+        n0, n1 = 64 * c, min(pb.nt, 64 * (c + 1))
+        st.run(fields, psi, n0, n1, inj=inj, series=pb.impulse()[None, :], dft=W, vol_re=vre, vol_im=vim)
+        R = (vre + 1j * vim).reshape(3, 2, pb.N)
+        if n1 < pb.nt and prev is not None:
+            a = np.abs(R).max(axis=(0, 2))
+            dd = np.abs(R - prev).max(axis=(0, 2))
+            if np.all(dd <= tol * a):
+                expect = n1
+                break
+        prev = R.copy()
+    assert steps == expect
+    g = fdtd.gradient(pb, wl.rho, E, V)
+    assert np.linalg.norm(g - g_full) <= 1e-4 * np.linalg.norm(g_full)
