@@ -53,3 +53,16 @@ def test_struct_layouts_match_header_sizes():
     assert ctypes.sizeof(_capi.PointsC) == 40
     assert ctypes.sizeof(_capi.Info) == 88
     assert ctypes.sizeof(_capi.Opts) == 80
+
+
+def test_header_is_plain_c(tmp_path):
+    """The boundary is a C ABI: the header compiles as C99 with warnings as errors."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    src = tmp_path / "use.c"
+    src.write_text('#include "csem.h"\nint main(void) { csem_opts o = {0}; o.order = 4; return o.order - 4; }\n')
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"), "-c",
+                    str(src), "-o", str(tmp_path / "use.o")], check=True)
