@@ -86,3 +86,25 @@ def test_paper_worked_example():
     Bp = basis.pinv_pushthrough(B, pr["gamma"])
     tail = int(0.9 * pr["nt"])
     assert np.all(np.abs(Bp[tail:]).max(axis=0) < 1e-2 * np.abs(Bp).max(axis=0))
+
+
+def test_eight_log_spaced_frequencies_need_less_regularisation():
+    """The reading behind the fit target: for 8 log-spaced frequencies over 0.1-1.5 Hz and
+    19 492 steps the Gram matrix B B^T has a condition number near 1e12, so gamma = 1e-12
+    relative leaves a fit residual near 0.2, while 1e-16 fits to ~1e-4 with B+ entries only
+    about twice as large; 4 frequencies over 0.25-1 Hz fit at 1e-12 already."""
+    from oracle import basis as B
+    from oracle import fdtd
+    from paper_2211_16665_gb300 import workloads as W
+    large = fdtd.problem_from_workload(W.large_gradient())
+    M = B.basis_matrix(large.dt, large.nt, large.freqs, large.f0)
+    ev = np.linalg.eigvalsh(M @ M.T)
+    assert 1e11 < ev.max() / ev.min() < 1e13
+    fits, amps = {}, {}
+    for g in (1e-12, 1e-16):
+        Bp = B.pinv_pushthrough(M, B.gamma_from_relative(M, g))
+        fits[g], amps[g] = B.fit_residual(M, Bp), np.abs(Bp).max()
+    assert fits[1e-12] > 0.1 and fits[1e-16] < 1e-3 and amps[1e-16] < 3 * amps[1e-12]
+    thin = fdtd.problem_from_workload(W.thin_reservoir())
+    Mt = B.basis_matrix(thin.dt, thin.nt, thin.freqs, thin.f0)
+    assert B.fit_residual(Mt, B.pinv_pushthrough(Mt, B.gamma_from_relative(Mt, 1e-12))) < 1e-3
