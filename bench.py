@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="thin_reservoir")
+    ap.add_argument("--workload", default="batched_towline")
     ap.add_argument("--vti", action="store_true", help="VTI medium: models (rho_h, rho_v), split gradient")
     ap.add_argument("--order", type=int, default=2, choices=[2, 4],
                     help="spatial order of the staggered differences (4: four-point kernels)")
@@ -61,13 +61,16 @@ def parse():
                     help="time forward data runs with the early end at this tolerance against full runs")
     ap.add_argument("--td", type=int, default=0,
                     help="time this many time-domain adjoint gradients against the basis route")
-    ap.add_argument("--cpu-steps", type=int, default=2000, help="time steps in the oracle sample")
+    ap.add_argument("--cpu-steps", type=int, default=300, help="time steps in the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--batched-vs-plain", action="store_true",
-                    help="side measurement on batched_towline: one batched Kahan gradient vs one source per launch")
-    ap.add_argument("--nt", type=int, default=0, help="time steps for --batched-vs-plain (0: the workload's)")
-    ap.add_argument("--check-sources", type=int, default=4, help="sources scored against FP64 in --batched-vs-plain")
+    ap.add_argument("--batch", type=int, default=2,
+                    help="sources per launch: each step runs one batched gradient of the next batch of the "
+                         "workload's sources")
+    ap.add_argument("--no-plain", action="store_true", help="skip the one-source-per-launch comparison")
+    ap.add_argument("--check-sources", type=int, default=1,
+                    help="sources of the first batch whose gradients are scored against the FP64 engine")
+    ap.add_argument("--e2e-steps", type=int, default=2, help="steps of the end-to-end measurement")
     return ap.parse_args()
 
 
@@ -154,63 +157,40 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
-def kernel_bytes(wl, eng):
-    """Algorithmic bytes per launch of each stepping kernel (one source batch).
-
-    Per cell (the work domain of the step kernels) and source, with r the real
-    size and f the CPML slab fraction sum_axes 2 npml / n_axis (two CPML
-    arrays per axis per half-step, read + written, inside the slabs only):
-      k_h     read E^n 3r, read + write H 6r, CPML 4 r f
-      k_e     read E^n 3r, write E^{n+1} 3r, read H 3r, read dt/eps 3r, CPML 4 r f
-      k_step  (fused) read E^n 3r, read H 3r, write H 3r, read dt/eps 3r,
-              write E^{n+1} 3r, CPML 8 r f
-      k_dft   one flush of M snapshots, per lattice node: read 3 M r, read + write
-              the 3 nf complex accumulators 3 nf 4r, and their Kahan terms as
-              much again
-    """
+def stencil_bytes(wl, eng):
+    """Algorithmic bytes of one fused H+E step per cell (the survey's byte model): the six
+    field components read and written once (6 x 2 x r), one material value per cell (r per
+    conductivity: 2 in a VTI medium), and the CPML memory, four arrays read and written on the
+    cells of each axis' two slabs (4 x 2 x r x sum over axes of 2 npml / n)."""
     r = 4 if eng.precision == 32 else 8
-    cells = wl.nx * wl.ny * wl.nz * wl.src.n
-    nodes = (wl.nx + 1) * (wl.ny + 1) * (wl.nz + 1) * wl.src.n
     f = sum(2 * wl.npml / n for n in (wl.nx, wl.ny, wl.nz))
-    per = {"k_h": 9 * r + 4 * r * f,
-           "k_e": 12 * r + 4 * r * f,
-           "k_step": 15 * r + 8 * r * f,
-           "k_dft": 3 * eng.flush_block() * r + 3 * eng.nf * 4 * r * (2 if eng.info.kahan else 1)}
-    units = {"k_h": cells, "k_e": cells, "k_step": cells, "k_dft": nodes}
-    return {k: v * units[k] for k, v in per.items()}, per
+    return 12 * r + r * (2 if eng.vti else 1) + 8 * r * f
 
 
-# DRAM bytes (read + write) per launch of a kernel from ncu captures of
-# dram__bytes_read.sum and dram__bytes_write.sum (cold cache, 128x128x96 thin reservoir,
-# nt = 256 through the profile driver with the launch configurations of
-# profiles/traffic_lean_thin_reservoir.md; the mean over the captured launches), valid only
-# for the source they were taken on: keyed by workload, kernel, launch code (Engine.kz
-# entry) and the SHA-1 of the kernel's source file, with the shared header's SHA-1
-# checked separately.  Any other kernel reports null.
-_LEAN = "78b60ad8187d51577bc248ded4ea5cffa931c7e7"
-_STEP = "2b13003dc0a546c8de35f6b3b533bac6c5297935"
-NCU_TRAFFIC = {
-    ("thin_reservoir_128x128x96_fp32", "k_e", 16422, _LEAN): 66.875e6 + 1.251e6,
-    ("thin_reservoir_128x128x96_fp32", "k_h", 16422, _LEAN): 47.268e6 + 0.002e6,
-    ("thin_reservoir_128x128x96_fp32", "k_e", 16424, _LEAN): 66.885e6 + 1.476e6,
-    ("thin_reservoir_128x128x96_fp32", "k_h", 16424, _LEAN): 47.270e6 + 0.001e6,
-    ("thin_reservoir_128x128x96_fp32", "k_dft", 129, _STEP): 980.377e6 + 288.796e6,
-    ("thin_reservoir_128x128x96_fp32", "k_dft", 131, _STEP): 980.487e6 + 288.802e6,
-}
-_HEADER_SHA = "d4d538b5843a1f7202e9ae15e2c39d39f857e817"
+def flush_bytes(wl, eng):
+    """Algorithmic bytes of one transform flush of M snapshots per lattice node: the M
+    snapshots read (3 M r) and the 3 n_freq complex accumulators read and written once
+    (3 n_freq 2r x 2), and their compensation terms as much again with Kahan."""
+    r = 4 if eng.precision == 32 else 8
+    M = eng.flush_block()
+    return 3 * M * r + 3 * eng.nf * 2 * r * 2 * (2 if eng.info.kahan else 1)
 
 
-def ncu_traffic(wl, eng, kernel):
+# DRAM bytes (read + write) per launch from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the named kernel on the named workload, for one source per launch,
+# valid only while the kernel's source file and the shared header are the ones captured
+# (SHA-1 of each); the figure is scaled by the sources of a launch.  Anything else reports null.
+NCU_TRAFFIC = {}
+
+
+def ncu_traffic(wl, kernel, S):
     import hashlib
-    code = {"k_h": eng.kz[0], "k_e": eng.kz[1], "k_dft": eng.kz[2]}.get(kernel) if eng.kz else None
-    src = {"k_h": "kern_lean.cu", "k_e": "kern_lean.cu", "k_dft": "kern_step.cu"}.get(kernel)
-    if code is None or src is None:
-        return None
     d = os.path.join(ROOT, "paper_2211_16665_gb300", "csrc")
     sha = lambda f: hashlib.sha1(open(os.path.join(d, f), "rb").read()).hexdigest()
-    if sha("csem_internal.cuh") != _HEADER_SHA:
-        return None
-    return NCU_TRAFFIC.get((wl.name, kernel, code, sha(src)))
+    for (name, kern, src, src_sha, hdr_sha), per_src in NCU_TRAFFIC.items():
+        if name == wl.name and kern == kernel and sha(src) == src_sha and sha("csem_internal.cuh") == hdr_sha:
+            return per_src * S
+    return None
 
 
 def cpu_baseline(wl, nt_sample, order=2):
@@ -230,13 +210,27 @@ def cpu_baseline(wl, nt_sample, order=2):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def gradient_step(eng, rho, src, rec, d_obs):
+    """One gradient of the hot path for a source batch: coefficient set-up and forward run
+    with the volumetric transform, misfit and residual, adjoint-source basis, adjoint run,
+    cell gradient with respect to ln rho."""
+    from paper_2211_16665_gb300.engine import misfit
+    d, E = eng.fwd_model(rho, src, rec, keep_volume=True)
+    phi, r = misfit(d_obs, d)
+    basis, fit, _ = eng.estimate_adjoint_basis(gamma=1e-12, relative=True, fit_target=1e-3)
+    V = eng.adjoint_model(rho, rec, r, basis)
+    g = eng.gradient(rho, E, V, wrt="lnrho")
+    del E, V
+    return phi, g, fit
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
     from paper_2211_16665_gb300 import _capi
     from paper_2211_16665_gb300 import dist as D
     from paper_2211_16665_gb300 import workloads as W
-    from paper_2211_16665_gb300.engine import Engine, misfit
+    from paper_2211_16665_gb300.engine import Engine, _ptr, _stream
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -247,20 +241,27 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     wl = make_workload(args.workload, rank, world, vti=args.vti, max_src=args.max_src)
-    eng = Engine.from_workload(wl, vti=args.vti, order=args.order)
-    S = wl.src.n
+    S_all = wl.src.n
+    B = max(1, min(args.batch, S_all))
+    nb = S_all // B
+    batches = [wl.src.subset(list(range(b * B, (b + 1) * B))) for b in range(nb)]
+    eng = Engine.from_workload(wl, max_src=B, vti=args.vti, order=args.order)
+    nt, dt, prec = eng.nt, eng.dt, eng.precision
     rho = eng.model_tensor(wl.rho)
     rho_true = eng.model_tensor(wl.rho_true)
-    d_obs = eng.fwd_model(rho_true, wl.src, wl.rec)
-    d_obs = torch.as_tensor(W.add_noise(d_obs.cpu().numpy(), wl.noise, wl.noise_seed), device=dev)
+    # observed data of every batch (the true model; data-only runs end early at 1e-6)
+    eng.set_early_stop(1e-6)
+    d_obs = []
+    for b in range(nb):
+        d = eng.fwd_model(rho_true, batches[b], wl.rec).cpu().numpy()
+        d_obs.append(torch.as_tensor(W.add_noise(d, wl.noise, wl.noise_seed + b), device=dev))
+    eng.set_early_stop(0.0)
     torch.cuda.synchronize()
 
-    def step(rho_in, d_obs_in):
-        d, E = eng.fwd_model(rho_in, wl.src, wl.rec, keep_volume=True)
-        phi, r = misfit(d_obs_in, d)
-        basis, fit, its = eng.estimate_adjoint_basis(gamma=1e-12, relative=True, fit_target=1e-3)
-        V = eng.adjoint_model(rho_in, wl.rec, r, basis)
-        g = eng.gradient(rho_in, E, V, wrt="lnrho")
+    def step(t, rho_in=None, d_in=None):
+        b = t % nb
+        phi, g, fit = gradient_step(eng, rho if rho_in is None else rho_in, batches[b], wl.rec,
+                                    d_obs[b] if d_in is None else d_in)
         D.sum_over_ranks(g, phi)          # the one exchange: sum of the per-source gradients
         return phi, g, fit
 
@@ -269,8 +270,8 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        step(rho, d_obs)
+    for t in range(args.warmup):
+        step(t)
     barrier()
 
     uuid = None
@@ -285,8 +286,8 @@ def run_ours(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     ev0.record(stream)
-    for _ in range(args.steps):
-        phi, g, fit = step(rho, d_obs)
+    for t in range(args.steps):
+        phi, g, fit = step(args.warmup + t)
     ev1.record(stream)
     barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
@@ -294,60 +295,127 @@ def run_ours(args):
     clk = clocks.stop()
     ms = D.max_over_ranks(ms, device=dev)
 
-    cell_updates = 2.0 * wl.cells * eng.nt * S * world
+    cell_updates = 2.0 * wl.cells * nt * B * world
     value = cell_updates / (ms / 1e3) / 1e9
 
-    # the adjoint-source basis solve alone (it is part of every timed step above; it blocks
-    # until its fit residual is on the host)
+    # the adjoint-source basis solve alone (part of every timed step above; it blocks until
+    # its fit residual is on the host)
     torch.cuda.synchronize()
     tb = time.perf_counter()
     eng.estimate_adjoint_basis(gamma=1e-12, relative=True, fit_target=1e-3)
     basis_ms = (time.perf_counter() - tb) * 1e3
 
-    # roofline of the dominant kernel, timed live with CUDA events on its stream
-    _, E = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)
-    from paper_2211_16665_gb300.engine import _ptr, _stream
-    kms = dict(zip(("k_h", "k_step", "k_e", "k_dft"), _capi.time_step_kernels(eng.ctx, S, _ptr(E), 200, _stream())))
-    bytes_launch, per_unit = kernel_bytes(wl, eng)
-    fused = kms["k_step"] > 0
-    per_step_ms = ({"k_step": kms["k_step"]} if fused else {"k_h": kms["k_h"], "k_e": kms["k_e"]})
-    per_step_ms["k_dft"] = kms["k_dft"] / eng.flush_block()
-    dom = max(per_step_ms, key=per_step_ms.get)
-    peak, peak_kind = hbm_peak()
-    gbs = {k: round(bytes_launch[k] / (kms[k] / 1e3) / 1e9, 1) for k in kms if kms[k] > 0}
-    achieved = gbs[dom]
-    tot = sum(per_step_ms.values())
-    roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "peak_kind": peak_kind, "traffic": ncu_traffic(wl, eng, dom),
-            "bytes_per_unit": round(per_unit[dom], 1), "unit_of_work": "lattice node" if dom == "k_dft" else "cell",
-            "ms_per_launch": {k: round(v, 5) for k, v in kms.items()},
-            "step_share": {k: round(v / tot, 3) for k, v in per_step_ms.items()},
-            "all_kernels_gbs": gbs}
+    # roofline: the stencil (split H + E pair or fused step) and the transform flush, timed
+    # live with CUDA events on the stream they are launched on
+    _, E = eng.fwd_model(rho, batches[0], wl.rec, keep_volume=True)
+    kms = dict(zip(("k_h", "k_step", "k_e", "k_dft"), _capi.time_step_kernels(eng.ctx, B, _ptr(E), 100, _stream())))
     del E
+    fused = kms["k_step"] > 0
+    st_ms = kms["k_step"] if fused else kms["k_h"] + kms["k_e"]
+    lc = eng.launch_config()
+    st_name = ("k_step_fz" if lc["step"]["kernel"].startswith("fused one-pass") else "k_step") if fused else \
+        "+".join(f"k_{w}_{lc['step'][w]['kernel'].split()[0]}" for w in ("h", "e"))
+    b_cell = stencil_bytes(wl, eng)
+    nodes = (wl.nx + 1) * (wl.ny + 1) * (wl.nz + 1)
+    M = eng.flush_block()
+    b_flush = flush_bytes(wl, eng)
+    peak, peak_kind = hbm_peak()
+    st_gbs = b_cell * wl.cells * B / (st_ms / 1e3) / 1e9
+    fl_gbs = b_flush * nodes * B / (kms["k_dft"] / 1e3) / 1e9
+    per_step = {"stencil": st_ms, "flush": kms["k_dft"] / M}
+    # the floor of one gradient step per cell update: the stencil's bytes plus the flush's per
+    # snapshot share (nodes per cell), both runs alike
+    floor_update = b_cell + b_flush / M * nodes / wl.cells
+    whole = floor_update * cell_updates / world / (ms / 1e3) / 1e9
+    roof = {"kernel": st_name, "bound": "hbm", "achieved": round(st_gbs, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(st_gbs / peak, 4), "peak_kind": peak_kind,
+            "traffic": ncu_traffic(wl, st_name, B),
+            "bytes_per_unit": round(b_cell, 2), "unit_of_work": "cell (one H + E step, every source of the launch)",
+            "units_per_launch": wl.cells * B, "ms_per_launch": round(st_ms, 5),
+            "flush": {"kernel": "k_dft_bulk" if lc["flush"]["kernel"] == "bulk-copy" else "k_dft",
+                      "snapshots": M, "bytes_per_node": b_flush, "achieved": round(fl_gbs, 1),
+                      "frac": round(fl_gbs / peak, 4), "ms_per_launch": round(kms["k_dft"], 5)},
+            "step_share": {k: round(v / sum(per_step.values()), 3) for k, v in per_step.items()},
+            "whole_step": {"bytes_per_cell_update": round(floor_update, 2), "achieved": round(whole, 1),
+                           "frac": round(whole / peak, 4)}}
 
-    # end to end: host model in, host gradient out
+    # end to end: host model and data in, host gradient and misfit out, every step
     e2e = None
     if not args.no_e2e:
+        k_e2e = max(1, min(args.steps, args.e2e_steps))
         rho_h = rho.cpu().pin_memory()
-        dobs_h = d_obs.cpu().pin_memory()
+        dobs_h = [d.cpu().pin_memory() for d in d_obs]
         g_h = torch.empty(g.shape, dtype=g.dtype).pin_memory()
         phi_h = torch.empty((), dtype=torch.float64).pin_memory()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for t in range(k_e2e):
             r_dev = rho_h.to(dev, non_blocking=True)
-            o_dev = dobs_h.to(dev, non_blocking=True)
-            phi2, g2, _ = step(r_dev, o_dev)
+            o_dev = dobs_h[t % nb].to(dev, non_blocking=True)
+            phi2, g2, _ = step(t, r_dev, o_dev)
             g_h.copy_(g2, non_blocking=True)
             phi_h.copy_(phi2, non_blocking=True)
         e1.record(stream)
         barrier()
-        ems = D.max_over_ranks(e0.elapsed_time(e1) / args.steps, device=dev)
+        ems = D.max_over_ranks(e0.elapsed_time(e1) / k_e2e, device=dev)
         e2e = {"value": round(cell_updates / (ems / 1e3) / 1e9, 3), "unit": "Gcell-updates/s",
-               "ms_per_step": round(ems, 3),
-               "h2d_bytes_per_step": int(rho_h.numel() * rho_h.element_size() + dobs_h.numel() * dobs_h.element_size()),
+               "ms_per_step": round(ems, 3), "steps": k_e2e,
+               "h2d_bytes_per_step": int(rho_h.numel() * rho_h.element_size() +
+                                         dobs_h[0].numel() * dobs_h[0].element_size()),
                "d2h_bytes_per_step": int(g_h.numel() * g_h.element_size() + 8)}
+
+    # batched (B sources per launch, compensated transform) against the plain path (one
+    # source per launch, plain FP32 transform) on the sources of the first batch, and each
+    # path's gradient against the FP64 engine on the first sources
+    bvp = None
+    if rank == 0 and not args.no_plain and B > 1:
+        eng.close()
+        del eng
+        torch.cuda.empty_cache()
+        ep = Engine.from_workload(wl, max_src=1, kahan=0, vti=args.vti, order=args.order)
+        rp = ep.model_tensor(wl.rho)
+        singles = [batches[0].subset([u]) for u in range(B)]
+        gradient_step(ep, rp, singles[0], wl.rec, d_obs[0][:1].contiguous())      # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for u in range(B):
+            gradient_step(ep, rp, singles[u], wl.rec, d_obs[0][u:u + 1].contiguous())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_s = e0.elapsed_time(e1) / 1e3 / B
+        bvp = {"batched": {"s_per_source": round(ms / 1e3 / B, 4), "sources_per_launch": B, "kahan": True,
+                           "launch": lc},
+               "plain": {"s_per_source": round(plain_s, 4), "sources_per_launch": 1, "kahan": False,
+                         "launch": ep.launch_config()},
+               "batched_over_plain": round(plain_s / (ms / 1e3 / B), 4)}
+        if args.check_sources > 0:
+            k = min(args.check_sources, B)
+            grads = {}
+            gp = torch.zeros_like(g)
+            for u in range(k):
+                gp += gradient_step(ep, rp, singles[u], wl.rec, d_obs[0][u:u + 1].contiguous())[1]
+            grads["plain"] = gp.double().cpu().numpy()
+            ep.close()
+            del ep
+            torch.cuda.empty_cache()
+            for name, prec, kahan in (("fp64", 64, 0), ("batched", 32, 1)):
+                e = Engine.from_workload(wl, max_src=k, precision=prec, kahan=kahan, vti=args.vti, order=args.order)
+                sub = batches[0].subset(list(range(k)))
+                gg = gradient_step(e, e.model_tensor(wl.rho), sub, wl.rec, d_obs[0][:k].contiguous())[1]
+                grads[name] = gg.double().cpu().numpy()
+                e.close()
+                del e
+                torch.cuda.empty_cache()
+            ref = grads["fp64"]
+            for name in ("batched", "plain"):
+                bvp[name]["grad_rel_l2_vs_fp64"] = float(np.linalg.norm(grads[name] - ref) / np.linalg.norm(ref))
+            bvp["checked_sources"] = k
+        else:
+            ep.close()
+    else:
+        eng.close()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -356,21 +424,25 @@ def run_ours(args):
     if rank == 0:
         out = {"metric": METRIC, "value": round(value, 3), "unit": "Gcell-updates/s", "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f32" if eng.precision == 32 else "f64",
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == 32 else "f64",
                "data": "synthetic",
-               "config": {"workload": wl.name, "cells": wl.cells, "grid": [wl.nx, wl.ny, wl.nz], "nt": eng.nt,
-                          "dt": eng.dt, "n_src_per_gpu": S, "n_rec": wl.rec.n, "freqs_hz": list(map(float, wl.freqs)),
-                          "kahan": bool(eng.info.kahan), "launch": eng.launch_config(), "l2": "inputs larger than L2 (each step streams "
-                          f"{2 * 3 * eng.nf * eng.vol * 8 * S * (2 if eng.info.kahan else 1) / 2**20:.0f} MiB of "
-                          "transform volumes)", "parallelism": f"sources sharded, dp{world}",
-                          "medium": "vti" if args.vti else "isotropic", "order": eng.order},
-               "grad_s_per_source": round(ms / 1e3 / S, 4),
-               "basis_fit": fit, "basis_gamma_rel": eng.basis_gamma, "basis_ms": round(basis_ms, 3),
+               "config": {"workload": wl.name, "cells": wl.cells, "grid": [wl.nx, wl.ny, wl.nz], "nt": nt, "dt": dt,
+                          "n_src_per_gpu": S_all, "sources_per_step": B, "batches": nb,
+                          "n_rec": wl.rec.n, "freqs_hz": list(map(float, wl.freqs)),
+                          "kahan": True, "launch": lc,
+                          "l2": "inputs larger than L2 (each step streams "
+                          f"{2 * 3 * wl.freqs.size * nodes * 8 * B * 2 / 2**20:.0f} MiB of transform volumes and "
+                          f"{2 * 6 * wl.cells * 4 * B / 2**20:.0f} MiB of fields per time step)",
+                          "parallelism": f"sources sharded, dp{world}",
+                          "medium": "vti" if args.vti else "isotropic", "order": args.order},
+               "grad_s_per_source": round(ms / 1e3 / B, 4),
+               "batched_vs_plain": bvp,
+               "basis_fit": fit, "basis_ms": round(basis_ms, 3),
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                "clocks": clk}
         print(json.dumps(out), flush=True)
-    eng.close()
     if world > 1:
+        dist.barrier()
         dist.destroy_process_group()
 
 
@@ -406,79 +478,6 @@ def run_reference(args):
                             "sample": f"{nt_s} of {pb.nt} steps of one forward run with the volumetric transform"},
            "e2e": {"value": round(value, 5), "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
-    print(json.dumps(out), flush=True)
-
-
-def run_batched_vs_plain(args):
-    """Gradient seconds per source: all sources in one launch (FP32 + Kahan) against one
-    source per launch (FP32, plain transform), and each gradient's error against FP64."""
-    import torch
-    from paper_2211_16665_gb300 import workloads as W
-    from paper_2211_16665_gb300.engine import Engine, misfit
-
-    torch.cuda.set_device(0)
-    wl = W.batched_towline()
-    S = wl.src.n
-
-    def gradient(eng, src, d_obs, out):
-        rho = eng.model_tensor(wl.rho)
-        d, E = eng.fwd_model(rho, src, wl.rec, keep_volume=True)
-        phi, r = misfit(d_obs, d)
-        basis, _, _ = eng.estimate_adjoint_basis()
-        V = eng.adjoint_model(rho, wl.rec, r, basis)
-        eng.gradient(rho, E, V, out=out)
-        del E, V
-
-    def timed(fn):
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / 1e3
-
-    Z = W.cell_centres(wl.xn, wl.yn, wl.zn)[2]
-    rho_obs = np.where(Z >= 1000.0, 1.3 * wl.rho, wl.rho)     # observed data: sediment 30 % more resistive
-    out = {"mode": "batched_vs_plain", "workload": wl.name, "n_src": S, "nt": None}
-    # batched: every source in each launch, compensated transform
-    eb = Engine.from_workload(wl, nt=args.nt or None, max_src=S, kahan=1)
-    out["nt"] = eb.nt
-    d_obs = eb.fwd_model(eb.model_tensor(rho_obs), wl.src, wl.rec)
-    gb = torch.zeros((wl.nz, wl.ny, wl.nx), dtype=torch.float32, device="cuda")
-    gradient(eb, wl.src, d_obs, gb)                       # warm-up
-    gb.zero_()
-    tb = timed(lambda: gradient(eb, wl.src, d_obs, gb))
-    out["batched"] = {"s_per_source": tb / S, "launch": eb.launch_config(), "kahan": True}
-    eb.close()
-    # plain: one source per launch, plain FP32 transform
-    ep = Engine.from_workload(wl, nt=args.nt or None, max_src=1, kahan=0)
-    gp = torch.zeros_like(gb)
-    gradient(ep, wl.src.subset([0]), d_obs[:1].contiguous(), gp)
-    gp.zero_()
-    tp = timed(lambda: [gradient(ep, wl.src.subset([s]), d_obs[s:s + 1].contiguous(), gp) for s in range(S)])
-    out["plain"] = {"s_per_source": tp / S, "launch": ep.launch_config(), "kahan": False}
-    ep.close()
-    # error of each path's gradient on the first sources against the FP64 engine
-    k = min(args.check_sources, S)
-    sub = wl.src.subset(list(range(k)))
-    errs = {}
-    ref = None
-    for name, prec, kahan in (("fp64", 64, 0), ("batched", 32, 1), ("plain", 32, 0)):
-        e = Engine.from_workload(wl, nt=args.nt or None, max_src=k, precision=prec, kahan=kahan)
-        g = torch.zeros((wl.nz, wl.ny, wl.nx), dtype=e.real, device="cuda")
-        gradient(e, sub, d_obs[:k].contiguous(), g)
-        g = g.double().cpu().numpy()
-        e.close()
-        if ref is None:
-            ref = g
-        else:
-            errs[name] = float(np.linalg.norm(g - ref) / np.linalg.norm(ref))
-    out["batched"]["grad_rel_l2_vs_fp64"] = errs["batched"]
-    out["plain"]["grad_rel_l2_vs_fp64"] = errs["plain"]
-    out["speedup_per_source"] = out["plain"]["s_per_source"] / out["batched"]["s_per_source"]
-    out["note"] = (f"nt = {out['nt']} time steps per run; the per-step cost does not depend on nt; errors on the "
-                   f"first {k} sources")
     print(json.dumps(out), flush=True)
 
 
@@ -720,9 +719,6 @@ def main():
         return
     if args.td:
         run_td(args)
-        return
-    if args.batched_vs_plain:
-        run_batched_vs_plain(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -93,6 +93,11 @@ typedef struct {
                            outer boundary); dt <= 0 then gives 2 s / (v(rho_max) sqrt(sum over
                            axes of the largest absolute weight-row sum squared)).  Order 4 runs
                            its own H and E kernels (csem_set_launch accepts no other family) */
+    int ring_slots;     /* cap on the ring of E snapshots kept per source for the deferred damped
+                           transform: <= 0 takes the largest of 129, 65, 33 and 17 slots that fits
+                           in 85 % of the free device memory beside the rest of the workspace; a
+                           positive value also caps it (17 slots at least).  A larger ring allows
+                           longer transform blocks (csem_set_launch) */
 } csem_opts;
 
 typedef struct {

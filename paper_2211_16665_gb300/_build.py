@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcsemfw.so")
-UNITS = ["kern_step.cu", "kern_vec.cu", "kern_tma.cu", "kern_fused.cu", "kern_lean.cu", "kern_aux.cu", "kern_td.cu", "kern_ho.cu", "capi.cu", "noalloc.cu"]
+UNITS = ["kern_step.cu", "kern_vec.cu", "kern_tma.cu", "kern_fused.cu", "kern_lean.cu", "kern_fz.cu", "kern_aux.cu", "kern_td.cu", "kern_ho.cu", "capi.cu", "noalloc.cu"]
 HEADERS = ["csem_internal.cuh", "csem_td.cuh", "csem_ho.cuh", "csem_es.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -39,7 +39,7 @@ class Opts(ctypes.Structure):
                 ("nt", ctypes.c_int), ("cfl_safety", ctypes.c_double), ("precision", ctypes.c_int),
                 ("kahan", ctypes.c_int), ("n_freq", ctypes.c_int), ("freqs", _D),
                 ("max_src", ctypes.c_int), ("max_rec", ctypes.c_int), ("anisotropy", ctypes.c_int),
-                ("order", ctypes.c_int)]
+                ("order", ctypes.c_int), ("ring_slots", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -122,13 +122,14 @@ def make_points(pts, keep: list) -> PointsC:
 
 
 def create(xn, yn, zn, npml, freqs, f0=1.0, rho_max=1.0, dt=0.0, nt=0, precision=32, kahan=1,
-           max_src=1, max_rec=0, cfl_safety=0.0, anisotropy=0, order=2):
+           max_src=1, max_rec=0, cfl_safety=0.0, anisotropy=0, order=2, ring_slots=0):
     import numpy as np
     keep = [np.ascontiguousarray(v, np.float64) for v in (xn, yn, zn, freqs)]
     g = Grid(keep[0].size - 1, keep[1].size - 1, keep[2].size - 1, _dptr(keep[0]), _dptr(keep[1]), _dptr(keep[2]),
              int(npml))
     o = Opts(float(f0), float(rho_max), float(dt), int(nt), float(cfl_safety), int(precision), int(kahan),
-             int(keep[3].size), _dptr(keep[3]), int(max_src), int(max_rec), int(anisotropy), int(order))
+             int(keep[3].size), _dptr(keep[3]), int(max_src), int(max_rec), int(anisotropy), int(order),
+             int(ring_slots))
     ctx = _V()
     _check(lib().csem_create(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(o)))
     return ctx

@@ -141,6 +141,7 @@ struct csem_ctx {
     int KZ_h = 4, KZ_e = 4;             // z planes per thread (autotuned)
     int MB_h = 4, MB_e = 4;             // min resident blocks per SM of the compiled variant (autotuned)
     int fused_kz = 0;                   // > 0: fused H+E step with this z blocking (autotuned)
+    int FZ_by = 0, FZ_mb = 4, FZ_kz = 16; // FZ_by > 0: fused one-pass FP32 step, rows per block (autotuned)
     int VEC_h = 0, VEC_e = 0;           // 1: four-cells-per-thread FP32 kernels (autotuned)
     int TMA_h = 0, TMA_e = 0;           // > 0: bulk-copy-staged FP32 kernels, rows per block (autotuned)
     int LEAN_h = 0, LEAN_e = 0;         // > 0: lean FP32 kernels, cells per thread (autotuned; needs d_psiL)
@@ -151,6 +152,8 @@ struct csem_ctx {
     double *d_h = nullptr;               // primal widths (double) hx|hy|hz
     void *d_tabL = nullptr;              // padded FP32 stepping tables (lean kernels)
     float *d_psiL = nullptr, *d_cEm = nullptr;   // lean kernels: CPML memory in volume arrays, masked dt/eps
+    float *d_q = nullptr;                // fused one-pass step: V sigma per cell [1 or 2][vol] (sigma_h, sigma_v)
+    float *d_tabG = nullptr;             // fused one-pass step: per-axis widths h [n] and sums s [n+1], padded
     void *d_cE = nullptr, *d_H = nullptr, *d_H2 = nullptr, *d_ering = nullptr, *d_psi = nullptr, *d_comp = nullptr, *d_edge = nullptr;
     int M = 16, nslot = 17;
     int flush_mode = 0;                  // bit 0: bulk-copy flush (FP32 only), else register flush;
@@ -230,6 +233,25 @@ void axis_tab(const csem_ctx *c, int a, csem::AxisTab<R> &t) {
 // lean_len(n) floats (16-byte groups, zero past the axis); b_n, a_n are zero on
 // the outer nodes 0 and n, which carry no CPML update.
 int lean_len(int n) { return (n + 1 + 3 + 3) / 4 * 4; }
+// The fused one-pass step's launch shape as one code (0: not selected): kz * 100 + rows * 10 + blocks;
+// csem_autotune and csem_set_launch report and take it as 10000 + that code.
+int fz_code(const csem_ctx *c) { return c->FZ_by ? c->FZ_kz * 100 + c->FZ_by * 10 + c->FZ_mb : 0; }
+// Per-axis widths of the fused one-pass step: h (primal, half nodes) and s = h[i-1] + h[i] at the
+// nodes (the outer nodes take their one width), each padded to lean_len(n) floats.
+int upload_geo_tables(csem_ctx *c) {
+    std::vector<float> tab;
+    for (int a = 0; a < 3; ++a) {
+        const Axis &A = c->ax[a];
+        const int n = A.n, L = lean_len(n);
+        std::vector<float> v(2 * (size_t)L, 0.f);
+        for (int i = 0; i < n; ++i) v[i] = (float)A.h[i];
+        for (int i = 0; i <= n; ++i) v[L + i] = (float)((i > 0 ? A.h[i - 1] : 0.0) + (i < n ? A.h[i] : 0.0));
+        tab.insert(tab.end(), v.begin(), v.end());
+    }
+    TRY(dalloc(c, &c->d_tabG, tab.size() * sizeof(float)));
+    CK(cudaMemcpy(c->d_tabG, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return CSEM_OK;
+}
 void lean_tab(const csem_ctx *c, int a, csem::AxisTab<float> &t) {
     const float *base = (const float *)c->d_tabL;
     long long off = 0;
@@ -411,6 +433,10 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
     p.LEAN_e = c->LEAN_e;
     p.lx = p.ly = p.lz = csem::AxisTab<R>{};
     p.lzero = nullptr;
+    p.FZ_by = 0; p.FZ_mb = 4; p.FZ_kz = 16;
+    p.qh = p.qv = nullptr;
+    p.gx = p.gy = p.gz = csem::GeoTab{nullptr, nullptr};
+    p.k2w0dt = 0.f;
     p.inc = nullptr;
     p.tapk = nullptr;
     p.psiL = nullptr;
@@ -426,6 +452,20 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
         p.cEm = c->d_cEm;
         p.inc = c->d_inc;
         p.tapk = c->d_tapk;
+        if (c->d_q && c->d_tabG) {
+            p.FZ_by = c->FZ_by; p.FZ_mb = c->FZ_mb; p.FZ_kz = c->FZ_kz;
+            p.qh = c->d_q;
+            p.qv = c->vti ? c->d_q + c->vol : c->d_q;
+            const csem::GeoTab *g[3] = {&p.gx, &p.gy, &p.gz};
+            long long off = 0;
+            for (int a = 0; a < 3; ++a) {
+                const int L = lean_len(c->ax[a].n);
+                const_cast<csem::GeoTab *>(g[a])->h = c->d_tabG + off;
+                const_cast<csem::GeoTab *>(g[a])->s = c->d_tabG + off + L;
+                off += 2LL * L;
+            }
+            p.k2w0dt = (float)(2.0 * c->w0 * c->dt);
+        }
     }
     p.err = c->d_bad;
     p.colmap = nullptr;
@@ -492,7 +532,7 @@ cudaError_t launch_any(const csem_ctx *c, const csem::StepParams<R> &p, const cs
 template <typename R>
 cudaError_t tap_prep(csem_ctx *c, const csem::StepParams<R> &p, int S, int nsteps, cudaStream_t st) {
     if constexpr (sizeof(R) == 4) {
-        if (p.inc && p.colmap && p.LEAN_e) return csem::launch_tap_inc(p, S, nsteps, c->nt, st);
+        if (p.inc && p.colmap && (p.LEAN_e || p.FZ_by)) return csem::launch_tap_inc(p, S, nsteps, c->nt, st);
     }
     return cudaSuccess;
 }
@@ -600,7 +640,7 @@ int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const 
     const bool overlap = (c->flush_mode & 2) != 0;
     const int full = c->nt / kChunk, rem = c->nt % kChunk;
     if (full > 0) {
-        const int key[8] = {S, vol ? 1 : 0, kahan ? 1 : 0, q.n_itaps > 0 ? 1 : 0, q.n_rec > 0 ? 1 : 0,
+        const int key[8] = {S, vol ? 1 : 0, kahan ? 1 : 0, (q.n_itaps > 0 ? 1 : 0) + 2 * fz_code(c), q.n_rec > 0 ? 1 : 0,
                             (int)sizeof(R), ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
                             ((((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e) * 25 +
                              c->TMA_h * 5 + c->TMA_e) * 4 + c->LEAN_h * 2 + c->LEAN_e};
@@ -647,6 +687,8 @@ int coef_init(csem_ctx *c, const void *rho, cudaStream_t st) {
     CK(csem::launch_coef_init<R>(geo(c), rho_h, rho_z, (R *)c->d_cE, 2.0 * c->w0 * c->dt, c->d_bad, st));
     if constexpr (sizeof(R) == 4) {
         if (c->d_cEm) CK(csem::launch_mask_coef(step_params<float>(c, false, nullptr), (const float *)c->d_cE, c->d_cEm, st));
+        if (c->d_q) CK(csem::launch_qcell(geo(c), (const float *)rho_h, (const float *)rho_z, c->d_q,
+                                          c->vti ? c->d_q + c->vol : nullptr, st));
     }
     return CSEM_OK;
 }
@@ -729,7 +771,7 @@ int run_steps_es(csem_ctx *c, int S, int NR, const csem::StepParams<R> &p, const
     CK(cudaMemsetAsync(c->d_es, 0, 2 * sizeof(int), st));
     bool ended = false;
     if (full > 0) {
-        const int key[8] = {S, 4, 0, q.n_itaps > 0 ? 1 : 0, 1, (int)sizeof(R),
+        const int key[8] = {S, 4, fz_code(c), q.n_itaps > 0 ? 1 : 0, 1, (int)sizeof(R),
                             ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
                             ((((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e) * 25 +
                              c->TMA_h * 5 + c->TMA_e) * 4 + c->LEAN_h * 2 + c->LEAN_e};
@@ -789,7 +831,7 @@ int run_steps_vol_es(csem_ctx *c, int S, const csem::StepParams<R> &p, const cse
     CK(cudaMemsetAsync(c->d_es, 0, 2 * sizeof(int), st));
     bool ended = false;
     if (full > 0) {
-        const int key[8] = {S, 5, kahan ? 1 : 0, q.n_itaps, q.n_rec > 0 ? 1 : 0, (int)sizeof(R),
+        const int key[8] = {S, 5, (kahan ? 1 : 0) + 2 * fz_code(c), q.n_itaps, q.n_rec > 0 ? 1 : 0, (int)sizeof(R),
                             ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
                             ((((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e) * 25 +
                              c->TMA_h * 5 + c->TMA_e) * 4 + c->LEAN_h * 2 + c->LEAN_e};
@@ -940,8 +982,8 @@ TdPlan td_layout(const csem_ctx *c, int S, int NR, int C) {
     P.K = (c->nt + C - 1) / C;
     P.nck = std::max(P.K - 2, 0);
     P.recompute = (long long)(P.K - 1) * C;
-    P.lean = c->d_psiL && (c->LEAN_h || c->LEAN_e);
-    P.fused = c->fused_kz > 0;
+    P.lean = c->d_psiL && (c->LEAN_h || c->LEAN_e) && !c->FZ_by;
+    P.fused = c->fused_kz > 0 || c->FZ_by > 0;
     const size_t R = c->rsize, v3 = 3 * (size_t)c->vol, Ss = (size_t)S;
     const size_t psi = Ss * (size_t)c->psi_stride * R, psiL = P.lean ? Ss * 12 * (size_t)c->vol * sizeof(float) : 0;
     size_t o = 0;
@@ -1014,7 +1056,7 @@ int run_range(csem_ctx *c, int S, int role, RoleGraph &g, const csem::StepParams
     CK(csem::launch_set_step(c->d_step, n0, st));
     const int full = L / kChunk, rem = L % kChunk;
     if (full > 0 && !g.exec) {
-        const int key[8] = {S, role, 0, q.n_itaps, q.n_emit, (int)sizeof(R),
+        const int key[8] = {S, role, fz_code(c), q.n_itaps, q.n_emit, (int)sizeof(R),
                             ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
                             (((c->fused_kz * 4 + c->VEC_h * 2 + c->VEC_e) * 25 + c->TMA_h * 5 + c->TMA_e) * 4 +
                              c->LEAN_h * 2 + c->LEAN_e)};
@@ -1189,15 +1231,16 @@ int time_impl(csem_ctx *c, int S, void *vol, int launches, double *ms, cudaStrea
     p.inc_ntl = c->last_ntl;
     p.itaps = c->d_itaps; p.itap_stride = 8;
     p.n_emit = 1; p.J = 1; p.coef = c->d_ones; p.T = c->d_T;
-    const int fkz = p.fused_kz;
+    const int fkz = p.fused_kz, fzb = p.FZ_by;
     const int jmod = std::max(1, std::min(kChunk, c->nt - 1));   // steps within one chunk's tap increments
     if constexpr (sizeof(R) == 4) CK(csem::launch_tap_inc(p, S, kChunk, c->nt, st));
     for (int w : {0, 1, 2, 3}) {
-        if (w == 1 && fkz == 0) { ms[1] = 0.0; continue; }
+        if (w == 1 && fkz == 0 && fzb == 0) { ms[1] = 0.0; continue; }
         auto go = [&](int j) -> cudaError_t {
             if (w == 3) return flush<R>(c, p, q, S, 0, cnt, true, c->kahan != 0, st);
             csem::StepParams<R> pp = p;
             pp.fused_kz = (w == 1) ? fkz : 0;
+            pp.FZ_by = (w == 1) ? fzb : 0;
             return launch_any<R>(c, pp, q, S, j % jmod, st, w == 1 ? 5 : (w == 0 ? 1 : 4));
         };
         for (int j = 0; j < 2; ++j) CK(go(j));
@@ -1263,16 +1306,26 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
             if (which == 1) { c->KZ_h = best_kz; c->MB_h = best_mb; c->VEC_h = best_vec; c->TMA_h = best_tma; c->LEAN_h = best_lean; }
             else { c->KZ_e = best_kz; c->MB_e = best_mb; c->VEC_e = best_vec; c->TMA_e = best_tma; c->LEAN_e = best_lean; }
         }
-        // fused H+E step (kz 4, 8, 16) against the best split pair
+        // fused H+E steps against the best split pair: the tiled kernel (kz 4, 8, 16) and,
+        // for FP32 with nx even, the one-pass kernel (rows per block and resident blocks
+        // (4, 4), (4, 6), (8, 2), (8, 3), z blocks of 8, 16, 32, 64 planes)
         {
             p.KZ_h = c->KZ_h; p.KZ_e = c->KZ_e; p.MB_h = c->MB_h; p.MB_e = c->MB_e;
             p.VEC_h = c->VEC_h; p.VEC_e = c->VEC_e;
             p.TMA_h = c->TMA_h; p.TMA_e = c->TMA_e;
             p.LEAN_h = c->LEAN_h; p.LEAN_e = c->LEAN_e;
+            struct Cand { int f, by, mb, kz; };
+            std::vector<Cand> cands = {{0, 0, 4, 16}, {4, 0, 4, 16}, {8, 0, 4, 16}, {16, 0, 4, 16}};
+            if (sizeof(R) == 4 && c->d_q && c->nx % 2 == 0) {
+                const int bm[4][2] = {{4, 4}, {4, 6}, {8, 2}, {8, 3}};
+                for (const auto &b : bm)
+                    for (int kz : {8, 16, 32, 64}) cands.push_back({0, b[0], b[1], kz});
+            }
             double best = 1e30;
-            int best_f = 0;
-            for (int f : {0, 4, 8, 16}) {
-                p.fused_kz = f;
+            Cand bc = cands[0];
+            for (const Cand &cd : cands) {
+                p.fused_kz = cd.f;
+                p.FZ_by = cd.by; p.FZ_mb = cd.mb; p.FZ_kz = cd.kz;
                 for (int j = 0; j < 3; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, 5));
                 CK(cudaEventRecord(e0, st));
                 const int reps = 20;
@@ -1281,10 +1334,12 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
                 CK(cudaEventSynchronize(e1));
                 float t = 0.f;
                 CK(cudaEventElapsedTime(&t, e0, e1));
-                if (t < best) { best = t; best_f = f; }
+                if (t < best) { best = t; bc = cd; }
             }
-            c->fused_kz = best_f;
+            c->fused_kz = bc.f;
+            c->FZ_by = bc.by; c->FZ_mb = bc.mb; c->FZ_kz = bc.kz;
             p.fused_kz = 0;
+            p.FZ_by = 0;
         }
     }
     // transform flush: register or bulk copy (FP32), 16 or 32 snapshots, after
@@ -1299,6 +1354,7 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
             p.acc = vol_tmp;
             p.comp = c->kahan ? (R2 *)c->d_comp : nullptr;
             p.fused_kz = c->fused_kz;
+            p.FZ_by = c->FZ_by; p.FZ_mb = c->FZ_mb; p.FZ_kz = c->FZ_kz;
             const bool kahan = c->kahan != 0;
             double best = 1e30;
             int bm = 0, bM = 16;
@@ -1336,7 +1392,7 @@ void free_ctx(csem_ctx *c) {
     if (!c) return;
     cudaDeviceSynchronize();
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
-    void *ptrs[] = {c->d_ho, c->d_tabL, c->d_psiL, c->d_cEm, c->d_inc, c->d_tapk, c->d_tab, c->d_h, c->d_cE, c->d_H, c->d_H2, c->d_ering, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
+    void *ptrs[] = {c->d_q, c->d_tabG, c->d_ho, c->d_tabL, c->d_psiL, c->d_cEm, c->d_inc, c->d_tapk, c->d_tab, c->d_h, c->d_cE, c->d_H, c->d_H2, c->d_ering, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
                     c->d_alpha, c->d_racc, c->d_coef, c->d_T, c->d_ones, c->d_rtaps, c->d_itaps, c->d_colmap, c->d_tflag, c->d_cpos, c->d_cval, c->d_step, c->d_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -1473,7 +1529,10 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
                             6 * V * r;
         c->nslot = 17;
         for (int ns : {129, 65, 33})
-            if (ns * slot + vols + rest < 0.85 * (double)free_b) { c->nslot = ns; break; }
+            if ((o->ring_slots <= 0 || ns <= o->ring_slots) && ns * slot + vols + rest < 0.85 * (double)free_b) {
+                c->nslot = ns;
+                break;
+            }
         c->M = 16;
     }
     int rc = CSEM_OK;
@@ -1521,16 +1580,24 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
                 rc = fail(CSEM_ERR_CUDA, "context initialisation failed");
         }
     }
-    if (rc == CSEM_OK && c->order == 2 && c->precision == 32 && c->nx % 4 == 0) {
+    // FP32 second order, nx even: tap increments, padded tables, and the fused one-pass
+    // step's per-cell material and widths; the lean split kernels (nx a multiple of 4)
+    // also need the CPML memory in 12 volume arrays per source, kept when it fits
+    if (rc == CSEM_OK && c->order == 2 && c->precision == 32 && c->nx % 2 == 0) {
+        step(dalloc(c, &c->d_inc, (size_t)kChunk * S * std::max(8, NR * 8) * sizeof(float)));
+        step(dalloc(c, &c->d_tapk, (size_t)std::max(S, NR) * 8 * sizeof(int)));
+        step(upload_lean_tables(c));
+        if (rc == CSEM_OK) step(upload_geo_tables(c));
+        const size_t qb = (size_t)(c->vti ? 2 : 1) * c->vol * sizeof(float);
+        step(dalloc(c, &c->d_q, qb));
+        if (rc == CSEM_OK && cudaMemset(c->d_q, 0, qb) != cudaSuccess)
+            rc = fail(CSEM_ERR_CUDA, "context initialisation failed");
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
         const double need = ((double)S * 12 + 3) * c->vol * sizeof(float);
-        if (need < 0.25 * (double)free_b) {
+        if (rc == CSEM_OK && c->nx % 4 == 0 && need < 0.25 * (double)free_b) {
             step(dalloc(c, &c->d_psiL, (size_t)S * 12 * c->vol * sizeof(float)));
             step(dalloc(c, &c->d_cEm, 3 * (size_t)c->vol * sizeof(float)));
-            step(dalloc(c, &c->d_inc, (size_t)kChunk * S * std::max(8, NR * 8) * sizeof(float)));
-            step(dalloc(c, &c->d_tapk, (size_t)std::max(S, NR) * 8 * sizeof(int)));
-            step(upload_lean_tables(c));
             if (rc == CSEM_OK && cudaMemset(c->d_cEm, 0, 3 * (size_t)c->vol * sizeof(float)) != cudaSuccess)
                 rc = fail(CSEM_ERR_CUDA, "context initialisation failed");
         }
@@ -1723,7 +1790,12 @@ long long csem_launch_count(void) { return csem::g_launches.load(); }
 
 int csem_set_launch(csem_ctx *c, const int *cfg) {
     if (!c || !cfg) return fail(CSEM_ERR_INVALID_ARG, "NULL argument");
-    const int kzh = cfg[0], mbh = cfg[1], kze = cfg[2], mbe = cfg[3], fkz = cfg[4], fm = cfg[5], M = cfg[6];
+    const int kzh = cfg[0], mbh = cfg[1], kze = cfg[2], mbe = cfg[3], fm = cfg[5], M = cfg[6];
+    // cfg[4] >= 10000: the fused one-pass step, 10000 + planes * 100 + rows * 10 + blocks
+    const int fz = cfg[4] >= 10000 ? cfg[4] - 10000 : 0, fkz = fz ? 0 : cfg[4];
+    const int fz_kz = fz / 100, fz_by = (fz / 10) % 10, fz_mb = fz % 10;
+    if (fz && (c->precision != 32 || c->order != 2 || !c->d_q || c->nx % 2 != 0 || !csem::fz_supported(fz_by, fz_mb, fz_kz)))
+        return fail(CSEM_ERR_INVALID_ARG, "fused one-pass step: FP32, second order, nx even, rows/blocks (4,4), (4,6), (8,2) or (8,3), 2-99 planes");
     const int vh = cfg[7], ve = cfg[8], th = cfg[9], te = cfg[10], lh = cfg[11], le = cfg[12];
     if (lh || le) {
         auto ok = [&](int l, int kz, int mb) {
@@ -1749,11 +1821,12 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
         fm < 0 || fm > 3 || ((fm & 1) && c->precision != 32) || !(M == 16 || M == 32 || M == 64) ||
         ((fm & 2) ? 2 * M : M) + 1 > c->nslot)
         return fail(CSEM_ERR_INVALID_ARG, "launch configuration not supported by this context");
-    if (c->order == 4 && (fkz || vh || ve || th || te || lh || le))
+    if (c->order == 4 && (fkz || fz || vh || ve || th || te || lh || le))
         return fail(CSEM_ERR_INVALID_ARG, "a fourth-order context runs its own H and E kernels only");
     CK(cudaDeviceSynchronize());
     c->KZ_h = kzh; c->MB_h = mbh; c->KZ_e = kze; c->MB_e = mbe;
     c->fused_kz = fkz; c->flush_mode = fm; c->M = M;
+    c->FZ_by = fz_by; c->FZ_mb = fz ? fz_mb : 4; c->FZ_kz = fz ? fz_kz : 16;
     c->VEC_h = vh; c->VEC_e = ve;
     c->TMA_h = th; c->TMA_e = te;
     c->LEAN_h = lh; c->LEAN_e = le;
@@ -1768,7 +1841,7 @@ int csem_autotune(csem_ctx *c, int n_src, int *kz_out, void *stream) {
         kz_out[0] = (c->KZ_h * 16 + c->MB_h) + 256 * c->VEC_h + 1024 * c->TMA_h + 8192 * c->LEAN_h;
         kz_out[1] = (c->KZ_e * 16 + c->MB_e) + 256 * c->VEC_e + 1024 * c->TMA_e + 8192 * c->LEAN_e;
         kz_out[2] = c->M * 4 + c->flush_mode;
-        kz_out[3] = c->fused_kz;
+        kz_out[3] = c->FZ_by ? 10000 + fz_code(c) : c->fused_kz;
     }
     return CSEM_OK;
 }

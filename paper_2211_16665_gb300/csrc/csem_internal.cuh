@@ -56,6 +56,11 @@ struct AxisTab {          // per-axis stepping tables (device, type R)
     const R *b_n, *a_n;   // CPML recursion at nodes [n+1]
 };
 
+struct GeoTab {            // per-axis FP32 widths for the fused one-pass step (padded to 16-byte groups)
+    const float *h;       // primal width at half nodes [n]
+    const float *s;       // sum of the two primal widths next to a node [n+1] (2 x the dual width)
+};
+
 template <typename R>
 struct StepParams {
     int nx, ny, nz, NX, NY, NZ, pitch, npml;
@@ -81,6 +86,13 @@ struct StepParams {
     const R *lzero;                // 4 zeros, 16-byte aligned (lean kernels)
     R *psiL;                       // [S][12][vol] CPML memory in the field layout (lean kernels)
     const R *cEm;                  // [3][vol] dt/eps, zero on the PEC edges (lean kernels)
+    // fused one-pass FP32 step (kern_fz.cu): FZ_by rows per block (0: off), FZ_mb resident
+    // blocks per SM, FZ_kz planes per z block; q = V sigma per cell on the lattice (qv = qh
+    // unless the medium is VTI), per-axis widths, 2 w0 dt
+    int FZ_by, FZ_mb, FZ_kz;
+    const float *qh, *qv;
+    GeoTab gx, gy, gz;
+    float k2w0dt;
     int *err;                      // device status word (bit 1: a bounded wait gave up)
     int nf;
     const typename C2<R>::T *w;    // [nt][nf] exp((-1+i) a_k n dt)
@@ -152,6 +164,9 @@ cudaError_t prepare_bulk_flush();
 template <typename R>
 cudaError_t launch_fused(const StepParams<R> &p, int S, int jstep, int kz, cudaStream_t st);
 cudaError_t prepare_fused_all();
+// fused one-pass FP32 step (kern_fz.cu): nx even, (by, mb) in {(4,4), (4,6), (8,2), (8,3)}, kz planes per z block
+cudaError_t launch_step_fz(const StepParams<float> &p, int S, int jstep, cudaStream_t st);
+bool fz_supported(int by, int mb, int kz);
 // FP32 H / E kernels with four cells per thread (kern_vec.cu), kz in {1,2,4,8}, mb in {4,6}
 // lean FP32 H / E kernels (kern_lean.cu), nx % 4 == 0, w (cells per thread) in {1,2}, kz in {1,2,4},
 // mb (resident 128-thread blocks per SM) in {6,8} for w = 1 and {4,6,8} for w = 2
@@ -175,6 +190,8 @@ struct GeoD {                      // double-precision geometry for set-up and g
     long long plane, vol;
     const double *hx, *hy, *hz;    // primal widths [n]
 };
+// q = V sigma per cell on the lattice (sigma_h into qh; sigma_v into qv when qv is not NULL)
+cudaError_t launch_qcell(const GeoD &g, const float *rho, const float *rho_z, float *qh, float *qv, cudaStream_t st);
 template <typename R>
 // dt/eps on every edge from the cell resistivity (rho_z on the z edges: rho_v of a VTI medium, else rho)
 cudaError_t launch_coef_init(const GeoD &g, const R *rho, const R *rho_z, R *cE, double two_w0_dt, int *bad_flag,

@@ -28,7 +28,7 @@
 // W stays small so that a plane's loaded values fit the register budget.
 // The block is 32 x 4 threads (32 W cells of 4 rows; 128 threads, so 4, 6 or 8
 // resident blocks per SM give 128, 85 or 64 registers per thread); blockIdx.z
-// runs over the z blocks of every source.
+// runs over (z block, source) with the source fastest.
 #include "csem_internal.cuh"
 
 namespace csem {
@@ -212,8 +212,9 @@ __global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_h_lean(const StepPa
     const int i = (blockIdx.x * kLeanX + threadIdx.x) * W;
     const int j = blockIdx.y * kLeanRows + threadIdx.y;
     const int nkb = (p.nz + KZ - 1) / KZ;
-    const int s = blockIdx.z / nkb;
-    const int k0 = (blockIdx.z - s * nkb) * KZ;
+    const int S = gridDim.z / nkb;
+    const int s = blockIdx.z % S;                 // the source runs fastest: the sources of one
+    const int k0 = (blockIdx.z / S) * KZ;         // z block follow one another
     if (i >= p.nx || j >= p.ny) return;
     const int k1 = min(k0 + KZ, p.nz);
     const int n = *p.step + jstep;
@@ -308,8 +309,9 @@ __global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_e_lean(const StepPa
     const int i = (blockIdx.x * kLeanX + threadIdx.x) * W;
     const int j = blockIdx.y * kLeanRows + threadIdx.y;
     const int nkb = (p.nz + KZ - 1) / KZ;
-    const int s = blockIdx.z / nkb;
-    const int k0 = (blockIdx.z - s * nkb) * KZ;
+    const int S = gridDim.z / nkb;
+    const int s = blockIdx.z % S;                 // the source runs fastest: the sources of one z
+    const int k0 = (blockIdx.z / S) * KZ;         // block share the dt/eps reads in L2
     if (i >= p.nx || j >= p.ny) return;
     const int k1 = min(k0 + KZ, p.nz);
     const int n = *p.step + jstep;
@@ -324,7 +326,6 @@ __global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_e_lean(const StepPa
     const int j0 = blockIdx.y * kLeanRows;
     const bool yblk = (j0 < npml) || (j0 + kLeanRows - 1 > p.ny - npml);
     const bool taps = p.colmap && p.inc && p.tflag[s * p.tflag_stride + j * p.nseg + (i >> 5)];
-    const int S = gridDim.z / nkb;
 
     int idx = k0 * plane + j * pitch + i;
     const int im = (k0 > 0) ? idx - plane : idx;      // clamped on the bottom face

@@ -46,14 +46,15 @@ class Engine:
     differences on the non-uniform grid instead of the two-point Yee ones."""
 
     def __init__(self, xn, yn, zn, npml, freqs, f0=1.0, rho_max=1.0, precision=32, kahan=1,
-                 max_src=1, max_rec=0, nt=0, dt=0.0, device=None, autotune=True, vti=False, order=2):
+                 max_src=1, max_rec=0, nt=0, dt=0.0, device=None, autotune=True, vti=False, order=2,
+                 ring_slots=0):
         if not torch.cuda.is_available():
             raise RuntimeError("the CSEM engine needs a CUDA device")
         self.device = torch.device(device or "cuda")
         with torch.cuda.device(self.device):
             self.ctx = _capi.create(xn, yn, zn, npml, freqs, f0=f0, rho_max=rho_max, dt=dt, nt=nt,
                                     precision=precision, kahan=kahan, max_src=max_src, max_rec=max_rec,
-                                    anisotropy=1 if vti else 0, order=order)
+                                    anisotropy=1 if vti else 0, order=order, ring_slots=ring_slots)
         info = _capi.get_info(self.ctx)
         self.info = info
         self.nx, self.ny, self.nz = info.nx, info.ny, info.nz
@@ -230,8 +231,13 @@ class Engine:
         _capi.check(self.ctx, _stream())
 
     def set_launch(self, kz_h=4, mb_h=4, kz_e=4, mb_e=4, fused_kz=0, flush_mode=0, block=16, vec_h=0, vec_e=0,
-                   tma_h=0, tma_e=0, lean_h=0, lean_e=0):
-        """Pins a launch configuration (see csem_set_launch); launch_config() then reports it."""
+                   tma_h=0, tma_e=0, lean_h=0, lean_e=0, onepass=None):
+        """Pins a launch configuration (see csem_set_launch); launch_config() then reports it.
+        onepass = (z planes, rows per block, resident blocks per SM) selects the fused
+        one-pass step kernel (code 10000 + planes * 100 + rows * 10 + blocks)."""
+        if onepass:
+            kz, by, mb = onepass
+            fused_kz = 10000 + kz * 100 + by * 10 + mb
         _capi.set_launch(self.ctx, kz_h, mb_h, kz_e, mb_e, fused_kz, flush_mode, block, vec_h, vec_e, tma_h, tma_e,
                          lean_h, lean_e)
         self.kz = (kz_h * 16 + mb_h + 256 * vec_h + 1024 * tma_h + 8192 * lean_h,
@@ -254,7 +260,14 @@ class Engine:
                 return {"kernel": "bulk-copy staged", "rows_per_block": code // 1024, "z_planes": (code % 1024) // 16}
             return {"kernel": "four cells per thread" if code >= 256 else "one cell per thread",
                     "z_planes": (code % 256) // 16, "blocks_per_sm": code % 16}
-        step = ({"kernel": "fused H+E", "z_planes": fz} if fz else {"kernel": "split", "h": one(h), "e": one(e)})
+        if fz >= 10000:
+            c = fz - 10000
+            step = {"kernel": "fused one-pass H+E", "z_planes": c // 100, "rows_per_block": (c // 10) % 10,
+                    "blocks_per_sm": c % 10}
+        elif fz:
+            step = {"kernel": "fused H+E", "z_planes": fz}
+        else:
+            step = {"kernel": "split", "h": one(h), "e": one(e)}
         return {"step": step, "flush": {"snapshots": f // 4, "kernel": "bulk-copy" if f % 2 == 1 else "register",
                                         "overlapped": f % 4 >= 2}}
 

@@ -164,11 +164,12 @@ def batched_towline() -> Workload:
     h = 50.0
     xn = stretched_axis(h, 196, 20, 20, 10, 1.05, -h * 98)
     zn = stretched_axis(h, 94, 6, 8, 10, 1.05, 0.0)
-    rho_true = add_slab(layered(xn, xn, zn), xn, xn, zn)
+    rho = layered(xn, xn, zn)                      # start model: no reservoir
+    rho_true = add_slab(rho, xn, xn, zn)
     src = Points.make([[-3875.0 + 250.0 * i, 0.0, 950.0] for i in range(32)], 0)
     g = np.arange(-1750.0, 1750.0 + 1, 500.0)
     rec = Points.make([[x, y, 1000.0] for y in g for x in g], 0)
-    return Workload("batched_towline_256x256x128_32src", xn, xn.copy(), zn, 10, rho_true.copy(), rho_true,
+    return Workload("batched_towline_256x256x128_32src", xn, xn.copy(), zn, 10, rho, rho_true,
                     src, rec, np.array([0.25, 0.5, 0.75, 1.0]), rho_max=100.0, precision=32, kahan=1)
 
 

@@ -52,7 +52,7 @@ def test_struct_layouts_match_header_sizes():
     assert ctypes.sizeof(_capi.Grid) == 48
     assert ctypes.sizeof(_capi.PointsC) == 40
     assert ctypes.sizeof(_capi.Info) == 88
-    assert ctypes.sizeof(_capi.Opts) == 80
+    assert ctypes.sizeof(_capi.Opts) == 88
 
 
 def test_header_is_plain_c(tmp_path):

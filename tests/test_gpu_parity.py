@@ -118,6 +118,10 @@ LAUNCH_VARIANTS = [
     dict(kz_h=2, mb_h=8, lean_h=2, kz_e=2, mb_e=6, lean_e=2, flush_mode=1, block=64),
     dict(kz_h=2, mb_h=4, lean_h=2, kz_e=1, mb_e=4, lean_e=2, flush_mode=3, block=64),
     dict(kz_h=4, mb_h=4, kz_e=4, mb_e=6, flush_mode=0, block=64),
+    dict(onepass=(8, 4, 4), flush_mode=1, block=32),
+    dict(onepass=(16, 8, 2), flush_mode=3, block=16),
+    dict(onepass=(5, 4, 6), flush_mode=0, block=64),
+    dict(onepass=(64, 8, 3), flush_mode=1, block=16),
 ]
 
 LEAN_VARIANTS = [
@@ -126,6 +130,10 @@ LEAN_VARIANTS = [
     dict(kz_h=4, mb_h=6, lean_h=1, kz_e=2, mb_e=8, lean_e=2, flush_mode=0, block=16),
     dict(kz_h=1, mb_h=6, lean_h=2, kz_e=4, mb_e=8, lean_e=1, flush_mode=2, block=16),
     dict(kz_h=4, mb_h=8, lean_h=1, vec_e=1, kz_e=1, mb_e=4, flush_mode=3, block=16),
+    dict(onepass=(8, 4, 4), flush_mode=1, block=16),
+    dict(onepass=(3, 8, 2), flush_mode=3, block=32),
+    dict(onepass=(16, 4, 6), flush_mode=0, block=16),
+    dict(onepass=(44, 8, 3), flush_mode=1, block=64),
 ]
 
 
@@ -183,6 +191,29 @@ def test_lean_kernels_refused_where_they_do_not_apply():
                 dict(lean_e=2, kz_e=1, mb_e=3)):
         with pytest.raises(CsemError):
             eng.set_launch(**bad)
+    eng.close()
+
+
+def test_onepass_step_refused_where_it_does_not_apply():
+    """The fused one-pass step needs FP32, second order, nx even and a supported block shape."""
+    odd = W.small_box(n_core=21, h=100.0, npml=8, ratio=1.05, n_st=3, n_rec=6, n_freq=2)
+    assert odd.nx % 2 == 1
+    eng = Engine.from_workload(odd, precision=32, autotune=False)
+    with pytest.raises(CsemError):
+        eng.set_launch(onepass=(8, 4, 4))
+    eng.close()
+    box = W.small_box(n_core=24, h=100.0, npml=8, ratio=1.08, n_st=4, n_rec=6, n_freq=2)
+    eng = Engine.from_workload(box, precision=64, autotune=False)
+    with pytest.raises(CsemError):
+        eng.set_launch(onepass=(8, 4, 4))
+    eng.close()
+    eng = Engine.from_workload(box, precision=32, autotune=False)
+    for bad in ((8, 4, 3), (8, 2, 4), (1, 4, 4), (8, 8, 4)):
+        with pytest.raises(CsemError):
+            eng.set_launch(onepass=bad)
+    eng.set_launch(onepass=(8, 8, 3))
+    assert eng.launch_config()["step"] == {"kernel": "fused one-pass H+E", "z_planes": 8, "rows_per_block": 8,
+                                           "blocks_per_sm": 3}
     eng.close()
 
 

@@ -81,6 +81,8 @@ TD_VARIANTS = [
     dict(kz_h=2, mb_h=4, kz_e=1, mb_e=6, vec_h=1, vec_e=1),
     dict(kz_h=4, mb_h=4, kz_e=2, mb_e=4, tma_h=4, tma_e=4),
     dict(kz_h=8, mb_h=4, kz_e=2, mb_e=4),
+    dict(onepass=(8, 4, 4)),
+    dict(onepass=(16, 8, 3)),
 ]
 
 
