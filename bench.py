@@ -143,10 +143,8 @@ def make_workload(name, rank, world, vti=False, max_src=0):
             rv = np.where(r > water, np.minimum(2.0 * r, wl.rho_max), r)
             return np.stack([r, rv])
         wl.rho, wl.rho_true = split(wl.rho), split(wl.rho_true)
-    if world > 1:
-        # weak scaling: a towline of `world` sources on the same model, one share per rank
-        line = D.towline(wl.src, world * wl.src.n)
-        wl.src = line.subset(list(D.shard(line.n, rank, world)))
+    # weak scaling: a towline of world x the workload's sources on the same model, one share per rank
+    wl.src = D.rank_sources(wl.src, rank, world)
     return wl
 
 

@@ -28,6 +28,16 @@ def towline(points, n: int, spacing: float = 250.0):
     return Points.make([[x, y0, z0] for x in xs], c0)
 
 
+def rank_sources(points, rank: int, world: int):
+    """The sources one rank models under weak scaling: a towline of world x points.n sources
+    (`towline`, centred on the first point) split into contiguous shares (`shard`).  With one
+    rank the points are returned as they are."""
+    if world <= 1:
+        return points
+    line = towline(points, world * points.n)
+    return line.subset(list(shard(line.n, rank, world)))
+
+
 def sum_over_ranks(*tensors):
     """In-place sum of each tensor over all ranks (no-op without a process group)."""
     import torch.distributed as dist
