@@ -340,10 +340,22 @@ int csem_set_launch(csem_ctx *ctx, const int *cfg);
 int csem_set_wavelet(csem_ctx *ctx, const double *wavelet_host);
 int csem_set_trace(csem_ctx *ctx, double *trace_dev);
 
+/* Test hook for failure detection: with extra_bytes > 0 (a multiple of 16, at most 4096)
+ * the first shared-memory stage of every block of the bulk-copy kernels (the transform
+ * flush, the row-staged step kernels, the fused one-pass step) expects extra_bytes more
+ * than its copies bring, so the bounded wait on it runs out after about a second: the
+ * block leaves without writing results, and the next csem_check reports CSEM_ERR_TIMEOUT.
+ * The copies themselves complete; nothing faults.  0 restores normal operation (the
+ * field state of the run that timed out is not usable).  Synchronises the device.
+ * Errors: INVALID_ARG. */
+int csem_set_copy_fault(csem_ctx *ctx, int extra_bytes);
+
 /* Synchronises stream and reports problems seen on the device since the last
- * check: TIMEOUT if a transform flush gave up waiting for its bulk copies
- * (its block's accumulators were left unchanged), NONFINITE if a resistivity
- * was non-positive or non-finite (such cells get zero conductivity). */
+ * check: TIMEOUT if a bulk-copy kernel gave up waiting for its copies (about a
+ * second per wait; a transform flush then leaves its block's accumulators
+ * unchanged, a step kernel its block's fields; the message names the kernel
+ * family), NONFINITE if a resistivity was non-positive or non-finite (such
+ * cells get zero conductivity). */
 int csem_check(csem_ctx *ctx, void *stream);
 
 /* Measurement hooks.

@@ -77,6 +77,7 @@ SIGNATURES = {
     "csem_set_launch": (ctypes.c_int, [_V, _I]),
     "csem_set_wavelet": (ctypes.c_int, [_V, _D]),
     "csem_set_trace": (ctypes.c_int, [_V, _V]),
+    "csem_set_copy_fault": (ctypes.c_int, [_V, ctypes.c_int]),
     "csem_check": (ctypes.c_int, [_V, _V]),
     "csem_launch_count": (ctypes.c_longlong, []),
     "csem_time_step_kernels": (ctypes.c_int, [_V, ctypes.c_int, _V, ctypes.c_int, _D, _V]),
@@ -242,6 +243,10 @@ def set_wavelet(ctx, wavelet=None):
 
 def set_trace(ctx, trace_ptr):
     _check(lib().csem_set_trace(ctx, trace_ptr))
+
+
+def set_copy_fault(ctx, extra_bytes):
+    _check(lib().csem_set_copy_fault(ctx, int(extra_bytes)))
 
 
 def check(ctx, stream):

@@ -142,6 +142,7 @@ struct csem_ctx {
     int MB_h = 4, MB_e = 4;             // min resident blocks per SM of the compiled variant (autotuned)
     int fused_kz = 0;                   // > 0: fused H+E step with this z blocking (autotuned)
     int FZ_by = 0, FZ_mb = 4, FZ_kz = 16; // FZ_by > 0: fused one-pass FP32 step, rows per block (autotuned)
+    int fault_tx = 0;                   // test hook: extra bytes the bulk-copy kernels' first barrier arm expects
     int VEC_h = 0, VEC_e = 0;           // 1: four-cells-per-thread FP32 kernels (autotuned)
     int TMA_h = 0, TMA_e = 0;           // > 0: bulk-copy-staged FP32 kernels, rows per block (autotuned)
     int LEAN_h = 0, LEAN_e = 0;         // > 0: lean FP32 kernels, cells per thread (autotuned; needs d_psiL)
@@ -468,6 +469,7 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
         }
     }
     p.err = c->d_bad;
+    p.fault_tx = c->fault_tx;
     p.colmap = nullptr;
     p.colmap_stride = 0;
     p.tflag = nullptr;
@@ -1659,6 +1661,14 @@ int csem_set_wavelet(csem_ctx *c, const double *w) {
     return update_wavelet(c);
 }
 
+int csem_set_copy_fault(csem_ctx *c, int extra_bytes) {
+    if (!c || extra_bytes < 0 || extra_bytes > 4096 || extra_bytes % 16 != 0)
+        return fail(CSEM_ERR_INVALID_ARG, "extra_bytes must be a multiple of 16 in 0..4096");
+    CK(cudaDeviceSynchronize());
+    c->fault_tx = extra_bytes;
+    return CSEM_OK;
+}
+
 int csem_set_trace(csem_ctx *c, double *trace_dev) {
     if (!c) return fail(CSEM_ERR_INVALID_ARG, "NULL context");
     c->d_trace = trace_dev;
@@ -1671,8 +1681,15 @@ int csem_check(csem_ctx *c, void *stream) {
     int bad = 0;
     CK(cudaMemcpy(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost));
     CK(cudaMemset(c->d_bad, 0, sizeof(int)));
-    if (bad & 2) return fail(CSEM_ERR_TIMEOUT, "a transform flush gave up waiting for its bulk copies");
-    if (bad & 1) return fail(CSEM_ERR_NONFINITE, "a resistivity was non-positive or non-finite");
+    if (bad & (csem::kErrFlushWait | csem::kErrStagedWait | csem::kErrOnepassWait)) {
+        std::string who;
+        auto add = [&](const char *w) { who += (who.empty() ? "" : " and ") + std::string(w); };
+        if (bad & csem::kErrFlushWait) add("a bulk-copy transform flush");
+        if (bad & csem::kErrStagedWait) add("a row-staged H/E step kernel");
+        if (bad & csem::kErrOnepassWait) add("the fused one-pass step kernel");
+        return fail(CSEM_ERR_TIMEOUT, who + " gave up waiting for its bulk copies (its results were not written)");
+    }
+    if (bad & csem::kErrNonfinite) return fail(CSEM_ERR_NONFINITE, "a resistivity was non-positive or non-finite");
     return CSEM_OK;
 }
 

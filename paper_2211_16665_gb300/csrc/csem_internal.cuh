@@ -26,6 +26,38 @@ extern std::atomic<long long> g_launches;   // kernels launched by this library
 template <typename R> __device__ __forceinline__ R ldg_r(const R *p) { return __ldg(p); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Bounded wait on an mbarrier phase, shared by the bulk-copy kernels: true once the phase of
+// this parity has completed; false after about kWaitNs of the global timer (or 2^26 polls),
+// so a kernel whose copies never arrive reports a timeout instead of hanging.
+constexpr unsigned long long kWaitNs = 1000000000ull;
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_done(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    const unsigned long long t0 = gtimer_ns();
+    for (int it = 0; it < (1 << 26); ++it) {
+        if (mbar_done(bar, parity)) return true;
+        if ((it & 255) == 255 && gtimer_ns() - t0 > kWaitNs) return false;
+    }
+    return false;
+}
+// Status bits the kernels raise in the context's device word (read and cleared by csem_check).
+constexpr int kErrNonfinite = 1;     // a resistivity was non-positive or non-finite
+constexpr int kErrFlushWait = 2;     // a bulk-copy transform flush gave up waiting for its copies
+constexpr int kErrStagedWait = 4;    // a row-staged H / E step kernel gave up waiting
+constexpr int kErrOnepassWait = 8;   // the fused one-pass step kernel gave up waiting
+
 template <typename R> struct C2;
 template <> struct C2<float> { typedef float2 T; };
 template <> struct C2<double> { typedef double2 T; };
@@ -93,7 +125,9 @@ struct StepParams {
     const float *qh, *qv;
     GeoTab gx, gy, gz;
     float k2w0dt;
-    int *err;                      // device status word (bit 1: a bounded wait gave up)
+    int *err;                      // device status word (kErr* bits)
+    int fault_tx;                  // test hook: extra bytes the first barrier arm of each block of a
+                                   // bulk-copy kernel expects, so that its bounded wait runs out
     int nf;
     const typename C2<R>::T *w;    // [nt][nf] exp((-1+i) a_k n dt)
     typename C2<R>::T *acc;        // [S][3][nf][vol] or nullptr

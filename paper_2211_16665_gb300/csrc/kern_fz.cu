@@ -37,9 +37,9 @@
 // with the source fastest, so the blocks of all sources of one tile run close
 // together and share the material reads in L2.
 //
-// Every wait on a stage barrier is bounded: a block that gives up raises bit 3
-// of *err, leaves the plane loop with all its threads together, waits (again
-// bounded) for the copies it issued and returns.
+// Every wait on a stage barrier is bounded (about a second): a block that gives
+// up leaves the plane loop with all its threads together, raises the one-pass
+// bit of *err, waits (again bounded) for the copies it issued and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -52,7 +52,6 @@ namespace csem {
 namespace {
 
 constexpr int kXW = 72;            // staged columns: x from i0 - 4 to i0 + 67
-constexpr int kFzWait = 1 << 22;   // try_wait rounds before a block gives up
 
 __device__ __forceinline__ uint32_t s_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void fz_bar_init(uint64_t *b) {
@@ -68,21 +67,6 @@ __device__ __forceinline__ void fz_tile4(void *dst, const CUtensorMap *m, int x,
         "l"(reinterpret_cast<uint64_t>(m)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(s_u32(b))
         : "memory");
 }
-__device__ __forceinline__ bool fz_try(uint64_t *b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(s_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool fz_wait(uint64_t *b, uint32_t parity) {
-    for (int it = 0; it < kFzWait; ++it)
-        if (fz_try(b, parity)) return true;
-    return false;
-}
-
 __device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
 __device__ __forceinline__ void st2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -263,7 +247,7 @@ __global__ void __launch_bounds__(32 * (BY + 1), MINB)
     // advances incrementally (no integer division in the plane loop)
     auto issue = [&](int m, int u) {
         float *d = sm + u * stf;
-        fz_expect(&bar[u], bytes);
+        fz_expect(&bar[u], bytes + (m == kstart ? (uint32_t)p.fault_tx : 0u));
         fz_tile4(d, &tmE, i0 - 4, j0 - 1, m, wE, &bar[u]);
         fz_tile4(d + B3, mH, i0 - 4, j0 - 1, m, s * 3, &bar[u]);
         fz_tile4(d + 2 * B3, &tmQ, i0 - 4, j0 - 1, m, 0, &bar[u]);
@@ -306,10 +290,10 @@ __global__ void __launch_bounds__(32 * (BY + 1), MINB)
     int k = kstart;
     int st0 = 0;                                           // stage of plane k
     uint32_t ph = 1;                                       // bit u: parity of stage u's next completion
-    bool ok = fz_wait(&bar[0], 0);
+    bool ok = mbar_wait_bounded(&bar[0], 0);
     for (; k < k1; ++k) {
         const int st1 = (st0 + 1 == NST) ? 0 : st0 + 1;    // stage of plane k+1
-        if (ok) ok = fz_wait(&bar[st1], (ph >> st1) & 1u);
+        if (ok) ok = mbar_wait_bounded(&bar[st1], (ph >> st1) & 1u);
         ph ^= 1u << st1;
         // every thread has its planes and the stage of plane k-1 and sHn are free; a
         // give-up anywhere ends the loop for the whole block
@@ -443,9 +427,9 @@ __global__ void __launch_bounds__(32 * (BY + 1), MINB)
     }
     if (k < k1) {                      // gave up on a stage: report, let the issued copies land
         if (tid == 0) {
-            atomicOr(p.err, 8);
+            atomicOr(p.err, kErrOnepassWait);
             for (int m = k; m < inext; ++m)
-                fz_wait(&bar[(m - kstart) % NST], (uint32_t)(((m - kstart) / NST) & 1));
+                mbar_wait_bounded(&bar[(m - kstart) % NST], (uint32_t)(((m - kstart) / NST) & 1));
         }
         __syncthreads();
     }

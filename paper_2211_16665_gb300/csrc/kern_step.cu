@@ -377,8 +377,8 @@ __global__ void __launch_bounds__(kBlock) k_dft(const StepParams<R> p, const Poi
 // rows -- MS snapshots of 256 lattice entries and the accumulator (and Kahan)
 // rows -- into shared memory with cp.async.bulk on one mbarrier, so every byte
 // of the block is in flight at once with few registers.  The wait on the
-// barrier is bounded: on timeout the block raises bit 1 of *err, waits once
-// more (bounded) for its own copies and returns.
+// barrier is bounded (about a second): on timeout the block raises the flush
+// bit of *err, waits once more (bounded) for its own copies and returns.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -401,17 +401,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-constexpr int kWaitLimit = 1 << 22;   // try_wait rounds before a flush block gives up
 
 // resident blocks per SM that the shared memory allows (MS snapshots of 1 KB + accumulators)
 template <int MS> constexpr int bulk_minb() { return MS <= 16 ? 6 : (MS <= 32 ? 4 : 2); }
@@ -480,7 +469,7 @@ __global__ void __launch_bounds__(kBulkThreads, bulk_minb<MS>()) k_dft_bulk(cons
     __syncthreads();
     if (threadIdx.x == 0) {
         const uint32_t rb = (uint32_t)rows * sizeof(float), cb = (uint32_t)rows * sizeof(float2);
-        mbar_expect_tx(&bar, MS * rb + p.nf * cb * (KAHAN ? 2u : 1u));
+        mbar_expect_tx(&bar, MS * rb + p.nf * cb * (KAHAN ? 2u : 1u) + (uint32_t)p.fault_tx);
         int sl = n0 % p.nslot;
         for (int m = 0; m < MS; ++m) {
             bulk_g2s(ring_s + m * kBlock, ring + (long long)sl * 3 * p.vol, rb, &bar);
@@ -496,14 +485,12 @@ __global__ void __launch_bounds__(kBulkThreads, bulk_minb<MS>()) k_dft_bulk(cons
         w_s[u] = (f < p.nf) ? p.w[(long long)(n0 + m) * p.nf + f] : make_float2(0.f, 0.f);
     }
     if (threadIdx.x < 32) {
-        bool ok = false;
-        for (int it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(&bar, 0);
-        if (!ok) {
+        if (!mbar_wait_bounded(&bar, 0)) {
             if (threadIdx.x == 0) {
-                atomicOr(err, 2);
+                atomicOr(err, kErrFlushWait);
                 bad = 1;
             }
-            for (int it = 0; it < kWaitLimit && !ok; ++it) ok = mbar_try_wait(&bar, 0);
+            mbar_wait_bounded(&bar, 0);     // once more, so no copy can still be landing at exit
         }
     }
     __syncthreads();

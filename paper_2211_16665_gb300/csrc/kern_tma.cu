@@ -6,9 +6,10 @@
 // the mbarrier of a three-deep ring of stages, so all rows of a plane and of
 // the next one are in flight at once; the other threads compute from shared
 // memory and store their results with coalesced row writes.  Waits on the
-// barriers are bounded: a block that gives up raises bit 1 of *err, waits once
-// more (bounded) and returns.  Same arithmetic, per entry, as the other step
-// kernels.
+// barriers are bounded (about a second): a block whose wait gives up leaves the
+// plane loop with all its threads together, raises the staged-kernel bit of
+// *err, waits (bounded) for every copy it issued and returns.  Same arithmetic,
+// per entry, as the other step kernels.
 //
 //   k_h_tma stage (plane k): E rows j0 .. j0+TY (3 components), H^{n-1/2} rows
 //           j0 .. j0+TY-1 (3 components); plane k also reads stage k+1's E.
@@ -37,28 +38,6 @@ __device__ __forceinline__ void bulk_row(float *dst, const float *src, uint32_t 
                  "l"(g), "r"(bytes), "r"(s_u32(b))
                  : "memory");
 }
-__device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(s_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-constexpr int kTmaWait = 1 << 22;
-
-// bounded wait on barrier b for parity ph; false when it gave up (flag raised)
-__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t ph, int *err) {
-    for (int it = 0; it < kTmaWait; ++it)
-        if (bar_try(b, ph)) return true;
-    if (threadIdx.x == 0) atomicOr(err, 2);
-    for (int it = 0; it < kTmaWait; ++it)
-        if (bar_try(b, ph)) break;
-    return false;
-}
-
 }  // namespace
 
 template <int TY>
@@ -84,7 +63,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_h_tma(const StepParams<float> p, 
     auto issue = [&](int k, bool with_h) {
         const int b = k % 3;
         float *st = sm + (size_t)b * RS * P;
-        uint32_t bytes = 0;
+        uint32_t bytes = (k == k0) ? (uint32_t)p.fault_tx : 0u;
         for (int c = 0; c < 3; ++c)
             for (int r = 0; r <= TY; ++r) if (j0 + r < p.NY) bytes += rowb;
         if (with_h)
@@ -111,18 +90,25 @@ __global__ void __launch_bounds__(kBlock, 1) k_h_tma(const StepParams<float> p, 
         issue(k0, true);
         issue(k0 + 1, k0 + 1 < k1);            // plane k1 <= nz exists: E only
     }
+    int hi = k0 + 1;                           // highest plane issued
     uint32_t ph = 0;
     const float cH = p.cH;
-    if (!bar_wait(&bar[k0 % 3], 0, err)) return;
+    bool ok = mbar_wait_bounded(&bar[k0 % 3], 0);
     ph ^= 1u << (k0 % 3);
-    for (int k = k0; k < k1; ++k) {
-        if (threadIdx.x == 0 && k + 2 <= k1) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(k + 2, k + 2 < k1);           // into the stage plane k-1 used
-        }
+    int k = k0;
+    for (; k < k1; ++k) {
         const int b = k % 3, b1 = (k + 1) % 3;
-        if (!bar_wait(&bar[b1], (ph >> b1) & 1, err)) return;   // plane k+1 (plane k is already in)
+        if (ok) ok = mbar_wait_bounded(&bar[b1], (ph >> b1) & 1);   // plane k+1 (plane k is already in)
         ph ^= 1u << b1;
+        // every thread has finished plane k-1 (its stage is free); a give-up ends the loop for all
+        if (__syncthreads_or(!ok)) break;
+        if (k + 2 <= k1) {
+            if (threadIdx.x == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(k + 2, k + 2 < k1);       // into the stage plane k-1 used
+            }
+            hi = k + 2;
+        }
         const float *st = sm + (size_t)b * RS * P, *st1 = sm + (size_t)b1 * RS * P;
         const int szh = slab_half(k, nz, npml);
         const float ihz = __ldg(p.az.ih_h + k);
@@ -167,7 +153,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_h_tma(const StepParams<float> p, 
             H[vol + idx] = hs[TY * P + i] - cH * (dEx_dz - dEz_dx);
             H[2 * vol + idx] = hs[2 * TY * P + i] - cH * (dEy_dx - dEx_dy);
         }
-        __syncthreads();                        // stage b is free for plane k+3
+    }
+    if (k < k1) {                              // gave up: report, let the issued copies land
+        if (threadIdx.x == 0) {
+            atomicOr(err, kErrStagedWait);
+            for (int m = k; m <= hi; ++m) mbar_wait_bounded(&bar[m % 3], (uint32_t)(((m - k0) / 3) & 1));
+        }
+        __syncthreads();
     }
 }
 
@@ -192,10 +184,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_e_tma(const StepParams<float> p, 
     const uint32_t rowb = (uint32_t)P * sizeof(float);
 
     // stage of plane k: H rows j0-1 .. j0+TY-1 (rows < 0 skipped), then E^n and dt/eps rows j0 .. j0+TY-1
+    const int kf = (k0 > 0) ? k0 - 1 : k0;     // first plane issued
     auto issue = [&](int k, bool h_only) {
         const int b = ((k % 3) + 3) % 3;
         float *st = sm + (size_t)b * RS * P;
-        uint32_t bytes = 0;
+        uint32_t bytes = (k == kf) ? (uint32_t)p.fault_tx : 0u;
         for (int c = 0; c < 3; ++c)
             for (int r = 0; r <= TY; ++r) if (j0 - 1 + r >= 0 && j0 - 1 + r < ny) bytes += rowb;
         if (!h_only)
@@ -227,19 +220,28 @@ __global__ void __launch_bounds__(kBlock, 1) k_e_tma(const StepParams<float> p, 
         if (k0 > 0) issue(k0 - 1, true);
         issue(k0, false);
     }
+    int hi = k0;                               // highest plane issued
     uint32_t ph = 0;
-    for (int k = k0; k < k1; ++k) {
-        if (threadIdx.x == 0 && k + 1 < k1) {
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(k + 1, false);                // into the stage plane k-2 used
-        }
+    bool ok = true;
+    int k = k0;
+    for (; k < k1; ++k) {
         const int b = k % 3, bm = (k + 2) % 3;  // bm: stage of plane k-1
         if (k == k0 && k0 > 0) {
-            if (!bar_wait(&bar[bm], (ph >> bm) & 1, err)) return;
+            ok = mbar_wait_bounded(&bar[bm], (ph >> bm) & 1);
             ph ^= 1u << bm;
         }
-        if (!bar_wait(&bar[b], (ph >> b) & 1, err)) return;
+        if (ok) ok = mbar_wait_bounded(&bar[b], (ph >> b) & 1);
         ph ^= 1u << b;
+        // every thread has finished plane k-1 (the stage of plane k-2 is free); a give-up ends
+        // the loop for all
+        if (__syncthreads_or(!ok)) break;
+        if (k + 1 < k1) {
+            if (threadIdx.x == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                issue(k + 1, false);            // into the stage plane k-2 used
+            }
+            hi = k + 1;
+        }
         const float *st = sm + (size_t)b * RS * P, *sm1 = sm + (size_t)bm * RS * P;
         const int szn = slab_node(k, nz, npml);
         const float ihz = __ldg(p.az.ih_n + k);
@@ -301,7 +303,14 @@ __global__ void __launch_bounds__(kBlock, 1) k_e_tma(const StepParams<float> p, 
                 En[2 * vol + idx] = eo[2 * TY * P + i] + ce[2 * TY * P + i] * (dHy_dx - dHx_dy);
             }
         }
-        __syncthreads();                        // stage b is free for plane k+3 (and plane k-1's for k+2)
+    }
+    if (k < k1) {                              // gave up: report, let the issued copies land
+        if (threadIdx.x == 0) {
+            atomicOr(err, kErrStagedWait);
+            for (int m = (k == k0) ? kf : k; m <= hi; ++m) mbar_wait_bounded(&bar[m % 3], (uint32_t)(((m - kf) / 3) & 1));
+        }
+        __syncthreads();
+        return;
     }
     // source term E^{n+1} -= dt/eps J'^{n+1/2}: each column of the tile is handled by one thread
     if (p.colmap) {

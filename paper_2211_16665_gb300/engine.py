@@ -230,6 +230,11 @@ class Engine:
     def check(self):
         _capi.check(self.ctx, _stream())
 
+    def set_copy_fault(self, extra_bytes=16):
+        """Test hook (csem_set_copy_fault): the bulk-copy kernels' first stage waits for
+        extra_bytes that never come, so their bounded waits run out; 0 turns it off."""
+        _capi.set_copy_fault(self.ctx, extra_bytes)
+
     def set_launch(self, kz_h=4, mb_h=4, kz_e=4, mb_e=4, fused_kz=0, flush_mode=0, block=16, vec_h=0, vec_e=0,
                    tma_h=0, tma_e=0, lean_h=0, lean_e=0, onepass=None):
         """Pins a launch configuration (see csem_set_launch); launch_config() then reports it.
