@@ -1270,7 +1270,32 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    if (c->order == 2) {   // the fourth-order kernels have one launch shape
+    if (c->order == 4 && sizeof(R) == 4 && c->d_cEm) {   // lean or plain fourth-order kernel per half
+        for (int which : {1, 4}) {
+            double best = 1e30;
+            int bl = 0, bkz = 4, bmb = 4;
+            for (int cand = 0; cand < 10; ++cand) {
+                const int lean = cand ? 2 : 0, kz = cand ? (2 << ((cand - 1) / 3)) : 4, mb = cand ? 4 + 2 * ((cand - 1) % 3) : 4;
+                p.LEAN_h = p.LEAN_e = lean;
+                p.KZ_h = p.KZ_e = kz;
+                p.MB_h = p.MB_e = mb;
+                for (int j = 0; j < 3; ++j) CK(launch_any<R>(c, p, q, S, 0, st, which));
+                CK(cudaEventRecord(e0, st));
+                const int reps = 20;
+                for (int j = 0; j < reps; ++j) CK(launch_any<R>(c, p, q, S, 0, st, which));
+                CK(cudaEventRecord(e1, st));
+                CK(cudaEventSynchronize(e1));
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, e0, e1));
+                if (t < best) { best = t; bl = lean; bkz = kz; bmb = mb; }
+            }
+            if (which == 1) { c->LEAN_h = bl; c->KZ_h = bkz; c->MB_h = bmb; }
+            else { c->LEAN_e = bl; c->KZ_e = bkz; c->MB_e = bmb; }
+        }
+        p.LEAN_h = c->LEAN_h; p.LEAN_e = c->LEAN_e;
+        p.KZ_h = c->KZ_h; p.KZ_e = c->KZ_e; p.MB_h = c->MB_h; p.MB_e = c->MB_e;
+    }
+    if (c->order == 2) {
         const int kzs[4] = {1, 2, 4, 8};
         const int mbs[3] = {4, 6, 8};
         for (int which : {1, 4}) {
@@ -1582,13 +1607,21 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
                 rc = fail(CSEM_ERR_CUDA, "context initialisation failed");
         }
     }
-    // FP32 second order, nx even: tap increments, padded tables, and the fused one-pass
-    // step's per-cell material and widths; the lean split kernels (nx a multiple of 4)
-    // also need the CPML memory in 12 volume arrays per source, kept when it fits
-    if (rc == CSEM_OK && c->order == 2 && c->precision == 32 && c->nx % 2 == 0) {
+    // FP32, nx even: tap increments and padded tables (and for the fourth order the masked
+    // dt/eps of its lean kernels); second order also the fused one-pass step's per-cell
+    // material and widths, and for the lean split kernels (nx a multiple of 4) the CPML
+    // memory in 12 volume arrays per source, kept when it fits
+    if (rc == CSEM_OK && c->precision == 32 && c->nx % 2 == 0) {
         step(dalloc(c, &c->d_inc, (size_t)kChunk * S * std::max(8, NR * 8) * sizeof(float)));
         step(dalloc(c, &c->d_tapk, (size_t)std::max(S, NR) * 8 * sizeof(int)));
         step(upload_lean_tables(c));
+        if (c->order == 4) {                 // lean fourth-order kernels: masked dt/eps
+            step(dalloc(c, &c->d_cEm, 3 * (size_t)c->vol * sizeof(float)));
+            if (rc == CSEM_OK && cudaMemset(c->d_cEm, 0, 3 * (size_t)c->vol * sizeof(float)) != cudaSuccess)
+                rc = fail(CSEM_ERR_CUDA, "context initialisation failed");
+        }
+    }
+    if (rc == CSEM_OK && c->order == 2 && c->precision == 32 && c->nx % 2 == 0) {
         if (rc == CSEM_OK) step(upload_geo_tables(c));
         const size_t qb = (size_t)(c->vti ? 2 : 1) * c->vol * sizeof(float);
         step(dalloc(c, &c->d_q, qb));
@@ -1814,6 +1847,21 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
     if (fz && (c->precision != 32 || c->order != 2 || !c->d_q || c->nx % 2 != 0 || !csem::fz_supported(fz_by, fz_mb, fz_kz)))
         return fail(CSEM_ERR_INVALID_ARG, "fused one-pass step: FP32, second order, nx even, rows/blocks (4,4), (4,6), (8,2) or (8,3), 2-99 planes");
     const int vh = cfg[7], ve = cfg[8], th = cfg[9], te = cfg[10], lh = cfg[11], le = cfg[12];
+    if (c->order == 4) {   // fourth order: its own kernels, the lean FP32 ones (2 cells) per half
+        if (fkz || fz || vh || ve || th || te)
+            return fail(CSEM_ERR_INVALID_ARG, "a fourth-order context runs its own H and E kernels only");
+        auto ok = [&](int l, int kz, int mb) { return l == 0 || (l == 2 && csem::ho4_supported(kz, mb)); };
+        if ((lh || le) && (c->precision != 32 || !c->d_cEm || !ok(lh, kzh, mbh) || !ok(le, kze, mbe)))
+            return fail(CSEM_ERR_INVALID_ARG, "lean fourth-order kernels: FP32, nx even, 2 cells, 2/4/8 planes, 4/6/8 blocks/SM");
+        if (fm < 0 || fm > 3 || ((fm & 1) && c->precision != 32) || !(M == 16 || M == 32 || M == 64) ||
+            ((fm & 2) ? 2 * M : M) + 1 > c->nslot)
+            return fail(CSEM_ERR_INVALID_ARG, "launch configuration not supported by this context");
+        CK(cudaDeviceSynchronize());
+        c->KZ_h = lh ? kzh : 4; c->MB_h = lh ? mbh : 4; c->KZ_e = le ? kze : 4; c->MB_e = le ? mbe : 4;
+        c->flush_mode = fm; c->M = M;
+        c->LEAN_h = lh; c->LEAN_e = le;
+        return CSEM_OK;
+    }
     if (lh || le) {
         auto ok = [&](int l, int kz, int mb) {
             return l == 0 || ((l == 1 || l == 2) && (kz == 1 || kz == 2 || kz == 4) &&
@@ -1838,8 +1886,6 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
         fm < 0 || fm > 3 || ((fm & 1) && c->precision != 32) || !(M == 16 || M == 32 || M == 64) ||
         ((fm & 2) ? 2 * M : M) + 1 > c->nslot)
         return fail(CSEM_ERR_INVALID_ARG, "launch configuration not supported by this context");
-    if (c->order == 4 && (fkz || fz || vh || ve || th || te || lh || le))
-        return fail(CSEM_ERR_INVALID_ARG, "a fourth-order context runs its own H and E kernels only");
     CK(cudaDeviceSynchronize());
     c->KZ_h = kzh; c->MB_h = mbh; c->KZ_e = kze; c->MB_e = mbe;
     c->fused_kz = fkz; c->flush_mode = fm; c->M = M;

@@ -19,8 +19,13 @@ struct HoTab {
     const R *wxh, *wxn, *wyh, *wyn, *wzh, *wzn;   // [n][4] and [n+1][4] per axis
 };
 
-// which: bit 0 = H half-step, bit 2 = E step with the source injection of p
+// which: bit 0 = H half-step, bit 2 = E step with the source injection of p.  FP32 halves whose
+// LEAN flag is set run the lean kernels (KZ planes per thread, MB resident 128-thread blocks).
 template <typename R>
 cudaError_t launch_ho(const StepParams<R> &p, const HoTab<R> &w, int S, int jstep, cudaStream_t st, int which);
+// lean FP32 kernels: nx even, kz in {2, 4, 8}, mb in {4, 6, 8}; need the masked dt/eps and the padded tables
+cudaError_t launch_ho4(const StepParams<float> &p, const HoTab<float> &w, int S, int jstep, cudaStream_t st, bool h,
+                       int kz, int mb);
+bool ho4_supported(int kz, int mb);
 
 }  // namespace csem

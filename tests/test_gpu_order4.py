@@ -80,8 +80,40 @@ def test_adjoint_and_gradient_order4(box, precision):
     eng.close()
 
 
-@pytest.mark.parametrize("precision", [64, 32])
-def test_td_gradient_order4(precision):
+ORDER4_FP32_LAUNCH = [
+    dict(flush_mode=1, block=32),                                                     # plain kernels
+    dict(lean_h=2, kz_h=4, mb_h=6, lean_e=2, kz_e=4, mb_e=6, flush_mode=1, block=32),
+    dict(lean_h=2, kz_h=2, mb_h=8, flush_mode=0, block=16),                           # lean H, plain E
+    dict(lean_e=2, kz_e=8, mb_e=4, flush_mode=3, block=16),                           # plain H, lean E
+    dict(lean_h=2, kz_h=8, mb_h=4, lean_e=2, kz_e=2, mb_e=8, flush_mode=1, block=16),
+]
+
+
+@pytest.mark.parametrize("variant", range(len(ORDER4_FP32_LAUNCH)))
+def test_order4_fp32_launch_variants(box, variant):
+    """The lean fourth-order kernels (two cells per thread, z window, branch-free boundary
+    rows) and the plain ones, alone or mixed per half, against the FP64 oracle."""
+    wl, pb, o = box
+    eng = Engine.from_workload(wl, precision=32, kahan=1, order=4, autotune=False)
+    eng.set_launch(**ORDER4_FP32_LAUNCH[variant])
+    rho = eng.model_tensor(wl.rho)
+    d, E, tr = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True, trace=True)
+    assert rel_l2(tr.cpu().numpy(), o["tr"]) <= 1e-4
+    assert rel_l2(d.cpu().numpy(), o["d"]) <= 1e-5
+    assert rel_l2(gpu_volume(eng, E), o["E"]) <= 1e-3
+    assert torch.count_nonzero(E[..., eng.nx + 1:]) == 0
+    phi, r = misfit(torch.as_tensor(o["d_obs"], device=eng.device), d)
+    basis, _, _ = eng.estimate_adjoint_basis(gamma=1e-12, relative=True)
+    V = eng.adjoint_model(rho, wl.rec, r, basis)
+    assert rel_l2(gpu_volume(eng, V), o["V"]) <= 1e-3
+    assert rel_l2(eng.gradient(rho, E, V, wrt="lnrho").cpu().numpy(), o["g"]) <= 1e-3
+    eng.check()
+    eng.close()
+
+
+@pytest.mark.parametrize("precision,launch", [(64, None), (32, None),
+                                              (32, dict(lean_h=2, kz_h=4, mb_h=6, lean_e=2, kz_e=8, mb_e=4))])
+def test_td_gradient_order4(precision, launch):
     wl = W.small_box(n_core=20, h=100.0, npml=6, ratio=1.08, n_st=2, n_rec=5, n_freq=2, n_core_y=14, n_core_z=10,
                      nt=1000)
     wl = dataclasses.replace(wl, src=W.Points.make([[30.0, 0.0, wl.src.z[0]], [-250.0, 40.0, wl.src.z[0]]], 0))
@@ -89,7 +121,9 @@ def test_td_gradient_order4(precision):
     d_obs = fdtd.forward(pb, wl.rho_true, wl.src, wl.rec)
     _, r = fdtd.misfit(d_obs, fdtd.forward(pb, wl.rho, wl.src, wl.rec))
     g_ref = fdtd.gradient_time_domain(pb, wl.rho, wl.src, wl.rec, r)
-    eng = Engine.from_workload(wl, precision=precision, kahan=1, order=4)
+    eng = Engine.from_workload(wl, precision=precision, kahan=1, order=4, autotune=launch is None)
+    if launch:
+        eng.set_launch(**launch)
     rg = torch.as_tensor(r, dtype=torch.complex128, device=eng.device)
     _, nbytes = eng.td_plan(wl.src.n, wl.rec.n, segment=128)
     work = torch.full((nbytes + 256,), 0xFF, dtype=torch.uint8, device=eng.device)
@@ -101,7 +135,8 @@ def test_td_gradient_order4(precision):
 def test_order4_refuses_other_kernel_families(box):
     wl, _, _ = box
     eng = Engine.from_workload(wl, precision=32, kahan=1, order=4, autotune=False)
-    for bad in (dict(lean_h=1, kz_h=1, mb_h=6), dict(fused_kz=4), dict(vec_e=1), dict(tma_h=1, kz_h=4)):
+    for bad in (dict(lean_h=1, kz_h=1, mb_h=6), dict(fused_kz=4), dict(vec_e=1), dict(tma_h=1, kz_h=4),
+                dict(lean_h=2, kz_h=16, mb_h=4), dict(lean_e=2, kz_e=4, mb_e=5)):
         with pytest.raises(CsemError):
             eng.set_launch(**bad)
     eng.set_launch(flush_mode=1, block=32)
