@@ -57,6 +57,9 @@ def parse():
                     help="time the FP64 oracle (1 thread and all cores) beside the device on three workloads")
     ap.add_argument("--early-stop-volumes", type=float, default=0.0,
                     help="time gradients with the early end of the forward and adjoint volume runs")
+    ap.add_argument("--es-floor", type=float, default=1e-4,
+                    help="--early-stop-volumes: entries below this fraction of their frequency's largest get an "
+                         "absolute bound")
     ap.add_argument("--early-stop", type=float, default=0.0,
                     help="time forward data runs with the early end at this tolerance against full runs")
     ap.add_argument("--td", type=int, default=0,
@@ -643,10 +646,11 @@ def run_early_stop_volumes(args):
     d_obs = torch.as_tensor(W.add_noise(eng.fwd_model(eng.model_tensor(wl.rho_true), wl.src, wl.rec).cpu().numpy(),
                                         wl.noise, wl.noise_seed), device=eng.device)
     basis, _, _ = eng.estimate_adjoint_basis(gamma=1e-12, relative=True, fit_target=1e-3)
-    out = {"mode": "early_stop_volumes", "workload": wl.name, "nt": eng.nt, "tol": args.early_stop_volumes}
+    out = {"mode": "early_stop_volumes", "workload": wl.name, "nt": eng.nt, "tol": args.early_stop_volumes,
+           "floor": args.es_floor}
     grads = {}
     for name, tol in (("full", 0.0), ("early", args.early_stop_volumes)):
-        eng.set_early_stop_volumes(tol)
+        eng.set_early_stop_volumes(tol, args.es_floor)
 
         def grad():
             d, E = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)

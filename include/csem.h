@@ -281,16 +281,20 @@ int csem_last_run_steps(csem_ctx *ctx, void *stream, int *steps);
 
 /* Early end of runs that keep volumes (csem_fwd_model with Evol_dev, csem_adjoint_model;
  * the same reading of Sec. 2 on the volumetric transform).  tol > 0: after every 64
- * steps one pass over the accumulators gives, per frequency k, A_k = max |acc| and
- * D_k = max |acc - acc at the previous check| over every source, component and entry;
- * the run ends after the first chunk c >= 1 with D_k <= tol A_k for every k (the
- * decision taken in FP32).  The volumes (and the receivers of a forward run) then hold
+ * steps one pass over the accumulators checks every entry of every source, component
+ * and frequency k: t_k |acc - acc at the previous check| <= tol max(|acc|, floor_frac
+ * A_k), A_k the largest |acc| of frequency k at the previous check and t_k = |q| / |1 - q|,
+ * q = exp((-1 + i) a_k 64 dt), the remainder an endless run would still add per unit of
+ * the last chunk's change if the field stayed as it was (the weights' geometric tail) --
+ * entries of at least floor_frac of the largest converge in relative terms, smaller ones
+ * to tol floor_frac A_k (floor_frac in [0, 1]); the run ends after the first chunk c >= 1
+ * where every entry passes (the decision taken in FP32).  The volumes (and the receivers of a forward run) then hold
  * the transform of the steps up to that chunk; csem_last_run_steps reports them.  The
  * host waits for each chunk's verdict before issuing the next, so nothing runs past the
  * end.  tol = 0 turns it off (the default); the first call with tol > 0 allocates a
  * copy of max_src volumes.  The time-domain gradient always takes nt steps.
  * Errors: INVALID_ARG, OOM, CUDA. */
-int csem_set_early_stop_volumes(csem_ctx *ctx, double tol);
+int csem_set_early_stop_volumes(csem_ctx *ctx, double tol, double floor_frac);
 
 /* Picks the launch shape of the H and E stepping kernels -- z planes per
  * thread (1, 2, 4, 8), the register budget (4, 6 or 8 resident 256-thread

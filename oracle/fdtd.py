@@ -577,16 +577,31 @@ def forward_early_stop(pb: Problem, rho, src, rec, tol: float, chunk: int = 64, 
     return R * norm[None, None, :], n1
 
 
-def _volume_converged(V, prev, tol):
-    """The early end of runs with volumes: per frequency, the largest change since the
-    previous check within tol of the largest magnitude, over every source, component
-    and entry.  V, prev: [n_src][3][n_freq][N] complex."""
-    a = np.abs(V).max(axis=(0, 1, 3))
-    d = np.abs(V - prev).max(axis=(0, 1, 3))
-    return bool(np.all(d <= tol * a))
+def volume_tail_factor(pb: Problem, chunk: int) -> np.ndarray:
+    """Per frequency: what the rest of an endless run adds, relative to the last chunk's
+    change, when the field stays as it was over that chunk -- the weights fall by the
+    factor q = exp((-1 + i) a_k chunk dt) from one chunk to the next (Eq. 6), so the
+    remainder is the geometric tail |q| / |1 - q| times the change."""
+    q = np.exp((-1.0 + 1.0j) * pb.a * chunk * pb.dt)
+    return np.abs(q) / np.abs(1.0 - q)
 
 
-def _volumes_in_chunks(pb, st, runs, tol, chunk):
+def _volume_converged(V, prev, prev_max, tol, floor_frac, tail):
+    """The early end of runs with volumes (Sec. 2: stop once the frequency-domain field is
+    steady): converged when, for every entry of every source, component and frequency k,
+    the remainder estimated from its change since the previous check, tail[k] |V - prev|,
+    is at most tol * max(|V|, floor_frac * prev_max[k]), with prev_max[k] the largest
+    |prev| of frequency k -- entries of at least floor_frac of the largest are held to a
+    relative bound, smaller ones to an absolute one.  The decision is taken in single
+    precision.  V, prev: [n_src][3][n_freq][N] complex."""
+    f32 = np.float32
+    a = np.abs(V).astype(f32)
+    d = np.abs(V - prev).astype(f32) * tail.astype(f32)[None, None, :, None]
+    floor = f32(floor_frac) * prev_max.astype(f32)[None, None, :, None]
+    return bool(np.all(d <= f32(tol) * np.maximum(a, floor)))
+
+
+def _volumes_in_chunks(pb, st, runs, tol, chunk, floor_frac):
     """Steps every source's run (fields, psi, inj, series) together in chunks, with the
     volumetric transform; ends after the first chunk c >= 1 that passes _volume_converged,
     or at nt.  Returns the raw transforms [n_src][3][n_freq][N] and the steps run."""
@@ -603,13 +618,15 @@ def _volumes_in_chunks(pb, st, runs, tol, chunk):
         V = np.stack([(vre[s] + 1j * vim[s]).reshape(3, nf, N) for s in range(len(runs))])
         if n1 == nt:
             break
-        if prev is not None and tol > 0 and _volume_converged(V, prev, tol):
-            break
+        if prev is not None and tol > 0:
+            prev_max = np.abs(prev).astype(np.float32).max(axis=(0, 1, 3))
+            if _volume_converged(V, prev, prev_max, tol, floor_frac, volume_tail_factor(pb, chunk)):
+                break
         prev = V
     return V, n1
 
 
-def forward_volumes_early_stop(pb: Problem, rho, src, rec, tol: float, chunk: int = 64):
+def forward_volumes_early_stop(pb: Problem, rho, src, rec, tol: float, chunk: int = 64, floor_frac: float = 1e-2):
     """Forward run with volumes and the early end of Sec. 2 applied to the volumetric
     transform (all sources together, checked every `chunk` steps).  Returns (d, volumes,
     steps) with d and the volumes normalised as in forward()."""
@@ -626,13 +643,13 @@ def forward_volumes_early_stop(pb: Problem, rho, src, rec, tol: float, chunk: in
         fields, psi = st.new_state()
         runs.append((fields, psi, point_taps(pb, src, s, scale_by_dV=st.dV, tag=0), wav[None, :],
                      dict(taps=taps, n_rec=rec.n, trace=traces[s])))
-    V, steps = _volumes_in_chunks(pb, st, runs, tol, chunk)
+    V, steps = _volumes_in_chunks(pb, st, runs, tol, chunk, floor_frac)
     d = np.stack([(tr.reshape(rec.n, pb.nt)[:, :steps] @ W[:steps]) * norm[None, :] for tr in traces])
     vols = V.reshape((src.n, 3, pb.freqs.size) + pb.shape_nodes) * norm[None, None, :, None, None, None]
     return d, vols, steps
 
 
-def adjoint_early_stop(pb: Problem, rho, rec, resid, Bp, tol: float, chunk: int = 64):
+def adjoint_early_stop(pb: Problem, rho, rec, resid, Bp, tol: float, chunk: int = 64, floor_frac: float = 1e-2):
     """adjoint() with the early end of Sec. 2 applied to the volumetric transform.
     Returns (conj(v) volumes, steps)."""
     st = Stepper(pb, rho)
@@ -644,7 +661,7 @@ def adjoint_early_stop(pb: Problem, rho, rec, resid, Bp, tol: float, chunk: int 
         coef = pb.k[None, :] * np.conj(resid[s]) / pb.dt
         fields, psi = st.new_state()
         runs.append((fields, psi, inj, _basis.synthesize(Bp, coef), {}))
-    V, steps = _volumes_in_chunks(pb, st, runs, tol, chunk)
+    V, steps = _volumes_in_chunks(pb, st, runs, tol, chunk, floor_frac)
     return pb.dt * V.reshape((resid.shape[0], 3, pb.freqs.size) + pb.shape_nodes), steps
 
 

@@ -72,7 +72,7 @@ SIGNATURES = {
                                         ctypes.c_int, _V, _V, ctypes.c_longlong, _V]),
     "csem_set_early_stop": (ctypes.c_int, [_V, ctypes.c_double]),
     "csem_last_run_steps": (ctypes.c_int, [_V, _V, _I]),
-    "csem_set_early_stop_volumes": (ctypes.c_int, [_V, ctypes.c_double]),
+    "csem_set_early_stop_volumes": (ctypes.c_int, [_V, ctypes.c_double, ctypes.c_double]),
     "csem_autotune": (ctypes.c_int, [_V, ctypes.c_int, _I, _V]),
     "csem_set_launch": (ctypes.c_int, [_V, _I]),
     "csem_set_wavelet": (ctypes.c_int, [_V, _D]),
@@ -208,8 +208,8 @@ def set_early_stop(ctx, tol):
     _check(lib().csem_set_early_stop(ctx, float(tol)))
 
 
-def set_early_stop_volumes(ctx, tol):
-    _check(lib().csem_set_early_stop_volumes(ctx, float(tol)))
+def set_early_stop_volumes(ctx, tol, floor_frac):
+    _check(lib().csem_set_early_stop_volumes(ctx, float(tol), float(floor_frac)))
 
 
 def last_run_steps(ctx, stream) -> int:

@@ -190,8 +190,9 @@ struct csem_ctx {
     bool last_es = false;                // the last forward or adjoint run used an early end
     // early end of runs that keep volumes (tol > 0): previous accumulators, per-frequency stats
     double es_vol_tol = 0.0;
+    double es_vol_floor = 1e-4;          // entries below this fraction of their frequency's largest: absolute bound
     void *d_vprev = nullptr;             // [max_src][3][nf][vol] complex (real)
-    unsigned *d_vstats = nullptr;        // [2 nf]
+    unsigned *d_vstats = nullptr;        // [3 nf]: max |acc|, moved flag, previous check's max
     struct GraphSlot { int key[8]; cudaGraphExec_t exec; };
     std::vector<GraphSlot> graphs;
 };
@@ -831,6 +832,14 @@ int run_steps_vol_es(csem_ctx *c, int S, const csem::StepParams<R> &p, const cse
     const int M = c->M, nt = c->nt, nf = c->nf;
     const int full = nt / kChunk, rem = nt % kChunk;
     CK(cudaMemsetAsync(c->d_es, 0, 2 * sizeof(int), st));
+    CK(cudaMemsetAsync(c->d_vstats, 0, 3 * nf * sizeof(unsigned), st));
+    // the transform weights fall by q = exp((-1 + i) a_k kChunk dt) per chunk (Eq. 6): a field
+    // that stays as it was over the last chunk adds |q| / |1 - q| times that chunk's change
+    csem::EsTail tail{};
+    for (int f = 0; f < nf; ++f) {
+        const std::complex<double> q = std::exp(std::complex<double>(-1.0, 1.0) * (c->a[f] * kChunk * c->dt));
+        tail.f[f] = (float)(std::abs(q) / std::abs(1.0 - q));
+    }
     bool ended = false;
     if (full > 0) {
         const int key[8] = {S, 5, (kahan ? 1 : 0) + 2 * fz_code(c), q.n_itaps, q.n_rec > 0 ? 1 : 0, (int)sizeof(R),
@@ -850,9 +859,9 @@ int run_steps_vol_es(csem_ctx *c, int S, const csem::StepParams<R> &p, const cse
             csem::g_launches += per_chunk;
             const bool last = (ch == full - 1 && rem == 0);
             CK(cudaMemsetAsync(c->d_vstats, 0, 2 * nf * sizeof(unsigned), st));
-            CK(csem::launch_es_vol_stats<R>((const R2 *)p.acc, (R2 *)c->d_vprev, c->vol, S, nf, c->d_vstats, st));
-            CK(csem::launch_es_vol_decide(c->d_vstats, nf, c->es_vol_tol, ch, last ? 1 : 0, (ch + 1) * kChunk,
-                                          c->d_es, st));
+            CK(csem::launch_es_vol_stats<R>((const R2 *)p.acc, (R2 *)c->d_vprev, c->vol, S, nf, c->es_vol_tol,
+                                            c->es_vol_floor, tail, c->d_vstats, st));
+            CK(csem::launch_es_vol_decide(c->d_vstats, nf, ch, last ? 1 : 0, (ch + 1) * kChunk, c->d_es, st));
             CK(cudaMemcpyAsync(&c->h_es[0], c->d_es, sizeof(int), cudaMemcpyDeviceToHost, st));
             CK(cudaEventRecord(c->es_ev[0], st));
             CK(cudaEventSynchronize(c->es_ev[0]));
@@ -867,7 +876,7 @@ int run_steps_vol_es(csem_ctx *c, int S, const csem::StepParams<R> &p, const cse
         }
         const int tail = rem % M;
         if (tail) CK(flush<R>(c, p, q, S, rem - tail, tail, true, kahan, st));
-        CK(csem::launch_es_vol_decide(c->d_vstats, nf, c->es_vol_tol, full, 1, nt, c->d_es, st));
+        CK(csem::launch_es_vol_decide(c->d_vstats, nf, full, 1, nt, c->d_es, st));
     }
     return CSEM_OK;
 }
@@ -1813,16 +1822,18 @@ int csem_set_early_stop(csem_ctx *c, double tol) {
     return CSEM_OK;
 }
 
-int csem_set_early_stop_volumes(csem_ctx *c, double tol) {
+int csem_set_early_stop_volumes(csem_ctx *c, double tol, double floor_frac) {
     if (!c || !(tol >= 0.0) || !std::isfinite(tol)) return fail(CSEM_ERR_INVALID_ARG, "tol must be finite and >= 0");
+    if (!(floor_frac >= 0.0) || !(floor_frac <= 1.0)) return fail(CSEM_ERR_INVALID_ARG, "floor_frac must be in [0, 1]");
     if (tol > 0.0) {
         TRY(es_state(c));
         if (!c->d_vprev) {
             TRY(dalloc(c, (char **)&c->d_vprev, (size_t)c->max_src * 3 * c->nf * c->vol * 2 * c->rsize));
-            TRY(dalloc(c, &c->d_vstats, 2 * (size_t)c->nf * sizeof(unsigned)));
+            TRY(dalloc(c, &c->d_vstats, 3 * (size_t)c->nf * sizeof(unsigned)));
         }
     }
     c->es_vol_tol = tol;
+    c->es_vol_floor = floor_frac;
     return CSEM_OK;
 }
 

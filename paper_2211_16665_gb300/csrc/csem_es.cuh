@@ -14,14 +14,21 @@ cudaError_t launch_es_check(const double2 *racc, double2 *prev, double2 *fin, in
                             int last, int steps_at, int *state, cudaStream_t st);
 
 // Runs that keep volumes.  Per frequency f, over every source, component and
-// entry of the accumulators acc [S][3][nf][vol]: stats[f] = max |acc| and
-// stats[nf + f] = max |acc - prev| (bit patterns of non-negative floats, combined by
-// atomicMax, cleared by the caller); prev takes acc.
+// entry of the accumulators acc [S][3][nf][vol]: stats[f] = max |acc| (bit pattern of
+// a non-negative float, combined by atomicMax) and stats[nf + f] = 1 if for some entry
+// tail.f[f] |acc - prev| > tol max(|acc|, floor_frac stats[2 nf + f]), stats[2 nf + f]
+// being the previous check's max (both cleared by the caller, the last kept); prev takes
+// acc.  Magnitudes and the comparison in FP32.  tail.f[f]: the remainder of an endless
+// run per unit change over the last chunk, for a field that stays as it was.
+struct EsTail {
+    float f[kMaxFreq];
+};
 template <typename R>
 cudaError_t launch_es_vol_stats(const typename C2<R>::T *acc, typename C2<R>::T *prev, long long vol, int S, int nf,
-                                unsigned *stats, cudaStream_t st);
-// state = {1, steps_at} when chunk >= 1 and stats[nf + f] <= tol stats[f] for every f, or when last.
-cudaError_t launch_es_vol_decide(const unsigned *stats, int nf, double tol, int chunk, int last, int steps_at,
-                                 int *state, cudaStream_t st);
+                                double tol, double floor_frac, const EsTail &tail, unsigned *stats, cudaStream_t st);
+// state = {1, steps_at} when chunk >= 1 and no frequency has a moved entry, or when last;
+// stats[2 nf + f] takes stats[f] for the next check.
+cudaError_t launch_es_vol_decide(unsigned *stats, int nf, int chunk, int last, int steps_at, int *state,
+                                 cudaStream_t st);
 
 }  // namespace csem

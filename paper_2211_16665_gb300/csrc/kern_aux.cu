@@ -235,67 +235,73 @@ cudaError_t launch_es_check(const double2 *racc, double2 *prev, double2 *fin, in
 
 template <typename R>
 __global__ void __launch_bounds__(256) k_es_vol_stats(const typename C2<R>::T *acc, typename C2<R>::T *prev,
-                                                      long long vol, int nf, unsigned *stats) {
+                                                      long long vol, int nf, float tol, float floor_frac,
+                                                      EsTail tail, unsigned *stats) {
     const int blk = blockIdx.y;                       // (s*3 + c)*nf + f
     const int f = blk % nf;
     const long long base = (long long)blk * vol;
-    float amax = 0.f, dmax = 0.f;
+    // entries below floor_frac of the frequency's largest magnitude at the previous check are
+    // held to an absolute bound (the decision is taken in FP32)
+    const float floor_a = floor_frac * __uint_as_float(stats[2 * nf + f]);
+    const float tf = tail.f[f];                       // remainder per unit change (geometric tail)
+    float amax = 0.f;
+    unsigned viol = 0u;
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < vol; e += (long long)gridDim.x * blockDim.x) {
         const typename C2<R>::T a = acc[base + e], b = prev[base + e];
-        const float ar = (float)a.x, ai = (float)a.y;                     // a decision, taken in FP32
-        const float dr = (float)(a.x - b.x), di = (float)(a.y - b.y);
-        amax = fmaxf(amax, hypotf(ar, ai));
-        dmax = fmaxf(dmax, hypotf(dr, di));
+        const float am = hypotf((float)a.x, (float)a.y);
+        const float dm = hypotf((float)(a.x - b.x), (float)(a.y - b.y)) * tf;
+        amax = fmaxf(amax, am);
+        if (dm > tol * fmaxf(am, floor_a)) viol = 1u;
         prev[base + e] = a;
     }
     for (int o = 16; o > 0; o >>= 1) {
         amax = fmaxf(amax, __shfl_down_sync(0xffffffffu, amax, o));
-        dmax = fmaxf(dmax, __shfl_down_sync(0xffffffffu, dmax, o));
+        viol |= __shfl_down_sync(0xffffffffu, viol, o);
     }
-    __shared__ float sa[8], sd[8];
+    __shared__ float sa[8];
+    __shared__ unsigned sv[8];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { sa[wid] = amax; sd[wid] = dmax; }
+    if (lane == 0) { sa[wid] = amax; sv[wid] = viol; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) { amax = fmaxf(amax, sa[k]); dmax = fmaxf(dmax, sd[k]); }
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) { amax = fmaxf(amax, sa[k]); viol |= sv[k]; }
         atomicMax(stats + f, __float_as_uint(amax));          // non-negative floats order like their bits
-        atomicMax(stats + nf + f, __float_as_uint(dmax));
+        if (viol) atomicOr(stats + nf + f, 1u);
     }
 }
 
 template <typename R>
 cudaError_t launch_es_vol_stats(const typename C2<R>::T *acc, typename C2<R>::T *prev, long long vol, int S, int nf,
-                                unsigned *stats, cudaStream_t st) {
-    const long long per = (vol + 255) / 256;
-    const dim3 grid((unsigned)std::min<long long>(per, 64), (unsigned)(S * 3 * nf));
-    k_es_vol_stats<R><<<grid, 256, 0, st>>>(acc, prev, vol, nf, stats);
+                                double tol, double floor_frac, const EsTail &tail, unsigned *stats, cudaStream_t st) {
+    const dim3 grid((unsigned)std::min<long long>((vol + 255) / 256, 64), (unsigned)(S * 3 * nf));
+    k_es_vol_stats<R><<<grid, 256, 0, st>>>(acc, prev, vol, nf, (float)tol, (float)floor_frac, tail, stats);
     g_launches++;
     return cudaGetLastError();
 }
 
-__global__ void k_es_vol_decide(const unsigned *stats, int nf, double tol, int chunk, int last, int steps_at,
-                                int *state) {
+__global__ void k_es_vol_decide(unsigned *stats, int nf, int chunk, int last, int steps_at, int *state) {
     if (state[0]) return;
     bool done = last != 0;
     if (!done && chunk >= 1) {
         done = true;
         for (int f = 0; f < nf; ++f)
-            if ((double)__uint_as_float(stats[nf + f]) > tol * (double)__uint_as_float(stats[f])) done = false;
+            if (stats[nf + f]) done = false;
     }
+    for (int f = 0; f < nf; ++f) stats[2 * nf + f] = stats[f];   // this check's maxima for the next one
     if (done) { state[1] = steps_at; state[0] = 1; }
 }
 
-cudaError_t launch_es_vol_decide(const unsigned *stats, int nf, double tol, int chunk, int last, int steps_at,
-                                 int *state, cudaStream_t st) {
-    k_es_vol_decide<<<1, 1, 0, st>>>(stats, nf, tol, chunk, last, steps_at, state);
+cudaError_t launch_es_vol_decide(unsigned *stats, int nf, int chunk, int last, int steps_at, int *state,
+                                 cudaStream_t st) {
+    k_es_vol_decide<<<1, 1, 0, st>>>(stats, nf, chunk, last, steps_at, state);
     g_launches++;
     return cudaGetLastError();
 }
 
-template cudaError_t launch_es_vol_stats<float>(const float2 *, float2 *, long long, int, int, unsigned *,
-                                                cudaStream_t);
-template cudaError_t launch_es_vol_stats<double>(const double2 *, double2 *, long long, int, int, unsigned *,
-                                                 cudaStream_t);
+template cudaError_t launch_es_vol_stats<float>(const float2 *, float2 *, long long, int, int, double, double,
+                                                const EsTail &, unsigned *, cudaStream_t);
+template cudaError_t launch_es_vol_stats<double>(const double2 *, double2 *, long long, int, int, double, double,
+                                                 const EsTail &, unsigned *, cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // misfit and weighted residual (Sec. 3.1, Eq. 7), one block

@@ -144,10 +144,11 @@ class Engine:
         _capi.set_early_stop(self.ctx, tol)
         self.early_stop_tol = float(tol)
 
-    def set_early_stop_volumes(self, tol=0.0):
-        """Forward runs with volumes and adjoint runs end once every frequency's volumetric
-        transform changes by at most tol of its largest magnitude over 64 steps (Sec. 2)."""
-        _capi.set_early_stop_volumes(self.ctx, tol)
+    def set_early_stop_volumes(self, tol=0.0, floor=1e-4):
+        """Forward runs with volumes and adjoint runs end once every entry of the volumetric
+        transform changes over 64 steps by at most tol times the larger of its magnitude and
+        `floor` times its frequency's largest magnitude (Sec. 2, csem_set_early_stop_volumes)."""
+        _capi.set_early_stop_volumes(self.ctx, tol, floor)
 
     def last_run_steps(self) -> int:
         """Steps the last fwd_model or adjoint_model run included (synchronises the current stream)."""

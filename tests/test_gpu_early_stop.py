@@ -84,8 +84,8 @@ def gpu_volume(eng, v):
     return v.cpu().numpy()[..., : eng.nx + 1].astype(np.complex128)
 
 
-@pytest.mark.parametrize("precision", [64, 32])
-def test_volume_early_end_matches_oracle(case, precision):
+@pytest.mark.parametrize("precision,floor", [(64, 1e-2), (32, 1e-2), (64, 1e-4)])
+def test_volume_early_end_matches_oracle(case, precision, floor):
     """Forward (with volumes) and adjoint runs ending on the volumetric transform: the same
     stop steps as the oracle in FP64 (within a chunk in FP32); volumes and gradient equal to
     the oracle's truncated at the device's steps; the gradient within 1e-5 of the full one."""
@@ -95,8 +95,8 @@ def test_volume_early_end_matches_oracle(case, precision):
     d_full, E_full = fdtd.forward(pb, wl.rho, wl.src, wl.rec, keep_volume=True)
     _, r = fdtd.misfit(d_obs, d_full)
     Bp, _ = fdtd.adjoint_basis(pb, 1e-12)
-    _, _, steps_ref = fdtd.forward_volumes_early_stop(pb, wl.rho, wl.src, wl.rec, tol)
-    _, sa_ref = fdtd.adjoint_early_stop(pb, wl.rho, wl.rec, r, Bp, tol)
+    _, _, steps_ref = fdtd.forward_volumes_early_stop(pb, wl.rho, wl.src, wl.rec, tol, floor_frac=floor)
+    _, sa_ref = fdtd.adjoint_early_stop(pb, wl.rho, wl.rec, r, Bp, tol, floor_frac=floor)
     assert steps_ref < pb.nt and sa_ref < pb.nt
 
     eng = Engine.from_workload(wl, precision=precision, kahan=1)
@@ -105,7 +105,7 @@ def test_volume_early_end_matches_oracle(case, precision):
     rg = torch.as_tensor(r, dtype=torch.complex128, device=eng.device)
     E_all, V_all = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)[1], eng.adjoint_model(rho, wl.rec, rg, basis)
     g_all = eng.gradient(rho, E_all, V_all).double().cpu().numpy()
-    eng.set_early_stop_volumes(tol)
+    eng.set_early_stop_volumes(tol, floor)
     d, E = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)
     steps = eng.last_run_steps()
     V = eng.adjoint_model(rho, wl.rec, rg, basis)
