@@ -626,7 +626,7 @@ def _volumes_in_chunks(pb, st, runs, tol, chunk, floor_frac):
     return V, n1
 
 
-def forward_volumes_early_stop(pb: Problem, rho, src, rec, tol: float, chunk: int = 64, floor_frac: float = 1e-2):
+def forward_volumes_early_stop(pb: Problem, rho, src, rec, tol: float, chunk: int = 64, floor_frac: float = 1e-4):
     """Forward run with volumes and the early end of Sec. 2 applied to the volumetric
     transform (all sources together, checked every `chunk` steps).  Returns (d, volumes,
     steps) with d and the volumes normalised as in forward()."""
@@ -649,7 +649,7 @@ def forward_volumes_early_stop(pb: Problem, rho, src, rec, tol: float, chunk: in
     return d, vols, steps
 
 
-def adjoint_early_stop(pb: Problem, rho, rec, resid, Bp, tol: float, chunk: int = 64, floor_frac: float = 1e-2):
+def adjoint_early_stop(pb: Problem, rho, rec, resid, Bp, tol: float, chunk: int = 64, floor_frac: float = 1e-4):
     """adjoint() with the early end of Sec. 2 applied to the volumetric transform.
     Returns (conj(v) volumes, steps)."""
     st = Stepper(pb, rho)

@@ -57,7 +57,7 @@ def test_stop_chunk_from_the_plain_run_and_error_bound():
 def test_volume_early_end():
     """V1 tol = 0 reproduces forward() and adjoint(); V2 the stop chunk is the first one
     where, in a plain run's chunked transforms, every entry moved by at most tol times the
-    larger of its magnitude and a hundredth of its frequency's largest magnitude at the
+    larger of its magnitude and 1e-4 of its frequency's largest magnitude at the
     previous check (single precision); V3 the truncated gradient stays close to the full
     one."""
     wl, pb = case()
@@ -91,7 +91,7 @@ def test_volume_early_end():
         R = (vre + 1j * vim).reshape(3, 2, pb.N)
         if n1 < pb.nt and prev is not None:
             f32 = np.float32
-            floor = f32(1e-2) * np.abs(prev).astype(f32).max(axis=(0, 2))          # per frequency
+            floor = f32(1e-4) * np.abs(prev).astype(f32).max(axis=(0, 2))          # per frequency
             bound = f32(tol) * np.maximum(np.abs(R).astype(f32), floor[None, :, None])
             # what later chunks add if the field stays as it was: the weights of Eq. 6 summed
             # chunk by chunk, sum_{m >= 1} exp((-1 + i) a_k 64 dt m), by brute force
