@@ -1357,9 +1357,7 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
                 for (const auto &b : bm)
                     for (int kz : {8, 16, 32, 64}) cands.push_back({0, b[0], b[1], kz});
             }
-            double best = 1e30;
-            Cand bc = cands[0];
-            for (const Cand &cd : cands) {
+            auto time_cand = [&](const Cand &cd, float *t) -> int {
                 p.fused_kz = cd.f;
                 p.FZ_by = cd.by; p.FZ_mb = cd.mb; p.FZ_kz = cd.kz;
                 for (int j = 0; j < 3; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, 5));
@@ -1368,10 +1366,27 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
                 for (int j = 0; j < reps; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, 5));
                 CK(cudaEventRecord(e1, st));
                 CK(cudaEventSynchronize(e1));
+                CK(cudaEventElapsedTime(t, e0, e1));
+                return CSEM_OK;
+            };
+            // first pass: the fastest fused candidate; then the split pair and that candidate
+            // are timed again, alternately, three times each, and the lower median wins, so the
+            // choice does not hang on one measurement (or on which candidate ran first)
+            double best = 1e30;
+            Cand bc = cands[0];
+            for (size_t u = 1; u < cands.size(); ++u) {
                 float t = 0.f;
-                CK(cudaEventElapsedTime(&t, e0, e1));
-                if (t < best) { best = t; bc = cd; }
+                TRY(time_cand(cands[u], &t));
+                if (t < best) { best = t; bc = cands[u]; }
             }
+            float ts[3], tf[3];
+            for (int r = 0; r < 3; ++r) {
+                TRY(time_cand(cands[0], &ts[r]));
+                TRY(time_cand(bc, &tf[r]));
+            }
+            std::sort(ts, ts + 3);
+            std::sort(tf, tf + 3);
+            if (!(tf[1] < ts[1])) bc = cands[0];
             c->fused_kz = bc.f;
             c->FZ_by = bc.by; c->FZ_mb = bc.mb; c->FZ_kz = bc.kz;
             p.fused_kz = 0;
@@ -1634,7 +1649,9 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
         if (rc == CSEM_OK) step(upload_geo_tables(c));
         const size_t qb = (size_t)(c->vti ? 2 : 1) * c->vol * sizeof(float);
         step(dalloc(c, &c->d_q, qb));
-        if (rc == CSEM_OK && cudaMemset(c->d_q, 0, qb) != cudaSuccess)
+        // finite, positive values (bytes 0x3f: 0.747f) until a run sets the model, so the
+        // autotuner times the fused step on finite arithmetic
+        if (rc == CSEM_OK && cudaMemset(c->d_q, 0x3f, qb) != cudaSuccess)
             rc = fail(CSEM_ERR_CUDA, "context initialisation failed");
         size_t free_b = 0, total_b = 0;
         cudaMemGetInfo(&free_b, &total_b);
