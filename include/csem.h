@@ -169,10 +169,15 @@ int csem_estimate_adjoint_basis(double dt, int nt, const double *freqs_host, int
  * vectors live in one file-scope device array of 8 MiB that every device
  * which loads the library keeps until the process exits.
  *  Limits: nt <= 32768 and n_freq <= 8, else INVALID_ARG with a message.
- *  The first call on a device resolves the array's device address
- *  (cudaGetSymbolAddress) with that device current; make that first call
- *  before any stream capture.
- *  Every call shares the one array and clears it on the stream first, so
+ *  Every call looks the array's device address up (cudaGetSymbolAddress)
+ *  with the caller's device current.  With lazy module loading (the CUDA
+ *  default) the first such lookup on a device loads the library's module,
+ *  which reserves the array and may synchronise the device: make one call
+ *  during setup, before any stream capture or latency-critical path.  After
+ *  cudaDeviceReset the next call loads the module again and finds the new
+ *  address.
+ *  Every call shares the one array and clears the part it uses on the
+ *  stream first, so
  *  calls that overlap on the GPU (two streams, two threads) race: serialise
  *  them.  Arguments, outputs and blocking behaviour are those of
  *  csem_estimate_adjoint_basis.

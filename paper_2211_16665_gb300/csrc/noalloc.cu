@@ -12,7 +12,6 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "../../include/csem.h"
@@ -31,29 +30,17 @@ constexpr size_t kScratchDoubles = kVecDoubles + kGramDoubles + kScalDoubles + k
 
 __device__ __align__(256) double g_basis_scratch[kScratchDoubles];   // 8 MiB + a few KiB
 
-constexpr int kMaxDevices = 64;
-double *g_scratch_ptr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mutex;
-
-
-// Host code cannot use g_basis_scratch's name as a device address: resolve it
-// once per device, with that device current.
+// Host code cannot use g_basis_scratch's name as a device address.  Resolve it
+// on every call, with the caller's device current: once the module is loaded this
+// is a table lookup, and a fresh lookup stays right after cudaDeviceReset (which
+// unloads the module; the next call loads it again at a new address).
 int scratch_for_current_device(double **out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-        return csem::set_last_error(CSEM_ERR_CUDA, "no usable current device");
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_basis_scratch);
+    if (e != cudaSuccess || !p) {
+        return csem::set_last_error(CSEM_ERR_CUDA, std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
     }
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_basis_scratch);
-        if (e != cudaSuccess || !p) {
-            return csem::set_last_error(CSEM_ERR_CUDA, std::string("cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
-        }
-        g_scratch_ptr[dev] = (double *)p;
-    }
-    *out = g_scratch_ptr[dev];
+    *out = (double *)p;
     return CSEM_OK;
 }
 
@@ -87,8 +74,13 @@ extern "C" int csem_estimate_adjoint_basis_noalloc(double dt, int nt, const doub
     double *gram = base + kVecDoubles;
     double *scal = gram + kGramDoubles;
     int *iters = (int *)(scal + kScalDoubles);
-    // every call shares the array: start from zeros so no value of a previous call can leak in
-    cudaError_t e = cudaMemsetAsync(base, 0, kScratchDoubles * sizeof(double), st);
+    // The basis kernels write every value of the array they later read, so a clear is
+    // not needed for the result; it is kept, limited to the part this call uses (its
+    // m CG vector pairs and the Gram/scalar/count block), so that a kernel fault can
+    // never show a previous call's numbers.
+    cudaError_t e = cudaMemsetAsync(vec, 0, (size_t)m * 2 * nt * sizeof(double), st);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(gram, 0, (kGramDoubles + kScalDoubles + kIterDoubles) * sizeof(double), st);
     if (e == cudaSuccess)
         e = csem::launch_basis(dt, nt, a, nf, gamma, gamma_is_relative, max_iter, tol, basis_dev, vec, gram, scal,
                                iters, st);
