@@ -2,9 +2,9 @@
 // Eq. 4, with the unsplit CPML): H^{n-1/2} -> H^{n+1/2} and E^n -> E^{n+1} in
 // one kernel, source injection included.
 //
-// A block of 32 x BY threads owns a tile of 64 cells (x) by BY rows (y) and
-// marches KZ planes along z; each thread owns two consecutive cells (i, i+1) of
-// one row.  The planes are staged into shared memory by the tensor memory
+// A block of 32 x (BY + 1) threads owns a tile of 64 cells (x) by BY rows (y)
+// and marches KZ planes along z; each of the first BY warps owns one row, each
+// thread two consecutive cells (i, i+1) of it; the last warp is the halo warp.  The planes are staged into shared memory by the tensor memory
 // accelerator: one thread issues, per plane m, three 4-D tile copies -- E^n
 // (Ex, Ey, Ez), H^{n-1/2} (Hx, Hy, Hz) and the per-cell material -- each 72
 // columns (x from i0-4, so the copy starts on a 16-byte boundary) by BY+2 rows
@@ -13,14 +13,18 @@
 // filled with zeros by the copy engine.  Planes m+1 .. m+NST-2 are in flight
 // while plane m is computed, so the DRAM latency is hidden by the ring rather
 // than by resident warps.  Per plane k, from shared memory:
-//  * H^{n+1/2} on the thread's own cells (stored), and the neighbour values its
-//    E update needs -- Hy, Hz at i-1 and Hx, Hz at j-1 -- recomputed from the
-//    staged E^n and H^{n-1/2} rather than exchanged, so no thread waits on
-//    another within a plane and no block reads a value another block has
-//    advanced.  H and the CPML memory of the H update are double buffered
-//    (step n reads the buffer of parity n and writes the other), E^n and E^{n+1}
-//    are different ring slots, and the CPML memory of the E update is touched
-//    only by the cell's owner;
+//  * phase 1: H^{n+1/2} of every thread's two cells into a shared plane (and to
+//    the second H buffer in global memory); the halo warp computes H^{n+1/2} of
+//    row j0-1 and, lane by lane, Hy and Hz of column i0-1 -- values the
+//    neighbouring blocks own, recomputed from the staged E^n and H^{n-1/2}
+//    rather than exchanged, so no block waits on another or reads a value
+//    another block has advanced.  H and the CPML memory of the H update are
+//    double buffered (step n reads the buffer of parity n and writes the
+//    other), E^n and E^{n+1} are different ring slots, and the CPML memory of
+//    the E update is touched only by the cell's owner;
+//  * phase 2, after a block barrier: E^{n+1} of the thread's cells with the
+//    neighbouring H values (i-1, j-1) from the shared plane and those of
+//    plane k-1 kept in registers;
 //  * dt/eps on the three edges of the node comes from one value per cell,
 //    q = V sigma (cell volume times conductivity): the edge conductivity is the
 //    volume-weighted mean of the four cells around the edge, so dt/eps = 2 w0 dt
