@@ -402,8 +402,35 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 }
 
 
+// Receiver transforms of source s over the ms snapshots from step n0 (FP64 sums of the
+// eight interpolation taps of each receiver), one receiver per thread.
+__device__ __forceinline__ void dft_receivers(const StepParams<float> &p, const PointParams<float> &q, int n0, int ms,
+                                              int s) {
+    const float *ring = p.ering + (long long)s * p.ering_stride;
+    for (int r = threadIdx.x; r < q.n_rec; r += blockDim.x) {
+        const Tap *tp = q.rtaps + (long long)r * 8;
+        double2 a[kMaxFreq];
+        double2 *dst = q.racc + ((long long)s * q.n_rec + r) * q.nf;
+        for (int f = 0; f < q.nf; ++f) a[f] = dst[f];
+        for (int m = 0; m < ms; ++m) {
+            const int n = n0 + m;
+            const float *E = ring + (long long)(n % p.nslot) * 3 * p.vol;
+            double v = 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v += tp[u].w * (double)E[(long long)tp[u].comp * p.vol + tp[u].idx];
+            const double2 *w = q.w64 + (long long)n * q.nf;
+            for (int f = 0; f < q.nf; ++f) {
+                a[f].x += v * w[f].x;
+                a[f].y += v * w[f].y;
+            }
+            if (q.trace) q.trace[((long long)s * q.n_rec + r) * q.nt + n] = v;
+        }
+        for (int f = 0; f < q.nf; ++f) dst[f] = a[f];
+    }
+}
+
 // resident blocks per SM that the shared memory allows (MS snapshots of 1 KB + accumulators)
-template <int MS> constexpr int bulk_minb() { return MS <= 16 ? 6 : (MS <= 32 ? 4 : 2); }
+template <int MS> constexpr int bulk_minb() { return MS <= 16 ? 6 : 4; }   // 16 or 32 snapshots
 constexpr int kBulkThreads = 128;       // two lattice entries per thread, 256 per block
 __host__ __device__ constexpr int nf_pad(int nf) { return nf <= 2 ? 2 : (nf <= 4 ? 4 : 8); }
 
@@ -429,28 +456,7 @@ __global__ void __launch_bounds__(kBulkThreads, bulk_minb<MS>()) k_dft_bulk(cons
     const int nrec_blocks = q.n_rec > 0 ? S : 0;
     const int blk = blockIdx.x;
     if (blk < nrec_blocks) {          // receivers: same as the register flush
-        const int s = blk;
-        const float *ring = p.ering + (long long)s * p.ering_stride;
-        for (int r = threadIdx.x; r < q.n_rec; r += blockDim.x) {
-            const Tap *tp = q.rtaps + (long long)r * 8;
-            double2 a[kMaxFreq];
-            double2 *dst = q.racc + ((long long)s * q.n_rec + r) * q.nf;
-            for (int f = 0; f < q.nf; ++f) a[f] = dst[f];
-            for (int m = 0; m < MS; ++m) {
-                const int n = n0 + m;
-                const float *E = ring + (long long)(n % p.nslot) * 3 * p.vol;
-                double v = 0.0;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) v += tp[u].w * (double)E[(long long)tp[u].comp * p.vol + tp[u].idx];
-                const double2 *w = q.w64 + (long long)n * q.nf;
-                for (int f = 0; f < q.nf; ++f) {
-                    a[f].x += v * w[f].x;
-                    a[f].y += v * w[f].y;
-                }
-                if (q.trace) q.trace[((long long)s * q.n_rec + r) * q.nt + n] = v;
-            }
-            for (int f = 0; f < q.nf; ++f) dst[f] = a[f];
-        }
+        dft_receivers(p, q, n0, MS, blk);
         return;
     }
     const int vblk = blk - nrec_blocks;
@@ -538,6 +544,153 @@ __global__ void __launch_bounds__(kBulkThreads, bulk_minb<MS>()) k_dft_bulk(cons
     }
 }
 
+// Streamed flush of 64 snapshots.  Holding all 64 snapshot rows of a block in
+// shared memory (64 KB) leaves two blocks per SM, and a block computes only
+// after its last copy landed.  Here the snapshots stream through kStN stages of
+// kStG rows each (one mbarrier per stage, 32 KB in all): while the block sums
+// the rows of one stage, the copies of the next kStN - 1 stages are in flight,
+// and four blocks fit an SM.  The accumulators (and compensation) arrive on a
+// barrier of their own and are added to once, at the end, as in k_dft_bulk;
+// the sums are the same as k_dft_bulk's with MS = 64, in the same order.
+// Each thread waits on each stage's barrier itself (bounded); a give-up
+// anywhere ends the loop for the whole block (__syncthreads_or), thread 0 then
+// waits (bounded) for every copy it issued that nobody consumed, and the block
+// returns with the flush bit of *err raised.
+constexpr int kStG = 8;                 // snapshot rows per stage
+constexpr int kStN = 4;                 // stages (a power of two)
+constexpr int kStMS = 64;               // snapshots per flush
+
+template <bool KAHAN, int NF>
+__global__ void __launch_bounds__(kBulkThreads, 3) k_dft_stream(const StepParams<float> p, const PointParams<float> q,
+                                                                const int n0_off, const int nvb, const int S,
+                                                                int *err) {
+    constexpr int NCH = kStMS / kStG;
+    __shared__ __align__(8) uint64_t full[kStN];
+    __shared__ __align__(8) uint64_t abar;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *st_s = reinterpret_cast<float *>(smem);                          // [kStN][kStG][256]
+    float2 *acc_s = reinterpret_cast<float2 *>(st_s + kStN * kStG * kBlock);  // [nf][256]
+    float2 *cmp_s = acc_s + p.nf * kBlock;                                  // [nf][256] (Kahan)
+    float2 *w_s = cmp_s + (KAHAN ? p.nf * kBlock : 0);                      // [64][NF], zero past nf
+    const int n0 = *p.step + n0_off;
+    if (n0 < 0) return;
+    const int nrec_blocks = q.n_rec > 0 ? S : 0;
+    const int blk = blockIdx.x;
+    if (blk < nrec_blocks) {
+        dft_receivers(p, q, n0, kStMS, blk);
+        return;
+    }
+    const int vblk = blk - nrec_blocks;
+    const int vb = vblk % nvb;
+    const int c = (vblk / nvb) % 3;
+    const int s = vblk / (nvb * 3);
+    const long long i0 = (long long)vb * kBlock;
+    const int rows = (int)min((long long)kBlock, p.vol - i0);      // a multiple of 8 entries
+    float2 *A = p.acc + ((long long)s * 3 + c) * p.nf * p.vol + i0;
+    float2 *C = KAHAN ? p.comp + ((long long)s * 3 + c) * p.nf * p.vol + i0 : nullptr;
+    const float *ring = p.ering + (long long)s * p.ering_stride + (long long)c * p.vol + i0;
+    const uint32_t rb = (uint32_t)rows * sizeof(float), cb = (uint32_t)rows * sizeof(float2);
+    if (threadIdx.x == 0) {
+        for (int u = 0; u < kStN; ++u) mbar_init(&full[u], 1);
+        mbar_init(&abar, 1);
+    }
+    __syncthreads();
+    int issued = 0;                     // chunks issued (meaningful in thread 0)
+    auto issue = [&](int ch) {          // snapshots ch*kStG .. into stage ch % kStN
+        const int u = ch & (kStN - 1);
+        mbar_expect_tx(&full[u], kStG * rb + (ch == 0 ? (uint32_t)p.fault_tx : 0u));
+        int sl = (n0 + ch * kStG) % p.nslot;
+        for (int g = 0; g < kStG; ++g) {
+            bulk_g2s(st_s + (u * kStG + g) * kBlock, ring + (long long)sl * 3 * p.vol, rb, &full[u]);
+            sl = (sl + 1 == p.nslot) ? 0 : sl + 1;
+        }
+        issued = ch + 1;
+    };
+    if (threadIdx.x == 0) {
+        for (int ch = 0; ch < kStN; ++ch) issue(ch);
+        mbar_expect_tx(&abar, p.nf * cb * (KAHAN ? 2u : 1u));
+        for (int f = 0; f < p.nf; ++f) {
+            bulk_g2s(acc_s + f * kBlock, A + (long long)f * p.vol, cb, &abar);
+            if (KAHAN) bulk_g2s(cmp_s + f * kBlock, C + (long long)f * p.vol, cb, &abar);
+        }
+    }
+    for (int u = threadIdx.x; u < kStMS * NF; u += blockDim.x) {
+        const int m = u / NF, f = u - m * NF;
+        w_s[u] = (f < p.nf) ? p.w[(long long)(n0 + m) * p.nf + f] : make_float2(0.f, 0.f);
+    }
+    const int t2 = 2 * threadIdx.x;
+    const bool mine = t2 < rows;
+    float2 b0[NF], b1[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) b0[f] = b1[f] = make_float2(0.f, 0.f);
+    const float4 *w4 = reinterpret_cast<const float4 *>(w_s);
+    bool ok = true;
+    int ch = 0;
+    for (; ch < NCH; ++ch) {
+        const int u = ch & (kStN - 1);
+        if (ok) ok = mbar_wait_bounded(&full[u], (uint32_t)(ch / kStN) & 1u);
+        // every thread has finished chunk ch - 1: its stage takes chunk ch - 1 + kStN
+        if (__syncthreads_or(!ok)) break;
+        if (threadIdx.x == 0 && ch >= 1 && ch - 1 + kStN < NCH) issue(ch - 1 + kStN);
+        if (!mine) continue;
+        const float *sg = st_s + u * kStG * kBlock + t2;
+#pragma unroll
+        for (int g = 0; g < kStG; ++g) {
+            const float2 e = *reinterpret_cast<const float2 *>(sg + g * kBlock);
+            const int m = ch * kStG + g;
+#pragma unroll
+            for (int h = 0; h < NF / 2; ++h) {
+                const float4 w = w4[m * (NF / 2) + h];       // frequencies 2h and 2h+1
+                b0[2 * h].x = fmaf(e.x, w.x, b0[2 * h].x);
+                b0[2 * h].y = fmaf(e.x, w.y, b0[2 * h].y);
+                b0[2 * h + 1].x = fmaf(e.x, w.z, b0[2 * h + 1].x);
+                b0[2 * h + 1].y = fmaf(e.x, w.w, b0[2 * h + 1].y);
+                b1[2 * h].x = fmaf(e.y, w.x, b1[2 * h].x);
+                b1[2 * h].y = fmaf(e.y, w.y, b1[2 * h].y);
+                b1[2 * h + 1].x = fmaf(e.y, w.z, b1[2 * h + 1].x);
+                b1[2 * h + 1].y = fmaf(e.y, w.w, b1[2 * h + 1].y);
+            }
+        }
+    }
+    const bool done = (ch == NCH);
+    if (done && ok) ok = mbar_wait_bounded(&abar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) {
+            atomicOr(err, kErrFlushWait);
+            // copies issued and not consumed: chunks ch .. issued - 1 (each in its own stage), and
+            // the accumulators; a wait that already completed returns at once
+            for (int x = ch; x < issued; ++x) mbar_wait_bounded(&full[x & (kStN - 1)], (uint32_t)(x / kStN) & 1u);
+            mbar_wait_bounded(&abar, 0);
+        }
+        return;
+    }
+    if (!mine) return;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        if (f >= p.nf) break;
+        float4 a = *reinterpret_cast<const float4 *>(acc_s + f * kBlock + t2);   // entries t2, t2+1
+        if (KAHAN) {
+            float4 cc = *reinterpret_cast<const float4 *>(cmp_s + f * kBlock + t2);
+            kahan_add(a.x, cc.x, b0[f].x);
+            kahan_add(a.y, cc.y, b0[f].y);
+            kahan_add(a.z, cc.z, b1[f].x);
+            kahan_add(a.w, cc.w, b1[f].y);
+            *reinterpret_cast<float4 *>(C + (long long)f * p.vol + t2) = cc;
+        } else {
+            a.x += b0[f].x;
+            a.y += b0[f].y;
+            a.z += b1[f].x;
+            a.w += b1[f].y;
+        }
+        *reinterpret_cast<float4 *>(A + (long long)f * p.vol + t2) = a;
+    }
+}
+
+size_t stream_smem_bytes(int nf, bool kahan) {
+    return (size_t)kStN * kStG * kBlock * sizeof(float) + (size_t)nf * kBlock * sizeof(float2) * (kahan ? 2 : 1) +
+           (size_t)kStMS * nf_pad(nf) * sizeof(float2);
+}
+
 size_t bulk_smem_bytes(int ms, int nf, bool kahan) {
     return (size_t)ms * kBlock * sizeof(float) + (size_t)nf * kBlock * sizeof(float2) * (kahan ? 2 : 1) +
            (size_t)ms * nf_pad(nf) * sizeof(float2);
@@ -556,6 +709,18 @@ cudaError_t bulk_attr_ms(int bytes) {
         if (r != cudaSuccess) e = r;
     return e;
 }
+template <bool KAHAN, int NF>
+cudaError_t stream_attr(int bytes) {
+    return cudaFuncSetAttribute(k_dft_stream<KAHAN, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+template <bool KAHAN>
+void stream_go(const StepParams<float> &p, const PointParams<float> &q, int S, int n0_off, int nvb, int nblk, size_t sm,
+               int *err, cudaStream_t st) {
+    const int np = nf_pad(p.nf);
+    if (np == 2) k_dft_stream<KAHAN, 2><<<nblk, kBulkThreads, sm, st>>>(p, q, n0_off, nvb, S, err);
+    else if (np == 4) k_dft_stream<KAHAN, 4><<<nblk, kBulkThreads, sm, st>>>(p, q, n0_off, nvb, S, err);
+    else k_dft_stream<KAHAN, 8><<<nblk, kBulkThreads, sm, st>>>(p, q, n0_off, nvb, S, err);
+}
 template <bool KAHAN, int MS>
 void bulk_go(const StepParams<float> &p, const PointParams<float> &q, int S, int n0_off, int nvb, int nblk, size_t sm,
              int *err, cudaStream_t st) {
@@ -567,10 +732,13 @@ void bulk_go(const StepParams<float> &p, const PointParams<float> &q, int S, int
 }  // namespace
 
 cudaError_t prepare_bulk_flush() {
-    const int big = (int)bulk_smem_bytes(64, kMaxFreq, true);
-    cudaError_t e = bulk_attr_ms<64>(big);
-    if (e == cudaSuccess) e = bulk_attr_ms<32>(big);
+    const int big = (int)bulk_smem_bytes(32, kMaxFreq, true);
+    cudaError_t e = bulk_attr_ms<32>(big);
     if (e == cudaSuccess) e = bulk_attr_ms<16>(big);
+    const int sbig = (int)stream_smem_bytes(kMaxFreq, true);
+    for (cudaError_t r : {stream_attr<true, 2>(sbig), stream_attr<true, 4>(sbig), stream_attr<true, 8>(sbig),
+                          stream_attr<false, 2>(sbig), stream_attr<false, 4>(sbig), stream_attr<false, 8>(sbig)})
+        if (e == cudaSuccess) e = r;
     return e;
 }
 
@@ -579,9 +747,10 @@ cudaError_t launch_dft_bulk(const StepParams<float> &p, const PointParams<float>
     const int nvb = (int)((p.vol + kBlock - 1) / kBlock);
     const int nblk = nvb * 3 * S + (q.n_rec > 0 ? S : 0);
     const size_t sm = bulk_smem_bytes(cnt, p.nf, kahan);
-    if (cnt == 64) {
-        if (kahan) bulk_go<true, 64>(p, q, S, n0_off, nvb, nblk, sm, err, st);
-        else bulk_go<false, 64>(p, q, S, n0_off, nvb, nblk, sm, err, st);
+    if (cnt == 64) {                  // 64 snapshots stream through a 4-stage ring (k_dft_stream)
+        const size_t ssm = stream_smem_bytes(p.nf, kahan);
+        if (kahan) stream_go<true>(p, q, S, n0_off, nvb, nblk, ssm, err, st);
+        else stream_go<false>(p, q, S, n0_off, nvb, nblk, ssm, err, st);
     } else if (cnt == 32) {
         if (kahan) bulk_go<true, 32>(p, q, S, n0_off, nvb, nblk, sm, err, st);
         else bulk_go<false, 32>(p, q, S, n0_off, nvb, nblk, sm, err, st);

@@ -6,8 +6,9 @@ every block expect 16 bytes more than its copies bring, so that wait runs out:
 the block leaves without writing, the kernel returns, and csem_check reports
 CSEM_ERR_TIMEOUT naming the kernel family.  The context stays usable: with the
 hook off, the next run gives the results of an engine that never saw the hook,
-bit for bit.  Covered: the transform flush, the row-staged H/E step kernels and
-the fused one-pass step kernel.
+bit for bit.  Covered: the transform flush (16 snapshots held at once, and 64
+streamed through a ring of stages), the row-staged H/E step kernels and the
+fused one-pass step kernel.
 """
 import pytest
 
@@ -26,6 +27,7 @@ TIMEOUT = -6
 CASES = {
     # family: (launch configuration, steps per run, words the timeout message names)
     "flush": (dict(kz_h=2, mb_h=8, lean_h=2, kz_e=2, mb_e=8, lean_e=2, flush_mode=1, block=16), 16, "flush"),
+    "streamed flush": (dict(kz_h=2, mb_h=8, lean_h=2, kz_e=2, mb_e=8, lean_e=2, flush_mode=1, block=64), 64, "flush"),
     "row-staged": (dict(kz_h=4, mb_h=4, kz_e=4, mb_e=4, tma_h=2, tma_e=2, flush_mode=0, block=16), 2, "row-staged"),
     "one-pass": (dict(onepass=(8, 4, 4), flush_mode=0, block=16), 2, "one-pass"),
 }
