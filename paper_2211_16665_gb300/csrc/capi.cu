@@ -646,7 +646,7 @@ int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const 
         const int key[8] = {S, vol ? 1 : 0, kahan ? 1 : 0, (q.n_itaps > 0 ? 1 : 0) + 2 * fz_code(c), q.n_rec > 0 ? 1 : 0,
                             (int)sizeof(R), ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
                             ((((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e) * 25 +
-                             c->TMA_h * 5 + c->TMA_e) * 4 + c->LEAN_h * 2 + c->LEAN_e};
+                             c->TMA_h * 5 + c->TMA_e) * 16 + c->LEAN_h * 4 + c->LEAN_e};
         cudaGraphExec_t exec = nullptr;
         long long per_chunk = 0;
         TRY(chunk_graph(c, key, [&](cudaStream_t cs) {
@@ -777,7 +777,7 @@ int run_steps_es(csem_ctx *c, int S, int NR, const csem::StepParams<R> &p, const
         const int key[8] = {S, 4, fz_code(c), q.n_itaps > 0 ? 1 : 0, 1, (int)sizeof(R),
                             ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
                             ((((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e) * 25 +
-                             c->TMA_h * 5 + c->TMA_e) * 4 + c->LEAN_h * 2 + c->LEAN_e};
+                             c->TMA_h * 5 + c->TMA_e) * 16 + c->LEAN_h * 4 + c->LEAN_e};
         cudaGraphExec_t exec = nullptr;
         long long per_chunk = 0;
         TRY(chunk_graph(c, key, [&](cudaStream_t cs) {
@@ -845,7 +845,7 @@ int run_steps_vol_es(csem_ctx *c, int S, const csem::StepParams<R> &p, const cse
         const int key[8] = {S, 5, (kahan ? 1 : 0) + 2 * fz_code(c), q.n_itaps, q.n_rec > 0 ? 1 : 0, (int)sizeof(R),
                             ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
                             ((((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e) * 25 +
-                             c->TMA_h * 5 + c->TMA_e) * 4 + c->LEAN_h * 2 + c->LEAN_e};
+                             c->TMA_h * 5 + c->TMA_e) * 16 + c->LEAN_h * 4 + c->LEAN_e};
         cudaGraphExec_t exec = nullptr;
         long long per_chunk = 0;
         TRY(chunk_graph(c, key, [&](cudaStream_t cs) {
@@ -1069,8 +1069,8 @@ int run_range(csem_ctx *c, int S, int role, RoleGraph &g, const csem::StepParams
     if (full > 0 && !g.exec) {
         const int key[8] = {S, role, fz_code(c), q.n_itaps, q.n_emit, (int)sizeof(R),
                             ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
-                            (((c->fused_kz * 4 + c->VEC_h * 2 + c->VEC_e) * 25 + c->TMA_h * 5 + c->TMA_e) * 4 +
-                             c->LEAN_h * 2 + c->LEAN_e)};
+                            (((c->fused_kz * 4 + c->VEC_h * 2 + c->VEC_e) * 25 + c->TMA_h * 5 + c->TMA_e) * 16 +
+                             c->LEAN_h * 4 + c->LEAN_e)};
         TRY(chunk_graph(c, key, [&](cudaStream_t cs) {
             cudaError_t e = tap_prep<R>(c, p, S, kChunk, cs);
             for (int j = 0; j < kChunk && e == cudaSuccess; ++j) e = launch_any<R>(c, p, q, S, j, cs);
