@@ -320,7 +320,8 @@ def run_ours(args):
     fused = kms["k_step"] > 0
     st_ms = kms["k_step"] if fused else kms["k_h"] + kms["k_e"]
     lc = eng.launch_config()
-    st_name = ("k_step_fz" if lc["step"]["kernel"].startswith("fused one-pass") else "k_step") if fused else \
+    st_name = ({"fused one-pass H+E": "k_step_fz", "fused warp-specialised H+E": "k_step_ws"}.get(
+        lc["step"]["kernel"], "k_step")) if fused else \
         "+".join(f"k_{w}_{lc['step'][w]['kernel'].split()[0]}" for w in ("h", "e"))
     b_cell = stencil_bytes(wl, eng)
     nodes = (wl.nx + 1) * (wl.ny + 1) * (wl.nz + 1)

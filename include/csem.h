@@ -316,14 +316,21 @@ int csem_set_early_stop_volumes(csem_ctx *ctx, double tol, double floor_frac);
  * (may be NULL, else 4 ints) receives, for H and E, 16 * planes + blocks
  * (+ 256 for the FP32 four-cells-per-thread kernel, + 1024 * rows for the
  * bulk-copy-staged kernel, + 8192 * cells per thread for the lean kernel), then 4 * snapshots per flush + flush mode (as in
- * csem_set_launch), then the fused z blocking (0: split).  Overwrites the
+ * csem_set_launch), then the step's form: 0 split, 4/8/16 the fused z
+ * blocking, 10000 + code the one-pass kernel, 30000 + code the
+ * warp-specialised fused kernel.  Overwrites the
  * context's field state and blocks until the timing is done.
  * Errors: INVALID_ARG, CUDA. */
 int csem_autotune(csem_ctx *ctx, int n_src, int *kz_out, void *stream);
 
 /* Sets the launch configuration by hand instead of csem_autotune (tests run
  * every variant through it): cfg = {H z planes, H blocks/SM, E z planes,
- * E blocks/SM, fused z blocking (0 = split kernels), flush mode (bit 0: bulk
+ * E blocks/SM, step form (0 = split kernels; 4, 8 or 16 = the tiled fused
+ * kernel's z blocking; 10000 + planes * 100 + rows * 10 + blocks = the one-pass
+ * kernel with TMA-staged planes; 30000 + planes * 100 + rows * 10 + blocks = the
+ * warp-specialised fused kernel: producer warps compute H^{n+1/2} of the tile and
+ * its one-cell halo into shared memory, consumer warps the E step from it; rows
+ * and blocks (4,2), (4,3), (6,2), (8,1), (8,2); FP32, second order), flush mode (bit 0: bulk
  * copy, FP32 only, else register kernel; bit 1: overlapped with the next
  * block on a second stream), snapshots per flush (16, 32 or 64; the context's
  * ring of 17, 33, 65 or 129 slots must hold snapshots + 1, or 2 * snapshots + 1
@@ -354,7 +361,10 @@ int csem_set_trace(csem_ctx *ctx, double *trace_dev);
  * flush, the row-staged step kernels, the fused one-pass step) expects extra_bytes more
  * than its copies bring, so the bounded wait on it runs out after about a second: the
  * block leaves without writing results, and the next csem_check reports CSEM_ERR_TIMEOUT.
- * The copies themselves complete; nothing faults.  0 restores normal operation (the
+ * The copies themselves complete; nothing faults.  In the warp-specialised fused step,
+ * whose warps hand planes over through shared memory without copies, the producer warps
+ * skip their first arrival instead, so the consumers' bounded wait runs out (and then the
+ * producers' own).  0 restores normal operation (the
  * field state of the run that timed out is not usable).  Synchronises the device.
  * Errors: INVALID_ARG. */
 int csem_set_copy_fault(csem_ctx *ctx, int extra_bytes);

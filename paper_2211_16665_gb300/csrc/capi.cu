@@ -142,6 +142,7 @@ struct csem_ctx {
     int MB_h = 4, MB_e = 4;             // min resident blocks per SM of the compiled variant (autotuned)
     int fused_kz = 0;                   // > 0: fused H+E step with this z blocking (autotuned)
     int FZ_by = 0, FZ_mb = 4, FZ_kz = 16; // FZ_by > 0: fused one-pass FP32 step, rows per block (autotuned)
+    int FZ_ws = 0;                        // 1: the warp-specialised fused step with those shape fields
     int fault_tx = 0;                   // test hook: extra bytes the bulk-copy kernels' first barrier arm expects
     int VEC_h = 0, VEC_e = 0;           // 1: four-cells-per-thread FP32 kernels (autotuned)
     int TMA_h = 0, TMA_e = 0;           // > 0: bulk-copy-staged FP32 kernels, rows per block (autotuned)
@@ -237,7 +238,9 @@ void axis_tab(const csem_ctx *c, int a, csem::AxisTab<R> &t) {
 int lean_len(int n) { return (n + 1 + 3 + 3) / 4 * 4; }
 // The fused one-pass step's launch shape as one code (0: not selected): kz * 100 + rows * 10 + blocks;
 // csem_autotune and csem_set_launch report and take it as 10000 + that code.
-int fz_code(const csem_ctx *c) { return c->FZ_by ? c->FZ_kz * 100 + c->FZ_by * 10 + c->FZ_mb : 0; }
+int fz_code(const csem_ctx *c) {
+    return c->FZ_by ? (c->FZ_ws ? 20000 : 0) + c->FZ_kz * 100 + c->FZ_by * 10 + c->FZ_mb : 0;
+}
 // Per-axis widths of the fused one-pass step: h (primal, half nodes) and s = h[i-1] + h[i] at the
 // nodes (the outer nodes take their one width), each padded to lean_len(n) floats.
 int upload_geo_tables(csem_ctx *c) {
@@ -435,7 +438,7 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
     p.LEAN_e = c->LEAN_e;
     p.lx = p.ly = p.lz = csem::AxisTab<R>{};
     p.lzero = nullptr;
-    p.FZ_by = 0; p.FZ_mb = 4; p.FZ_kz = 16;
+    p.FZ_by = 0; p.FZ_mb = 4; p.FZ_kz = 16; p.FZ_ws = 0;
     p.qh = p.qv = nullptr;
     p.gx = p.gy = p.gz = csem::GeoTab{nullptr, nullptr};
     p.k2w0dt = 0.f;
@@ -455,7 +458,7 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
         p.inc = c->d_inc;
         p.tapk = c->d_tapk;
         if (c->d_q && c->d_tabG) {
-            p.FZ_by = c->FZ_by; p.FZ_mb = c->FZ_mb; p.FZ_kz = c->FZ_kz;
+            p.FZ_by = c->FZ_by; p.FZ_mb = c->FZ_mb; p.FZ_kz = c->FZ_kz; p.FZ_ws = c->FZ_ws;
             p.qh = c->d_q;
             p.qv = c->vti ? c->d_q + c->vol : c->d_q;
             const csem::GeoTab *g[3] = {&p.gx, &p.gy, &p.gz};
@@ -1350,16 +1353,21 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
             p.VEC_h = c->VEC_h; p.VEC_e = c->VEC_e;
             p.TMA_h = c->TMA_h; p.TMA_e = c->TMA_e;
             p.LEAN_h = c->LEAN_h; p.LEAN_e = c->LEAN_e;
-            struct Cand { int f, by, mb, kz; };
-            std::vector<Cand> cands = {{0, 0, 4, 16}, {4, 0, 4, 16}, {8, 0, 4, 16}, {16, 0, 4, 16}};
+            struct Cand { int f, by, mb, kz, ws; };
+            std::vector<Cand> cands = {{0, 0, 4, 16, 0}, {4, 0, 4, 16, 0}, {8, 0, 4, 16, 0}, {16, 0, 4, 16, 0}};
             if (sizeof(R) == 4 && c->d_q && c->nx % 2 == 0) {
                 const int bm[4][2] = {{4, 4}, {4, 6}, {8, 2}, {8, 3}};
                 for (const auto &b : bm)
-                    for (int kz : {8, 16, 32, 64}) cands.push_back({0, b[0], b[1], kz});
+                    for (int kz : {8, 16, 32, 64}) cands.push_back({0, b[0], b[1], kz, 0});
+                if (c->d_cEm && c->d_psi) {        // the warp-specialised fused step
+                    const int wm[5][2] = {{4, 2}, {4, 3}, {6, 2}, {8, 1}, {8, 2}};
+                    for (const auto &b : wm)
+                        for (int kz : {8, 16, 32, 64}) cands.push_back({0, b[0], b[1], kz, 1});
+                }
             }
             auto time_cand = [&](const Cand &cd, float *t) -> int {
                 p.fused_kz = cd.f;
-                p.FZ_by = cd.by; p.FZ_mb = cd.mb; p.FZ_kz = cd.kz;
+                p.FZ_by = cd.by; p.FZ_mb = cd.mb; p.FZ_kz = cd.kz; p.FZ_ws = cd.ws;
                 for (int j = 0; j < 3; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, 5));
                 CK(cudaEventRecord(e0, st));
                 const int reps = 20;
@@ -1388,7 +1396,7 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
             std::sort(tf, tf + 3);
             if (!(tf[1] < ts[1])) bc = cands[0];
             c->fused_kz = bc.f;
-            c->FZ_by = bc.by; c->FZ_mb = bc.mb; c->FZ_kz = bc.kz;
+            c->FZ_by = bc.by; c->FZ_mb = bc.mb; c->FZ_kz = bc.kz; c->FZ_ws = bc.ws;
             p.fused_kz = 0;
             p.FZ_by = 0;
         }
@@ -1405,7 +1413,7 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
             p.acc = vol_tmp;
             p.comp = c->kahan ? (R2 *)c->d_comp : nullptr;
             p.fused_kz = c->fused_kz;
-            p.FZ_by = c->FZ_by; p.FZ_mb = c->FZ_mb; p.FZ_kz = c->FZ_kz;
+            p.FZ_by = c->FZ_by; p.FZ_mb = c->FZ_mb; p.FZ_kz = c->FZ_kz; p.FZ_ws = c->FZ_ws;
             const bool kahan = c->kahan != 0;
             double best = 1e30;
             int bm = 0, bM = 16;
@@ -1745,7 +1753,7 @@ int csem_check(csem_ctx *c, void *stream) {
         auto add = [&](const char *w) { who += (who.empty() ? "" : " and ") + std::string(w); };
         if (bad & csem::kErrFlushWait) add("a bulk-copy transform flush");
         if (bad & csem::kErrStagedWait) add("a row-staged H/E step kernel");
-        if (bad & csem::kErrOnepassWait) add("the fused one-pass step kernel");
+        if (bad & csem::kErrOnepassWait) add("a fused step kernel (one-pass or warp-specialised)");
         return fail(CSEM_ERR_TIMEOUT, who + " gave up waiting for its bulk copies (its results were not written)");
     }
     if (bad & csem::kErrNonfinite) return fail(CSEM_ERR_NONFINITE, "a resistivity was non-positive or non-finite");
@@ -1869,11 +1877,16 @@ long long csem_launch_count(void) { return csem::g_launches.load(); }
 int csem_set_launch(csem_ctx *c, const int *cfg) {
     if (!c || !cfg) return fail(CSEM_ERR_INVALID_ARG, "NULL argument");
     const int kzh = cfg[0], mbh = cfg[1], kze = cfg[2], mbe = cfg[3], fm = cfg[5], M = cfg[6];
-    // cfg[4] >= 10000: the fused one-pass step, 10000 + planes * 100 + rows * 10 + blocks
-    const int fz = cfg[4] >= 10000 ? cfg[4] - 10000 : 0, fkz = fz ? 0 : cfg[4];
+    // cfg[4] >= 10000: the fused one-pass step, 10000 + planes * 100 + rows * 10 + blocks;
+    // cfg[4] >= 30000: the warp-specialised fused step, 30000 + the same code
+    const int ws = cfg[4] >= 30000 ? 1 : 0;
+    const int fz = cfg[4] >= 10000 ? cfg[4] - (ws ? 30000 : 10000) : 0, fkz = fz ? 0 : cfg[4];
     const int fz_kz = fz / 100, fz_by = (fz / 10) % 10, fz_mb = fz % 10;
-    if (fz && (c->precision != 32 || c->order != 2 || !c->d_q || c->nx % 2 != 0 || !csem::fz_supported(fz_by, fz_mb, fz_kz)))
+    if (fz && !ws && (c->precision != 32 || c->order != 2 || !c->d_q || c->nx % 2 != 0 || !csem::fz_supported(fz_by, fz_mb, fz_kz)))
         return fail(CSEM_ERR_INVALID_ARG, "fused one-pass step: FP32, second order, nx even, rows/blocks (4,4), (4,6), (8,2) or (8,3), 2-99 planes");
+    if (ws && (c->precision != 32 || c->order != 2 || !c->d_q || !c->d_cEm || !c->d_psi || c->nx % 2 != 0 ||
+               !csem::ws_supported(fz_by, fz_mb, fz_kz)))
+        return fail(CSEM_ERR_INVALID_ARG, "warp-specialised fused step: FP32, second order, nx a multiple of 4, rows/blocks (4,2), (4,3), (6,2), (8,1) or (8,2), 2-99 planes");
     const int vh = cfg[7], ve = cfg[8], th = cfg[9], te = cfg[10], lh = cfg[11], le = cfg[12];
     if (c->order == 4) {   // fourth order: its own kernels, the lean FP32 ones (2 cells) per half
         if (fkz || fz || vh || ve || th || te)
@@ -1917,7 +1930,7 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
     CK(cudaDeviceSynchronize());
     c->KZ_h = kzh; c->MB_h = mbh; c->KZ_e = kze; c->MB_e = mbe;
     c->fused_kz = fkz; c->flush_mode = fm; c->M = M;
-    c->FZ_by = fz_by; c->FZ_mb = fz ? fz_mb : 4; c->FZ_kz = fz ? fz_kz : 16;
+    c->FZ_by = fz_by; c->FZ_mb = fz ? fz_mb : 4; c->FZ_kz = fz ? fz_kz : 16; c->FZ_ws = ws;
     c->VEC_h = vh; c->VEC_e = ve;
     c->TMA_h = th; c->TMA_e = te;
     c->LEAN_h = lh; c->LEAN_e = le;

@@ -122,6 +122,7 @@ struct StepParams {
     // blocks per SM, FZ_kz planes per z block; q = V sigma per cell on the lattice (qv = qh
     // unless the medium is VTI), per-axis widths, 2 w0 dt
     int FZ_by, FZ_mb, FZ_kz;
+    int FZ_ws;                     // 1: the warp-specialised fused kernel with the same shape fields
     const float *qh, *qv;
     GeoTab gx, gy, gz;
     float k2w0dt;
@@ -201,6 +202,10 @@ cudaError_t prepare_fused_all();
 // fused one-pass FP32 step (kern_fz.cu): nx even, (by, mb) in {(4,4), (4,6), (8,2), (8,3)}, kz planes per z block
 cudaError_t launch_step_fz(const StepParams<float> &p, int S, int jstep, cudaStream_t st);
 bool fz_supported(int by, int mb, int kz);
+// warp-specialised fused FP32 step (kern_fz.cu, FZ_ws = 1): nx even, (by, mb) in {(4,2), (4,3), (6,2),
+// (8,1), (8,2)}, kz planes per z block; reads the masked dt/eps and the slab CPML memory
+cudaError_t launch_step_ws(const StepParams<float> &p, int S, int jstep, cudaStream_t st);
+bool ws_supported(int by, int mb, int kz);
 // FP32 H / E kernels with four cells per thread (kern_vec.cu), kz in {1,2,4,8}, mb in {4,6}
 // lean FP32 H / E kernels (kern_lean.cu), nx % 4 == 0, w (cells per thread) in {1,2}, kz in {1,2,4},
 // mb (resident 128-thread blocks per SM) in {6,8} for w = 1 and {4,6,8} for w = 2

@@ -439,6 +439,308 @@ __global__ void __launch_bounds__(32 * (BY + 1), MINB)
     }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised fused step (Sec. 2, Eq. 4 with the unsplit CPML): the H
+// half-step and the E step of one step in one kernel, each field read from DRAM
+// once, with the two halves on different warps.
+//
+// A block owns 64 cells (x) by BY rows (y) and marches a z block of KZ planes;
+// every thread of a row warp owns two consecutive cells (i, i+1).  Its warps:
+//  * BY + 1 producer warps: H^{n+1/2} of rows j0-1 .. j0+BY-1 from E^n and
+//    H^{n-1/2} in global memory (L1/L2 serve the neighbours), written to a
+//    shared plane buffer and, for the block's own rows and planes, to the other
+//    H buffer in global memory.  Row j0-1 belongs to the block below in y: it is
+//    recomputed here, not exchanged, so no block waits on another; H and the CPML
+//    memory of the H update are therefore double buffered (step n reads the
+//    buffer of parity n, writes the other), as for k_step_fz;
+//  * one column warp: Hy and Hz of column i0-1 (lane l: row j0+l), recomputed
+//    the same way;
+//  * BY consumer warps: E^{n+1} of rows j0 .. j0+BY-1 from E^n (just read by the
+//    producers: an L1 hit), dt/eps with the PEC edges zeroed, H^{n+1/2} of the
+//    plane from the shared buffer (i-1 and j-1 neighbours included) and of plane
+//    k-1 from registers; the CPML memory of the E update in place (one owner).
+// The producers fill one of two plane buffers while the consumers drain the
+// other: per buffer a "full" mbarrier (every producer thread arrives) and an
+// "empty" mbarrier (every consumer thread arrives after reading, only when the
+// producers will refill it), every wait bounded (about a second); a thread that
+// gives up raises the one-pass bit of *err and leaves its loop, so the others'
+// waits run out too and the kernel returns (the copy-fault test hook makes the
+// producers skip their first arrival).  A z block starting at k0 > 0 first
+// produces plane k0-1 (not stored) for the consumers' k-1 values.  blockIdx.x
+// runs over (x tile, source) with the source fastest.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kWsW = 68;           // shared row: column c holds cell i0 - 2 + c (i0-1 at 1, i0 at 2)
+
+__device__ __forceinline__ void ws_bar_init(uint64_t *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void ws_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(b)) : "memory");
+}
+}  // namespace
+
+template <int BY, int MINB>
+__global__ void __launch_bounds__(32 * (2 * BY + 2), MINB)
+    k_step_ws(const StepParams<float> p, const int jstep, const int KZ, const int S) {
+    constexpr int NB = 2, RW = BY + 1, PLF = 3 * RW * kWsW;
+    __shared__ __align__(16) float sH[NB * PLF];
+    __shared__ __align__(8) uint64_t full[NB], empty[NB];
+    const int w = threadIdx.y, lane = threadIdx.x;
+    const int tid = w * 32 + lane;
+    const int s = blockIdx.x % S;
+    const int i0 = (blockIdx.x / S) * 64, j0 = blockIdx.y * BY;
+    const int i = i0 + 2 * lane;
+    const int k0 = blockIdx.z * KZ;
+    const int k1 = min(k0 + KZ, p.nz);
+    const int kstart = (k0 > 0) ? k0 - 1 : 0;
+    const int T = k1 - kstart;                     // planes produced (the first is k0-1 when k0 > 0)
+    constexpr int NPROD = 32 * (BY + 2), NCONS = 32 * BY;
+    if (tid == 0) {
+        for (int b = 0; b < NB; ++b) {
+            ws_bar_init(&full[b], NPROD);
+            ws_bar_init(&empty[b], NCONS);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int u = tid; u < NB * PLF; u += 32 * (2 * BY + 2)) sH[u] = 0.f;   // cells nobody computes stay zero
+    __syncthreads();
+
+    const int n = *p.step + jstep;
+    const int vol = (int)p.vol, plane = (int)p.plane, pitch = p.pitch, NY = p.NY;
+    const int nx = p.nx, ny = p.ny, npml = p.npml, np2 = 2 * npml;
+    const long long sb = (long long)s * p.ering_stride;
+    const float *__restrict__ E = p.ering + sb + (long long)(n % p.nslot) * 3 * p.vol;      // E^n
+    const int hin = (n & 1) ? 4 : 0, hout = 4 - hin;
+    float *P = p.psi + (long long)s * p.psi_stride;
+    float *psx = P, *psy = P + 6 * p.sx, *psz = P + 6 * p.sx + 6 * p.sy;
+    const long long sx = p.sx, sy = p.sy, sz = p.sz;
+    const float cH = p.cH;
+    bool ok = true;
+
+    if (w <= BY) {
+        // ---- producer: H^{n+1/2} of row j0-1+w
+        const float *__restrict__ Hi = ((n & 1) ? p.H2 : p.H) + (long long)s * 3 * vol;
+        float *__restrict__ Ho = ((n & 1) ? p.H : p.H2) + (long long)s * 3 * vol;
+        const int j = j0 - 1 + w;
+        const bool act = (i < nx) && (j >= 0) && (j < ny);
+        const bool own = (w >= 1);
+        const int ic = act ? i : 0, jc = act ? j : 0;
+        const XH xh = xh_of(p, ic);
+        const YH yh = yh_of(p, jc);
+        const int o = w * kWsW + 2 + 2 * lane;     // shared offset of cell i in row w
+        int idx = kstart * plane + jc * pitch + ic;
+        float2 ex = act ? ld2(E + idx) : f2(0.f, 0.f), ey = act ? ld2(E + vol + idx) : f2(0.f, 0.f);
+        for (int t = 0; t < T; ++t, idx += plane) {
+            const int k = kstart + t, b = t & 1;
+            // H^{n+1/2} of the plane in registers first (its loads need no buffer), then the wait
+            // for the buffer, so the wait overlaps the loads
+            float2 hx = f2(0.f, 0.f), hy = hx, hz = hx;
+            if (act) {
+                const float2 ez = ld2(E + 2 * vol + idx);
+                const float2 exk = ld2(E + idx + plane), eyk = ld2(E + vol + idx + plane);
+                const float ezR = __ldg(E + 2 * vol + idx + 2), eyR = __ldg(E + vol + idx + 2);
+                const float2 exU = ld2(E + idx + pitch), ezU = ld2(E + 2 * vol + idx + pitch);
+                const float ihz = __ldg(p.lz.ih_h + k);
+                float2 dEz_dy = dsc(ezU, ez, yh.ih), dEx_dy = dsc(exU, ex, yh.ih);
+                float2 dEy_dz = dsc(eyk, ey, ihz), dEx_dz = dsc(exk, ex, ihz);
+                float2 dEz_dx = dsc(f2(ez.y, ezR), ez, xh.ih), dEy_dx = dsc(f2(ey.y, eyR), ey, xh.ih);
+                const bool wr = own && (k >= k0);
+                if (yh.s >= 0) {
+                    const int po = (k * np2 + yh.s) * pitch + i;
+                    float2 q0 = ld2(psy + hin * sy + po), q1 = ld2(psy + (hin + 1) * sy + po);
+                    rec2(q0, dEz_dy, yh.b, yh.a);
+                    rec2(q1, dEx_dy, yh.b, yh.a);
+                    if (wr) { st2(psy + hout * sy + po, q0); st2(psy + (hout + 1) * sy + po, q1); }
+                }
+                const int szh = slab_half(k, p.nz, npml);
+                if (szh >= 0) {
+                    const float bz = __ldg(p.lz.b_h + k), az = __ldg(p.lz.a_h + k);
+                    const int po = (szh * NY + j) * pitch + i;
+                    float2 q0 = ld2(psz + hin * sz + po), q1 = ld2(psz + (hin + 1) * sz + po);
+                    rec2(q0, dEy_dz, bz, az);
+                    rec2(q1, dEx_dz, bz, az);
+                    if (wr) { st2(psz + hout * sz + po, q0); st2(psz + (hout + 1) * sz + po, q1); }
+                }
+                if (xh.s0 >= 0 || xh.s1 >= 0) {
+                    const int ro = (k * NY + j) * np2;
+                    if (xh.s0 >= 0) {
+                        float q0 = psx[hin * sx + ro + xh.s0], q1 = psx[(hin + 1) * sx + ro + xh.s0];
+                        rec1(q0, dEz_dx.x, xh.b0, xh.a0);
+                        rec1(q1, dEy_dx.x, xh.b0, xh.a0);
+                        if (wr) { psx[hout * sx + ro + xh.s0] = q0; psx[(hout + 1) * sx + ro + xh.s0] = q1; }
+                    }
+                    if (xh.s1 >= 0) {
+                        float q0 = psx[hin * sx + ro + xh.s1], q1 = psx[(hin + 1) * sx + ro + xh.s1];
+                        rec1(q0, dEz_dx.y, xh.b1, xh.a1);
+                        rec1(q1, dEy_dx.y, xh.b1, xh.a1);
+                        if (wr) { psx[hout * sx + ro + xh.s1] = q0; psx[(hout + 1) * sx + ro + xh.s1] = q1; }
+                    }
+                }
+                hx = hupd(ld2(Hi + idx), cH, dEz_dy, dEy_dz);
+                hy = hupd(ld2(Hi + vol + idx), cH, dEx_dz, dEz_dx);
+                hz = hupd(ld2(Hi + 2 * vol + idx), cH, dEy_dx, dEx_dy);
+                if (wr) {
+                    st2(Ho + idx, hx);
+                    st2(Ho + vol + idx, hy);
+                    st2(Ho + 2 * vol + idx, hz);
+                }
+                ex = exk;
+                ey = eyk;
+            }
+            if (t >= NB && ok) ok = mbar_wait_bounded(&empty[b], (uint32_t)((t / NB - 1) & 1));
+            if (!ok) break;
+            if (act) {
+                float *sb_ = sH + b * PLF;
+                st2(sb_ + o, hx);
+                st2(sb_ + RW * kWsW + o, hy);
+                st2(sb_ + 2 * RW * kWsW + o, hz);
+            }
+            if (!(t == 0 && p.fault_tx)) ws_arrive(&full[b]);   // test hook: the first arrival never comes
+        }
+    } else if (w == BY + 1) {
+        // ---- column warp: Hy, Hz of cell i0-1 in row j0+lane (CPML memory read only)
+        const float *__restrict__ Hi = ((n & 1) ? p.H2 : p.H) + (long long)s * 3 * vol;
+        const int ci = i0 - 1, cj = j0 + lane;
+        const bool act = (lane < BY) && (i0 > 0) && (cj < ny);
+        const int cic = act ? ci : 0, cjc = act ? cj : 0;
+        const float ihx = __ldg(p.lx.ih_h + cic), ihy = __ldg(p.ly.ih_h + cjc);
+        const int sxh = slab_half(cic, nx, npml), syh = slab_half(cjc, ny, npml);
+        const float bx = act && sxh >= 0 ? __ldg(p.lx.b_h + cic) : 0.f, ax = act && sxh >= 0 ? __ldg(p.lx.a_h + cic) : 0.f;
+        const float by = act && syh >= 0 ? __ldg(p.ly.b_h + cjc) : 0.f, ay = act && syh >= 0 ? __ldg(p.ly.a_h + cjc) : 0.f;
+        const int co = (1 + lane) * kWsW + 1;
+        int idx = kstart * plane + cjc * pitch + cic;
+        for (int t = 0; t < T; ++t, idx += plane) {
+            const int k = kstart + t, b = t & 1;
+            float hy = 0.f, hz = 0.f;
+            if (act) {
+                const float ihz = __ldg(p.lz.ih_h + k);
+                const float exc = __ldg(E + idx);
+                float d_xz = (__ldg(E + idx + plane) - exc) * ihz;
+                float d_zx = (__ldg(E + 2 * vol + idx + 1) - __ldg(E + 2 * vol + idx)) * ihx;
+                float d_yx = (__ldg(E + vol + idx + 1) - __ldg(E + vol + idx)) * ihx;
+                float d_xy = (__ldg(E + idx + pitch) - exc) * ihy;
+                const int szh = slab_half(k, p.nz, npml);
+                if (szh >= 0) {
+                    const float bz = __ldg(p.lz.b_h + k), az = __ldg(p.lz.a_h + k);
+                    d_xz += bz * psz[(hin + 1) * sz + (szh * NY + cj) * pitch + ci] + az * d_xz;
+                }
+                if (sxh >= 0) {
+                    const int po = (k * NY + cj) * np2 + sxh;
+                    d_zx += bx * psx[hin * sx + po] + ax * d_zx;
+                    d_yx += bx * psx[(hin + 1) * sx + po] + ax * d_yx;
+                }
+                if (syh >= 0) d_xy += by * psy[(hin + 1) * sy + (k * np2 + syh) * pitch + ci] + ay * d_xy;
+                hy = __ldg(Hi + vol + idx) - cH * (d_xz - d_zx);
+                hz = __ldg(Hi + 2 * vol + idx) - cH * (d_yx - d_xy);
+            }
+            if (t >= NB && ok) ok = mbar_wait_bounded(&empty[b], (uint32_t)((t / NB - 1) & 1));
+            if (!ok) break;
+            if (act) {
+                float *sb_ = sH + b * PLF;
+                sb_[RW * kWsW + co] = hy;
+                sb_[2 * RW * kWsW + co] = hz;
+            }
+            if (!(t == 0 && p.fault_tx)) ws_arrive(&full[b]);   // test hook: the first arrival never comes
+        }
+    } else {
+        // ---- consumer: E^{n+1} of row j0 + r - 1
+        const int r = w - BY - 1;                  // shared row of the thread's cells (1 .. BY)
+        const int j = j0 + r - 1;
+        const bool act = (i < nx) && (j < ny);
+        const int ic = act ? i : 0, jc = act ? j : 0;
+        float *__restrict__ En = p.ering + sb + (long long)((n + 1) % p.nslot) * 3 * p.vol;
+        const float2 ihxn = ld2(p.lx.ih_n + ic);
+        const int sxn0 = slab_node(ic, nx, npml), sxn1 = slab_node(ic + 1, nx, npml);
+        const float ihyn = __ldg(p.ly.ih_n + jc), byn = __ldg(p.ly.b_n + jc), ayn = __ldg(p.ly.a_n + jc);
+        const int syn = slab_node(jc, ny, npml);
+        const bool taps = act && p.colmap && p.inc && p.tflag[s * p.tflag_stride + jc * p.nseg + (ic >> 5)];
+        const float *__restrict__ cE = p.cEm;
+        const int o = r * kWsW + 2 + 2 * lane;
+        float2 hxm = f2(0.f, 0.f), hym = f2(0.f, 0.f);   // H^{n+1/2} of plane k-1 at the thread's cells
+        int idx = kstart * plane + jc * pitch + ic;
+        for (int t = 0; t < T; ++t, idx += plane) {
+            const int k = kstart + t, b = t & 1;
+            const bool upd = act && (k >= k0);
+            // the values that do not depend on the plane's H first, so their loads overlap the wait
+            float2 ex = f2(0.f, 0.f), ey = ex, ez = ex, c0 = ex, c1 = ex, c2 = ex;
+            if (upd) {
+                ex = ld2(E + idx); ey = ld2(E + vol + idx); ez = ld2(E + 2 * vol + idx);
+                c0 = ld2(cE + idx); c1 = ld2(cE + vol + idx); c2 = ld2(cE + 2 * vol + idx);
+            }
+            if (ok) ok = mbar_wait_bounded(&full[b], (uint32_t)((t / NB) & 1));
+            if (!ok) break;
+            const float *sb_ = sH + b * PLF;
+            const float *SX = sb_, *SY = sb_ + RW * kWsW, *SZ = sb_ + 2 * RW * kWsW;
+            const float2 hxn = ld2(SX + o), hyn = ld2(SY + o), hzn = ld2(SZ + o);
+            const float hzL = SZ[o - 1], hyL = SY[o - 1];
+            const float2 hzD = ld2(SZ + o - kWsW), hxD = ld2(SX + o - kWsW);
+            if (t + NB < T) ws_arrive(&empty[b]);
+            if (!upd) {                            // plane k0-1: only its H is needed
+                hxm = hxn; hym = hyn;
+                continue;
+            }
+            const float ihz = __ldg(p.lz.ih_n + k);
+            float2 dHz_dy = dsc(hzn, hzD, ihyn), dHy_dz = dsc(hyn, hym, ihz);
+            float2 dHx_dz = dsc(hxn, hxm, ihz), dHz_dx = dsc(hzn, f2(hzL, hzn.x), ihxn);
+            float2 dHy_dx = dsc(hyn, f2(hyL, hyn.x), ihxn), dHx_dy = dsc(hxn, hxD, ihyn);
+            if (syn >= 0) {
+                const int po = (k * np2 + syn) * pitch + i;
+                float2 q2 = ld2(psy + 2 * sy + po), q3 = ld2(psy + 3 * sy + po);
+                rec2(q2, dHz_dy, byn, ayn);
+                rec2(q3, dHx_dy, byn, ayn);
+                st2(psy + 2 * sy + po, q2);
+                st2(psy + 3 * sy + po, q3);
+            }
+            const int szn = slab_node(k, p.nz, npml);
+            if (szn >= 0) {
+                const float bz = __ldg(p.lz.b_n + k), az = __ldg(p.lz.a_n + k);
+                const int po = (szn * NY + j) * pitch + i;
+                float2 q2 = ld2(psz + 2 * sz + po), q3 = ld2(psz + 3 * sz + po);
+                rec2(q2, dHy_dz, bz, az);
+                rec2(q3, dHx_dz, bz, az);
+                st2(psz + 2 * sz + po, q2);
+                st2(psz + 3 * sz + po, q3);
+            }
+            if (sxn0 >= 0 || sxn1 >= 0) {
+                const int ro = (k * NY + j) * np2;
+                if (sxn0 >= 0) {
+                    const float bb = __ldg(p.lx.b_n + i), aa = __ldg(p.lx.a_n + i);
+                    float q2 = psx[2 * sx + ro + sxn0], q3 = psx[3 * sx + ro + sxn0];
+                    rec1(q2, dHz_dx.x, bb, aa);
+                    rec1(q3, dHy_dx.x, bb, aa);
+                    psx[2 * sx + ro + sxn0] = q2;
+                    psx[3 * sx + ro + sxn0] = q3;
+                }
+                if (sxn1 >= 0) {
+                    const float bb = __ldg(p.lx.b_n + i + 1), aa = __ldg(p.lx.a_n + i + 1);
+                    float q2 = psx[2 * sx + ro + sxn1], q3 = psx[3 * sx + ro + sxn1];
+                    rec1(q2, dHz_dx.y, bb, aa);
+                    rec1(q3, dHy_dx.y, bb, aa);
+                    psx[2 * sx + ro + sxn1] = q2;
+                    psx[3 * sx + ro + sxn1] = q3;
+                }
+            }
+            float2 exn = f2(ex.x + c0.x * (dHz_dy.x - dHy_dz.x), ex.y + c0.y * (dHz_dy.y - dHy_dz.y));
+            float2 eyn = f2(ey.x + c1.x * (dHx_dz.x - dHz_dx.x), ey.y + c1.y * (dHx_dz.y - dHz_dx.y));
+            float2 ezn = f2(ez.x + c2.x * (dHy_dx.x - dHx_dy.x), ez.y + c2.y * (dHy_dx.y - dHx_dy.y));
+            if (taps) {
+                const int2 *cm = p.colmap + (long long)s * p.colmap_stride + j * pitch + i;
+                const int *tk = p.tapk + (long long)s * p.itap_stride;
+                const float *inc = p.inc + ((long long)jstep * S + s) * p.inc_ntl;
+                const int2 m0 = __ldg(cm), m1 = __ldg(cm + 1);
+                if (m0.y) { const float3 a = taps_at(tk, inc, k, m0); exn.x += a.x; eyn.x += a.y; ezn.x += a.z; }
+                if (m1.y) { const float3 a = taps_at(tk, inc, k, m1); exn.y += a.x; eyn.y += a.y; ezn.y += a.z; }
+            }
+            st2(En + idx, exn);
+            st2(En + vol + idx, eyn);
+            st2(En + 2 * vol + idx, ezn);
+            hxm = hxn; hym = hyn;
+        }
+    }
+    if (!ok) atomicOr(p.err, kErrOnepassWait);
+}
+
 // V sigma of every cell on the lattice (zero off the cells), sigma_h into qh and,
 // for a VTI medium, sigma_v into qv: the per-cell material value of k_step_fz.
 __global__ void k_qcell(const GeoD g, const float *__restrict__ rho, const float *__restrict__ rho_z,
@@ -522,6 +824,31 @@ cudaError_t go_fz(const StepParams<float> &p, int S, int jstep, cudaStream_t st)
     return cudaSuccess;
 }
 }  // namespace
+
+template <int BY, int MB>
+void go_ws(const StepParams<float> &p, int S, int jstep, cudaStream_t st) {
+    const int kz = p.FZ_kz;
+    const dim3 grid((unsigned)(((p.nx / 2 + 31) / 32) * S), (unsigned)((p.ny + BY - 1) / BY),
+                    (unsigned)((p.nz + kz - 1) / kz));
+    k_step_ws<BY, MB><<<grid, dim3(32, 2 * BY + 2), 0, st>>>(p, jstep, kz, S);
+}
+
+bool ws_supported(int by, int mb, int kz) {
+    return ((by == 4 && (mb == 2 || mb == 3)) || (by == 6 && mb == 2) || (by == 8 && (mb == 1 || mb == 2))) &&
+           kz >= 2 && kz <= 256;
+}
+
+cudaError_t launch_step_ws(const StepParams<float> &p, int S, int jstep, cudaStream_t st) {
+    if (p.nx % 2 != 0 || !p.cEm || !p.lx.ih_h || !p.err || !p.H2 || !p.psi || !ws_supported(p.FZ_by, p.FZ_mb, p.FZ_kz))
+        return cudaErrorInvalidValue;
+    if (p.FZ_by == 4 && p.FZ_mb == 2) go_ws<4, 2>(p, S, jstep, st);
+    else if (p.FZ_by == 4 && p.FZ_mb == 3) go_ws<4, 3>(p, S, jstep, st);
+    else if (p.FZ_by == 6 && p.FZ_mb == 2) go_ws<6, 2>(p, S, jstep, st);
+    else if (p.FZ_by == 8 && p.FZ_mb == 1) go_ws<8, 1>(p, S, jstep, st);
+    else go_ws<8, 2>(p, S, jstep, st);
+    g_launches++;
+    return cudaGetLastError();
+}
 
 bool fz_supported(int by, int mb, int kz) {
     return ((by == 4 && (mb == 4 || mb == 6)) || (by == 8 && (mb == 2 || mb == 3))) && kz >= 2 && kz <= 256;

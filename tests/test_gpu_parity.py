@@ -122,6 +122,8 @@ LAUNCH_VARIANTS = [
     dict(onepass=(16, 8, 2), flush_mode=3, block=16),
     dict(onepass=(5, 4, 6), flush_mode=0, block=64),
     dict(onepass=(64, 8, 3), flush_mode=1, block=16),
+    dict(wspec=(8, 4, 3), flush_mode=1, block=32),
+    dict(wspec=(16, 8, 2), flush_mode=3, block=16),
 ]
 
 LEAN_VARIANTS = [
@@ -134,6 +136,11 @@ LEAN_VARIANTS = [
     dict(onepass=(3, 8, 2), flush_mode=3, block=32),
     dict(onepass=(16, 4, 6), flush_mode=0, block=16),
     dict(onepass=(44, 8, 3), flush_mode=1, block=64),
+    dict(wspec=(8, 4, 3), flush_mode=1, block=16),
+    dict(wspec=(3, 4, 2), flush_mode=3, block=32),
+    dict(wspec=(16, 6, 2), flush_mode=0, block=16),
+    dict(wspec=(44, 8, 1), flush_mode=1, block=64),
+    dict(wspec=(5, 8, 2), flush_mode=1, block=16),
 ]
 
 
@@ -214,6 +221,16 @@ def test_onepass_step_refused_where_it_does_not_apply():
     eng.set_launch(onepass=(8, 8, 3))
     assert eng.launch_config()["step"] == {"kernel": "fused one-pass H+E", "z_planes": 8, "rows_per_block": 8,
                                            "blocks_per_sm": 3}
+    for bad in ((8, 4, 4), (8, 6, 3), (1, 4, 3), (8, 2, 2)):
+        with pytest.raises(CsemError):
+            eng.set_launch(wspec=bad)
+    eng.set_launch(wspec=(16, 6, 2))
+    assert eng.launch_config()["step"] == {"kernel": "fused warp-specialised H+E", "z_planes": 16,
+                                           "rows_per_block": 6, "blocks_per_sm": 2}
+    eng.close()
+    eng = Engine.from_workload(box, precision=64, autotune=False)
+    with pytest.raises(CsemError):
+        eng.set_launch(wspec=(8, 4, 3))
     eng.close()
 
 

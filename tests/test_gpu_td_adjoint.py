@@ -83,6 +83,8 @@ TD_VARIANTS = [
     dict(kz_h=8, mb_h=4, kz_e=2, mb_e=4),
     dict(onepass=(8, 4, 4)),
     dict(onepass=(16, 8, 3)),
+    dict(wspec=(8, 4, 3)),
+    dict(wspec=(16, 8, 2)),
 ]
 
 

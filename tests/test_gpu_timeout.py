@@ -8,7 +8,8 @@ CSEM_ERR_TIMEOUT naming the kernel family.  The context stays usable: with the
 hook off, the next run gives the results of an engine that never saw the hook,
 bit for bit.  Covered: the transform flush (16 snapshots held at once, and 64
 streamed through a ring of stages), the row-staged H/E step kernels and the
-fused one-pass step kernel.
+fused one-pass step kernel; and the warp-specialised fused step, whose producer
+warps skip their first hand-over under the hook.
 """
 import pytest
 
@@ -30,6 +31,7 @@ CASES = {
     "streamed flush": (dict(kz_h=2, mb_h=8, lean_h=2, kz_e=2, mb_e=8, lean_e=2, flush_mode=1, block=64), 64, "flush"),
     "row-staged": (dict(kz_h=4, mb_h=4, kz_e=4, mb_e=4, tma_h=2, tma_e=2, flush_mode=0, block=16), 2, "row-staged"),
     "one-pass": (dict(onepass=(8, 4, 4), flush_mode=0, block=16), 2, "one-pass"),
+    "warp-specialised": (dict(wspec=(8, 4, 3), flush_mode=0, block=16), 2, "warp-specialised"),
 }
 
 

@@ -76,11 +76,14 @@ def test_vti_forward_adjoint_gradient_match_oracle(case, precision):
     eng.close()
 
 
-def test_vti_onepass_step_matches_oracle(case):
-    """The fused one-pass step averages sigma_v on the z edges from its own per-cell values."""
+@pytest.mark.parametrize("launch", [dict(onepass=(8, 4, 4), flush_mode=1, block=32),
+                                    dict(wspec=(8, 4, 3), flush_mode=1, block=32)])
+def test_vti_onepass_step_matches_oracle(case, launch):
+    """The fused one-pass step averages sigma_v on the z edges from its own per-cell values;
+    the warp-specialised fused step reads the edges' dt/eps."""
     wl, pb, model, o = case
     eng = Engine.from_workload(wl, precision=32, kahan=1, vti=True, autotune=False)
-    eng.set_launch(onepass=(8, 4, 4), flush_mode=1, block=32)
+    eng.set_launch(**launch)
     rho = eng.model_tensor(model)
     d, E = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)
     assert rel_l2(d.cpu().numpy(), o["d"]) <= 1e-5
@@ -96,12 +99,15 @@ def test_vti_onepass_step_matches_oracle(case):
     eng.close()
 
 
-@pytest.mark.parametrize("onepass", [None, (8, 4, 4)])
+@pytest.mark.parametrize("onepass", [None, (8, 4, 4), "wspec"])
 def test_vti_with_equal_parts_is_the_isotropic_engine(case, onepass):
     wl, pb, model, o = case
     iso = Engine.from_workload(wl, precision=32, kahan=1, autotune=False)
     ani = Engine.from_workload(wl, precision=32, kahan=1, autotune=False, vti=True)
-    if onepass:
+    if onepass == "wspec":
+        iso.set_launch(wspec=(8, 4, 3))
+        ani.set_launch(wspec=(8, 4, 3))
+    elif onepass:
         iso.set_launch(onepass=onepass)
         ani.set_launch(onepass=onepass)
     rho = iso.model_tensor(wl.rho)
