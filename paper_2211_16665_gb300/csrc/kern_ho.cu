@@ -199,9 +199,8 @@ __device__ __forceinline__ float3 ho_taps(const int *__restrict__ tk, const floa
     return r;
 }
 
-template <int MINB>
-__global__ void __launch_bounds__(128, MINB) k_h_ho4(const StepParams<float> p, const HoTab<float> w, const int jstep,
-                                                   const int KZ) {
+template <int KZ, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_h_ho4(const StepParams<float> p, const HoTab<float> w, const int jstep) {
     const int i = (blockIdx.x * 32 + threadIdx.x) * 2;
     const int j = blockIdx.y * 4 + threadIdx.y;
     const int nkb = (p.nz + KZ - 1) / KZ;
@@ -233,7 +232,10 @@ __global__ void __launch_bounds__(128, MINB) k_h_ho4(const StepParams<float> p, 
     int km = (k0 > 0) ? k0 - 1 : 0;
     float2 xa = f2g(Ex + km * plane + base), xb = f2g(Ex + k0 * plane + base), xc = f2g(Ex + (k0 + 1) * plane + base);
     float2 ya = f2g(Ey + km * plane + base), yb = f2g(Ey + k0 * plane + base), yc = f2g(Ey + (k0 + 1) * plane + base);
-    for (int k = k0; k < k1; ++k) {
+#pragma unroll
+    for (int kk = 0; kk < KZ; ++kk) {
+        const int k = k0 + kk;
+        if (k >= k1) break;
         const int idx = k * plane + base;
         const int kp2 = (k + 2 <= nz) ? k + 2 : nz;
         const float2 xd = f2g(Ex + kp2 * plane + base), yd = f2g(Ey + kp2 * plane + base);
@@ -269,9 +271,8 @@ __global__ void __launch_bounds__(128, MINB) k_h_ho4(const StepParams<float> p, 
     }
 }
 
-template <int MINB>
-__global__ void __launch_bounds__(128, MINB) k_e_ho4(const StepParams<float> p, const HoTab<float> w, const int jstep,
-                                                   const int KZ) {
+template <int KZ, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_e_ho4(const StepParams<float> p, const HoTab<float> w, const int jstep) {
     const int i = (blockIdx.x * 32 + threadIdx.x) * 2;
     const int j = blockIdx.y * 4 + threadIdx.y;
     const int nkb = (p.nz + KZ - 1) / KZ;
@@ -305,7 +306,10 @@ __global__ void __launch_bounds__(128, MINB) k_e_ho4(const StepParams<float> p, 
     const int ka = (k0 >= 2) ? k0 - 2 : 0, kb = (k0 >= 1) ? k0 - 1 : 0;
     float2 xa = f2g(Hx + ka * plane + base), xb = f2g(Hx + kb * plane + base), xc = f2g(Hx + k0 * plane + base);
     float2 ya = f2g(Hy + ka * plane + base), yb = f2g(Hy + kb * plane + base), yc = f2g(Hy + k0 * plane + base);
-    for (int k = k0; k < k1; ++k) {
+#pragma unroll
+    for (int kk = 0; kk < KZ; ++kk) {
+        const int k = k0 + kk;
+        if (k >= k1) break;
         const int idx = k * plane + base;
         const float2 xd = f2g(Hx + idx + plane), yd = f2g(Hy + idx + plane);   // plane k+1 <= nz
         const float4 wz = f4g(w.wzn + 4 * k);
@@ -352,11 +356,17 @@ __global__ void __launch_bounds__(128, MINB) k_e_ho4(const StepParams<float> p, 
     }
 }
 
+template <int KZ, int MB>
+void go_ho4k(const StepParams<float> &p, const HoTab<float> &w, int S, int jstep, cudaStream_t st, bool h) {
+    const dim3 grid((unsigned)((p.nx / 2 + 31) / 32), (unsigned)((p.ny + 3) / 4), (unsigned)(((p.nz + KZ - 1) / KZ) * S));
+    if (h) k_h_ho4<KZ, MB><<<grid, dim3(32, 4), 0, st>>>(p, w, jstep);
+    else k_e_ho4<KZ, MB><<<grid, dim3(32, 4), 0, st>>>(p, w, jstep);
+}
 template <int MB>
 void go_ho4(const StepParams<float> &p, const HoTab<float> &w, int S, int jstep, cudaStream_t st, bool h, int kz) {
-    const dim3 grid((unsigned)((p.nx / 2 + 31) / 32), (unsigned)((p.ny + 3) / 4), (unsigned)(((p.nz + kz - 1) / kz) * S));
-    if (h) k_h_ho4<MB><<<grid, dim3(32, 4), 0, st>>>(p, w, jstep, kz);
-    else k_e_ho4<MB><<<grid, dim3(32, 4), 0, st>>>(p, w, jstep, kz);
+    if (kz == 2) go_ho4k<2, MB>(p, w, S, jstep, st, h);
+    else if (kz == 4) go_ho4k<4, MB>(p, w, S, jstep, st, h);
+    else go_ho4k<8, MB>(p, w, S, jstep, st, h);
 }
 
 }  // namespace
