@@ -74,6 +74,10 @@ def parse():
     ap.add_argument("--check-sources", type=int, default=1,
                     help="sources of the first batch whose gradients are scored against the FP64 engine")
     ap.add_argument("--e2e-steps", type=int, default=2, help="steps of the end-to-end measurement")
+    ap.add_argument("--batch-sweep", default="",
+                    help="comma-separated sources per launch (e.g. 1,2,4,8,16,32): one JSON line per batch size "
+                         "with the gradient seconds per source, compensated, and the plain path at 1 source")
+    ap.add_argument("--nt", type=int, default=0, help="--batch-sweep: time steps per run (0: the workload's)")
     return ap.parse_args()
 
 
@@ -682,6 +686,43 @@ def run_early_stop_volumes(args):
     print(json.dumps(out))
 
 
+def run_batch_sweep(args):
+    """Gradient seconds per source against the sources per launch: each batch size gets its
+    own context (ring sized against free memory, autotuned kernels and flush), one warm-up
+    gradient and args.steps timed ones over the first B sources of the workload; the plain
+    path (1 source, no compensation) last."""
+    import torch
+    from paper_2211_16665_gb300.engine import Engine
+    torch.cuda.set_device(0)
+    wl = make_workload(args.workload, 0, 1)
+    sizes = [int(v) for v in args.batch_sweep.split(",") if v.strip()]
+    runs = [(B, 1) for B in sizes] + [(1, 0)]
+    for B, kahan in runs:
+        B = min(B, wl.src.n)
+        src = wl.src.subset(list(range(B)))
+        eng = Engine.from_workload(wl, max_src=B, kahan=kahan, nt=args.nt)
+        rho, rho_t = eng.model_tensor(wl.rho), eng.model_tensor(wl.rho_true)
+        eng.set_early_stop(1e-6)
+        d_obs = eng.fwd_model(rho_t, src, wl.rec)
+        eng.set_early_stop(0.0)
+        gradient_step(eng, rho, src, wl.rec, d_obs)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            gradient_step(eng, rho, src, wl.rec, d_obs)
+        e1.record()
+        torch.cuda.synchronize()
+        s = e0.elapsed_time(e1) / 1e3 / args.steps
+        print(json.dumps({"mode": "batch_sweep", "workload": wl.name, "nt": eng.nt, "sources_per_launch": B,
+                          "kahan": bool(kahan), "s_per_gradient": round(s, 4), "s_per_source": round(s / B, 5),
+                          "gcell_updates_per_s": round(2.0 * wl.cells * eng.nt * B / s / 1e9, 3),
+                          "launch": eng.launch_config()}), flush=True)
+        eng.close()
+        del eng
+        torch.cuda.empty_cache()
+
+
 def run_early_stop(args):
     """Forward data runs (receivers only) on the thin reservoir with the early end of Sec. 2
     at the given tolerance against full runs: ms per run, steps, relative L2 change of the data."""
@@ -728,6 +769,9 @@ def main():
         return
     if args.td:
         run_td(args)
+        return
+    if args.batch_sweep:
+        run_batch_sweep(args)
         return
     if args.impl == "reference":
         run_reference(args)
