@@ -239,7 +239,7 @@ int lean_len(int n) { return (n + 1 + 3 + 3) / 4 * 4; }
 // The fused one-pass step's launch shape as one code (0: not selected): kz * 100 + rows * 10 + blocks;
 // csem_autotune and csem_set_launch report and take it as 10000 + that code.
 int fz_code(const csem_ctx *c) {
-    return c->FZ_by ? (c->FZ_ws ? 20000 : 0) + c->FZ_kz * 100 + c->FZ_by * 10 + c->FZ_mb : 0;
+    return c->FZ_by ? c->FZ_ws * 20000 + c->FZ_kz * 100 + c->FZ_by * 10 + c->FZ_mb : 0;
 }
 // Per-axis widths of the fused one-pass step: h (primal, half nodes) and s = h[i-1] + h[i] at the
 // nodes (the outer nodes take their one width), each padded to lean_len(n) floats.

@@ -480,6 +480,23 @@ __device__ __forceinline__ void ws_arrive(uint64_t *b) {
 }
 }  // namespace
 
+// Inputs of one producer plane k at the thread's cells: E^n (Ez at k, Ex and Ey at k+1, the i+2
+// and j+1 neighbours) and H^{n-1/2}, all loaded before any is used.
+struct WsIn {
+    float2 ez, exk, eyk, exU, ezU, hx, hy, hz;
+    float ezR, eyR;
+};
+__device__ __forceinline__ WsIn ws_load(const float *__restrict__ E, const float *__restrict__ Hi, int idx, int vol,
+                                        int plane, int pitch) {
+    WsIn a;
+    a.ez = ld2(E + 2 * vol + idx);
+    a.exk = ld2(E + idx + plane); a.eyk = ld2(E + vol + idx + plane);
+    a.ezR = __ldg(E + 2 * vol + idx + 2); a.eyR = __ldg(E + vol + idx + 2);
+    a.exU = ld2(E + idx + pitch); a.ezU = ld2(E + 2 * vol + idx + pitch);
+    a.hx = ld2(Hi + idx); a.hy = ld2(Hi + vol + idx); a.hz = ld2(Hi + 2 * vol + idx);
+    return a;
+}
+
 template <int BY, int MINB>
 __global__ void __launch_bounds__(32 * (2 * BY + 2), MINB)
     k_step_ws(const StepParams<float> p, const int jstep, const int KZ, const int S) {
@@ -537,10 +554,9 @@ __global__ void __launch_bounds__(32 * (2 * BY + 2), MINB)
             // for the buffer, so the wait overlaps the loads
             float2 hx = f2(0.f, 0.f), hy = hx, hz = hx;
             if (act) {
-                const float2 ez = ld2(E + 2 * vol + idx);
-                const float2 exk = ld2(E + idx + plane), eyk = ld2(E + vol + idx + plane);
-                const float ezR = __ldg(E + 2 * vol + idx + 2), eyR = __ldg(E + vol + idx + 2);
-                const float2 exU = ld2(E + idx + pitch), ezU = ld2(E + 2 * vol + idx + pitch);
+                const WsIn cur = ws_load(E, Hi, idx, vol, plane, pitch);   // every load of the plane first
+                const float2 ez = cur.ez, exk = cur.exk, eyk = cur.eyk, exU = cur.exU, ezU = cur.ezU;
+                const float ezR = cur.ezR, eyR = cur.eyR;
                 const float ihz = __ldg(p.lz.ih_h + k);
                 float2 dEz_dy = dsc(ezU, ez, yh.ih), dEx_dy = dsc(exU, ex, yh.ih);
                 float2 dEy_dz = dsc(eyk, ey, ihz), dEx_dz = dsc(exk, ex, ihz);
@@ -577,9 +593,9 @@ __global__ void __launch_bounds__(32 * (2 * BY + 2), MINB)
                         if (wr) { psx[hout * sx + ro + xh.s1] = q0; psx[(hout + 1) * sx + ro + xh.s1] = q1; }
                     }
                 }
-                hx = hupd(ld2(Hi + idx), cH, dEz_dy, dEy_dz);
-                hy = hupd(ld2(Hi + vol + idx), cH, dEx_dz, dEz_dx);
-                hz = hupd(ld2(Hi + 2 * vol + idx), cH, dEy_dx, dEx_dy);
+                hx = hupd(cur.hx, cH, dEz_dy, dEy_dz);
+                hy = hupd(cur.hy, cH, dEx_dz, dEz_dx);
+                hz = hupd(cur.hz, cH, dEy_dx, dEx_dy);
                 if (wr) {
                     st2(Ho + idx, hx);
                     st2(Ho + vol + idx, hy);
