@@ -384,6 +384,43 @@ def test_error_statuses(box):
     assert e.value.code == -3
 
 
+@pytest.mark.parametrize("launch", [None, dict(kz_h=2, mb_h=8, lean_h=2, kz_e=2, mb_e=8, lean_e=2, flush_mode=1, block=64),
+                                    dict(wspec=(8, 4, 3), flush_mode=1, block=16)])
+def test_single_frequency_and_a_run_without_receivers(launch):
+    """One frequency (the flush kernels' two-frequency padding, a two-column basis) through
+    forward, adjoint and gradient against the oracle, autotuned and on the streamed 64-snapshot
+    flush and the warp-specialised step; a forward run without receivers gives the same volumes."""
+    wl = W.small_box(n_core=20, h=100.0, npml=6, ratio=1.08, n_st=2, n_rec=5, n_freq=1)
+    pb = fdtd.problem_from_workload(wl)
+    d_obs = fdtd.forward(pb, wl.rho_true, wl.src, wl.rec)
+    d_o, E_o = fdtd.forward(pb, wl.rho, wl.src, wl.rec, keep_volume=True)
+    phi_o, r_o = fdtd.misfit(d_obs, d_o)
+    Bp, _ = fdtd.adjoint_basis(pb, 1e-12)
+    V_o = fdtd.adjoint(pb, wl.rho, wl.rec, r_o, Bp)
+    g_o = fdtd.gradient(pb, wl.rho, E_o, V_o, wrt="lnrho")
+    eng = Engine.from_workload(wl, precision=32, kahan=1, autotune=launch is None)
+    if launch:
+        eng.set_launch(**launch)
+    rho = eng.model_tensor(wl.rho)
+    d, E = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)
+    assert rel_l2(d.cpu().numpy(), d_o) <= 1e-5
+    assert rel_l2(gpu_volume(eng, E), E_o) <= 1e-3
+    phi, r = misfit(torch.as_tensor(d_obs, device=eng.device), d)
+    basis, _, _ = eng.estimate_adjoint_basis(gamma=1e-12, relative=True)
+    assert basis.shape[-1] == 2
+    V = eng.adjoint_model(rho, wl.rec, r, basis)
+    assert rel_l2(gpu_volume(eng, V), V_o) <= 1e-3
+    assert rel_l2(eng.gradient(rho, E, V, wrt="lnrho").cpu().numpy(), g_o) <= 1e-3
+    none = W.Points.make(np.zeros((0, 3)), 0)
+    d0, E0 = eng.fwd_model(rho, wl.src, none, keep_volume=True)
+    assert d0.shape[1] == 0 and torch.equal(E0, E)
+    with pytest.raises(CsemError) as e:            # no sources: refused, nothing runs
+        eng.fwd_model(rho, none, wl.rec)
+    assert e.value.code == -1
+    eng.check()
+    eng.close()
+
+
 def test_basis_fit_target_on_eight_widely_spaced_frequencies():
     """The Gram matrix of 8 log-spaced frequencies 0.1-1.5 Hz over 19 492 steps has a
     condition number near 1e12: gamma = 1e-12 relative leaves a fit residual of 0.19, and
