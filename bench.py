@@ -204,15 +204,25 @@ def ncu_traffic(wl, kernel, S):
     return None
 
 
-def cpu_baseline(wl, nt_sample, order=2):
+def cpu_baseline(wl, nt_sample, order=2, threads=0):
+    """The CPU baseline leg: the FP64 oracle, as it stands, timed on a bounded sample (one
+    source's forward run with the volumetric transform for nt_sample steps) on `threads` host
+    threads (0: all, or OMP_NUM_THREADS)."""
     from oracle import fdtd
     pb = fdtd.problem_from_workload(wl, order=order)
     nt_sample = min(nt_sample, pb.nt)
-    t0 = time.perf_counter()
-    fdtd.forward(pb, wl.rho, wl.src.subset([0]), wl.rec, keep_volume=True, nt_run=nt_sample)
-    t = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    prev = fdtd.get_threads()
+    if threads:
+        fdtd.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        fdtd.forward(pb, wl.rho, wl.src.subset([0]), wl.rec, keep_volume=True, nt_run=nt_sample)
+        t = time.perf_counter() - t0
+    finally:
+        fdtd.set_threads(prev)
+    cores = threads or int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": wl.cells * nt_sample / t / 1e9, "unit": "Gcell-updates/s", "cores": cores, "kind": "oracle",
+            "nt_sample": nt_sample, "nt": pb.nt,
             "sample": f"FP64 oracle, {nt_sample} of {pb.nt} steps of one source with the volumetric transform "
                       f"into {wl.freqs.size} frequencies on the full {wl.nx}x{wl.ny}x{wl.nz} grid "
                       f"(a gradient is 2 such runs per source); {t:.1f} s"}
@@ -600,7 +610,6 @@ def run_oracle_timings(args):
     model (one source, forward run with the volumetric transform), beside the device's
     gradient on the same workloads (Gcell-updates/s over both runs of all sources)."""
     import torch
-    from oracle import fdtd
     from paper_2211_16665_gb300 import workloads as W
     from paper_2211_16665_gb300.engine import Engine, misfit
     torch.cuda.set_device(0)
@@ -609,16 +618,10 @@ def run_oracle_timings(args):
     for name, nt_sample in (("plain_tiny", 300), ("thin_reservoir", 200), ("heterogeneous_crop96", 200)):
         wl = W.ALL[name]()
         row = {"workload": wl.name, "cells": wl.cells, "precision": wl.precision}
-        pb = fdtd.problem_from_workload(wl)
-        n = min(nt_sample, pb.nt)
-        for threads in (1, all_threads):
-            fdtd.set_threads(threads)
-            t0 = time.perf_counter()
-            fdtd.forward(pb, wl.rho, wl.src.subset([0]), wl.rec, keep_volume=True, nt_run=n)
-            t = time.perf_counter() - t0
-            row[f"oracle_gcell_s_{threads}_threads"] = round(wl.cells * n / t / 1e9, 5)
-        row["oracle_sample"] = f"{n} of {pb.nt} steps, one source, volumetric transform"
-        fdtd.set_threads(all_threads)
+        for threads in (1, all_threads):         # the cpu_baseline leg on one and on all host threads
+            cb = cpu_baseline(wl, nt_sample, threads=threads)
+            row[f"oracle_gcell_s_{threads}_threads"] = round(cb["value"], 5)
+        row["oracle_sample"] = f"{cb['nt_sample']} of {cb['nt']} steps, one source, volumetric transform"
         eng = Engine.from_workload(wl)
         rho = eng.model_tensor(wl.rho)
         d_obs = eng.fwd_model(eng.model_tensor(wl.rho_true), wl.src, wl.rec)
