@@ -354,7 +354,7 @@ def run_ours(args):
             "traffic": ncu_traffic(wl, st_name, B),
             "bytes_per_unit": round(b_cell, 2), "unit_of_work": "cell (one H + E step, every source of the launch)",
             "units_per_launch": wl.cells * B, "ms_per_launch": round(st_ms, 5),
-            "flush": {"kernel": ("k_dft_stream" if M == 64 else "k_dft_bulk") if lc["flush"]["kernel"] == "bulk-copy"
+            "flush": {"kernel": ("k_dft_stream" if M >= 64 else "k_dft_bulk") if lc["flush"]["kernel"] == "bulk-copy"
                       else "k_dft",
                       "snapshots": M, "bytes_per_node": b_flush, "achieved": round(fl_gbs, 1),
                       "frac": round(fl_gbs / peak, 4), "ms_per_launch": round(kms["k_dft"], 5)},

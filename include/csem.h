@@ -108,7 +108,7 @@ typedef struct {
     int nt;                       /* steps per run */
     int precision, kahan, n_freq, max_src, max_rec;
     long long workspace_bytes;    /* device memory the context holds */
-    int transform_block;          /* E snapshots per damped-transform flush (16, 32 or 64) */
+    int transform_block;          /* E snapshots per damped-transform flush (16, 32, 64 or 128) */
     int anisotropy;               /* as in csem_opts */
     int order;                    /* 2 or 4, as in csem_opts */
 } csem_info;
@@ -310,7 +310,7 @@ int csem_set_early_stop_volumes(csem_ctx *ctx, double tol, double floor_frac);
  * later calls use the fastest.  It then times the fused H+E step kernel (z
  * blocking 4, 8 or 16) against the best split pair and keeps the faster, and
  * last, when nt >= 256, the transform flush over 128 steps: the register
- * kernel or (FP32) the bulk-copy kernel, over 16, 32 or 64 snapshots, run after
+ * kernel or (FP32) the bulk-copy kernel, over 16, 32, 64 or 128 snapshots, run after
  * its block or on a second stream overlapping the next block (needs a ring of
  * 2 * snapshots + 1 slots; the results are the same bit for bit).  kz_out
  * (may be NULL, else 4 ints) receives, for H and E, 16 * planes + blocks
@@ -332,9 +332,10 @@ int csem_autotune(csem_ctx *ctx, int n_src, int *kz_out, void *stream);
  * its one-cell halo into shared memory, consumer warps the E step from it; rows
  * and blocks (4,2), (4,3), (6,2), (8,1), (8,2); FP32, second order), flush mode (bit 0: bulk
  * copy, FP32 only, else register kernel; bit 1: overlapped with the next
- * block on a second stream), snapshots per flush (16, 32 or 64; the context's
- * ring of 17, 33, 65 or 129 slots must hold snapshots + 1, or 2 * snapshots + 1
- * when overlapped), H four-cells-per-thread (0/1, FP32, 4 or 6 blocks/SM),
+ * block on a second stream), snapshots per flush (16, 32, 64 or 128; the
+ * context's ring of 17, 33, 65 or 129 slots must hold snapshots + 1, or
+ * 2 * snapshots + 1 when overlapped; runs with an early end flush at most 64 at
+ * a time), H four-cells-per-thread (0/1, FP32, 4 or 6 blocks/SM),
  * E four-cells-per-thread (0/1), H bulk-copy-staged rows per block (0, or
  * 1/2/4 for FP32 when the staged planes fit shared memory; z planes 2-16),
  * E bulk-copy-staged rows per block, H lean kernel (0 off, or 1 or 2 cells

@@ -42,7 +42,6 @@ constexpr double kMu0 = 4e-7 * M_PI;
 constexpr double kCpmlR = 1e-6;
 constexpr double kDecaySpan = 35.0;
 constexpr int kChunk = 64;        // time steps per captured graph
-constexpr int kBlockM = 64;        // largest snapshots per transform flush (divides kChunk)
 constexpr int kMaxSide = 4;       // event slots for overlapped flushes (at most two are in flight)
 constexpr int kEsDepth = 4;       // early end: chunks in flight before the host reads a convergence flag
 
@@ -509,7 +508,7 @@ template <typename R>
 cudaError_t flush(csem_ctx *c, const csem::StepParams<R> &p, const csem::PointParams<R> &q, int S, int n0_off,
                   int cnt, bool vol, bool kahan, cudaStream_t st) {
     if constexpr (sizeof(R) == 4) {
-        if ((c->flush_mode & 1) && vol && (cnt == 16 || cnt == 32 || cnt == 64))
+        if ((c->flush_mode & 1) && vol && (cnt == 16 || cnt == 32 || cnt == 64 || cnt == 128))
             return csem::launch_dft_bulk(p, q, S, n0_off, cnt, kahan, c->d_bad, st);
     }
     return csem::launch_dft<R>(p, q, S, n0_off, cnt, vol, kahan, st);
@@ -645,33 +644,49 @@ int run_steps(csem_ctx *c, int S, bool vol, const csem::StepParams<R> &p, const 
     const int M = c->M;
     const bool overlap = (c->flush_mode & 2) != 0;
     const int full = c->nt / kChunk, rem = c->nt % kChunk;
+    // M = 2 kChunk (never overlapped): chunks alternate between a graph without a flush and one
+    // that ends with the flush of both chunks' snapshots
+    const bool two = M > kChunk;
+    int pending = 0;                // steps before the device counter not yet transformed
     if (full > 0) {
-        const int key[8] = {S, vol ? 1 : 0, kahan ? 1 : 0, (q.n_itaps > 0 ? 1 : 0) + 2 * fz_code(c), q.n_rec > 0 ? 1 : 0,
-                            (int)sizeof(R), ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
-                            ((((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e) * 25 +
-                             c->TMA_h * 5 + c->TMA_e) * 16 + c->LEAN_h * 4 + c->LEAN_e};
-        cudaGraphExec_t exec = nullptr;
-        long long per_chunk = 0;
+        int key[8] = {S, vol ? 1 : 0, kahan ? 1 : 0, (q.n_itaps > 0 ? 1 : 0) + 2 * fz_code(c), q.n_rec > 0 ? 1 : 0,
+                      (int)sizeof(R), ((c->KZ_h * 16 + c->KZ_e) * 16 + c->MB_h) * 16 + c->MB_e,
+                      ((((M * 4 + c->flush_mode) * 32 + c->fused_kz) * 4 + c->VEC_h * 2 + c->VEC_e) * 25 +
+                       c->TMA_h * 5 + c->TMA_e) * 16 + c->LEAN_h * 4 + c->LEAN_e};
+        cudaGraphExec_t exec = nullptr, exec2 = nullptr;
+        long long per_chunk = 0, per_chunk2 = 0;
         TRY(chunk_graph(c, key, [&](cudaStream_t cs) {
             cudaError_t le = tap_prep<R>(c, p, S, kChunk, cs);
             if (le == cudaSuccess) le = emit_steps<R>(c, S, vol, kahan, p, q, kChunk, overlap, !overlap, cs);
             if (le == cudaSuccess) le = csem::launch_advance(c->d_step, kChunk, cs);
             return le;
         }, &exec, &per_chunk));
+        if (two) {
+            key[1] += 2;            // the second graph of the pair
+            TRY(chunk_graph(c, key, [&](cudaStream_t cs) {
+                cudaError_t le = tap_prep<R>(c, p, S, kChunk, cs);
+                if (le == cudaSuccess) le = emit_steps<R>(c, S, vol, kahan, p, q, kChunk, false, true, cs);
+                if (le == cudaSuccess) le = flush<R>(c, p, q, S, kChunk - M, M, vol, kahan, cs);
+                if (le == cudaSuccess) le = csem::launch_advance(c->d_step, kChunk, cs);
+                return le;
+            }, &exec2, &per_chunk2));
+        }
         for (int ch = 0; ch < full; ++ch) {
-            CK(cudaGraphLaunch(exec, st));
-            csem::g_launches += per_chunk;
+            const bool second = two && (ch % 2 == 1);
+            CK(cudaGraphLaunch(second ? exec2 : exec, st));
+            csem::g_launches += second ? per_chunk2 : per_chunk;
         }
         if (overlap) CK(flush<R>(c, p, q, S, -M, M, vol, kahan, st));
+        if (two && full % 2 == 1) pending = kChunk;
     }
     auto emit = [&](int j, cudaStream_t s2) -> cudaError_t {
         cudaError_t e = launch_any<R>(c, p, q, S, j, s2);
-        if (e == cudaSuccess && (j + 1) % M == 0) e = flush<R>(c, p, q, S, j + 1 - M, M, vol, kahan, s2);
+        if (e == cudaSuccess && (pending + j + 1) % M == 0) e = flush<R>(c, p, q, S, j + 1 - M, M, vol, kahan, s2);
         return e;
     };
     if (rem > 0) CK(tap_prep<R>(c, p, S, rem, st));
     for (int j = 0; j < rem; ++j) CK(emit(j, st));
-    const int tail = c->nt % M;     // M divides kChunk, so this is also rem % M
+    const int tail = (pending + rem) % M;   // the steps after the last whole block
     if (tail) CK(flush<R>(c, p, q, S, rem - tail, tail, vol, kahan, st));
     return CSEM_OK;
 }
@@ -769,9 +784,10 @@ int upload_injection(csem_ctx *c, std::vector<Tap> &taps, int n_lists, int per_l
 template <typename R>
 int run_steps_es(csem_ctx *c, int S, int NR, const csem::StepParams<R> &p, const csem::PointParams<R> &q,
                  cudaStream_t st) {
-    const int saved = c->flush_mode;
+    const int saved = c->flush_mode, savedM = c->M;
     c->flush_mode &= 1;
-    struct Restore { csem_ctx *c; int m; ~Restore() { c->flush_mode = m; } } restore{c, saved};
+    c->M = std::min(c->M, kChunk);       // a check after every chunk: whole blocks within a chunk
+    struct Restore { csem_ctx *c; int m, M; ~Restore() { c->flush_mode = m; c->M = M; } } restore{c, saved, savedM};
     const int M = c->M, nt = c->nt, n = S * NR * c->nf;
     const int full = nt / kChunk, rem = nt % kChunk;
     CK(cudaMemsetAsync(c->d_es, 0, 2 * sizeof(int), st));
@@ -828,9 +844,10 @@ template <typename R>
 int run_steps_vol_es(csem_ctx *c, int S, const csem::StepParams<R> &p, const csem::PointParams<R> &q,
                      cudaStream_t st) {
     typedef typename C2<R>::T R2;
-    const int saved = c->flush_mode;
+    const int saved = c->flush_mode, savedM = c->M;
     c->flush_mode &= 1;
-    struct Restore { csem_ctx *c; int m; ~Restore() { c->flush_mode = m; } } restore{c, saved};
+    c->M = std::min(c->M, kChunk);       // a check after every chunk: whole blocks within a chunk
+    struct Restore { csem_ctx *c; int m, M; ~Restore() { c->flush_mode = m; c->M = M; } } restore{c, saved, savedM};
     const bool kahan = c->kahan != 0;
     const int M = c->M, nt = c->nt, nf = c->nf;
     const int full = nt / kChunk, rem = nt % kChunk;
@@ -1418,7 +1435,7 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
             double best = 1e30;
             int bm = 0, bM = 16;
             for (int mode = 0; mode < 4; ++mode)
-                for (int m : {16, 32, 64}) {
+                for (int m : {16, 32, 64, 128}) {
                     if ((mode & 1) && sizeof(R) != 4) continue;
                     if (((mode & 2) ? 2 * m : m) + 1 > c->nslot) continue;
                     c->flush_mode = mode;
@@ -1894,7 +1911,7 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
         auto ok = [&](int l, int kz, int mb) { return l == 0 || (l == 2 && csem::ho4_supported(kz, mb)); };
         if ((lh || le) && (c->precision != 32 || !c->d_cEm || !ok(lh, kzh, mbh) || !ok(le, kze, mbe)))
             return fail(CSEM_ERR_INVALID_ARG, "lean fourth-order kernels: FP32, nx even, 2 cells, 2/4/8 planes, 4/6/8 blocks/SM");
-        if (fm < 0 || fm > 3 || ((fm & 1) && c->precision != 32) || !(M == 16 || M == 32 || M == 64) ||
+        if (fm < 0 || fm > 3 || ((fm & 1) && c->precision != 32) || !(M == 16 || M == 32 || M == 64 || M == 128) ||
             ((fm & 2) ? 2 * M : M) + 1 > c->nslot)
             return fail(CSEM_ERR_INVALID_ARG, "launch configuration not supported by this context");
         CK(cudaDeviceSynchronize());
@@ -1924,7 +1941,7 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
     auto kz_ok = [](int v) { return v == 1 || v == 2 || v == 4 || v == 8 || v == 16; };
     auto mb_ok = [](int v) { return v == 4 || v == 6 || v == 8; };
     if (!kz_ok(kzh) || !kz_ok(kze) || !mb_ok(mbh) || !mb_ok(mbe) || !(fkz == 0 || fkz == 4 || fkz == 8 || fkz == 16) ||
-        fm < 0 || fm > 3 || ((fm & 1) && c->precision != 32) || !(M == 16 || M == 32 || M == 64) ||
+        fm < 0 || fm > 3 || ((fm & 1) && c->precision != 32) || !(M == 16 || M == 32 || M == 64 || M == 128) ||
         ((fm & 2) ? 2 * M : M) + 1 > c->nslot)
         return fail(CSEM_ERR_INVALID_ARG, "launch configuration not supported by this context");
     CK(cudaDeviceSynchronize());

@@ -544,23 +544,22 @@ __global__ void __launch_bounds__(kBulkThreads, bulk_minb<MS>()) k_dft_bulk(cons
     }
 }
 
-// Streamed flush of 64 snapshots.  Holding all 64 snapshot rows of a block in
-// shared memory (64 KB) leaves two blocks per SM, and a block computes only
-// after its last copy landed.  Here the snapshots stream through kStN stages of
+// Streamed flush of kStMS = 64 or 128 snapshots.  Holding all 64 snapshot rows of
+// a block in shared memory (64 KB) leaves two blocks per SM, and a block computes
+// only after its last copy landed.  Here the snapshots stream through kStN stages of
 // kStG rows each (one mbarrier per stage, 32 KB in all): while the block sums
 // the rows of one stage, the copies of the next kStN - 1 stages are in flight,
 // and four blocks fit an SM.  The accumulators (and compensation) arrive on a
 // barrier of their own and are added to once, at the end, as in k_dft_bulk;
-// the sums are the same as k_dft_bulk's with MS = 64, in the same order.
+// the sums are the ones k_dft_bulk would form over the same snapshots, in the same order.
 // Each thread waits on each stage's barrier itself (bounded); a give-up
 // anywhere ends the loop for the whole block (__syncthreads_or), thread 0 then
 // waits (bounded) for every copy it issued that nobody consumed, and the block
 // returns with the flush bit of *err raised.
 constexpr int kStG = 8;                 // snapshot rows per stage
 constexpr int kStN = 4;                 // stages (a power of two)
-constexpr int kStMS = 64;               // snapshots per flush
 
-template <bool KAHAN, int NF>
+template <bool KAHAN, int NF, int kStMS>
 __global__ void __launch_bounds__(kBulkThreads, 3) k_dft_stream(const StepParams<float> p, const PointParams<float> q,
                                                                 const int n0_off, const int nvb, const int S,
                                                                 int *err) {
@@ -571,7 +570,7 @@ __global__ void __launch_bounds__(kBulkThreads, 3) k_dft_stream(const StepParams
     float *st_s = reinterpret_cast<float *>(smem);                          // [kStN][kStG][256]
     float2 *acc_s = reinterpret_cast<float2 *>(st_s + kStN * kStG * kBlock);  // [nf][256]
     float2 *cmp_s = acc_s + p.nf * kBlock;                                  // [nf][256] (Kahan)
-    float2 *w_s = cmp_s + (KAHAN ? p.nf * kBlock : 0);                      // [64][NF], zero past nf
+    float2 *w_s = cmp_s + (KAHAN ? p.nf * kBlock : 0);                      // [kStMS][NF], zero past nf
     const int n0 = *p.step + n0_off;
     if (n0 < 0) return;
     const int nrec_blocks = q.n_rec > 0 ? S : 0;
@@ -686,9 +685,9 @@ __global__ void __launch_bounds__(kBulkThreads, 3) k_dft_stream(const StepParams
     }
 }
 
-size_t stream_smem_bytes(int nf, bool kahan) {
+size_t stream_smem_bytes(int nf, bool kahan, int ms) {
     return (size_t)kStN * kStG * kBlock * sizeof(float) + (size_t)nf * kBlock * sizeof(float2) * (kahan ? 2 : 1) +
-           (size_t)kStMS * nf_pad(nf) * sizeof(float2);
+           (size_t)ms * nf_pad(nf) * sizeof(float2);
 }
 
 size_t bulk_smem_bytes(int ms, int nf, bool kahan) {
@@ -709,17 +708,25 @@ cudaError_t bulk_attr_ms(int bytes) {
         if (r != cudaSuccess) e = r;
     return e;
 }
-template <bool KAHAN, int NF>
+template <bool KAHAN, int NF, int MS>
 cudaError_t stream_attr(int bytes) {
-    return cudaFuncSetAttribute(k_dft_stream<KAHAN, NF>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return cudaFuncSetAttribute(k_dft_stream<KAHAN, NF, MS>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
 }
-template <bool KAHAN>
+template <int MS>
+cudaError_t stream_attr_ms(int bytes) {
+    cudaError_t e = cudaSuccess;
+    for (cudaError_t r : {stream_attr<true, 2, MS>(bytes), stream_attr<true, 4, MS>(bytes), stream_attr<true, 8, MS>(bytes),
+                          stream_attr<false, 2, MS>(bytes), stream_attr<false, 4, MS>(bytes), stream_attr<false, 8, MS>(bytes)})
+        if (r != cudaSuccess) e = r;
+    return e;
+}
+template <bool KAHAN, int MS>
 void stream_go(const StepParams<float> &p, const PointParams<float> &q, int S, int n0_off, int nvb, int nblk, size_t sm,
                int *err, cudaStream_t st) {
     const int np = nf_pad(p.nf);
-    if (np == 2) k_dft_stream<KAHAN, 2><<<nblk, kBulkThreads, sm, st>>>(p, q, n0_off, nvb, S, err);
-    else if (np == 4) k_dft_stream<KAHAN, 4><<<nblk, kBulkThreads, sm, st>>>(p, q, n0_off, nvb, S, err);
-    else k_dft_stream<KAHAN, 8><<<nblk, kBulkThreads, sm, st>>>(p, q, n0_off, nvb, S, err);
+    if (np == 2) k_dft_stream<KAHAN, 2, MS><<<nblk, kBulkThreads, sm, st>>>(p, q, n0_off, nvb, S, err);
+    else if (np == 4) k_dft_stream<KAHAN, 4, MS><<<nblk, kBulkThreads, sm, st>>>(p, q, n0_off, nvb, S, err);
+    else k_dft_stream<KAHAN, 8, MS><<<nblk, kBulkThreads, sm, st>>>(p, q, n0_off, nvb, S, err);
 }
 template <bool KAHAN, int MS>
 void bulk_go(const StepParams<float> &p, const PointParams<float> &q, int S, int n0_off, int nvb, int nblk, size_t sm,
@@ -735,10 +742,9 @@ cudaError_t prepare_bulk_flush() {
     const int big = (int)bulk_smem_bytes(32, kMaxFreq, true);
     cudaError_t e = bulk_attr_ms<32>(big);
     if (e == cudaSuccess) e = bulk_attr_ms<16>(big);
-    const int sbig = (int)stream_smem_bytes(kMaxFreq, true);
-    for (cudaError_t r : {stream_attr<true, 2>(sbig), stream_attr<true, 4>(sbig), stream_attr<true, 8>(sbig),
-                          stream_attr<false, 2>(sbig), stream_attr<false, 4>(sbig), stream_attr<false, 8>(sbig)})
-        if (e == cudaSuccess) e = r;
+    const int sbig = (int)stream_smem_bytes(kMaxFreq, true, 128);
+    if (e == cudaSuccess) e = stream_attr_ms<64>(sbig);
+    if (e == cudaSuccess) e = stream_attr_ms<128>(sbig);
     return e;
 }
 
@@ -747,10 +753,15 @@ cudaError_t launch_dft_bulk(const StepParams<float> &p, const PointParams<float>
     const int nvb = (int)((p.vol + kBlock - 1) / kBlock);
     const int nblk = nvb * 3 * S + (q.n_rec > 0 ? S : 0);
     const size_t sm = bulk_smem_bytes(cnt, p.nf, kahan);
-    if (cnt == 64) {                  // 64 snapshots stream through a 4-stage ring (k_dft_stream)
-        const size_t ssm = stream_smem_bytes(p.nf, kahan);
-        if (kahan) stream_go<true>(p, q, S, n0_off, nvb, nblk, ssm, err, st);
-        else stream_go<false>(p, q, S, n0_off, nvb, nblk, ssm, err, st);
+    if (cnt == 64 || cnt == 128) {    // 64 or 128 snapshots stream through a 4-stage ring (k_dft_stream)
+        const size_t ssm = stream_smem_bytes(p.nf, kahan, cnt);
+        if (cnt == 64) {
+            if (kahan) stream_go<true, 64>(p, q, S, n0_off, nvb, nblk, ssm, err, st);
+            else stream_go<false, 64>(p, q, S, n0_off, nvb, nblk, ssm, err, st);
+        } else {
+            if (kahan) stream_go<true, 128>(p, q, S, n0_off, nvb, nblk, ssm, err, st);
+            else stream_go<false, 128>(p, q, S, n0_off, nvb, nblk, ssm, err, st);
+        }
     } else if (cnt == 32) {
         if (kahan) bulk_go<true, 32>(p, q, S, n0_off, nvb, nblk, sm, err, st);
         else bulk_go<false, 32>(p, q, S, n0_off, nvb, nblk, sm, err, st);

@@ -122,6 +122,8 @@ LAUNCH_VARIANTS = [
     dict(onepass=(16, 8, 2), flush_mode=3, block=16),
     dict(onepass=(5, 4, 6), flush_mode=0, block=64),
     dict(onepass=(64, 8, 3), flush_mode=1, block=16),
+    dict(kz_h=4, mb_h=8, lean_h=2, kz_e=4, mb_e=8, lean_e=2, flush_mode=1, block=128),
+    dict(kz_h=4, mb_h=4, kz_e=4, mb_e=4, flush_mode=0, block=128),
     dict(wspec=(8, 4, 3), flush_mode=1, block=32),
     dict(wspec=(16, 8, 2), flush_mode=3, block=16),
 ]
@@ -279,6 +281,58 @@ def test_overlapped_flush_is_bitwise_the_in_order_flush(box, precision, nt):
             ref = out[(fm & 1, m)]
             for a, b in zip(got, ref):
                 assert torch.equal(a, b), (fm, m)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+@pytest.mark.parametrize("nt", [40, 64, 100, 128, 192, 250, 320, 0])
+def test_128_snapshot_flush_is_the_64_snapshot_sum(box, precision, nt):
+    """With 128 snapshots per flush the chunks alternate between a graph without a flush and
+    one that transforms both chunks' snapshots; an odd last chunk and the remainder are
+    transformed together at the end.  Only the grouping of the sums changes: receivers (FP64)
+    and traces equal the 64-snapshot run's to rounding, volumes within the compensated FP32
+    grouping error, below one chunk, at whole and odd chunk counts, with remainders and at
+    the full nt."""
+    wl, pb = box
+    kinds = [0, 1] if precision == 32 else [0]
+    for fm in kinds:
+        out = {}
+        for m in (64, 128):
+            eng = Engine.from_workload(wl, precision=precision, kahan=1, autotune=False, nt=nt)
+            eng.set_launch(kz_h=4, mb_h=4, kz_e=4, mb_e=4, flush_mode=fm, block=m)
+            assert eng.launch_config()["flush"]["snapshots"] == m
+            d, E, tr = eng.fwd_model(eng.model_tensor(wl.rho), wl.src, wl.rec, keep_volume=True, trace=True)
+            out[m] = (d.cpu().numpy(), gpu_volume(eng, E), tr.cpu().numpy())
+            eng.check()
+            eng.close()
+        (d1, E1, t1), (d2, E2, t2) = out[64], out[128]
+        assert np.array_equal(t1, t2)
+        assert rel_l2(d2, d1) <= 1e-12
+        assert rel_l2(E2, E1) <= (1e-12 if precision == 64 else 1e-6)
+
+
+def test_early_end_runs_flush_at_most_64_snapshots(box):
+    """Runs with an early end check after every 64-step chunk, so a context set to 128
+    snapshots per flush transforms 64 at a time there: the same data and volumes as a
+    context set to 64."""
+    wl, pb = box
+    out = {}
+    for m in (64, 128):
+        eng = Engine.from_workload(wl, precision=32, kahan=1, autotune=False)
+        eng.set_launch(kz_h=4, mb_h=4, kz_e=4, mb_e=4, flush_mode=1, block=m)
+        rho = eng.model_tensor(wl.rho)
+        eng.set_early_stop(1e-6)
+        d = eng.fwd_model(rho, wl.src, wl.rec)
+        s1 = eng.last_run_steps()
+        eng.set_early_stop(0.0)
+        eng.set_early_stop_volumes(1e-6)
+        dv, E = eng.fwd_model(rho, wl.src, wl.rec, keep_volume=True)
+        s2 = eng.last_run_steps()
+        eng.check()
+        out[m] = (d.clone(), s1, dv.clone(), E.clone(), s2)
+        eng.close()
+    a, b = out[64], out[128]
+    assert a[1] == b[1] and a[4] == b[4]
+    assert torch.equal(a[0], b[0]) and torch.equal(a[2], b[2]) and torch.equal(a[3], b[3])
 
 
 def test_fused_and_split_steps_agree_in_fp64(box):
