@@ -163,7 +163,7 @@ def hbm_peak():
 
 
 def stencil_bytes(wl, eng):
-    """Algorithmic bytes of one fused H+E step per cell (the survey's byte model): the six
+    """Algorithmic bytes of one fused H+E step per cell (the floor of the byte model): the six
     field components read and written once (6 x 2 x r), one material value per cell (r per
     conductivity: 2 in a VTI medium), and the CPML memory, four arrays read and written on the
     cells of each axis' two slabs (4 x 2 x r x sum over axes of 2 npml / n)."""
