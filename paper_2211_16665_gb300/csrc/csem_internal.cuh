@@ -64,7 +64,7 @@ template <> struct C2<double> { typedef double2 T; };
 
 constexpr int kMaxFreq = 8;
 constexpr int kBlock = 256;
-constexpr int kMaxBlockSteps = 64;   // largest transform block (snapshots per flush)
+constexpr int kMaxBlockSteps = 128;  // largest transform block (snapshots per flush)
 
 // Slab index of a half node i (between nodes i and i+1) on an axis of n cells:
 // the first npml and the last npml half nodes lie in the CPML.

@@ -834,6 +834,8 @@ cudaError_t launch_dft(const StepParams<R> &p, const PointParams<R> &q, int S, i
     const int nvb = (int)((p.vol + kBlock - 1) / kBlock);
     const int nblk = (vol ? nvb * 3 * S : 0) + (q.n_rec > 0 ? S : 0);
     if (nblk == 0 || cnt <= 0) return cudaSuccess;
+    // the weights of all cnt snapshots and nf frequencies are staged in shared memory at once
+    if (cnt > kMaxBlockSteps || q.nf > kMaxFreq || p.nf > kMaxFreq) return cudaErrorInvalidValue;
     const bool full = (cnt % 16 == 0);
     if (!vol) k_dft<R, false, false, 0><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
     else if (kahan && full) k_dft<R, true, true, 16><<<nblk, kBlock, 0, st>>>(p, q, n0_off, cnt, nvb, S);
