@@ -402,6 +402,24 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 }
 
 
+// Packed FP32 pairs for the flush sums: a complex accumulator (re, im) or a weight pair in
+// one 64-bit register, and a real value duplicated into both lanes.  fma.rn.f32x2 does one
+// fused multiply-add per lane, each rounded to nearest once, so a sum built with it equals
+// the sum of the same fmaf calls bit for bit, with half the instructions.
+__device__ __forceinline__ uint64_t dup_f32x2(float v) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ void fma_f32x2(uint64_t &acc, uint64_t a, uint64_t b) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+__device__ __forceinline__ float2 unpack_f32x2(uint64_t v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
 // Receiver transforms of source s over the ms snapshots from step n0 (FP64 sums of the
 // eight interpolation taps of each receiver), one receiver per thread.
 __device__ __forceinline__ void dft_receivers(const StepParams<float> &p, const PointParams<float> &q, int n0, int ms,
@@ -437,7 +455,7 @@ __host__ __device__ constexpr int nf_pad(int nf) { return nf <= 2 ? 2 : (nf <= 4
 // Each thread sums its two entries' MS snapshots into NF frequencies (NF a
 // compile-time bound, the weights of frequencies >= nf are zero and their sums
 // are dropped), reading each snapshot pair with one 8-byte load and each pair
-// of complex weights with one 16-byte broadcast.  One warp waits on the
+// of complex weights with one 16-byte broadcast, and summing with packed FMAs.  One warp waits on the
 // barrier; the others wait at __syncthreads without issuing.
 template <bool KAHAN, int MS, int NF>
 __global__ void __launch_bounds__(kBulkThreads, bulk_minb<MS>()) k_dft_bulk(const StepParams<float> p,
@@ -503,42 +521,40 @@ __global__ void __launch_bounds__(kBulkThreads, bulk_minb<MS>()) k_dft_bulk(cons
     if (bad) return;
     const int t2 = 2 * threadIdx.x;
     if (t2 >= rows) return;
-    float2 b0[NF], b1[NF];
+    uint64_t p0[NF], p1[NF];            // packed (re, im) block sums of entries t2, t2 + 1
 #pragma unroll
-    for (int f = 0; f < NF; ++f) b0[f] = b1[f] = make_float2(0.f, 0.f);
-    const float4 *w4 = reinterpret_cast<const float4 *>(w_s);
+    for (int f = 0; f < NF; ++f) p0[f] = p1[f] = 0ull;
+    const ulonglong2 *w2 = reinterpret_cast<const ulonglong2 *>(w_s);
 #pragma unroll 4
     for (int m = 0; m < MS; ++m) {
         const float2 e = *reinterpret_cast<const float2 *>(ring_s + m * kBlock + t2);
+        const uint64_t ex = dup_f32x2(e.x), ey = dup_f32x2(e.y);
 #pragma unroll
         for (int g = 0; g < NF / 2; ++g) {
-            const float4 w = w4[m * (NF / 2) + g];       // frequencies 2g and 2g+1
-            b0[2 * g].x = fmaf(e.x, w.x, b0[2 * g].x);
-            b0[2 * g].y = fmaf(e.x, w.y, b0[2 * g].y);
-            b0[2 * g + 1].x = fmaf(e.x, w.z, b0[2 * g + 1].x);
-            b0[2 * g + 1].y = fmaf(e.x, w.w, b0[2 * g + 1].y);
-            b1[2 * g].x = fmaf(e.y, w.x, b1[2 * g].x);
-            b1[2 * g].y = fmaf(e.y, w.y, b1[2 * g].y);
-            b1[2 * g + 1].x = fmaf(e.y, w.z, b1[2 * g + 1].x);
-            b1[2 * g + 1].y = fmaf(e.y, w.w, b1[2 * g + 1].y);
+            const ulonglong2 w = w2[m * (NF / 2) + g];   // (re, im) of frequencies 2g and 2g+1
+            fma_f32x2(p0[2 * g], ex, w.x);
+            fma_f32x2(p0[2 * g + 1], ex, w.y);
+            fma_f32x2(p1[2 * g], ey, w.x);
+            fma_f32x2(p1[2 * g + 1], ey, w.y);
         }
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         if (f >= p.nf) break;
+        const float2 s0 = unpack_f32x2(p0[f]), s1 = unpack_f32x2(p1[f]);
         float4 a = *reinterpret_cast<const float4 *>(acc_s + f * kBlock + t2);   // entries t2, t2+1
         if (KAHAN) {
             float4 cc = *reinterpret_cast<const float4 *>(cmp_s + f * kBlock + t2);
-            kahan_add(a.x, cc.x, b0[f].x);
-            kahan_add(a.y, cc.y, b0[f].y);
-            kahan_add(a.z, cc.z, b1[f].x);
-            kahan_add(a.w, cc.w, b1[f].y);
+            kahan_add(a.x, cc.x, s0.x);
+            kahan_add(a.y, cc.y, s0.y);
+            kahan_add(a.z, cc.z, s1.x);
+            kahan_add(a.w, cc.w, s1.y);
             *reinterpret_cast<float4 *>(C + (long long)f * p.vol + t2) = cc;
         } else {
-            a.x += b0[f].x;
-            a.y += b0[f].y;
-            a.z += b1[f].x;
-            a.w += b1[f].y;
+            a.x += s0.x;
+            a.y += s0.y;
+            a.z += s1.x;
+            a.w += s1.y;
         }
         *reinterpret_cast<float4 *>(A + (long long)f * p.vol + t2) = a;
     }
@@ -619,10 +635,10 @@ __global__ void __launch_bounds__(kBulkThreads, 3) k_dft_stream(const StepParams
     }
     const int t2 = 2 * threadIdx.x;
     const bool mine = t2 < rows;
-    float2 b0[NF], b1[NF];
+    uint64_t p0[NF], p1[NF];            // packed (re, im) block sums of entries t2, t2 + 1
 #pragma unroll
-    for (int f = 0; f < NF; ++f) b0[f] = b1[f] = make_float2(0.f, 0.f);
-    const float4 *w4 = reinterpret_cast<const float4 *>(w_s);
+    for (int f = 0; f < NF; ++f) p0[f] = p1[f] = 0ull;
+    const ulonglong2 *w2 = reinterpret_cast<const ulonglong2 *>(w_s);
     bool ok = true;
     int ch = 0;
     for (; ch < NCH; ++ch) {
@@ -636,18 +652,15 @@ __global__ void __launch_bounds__(kBulkThreads, 3) k_dft_stream(const StepParams
 #pragma unroll
         for (int g = 0; g < kStG; ++g) {
             const float2 e = *reinterpret_cast<const float2 *>(sg + g * kBlock);
+            const uint64_t ex = dup_f32x2(e.x), ey = dup_f32x2(e.y);
             const int m = ch * kStG + g;
 #pragma unroll
             for (int h = 0; h < NF / 2; ++h) {
-                const float4 w = w4[m * (NF / 2) + h];       // frequencies 2h and 2h+1
-                b0[2 * h].x = fmaf(e.x, w.x, b0[2 * h].x);
-                b0[2 * h].y = fmaf(e.x, w.y, b0[2 * h].y);
-                b0[2 * h + 1].x = fmaf(e.x, w.z, b0[2 * h + 1].x);
-                b0[2 * h + 1].y = fmaf(e.x, w.w, b0[2 * h + 1].y);
-                b1[2 * h].x = fmaf(e.y, w.x, b1[2 * h].x);
-                b1[2 * h].y = fmaf(e.y, w.y, b1[2 * h].y);
-                b1[2 * h + 1].x = fmaf(e.y, w.z, b1[2 * h + 1].x);
-                b1[2 * h + 1].y = fmaf(e.y, w.w, b1[2 * h + 1].y);
+                const ulonglong2 w = w2[m * (NF / 2) + h];   // (re, im) of frequencies 2h and 2h+1
+                fma_f32x2(p0[2 * h], ex, w.x);
+                fma_f32x2(p0[2 * h + 1], ex, w.y);
+                fma_f32x2(p1[2 * h], ey, w.x);
+                fma_f32x2(p1[2 * h + 1], ey, w.y);
             }
         }
     }
@@ -667,19 +680,20 @@ __global__ void __launch_bounds__(kBulkThreads, 3) k_dft_stream(const StepParams
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         if (f >= p.nf) break;
+        const float2 s0 = unpack_f32x2(p0[f]), s1 = unpack_f32x2(p1[f]);
         float4 a = *reinterpret_cast<const float4 *>(acc_s + f * kBlock + t2);   // entries t2, t2+1
         if (KAHAN) {
             float4 cc = *reinterpret_cast<const float4 *>(cmp_s + f * kBlock + t2);
-            kahan_add(a.x, cc.x, b0[f].x);
-            kahan_add(a.y, cc.y, b0[f].y);
-            kahan_add(a.z, cc.z, b1[f].x);
-            kahan_add(a.w, cc.w, b1[f].y);
+            kahan_add(a.x, cc.x, s0.x);
+            kahan_add(a.y, cc.y, s0.y);
+            kahan_add(a.z, cc.z, s1.x);
+            kahan_add(a.w, cc.w, s1.y);
             *reinterpret_cast<float4 *>(C + (long long)f * p.vol + t2) = cc;
         } else {
-            a.x += b0[f].x;
-            a.y += b0[f].y;
-            a.z += b1[f].x;
-            a.w += b1[f].y;
+            a.x += s0.x;
+            a.y += s0.y;
+            a.z += s1.x;
+            a.w += s1.y;
         }
         *reinterpret_cast<float4 *>(A + (long long)f * p.vol + t2) = a;
     }
