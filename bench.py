@@ -334,7 +334,8 @@ def run_ours(args):
     fused = kms["k_step"] > 0
     st_ms = kms["k_step"] if fused else kms["k_h"] + kms["k_e"]
     lc = eng.launch_config()
-    st_name = ({"fused one-pass H+E": "k_step_fz", "fused warp-specialised H+E": "k_step_ws"}.get(
+    st_name = ({"fused one-pass H+E": "k_step_fz", "fused warp-specialised H+E": "k_step_ws",
+                "wave-ordered H+E": "k_step_wave"}.get(
         lc["step"]["kernel"], "k_step")) if fused else \
         "+".join(f"k_{w}_{lc['step'][w]['kernel'].split()[0]}" for w in ("h", "e"))
     b_cell = stencil_bytes(wl, eng)

@@ -307,8 +307,9 @@ int csem_set_early_stop_volumes(csem_ctx *ctx, double tol, double floor_frac);
  * bulk-copy-staged kernels (1, 2 or 4 rows per block, 2-16 planes) or the
  * lean four-cell kernels (1, 2 or 4 planes; see csem_set_launch) -- by
  * timing each candidate on n_src sources of this grid;
- * later calls use the fastest.  It then times the fused H+E step kernel (z
- * blocking 4, 8 or 16) against the best split pair and keeps the faster, and
+ * later calls use the fastest.  It then times the fused H+E step kernels (the
+ * tiled one with z blocking 4, 8 or 16; for FP32 the one-pass, warp-specialised
+ * and wave-ordered steps) against the best split pair and keeps the fastest, and
  * last, when nt >= 256, the transform flush over 128 steps: the register
  * kernel or (FP32) the bulk-copy kernel, over 16, 32, 64 or 128 snapshots, run after
  * its block or on a second stream overlapping the next block (needs a ring of
@@ -318,7 +319,7 @@ int csem_set_early_stop_volumes(csem_ctx *ctx, double tol, double floor_frac);
  * bulk-copy-staged kernel, + 8192 * cells per thread for the lean kernel), then 4 * snapshots per flush + flush mode (as in
  * csem_set_launch), then the step's form: 0 split, 4/8/16 the fused z
  * blocking, 10000 + code the one-pass kernel, 30000 + code the
- * warp-specialised fused kernel.  Overwrites the
+ * warp-specialised fused kernel, 50000 + code the wave-ordered step.  Overwrites the
  * context's field state and blocks until the timing is done.
  * Errors: INVALID_ARG, CUDA. */
 int csem_autotune(csem_ctx *ctx, int n_src, int *kz_out, void *stream);
@@ -330,7 +331,12 @@ int csem_autotune(csem_ctx *ctx, int n_src, int *kz_out, void *stream);
  * kernel with TMA-staged planes; 30000 + planes * 100 + rows * 10 + blocks = the
  * warp-specialised fused kernel: producer warps compute H^{n+1/2} of the tile and
  * its one-cell halo into shared memory, consumer warps the E step from it; rows
- * and blocks (4,2), (4,3), (6,2), (8,1), (8,2); FP32, second order), flush mode (bit 0: bulk
+ * and blocks (4,2), (4,3), (6,2), (8,1), (8,2); FP32, second order; 50000 + lag * 100 +
+ * planes * 10 + blocks = the wave-ordered step: the lean H and E tiles (2 cells per
+ * thread, 2 or 4 planes, 6 or 8 blocks/SM) of one step in one launch, each block taking
+ * the next ticket of a counter, E of z block c after H of z block c + lag, so that E reads
+ * E^n and H^{n+1/2} while they are still in L2; an E tile waits (bounded) until H of its
+ * z block and the one below is complete; FP32, second order, nx a multiple of 4), flush mode (bit 0: bulk
  * copy, FP32 only, else register kernel; bit 1: overlapped with the next
  * block on a second stream), snapshots per flush (16, 32, 64 or 128; the
  * context's ring of 17, 33, 65 or 129 slots must hold snapshots + 1, or
@@ -365,7 +371,9 @@ int csem_set_trace(csem_ctx *ctx, double *trace_dev);
  * The copies themselves complete; nothing faults.  In the warp-specialised fused step,
  * whose warps hand planes over through shared memory without copies, the producer warps
  * skip their first arrival instead, so the consumers' bounded wait runs out (and then the
- * producers' own).  0 restores normal operation (the
+ * producers' own).  In the wave-ordered step the E tiles wait for one H tile more than
+ * there are, so the first wave of E tiles gives up after about a second and the rest skip
+ * the wait.  0 restores normal operation (the
  * field state of the run that timed out is not usable).  Synchronises the device.
  * Errors: INVALID_ARG. */
 int csem_set_copy_fault(csem_ctx *ctx, int extra_bytes);

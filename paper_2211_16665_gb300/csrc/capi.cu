@@ -142,6 +142,7 @@ struct csem_ctx {
     int fused_kz = 0;                   // > 0: fused H+E step with this z blocking (autotuned)
     int FZ_by = 0, FZ_mb = 4, FZ_kz = 16; // FZ_by > 0: fused one-pass FP32 step, rows per block (autotuned)
     int FZ_ws = 0;                        // 1: the warp-specialised fused step with those shape fields
+    int WAVE_lag = 0, WAVE_kz = 4, WAVE_mb = 8; // WAVE_lag > 0: wave-ordered FP32 step (autotuned)
     int fault_tx = 0;                   // test hook: extra bytes the bulk-copy kernels' first barrier arm expects
     int VEC_h = 0, VEC_e = 0;           // 1: four-cells-per-thread FP32 kernels (autotuned)
     int TMA_h = 0, TMA_e = 0;           // > 0: bulk-copy-staged FP32 kernels, rows per block (autotuned)
@@ -155,6 +156,7 @@ struct csem_ctx {
     float *d_psiL = nullptr, *d_cEm = nullptr;   // lean kernels: CPML memory in volume arrays, masked dt/eps
     float *d_q = nullptr;                // fused one-pass step: V sigma per cell [1 or 2][vol] (sigma_h, sigma_v)
     float *d_tabG = nullptr;             // fused one-pass step: per-axis widths h [n] and sums s [n+1], padded
+    unsigned *d_wave = nullptr;          // wave-ordered step: ticket, finished-block and per-z-block counters
     void *d_cE = nullptr, *d_H = nullptr, *d_H2 = nullptr, *d_ering = nullptr, *d_psi = nullptr, *d_comp = nullptr, *d_edge = nullptr;
     int M = 16, nslot = 17;
     int flush_mode = 0;                  // bit 0: bulk-copy flush (FP32 only), else register flush;
@@ -237,7 +239,9 @@ void axis_tab(const csem_ctx *c, int a, csem::AxisTab<R> &t) {
 int lean_len(int n) { return (n + 1 + 3 + 3) / 4 * 4; }
 // The fused one-pass step's launch shape as one code (0: not selected): kz * 100 + rows * 10 + blocks;
 // csem_autotune and csem_set_launch report and take it as 10000 + that code.
+// The wave-ordered step (kern_lean.cu) takes 40000 + lag * 100 + planes * 10 + blocks.
 int fz_code(const csem_ctx *c) {
+    if (c->WAVE_lag) return 40000 + c->WAVE_lag * 100 + c->WAVE_kz * 10 + c->WAVE_mb;
     return c->FZ_by ? c->FZ_ws * 20000 + c->FZ_kz * 100 + c->FZ_by * 10 + c->FZ_mb : 0;
 }
 // Per-axis widths of the fused one-pass step: h (primal, half nodes) and s = h[i-1] + h[i] at the
@@ -438,6 +442,8 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
     p.lx = p.ly = p.lz = csem::AxisTab<R>{};
     p.lzero = nullptr;
     p.FZ_by = 0; p.FZ_mb = 4; p.FZ_kz = 16; p.FZ_ws = 0;
+    p.WAVE_lag = 0; p.WAVE_kz = 4; p.WAVE_mb = 8;
+    p.wave = nullptr;
     p.qh = p.qv = nullptr;
     p.gx = p.gy = p.gz = csem::GeoTab{nullptr, nullptr};
     p.k2w0dt = 0.f;
@@ -454,6 +460,8 @@ csem::StepParams<R> step_params(csem_ctx *c, bool dft, void *acc) {
         }
         p.psiL = c->d_psiL;
         p.cEm = c->d_cEm;
+        p.wave = c->d_wave;
+        if (c->d_wave && c->d_psiL) { p.WAVE_lag = c->WAVE_lag; p.WAVE_kz = c->WAVE_kz; p.WAVE_mb = c->WAVE_mb; }
         p.inc = c->d_inc;
         p.tapk = c->d_tapk;
         if (c->d_q && c->d_tabG) {
@@ -537,7 +545,7 @@ cudaError_t launch_any(const csem_ctx *c, const csem::StepParams<R> &p, const cs
 template <typename R>
 cudaError_t tap_prep(csem_ctx *c, const csem::StepParams<R> &p, int S, int nsteps, cudaStream_t st) {
     if constexpr (sizeof(R) == 4) {
-        if (p.inc && p.colmap && (p.LEAN_e || p.FZ_by)) return csem::launch_tap_inc(p, S, nsteps, c->nt, st);
+        if (p.inc && p.colmap && (p.LEAN_e || p.FZ_by || p.WAVE_lag)) return csem::launch_tap_inc(p, S, nsteps, c->nt, st);
     }
     return cudaSuccess;
 }
@@ -1013,7 +1021,7 @@ TdPlan td_layout(const csem_ctx *c, int S, int NR, int C) {
     P.K = (c->nt + C - 1) / C;
     P.nck = std::max(P.K - 2, 0);
     P.recompute = (long long)(P.K - 1) * C;
-    P.lean = c->d_psiL && (c->LEAN_h || c->LEAN_e) && !c->FZ_by;
+    P.lean = c->d_psiL && (c->LEAN_h || c->LEAN_e || c->WAVE_lag) && !c->FZ_by;
     P.fused = c->fused_kz > 0 || c->FZ_by > 0;
     const size_t R = c->rsize, v3 = 3 * (size_t)c->vol, Ss = (size_t)S;
     const size_t psi = Ss * (size_t)c->psi_stride * R, psiL = P.lean ? Ss * 12 * (size_t)c->vol * sizeof(float) : 0;
@@ -1262,16 +1270,17 @@ int time_impl(csem_ctx *c, int S, void *vol, int launches, double *ms, cudaStrea
     p.inc_ntl = c->last_ntl;
     p.itaps = c->d_itaps; p.itap_stride = 8;
     p.n_emit = 1; p.J = 1; p.coef = c->d_ones; p.T = c->d_T;
-    const int fkz = p.fused_kz, fzb = p.FZ_by;
+    const int fkz = p.fused_kz, fzb = p.FZ_by, wlag = p.WAVE_lag;
     const int jmod = std::max(1, std::min(kChunk, c->nt - 1));   // steps within one chunk's tap increments
     if constexpr (sizeof(R) == 4) CK(csem::launch_tap_inc(p, S, kChunk, c->nt, st));
     for (int w : {0, 1, 2, 3}) {
-        if (w == 1 && fkz == 0 && fzb == 0) { ms[1] = 0.0; continue; }
+        if (w == 1 && fkz == 0 && fzb == 0 && wlag == 0) { ms[1] = 0.0; continue; }
         auto go = [&](int j) -> cudaError_t {
             if (w == 3) return flush<R>(c, p, q, S, 0, cnt, true, c->kahan != 0, st);
             csem::StepParams<R> pp = p;
             pp.fused_kz = (w == 1) ? fkz : 0;
             pp.FZ_by = (w == 1) ? fzb : 0;
+            pp.WAVE_lag = (w == 1) ? wlag : 0;
             return launch_any<R>(c, pp, q, S, j % jmod, st, w == 1 ? 5 : (w == 0 ? 1 : 4));
         };
         for (int j = 0; j < 2; ++j) CK(go(j));
@@ -1364,27 +1373,36 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
         }
         // fused H+E steps against the best split pair: the tiled kernel (kz 4, 8, 16) and,
         // for FP32 with nx even, the one-pass kernel (rows per block and resident blocks
-        // (4, 4), (4, 6), (8, 2), (8, 3), z blocks of 8, 16, 32, 64 planes)
+        // (4, 4), (4, 6), (8, 2), (8, 3), z blocks of 8, 16, 32, 64 planes), the
+        // warp-specialised one, and the wave-ordered step (both lean halves in one launch)
         {
             p.KZ_h = c->KZ_h; p.KZ_e = c->KZ_e; p.MB_h = c->MB_h; p.MB_e = c->MB_e;
             p.VEC_h = c->VEC_h; p.VEC_e = c->VEC_e;
             p.TMA_h = c->TMA_h; p.TMA_e = c->TMA_e;
             p.LEAN_h = c->LEAN_h; p.LEAN_e = c->LEAN_e;
-            struct Cand { int f, by, mb, kz, ws; };
-            std::vector<Cand> cands = {{0, 0, 4, 16, 0}, {4, 0, 4, 16, 0}, {8, 0, 4, 16, 0}, {16, 0, 4, 16, 0}};
+            struct Cand { int f, by, mb, kz, ws, lag; };
+            std::vector<Cand> cands = {{0, 0, 4, 16, 0, 0}, {4, 0, 4, 16, 0, 0}, {8, 0, 4, 16, 0, 0}, {16, 0, 4, 16, 0, 0}};
             if (sizeof(R) == 4 && c->d_q && c->nx % 2 == 0) {
                 const int bm[4][2] = {{4, 4}, {4, 6}, {8, 2}, {8, 3}};
                 for (const auto &b : bm)
-                    for (int kz : {8, 16, 32, 64}) cands.push_back({0, b[0], b[1], kz, 0});
+                    for (int kz : {8, 16, 32, 64}) cands.push_back({0, b[0], b[1], kz, 0, 0});
                 if (c->d_cEm && c->d_psi) {        // the warp-specialised fused step
                     const int wm[5][2] = {{4, 2}, {4, 3}, {6, 2}, {8, 1}, {8, 2}};
                     for (const auto &b : wm)
-                        for (int kz : {8, 16, 32, 64}) cands.push_back({0, b[0], b[1], kz, 1});
+                        for (int kz : {8, 16, 32, 64}) cands.push_back({0, b[0], b[1], kz, 1, 0});
+                }
+                // the wave-ordered step: E lagging H by 1 to 4 z blocks of 2 or 4 planes, 6 or 8 blocks/SM
+                if constexpr (sizeof(R) == 4) {
+                    for (int kz : {2, 4})
+                        for (int mb : {6, 8})
+                            if (csem::wave_supported(p, kz, mb))
+                                for (int lag : {1, 2, 3, 4}) cands.push_back({0, 0, mb, kz, 0, lag});
                 }
             }
             auto time_cand = [&](const Cand &cd, float *t) -> int {
                 p.fused_kz = cd.f;
                 p.FZ_by = cd.by; p.FZ_mb = cd.mb; p.FZ_kz = cd.kz; p.FZ_ws = cd.ws;
+                p.WAVE_lag = cd.lag; p.WAVE_kz = cd.lag ? cd.kz : 4; p.WAVE_mb = cd.lag ? cd.mb : 8;
                 for (int j = 0; j < 3; ++j) CK(csem::launch_step<R>(p, q, S, 0, st, 5));
                 CK(cudaEventRecord(e0, st));
                 const int reps = 20;
@@ -1414,8 +1432,10 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
             if (!(tf[1] < ts[1])) bc = cands[0];
             c->fused_kz = bc.f;
             c->FZ_by = bc.by; c->FZ_mb = bc.mb; c->FZ_kz = bc.kz; c->FZ_ws = bc.ws;
+            c->WAVE_lag = bc.lag; c->WAVE_kz = bc.lag ? bc.kz : 4; c->WAVE_mb = bc.lag ? bc.mb : 8;
             p.fused_kz = 0;
             p.FZ_by = 0;
+            p.WAVE_lag = 0;
         }
     }
     // transform flush: register or bulk copy (FP32), 16 or 32 snapshots, after
@@ -1431,6 +1451,7 @@ int autotune_impl(csem_ctx *c, int S, cudaStream_t st) {
             p.comp = c->kahan ? (R2 *)c->d_comp : nullptr;
             p.fused_kz = c->fused_kz;
             p.FZ_by = c->FZ_by; p.FZ_mb = c->FZ_mb; p.FZ_kz = c->FZ_kz; p.FZ_ws = c->FZ_ws;
+            p.WAVE_lag = c->WAVE_lag; p.WAVE_kz = c->WAVE_kz; p.WAVE_mb = c->WAVE_mb;
             const bool kahan = c->kahan != 0;
             double best = 1e30;
             int bm = 0, bM = 16;
@@ -1468,7 +1489,7 @@ void free_ctx(csem_ctx *c) {
     if (!c) return;
     cudaDeviceSynchronize();
     for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
-    void *ptrs[] = {c->d_q, c->d_tabG, c->d_ho, c->d_tabL, c->d_psiL, c->d_cEm, c->d_inc, c->d_tapk, c->d_tab, c->d_h, c->d_cE, c->d_H, c->d_H2, c->d_ering, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
+    void *ptrs[] = {c->d_wave, c->d_q, c->d_tabG, c->d_ho, c->d_tabL, c->d_psiL, c->d_cEm, c->d_inc, c->d_tapk, c->d_tab, c->d_h, c->d_cE, c->d_H, c->d_H2, c->d_ering, c->d_psi, c->d_comp, c->d_edge, c->d_wR, c->d_w64,
                     c->d_alpha, c->d_racc, c->d_coef, c->d_T, c->d_ones, c->d_rtaps, c->d_itaps, c->d_colmap, c->d_tflag, c->d_cpos, c->d_cval, c->d_step, c->d_bad};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -1684,7 +1705,9 @@ int csem_create(csem_ctx **out, const csem_grid *g, const csem_opts *o) {
         if (rc == CSEM_OK && c->nx % 4 == 0 && need < 0.25 * (double)free_b) {
             step(dalloc(c, &c->d_psiL, (size_t)S * 12 * c->vol * sizeof(float)));
             step(dalloc(c, &c->d_cEm, 3 * (size_t)c->vol * sizeof(float)));
-            if (rc == CSEM_OK && cudaMemset(c->d_cEm, 0, 3 * (size_t)c->vol * sizeof(float)) != cudaSuccess)
+            step(dalloc(c, &c->d_wave, (2 + csem::kMaxWaveChunks) * sizeof(unsigned)));
+            if (rc == CSEM_OK && (cudaMemset(c->d_cEm, 0, 3 * (size_t)c->vol * sizeof(float)) != cudaSuccess ||
+                                  cudaMemset(c->d_wave, 0, (2 + csem::kMaxWaveChunks) * sizeof(unsigned)) != cudaSuccess))
                 rc = fail(CSEM_ERR_CUDA, "context initialisation failed");
         }
     }
@@ -1765,13 +1788,14 @@ int csem_check(csem_ctx *c, void *stream) {
     int bad = 0;
     CK(cudaMemcpy(&bad, c->d_bad, sizeof(int), cudaMemcpyDeviceToHost));
     CK(cudaMemset(c->d_bad, 0, sizeof(int)));
-    if (bad & (csem::kErrFlushWait | csem::kErrStagedWait | csem::kErrOnepassWait)) {
+    if (bad & (csem::kErrFlushWait | csem::kErrStagedWait | csem::kErrOnepassWait | csem::kErrWaveWait)) {
         std::string who;
         auto add = [&](const char *w) { who += (who.empty() ? "" : " and ") + std::string(w); };
         if (bad & csem::kErrFlushWait) add("a bulk-copy transform flush");
         if (bad & csem::kErrStagedWait) add("a row-staged H/E step kernel");
         if (bad & csem::kErrOnepassWait) add("a fused step kernel (one-pass or warp-specialised)");
-        return fail(CSEM_ERR_TIMEOUT, who + " gave up waiting for its bulk copies (its results were not written)");
+        if (bad & csem::kErrWaveWait) add("an E tile of the wave-ordered step");
+        return fail(CSEM_ERR_TIMEOUT, who + " gave up a bounded wait (the results of that run are not valid)");
     }
     if (bad & csem::kErrNonfinite) return fail(CSEM_ERR_NONFINITE, "a resistivity was non-positive or non-finite");
     return CSEM_OK;
@@ -1895,9 +1919,19 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
     if (!c || !cfg) return fail(CSEM_ERR_INVALID_ARG, "NULL argument");
     const int kzh = cfg[0], mbh = cfg[1], kze = cfg[2], mbe = cfg[3], fm = cfg[5], M = cfg[6];
     // cfg[4] >= 10000: the fused one-pass step, 10000 + planes * 100 + rows * 10 + blocks;
-    // cfg[4] >= 30000: the warp-specialised fused step, 30000 + the same code
-    const int ws = cfg[4] >= 30000 ? 1 : 0;
-    const int fz = cfg[4] >= 10000 ? cfg[4] - (ws ? 30000 : 10000) : 0, fkz = fz ? 0 : cfg[4];
+    // cfg[4] >= 30000: the warp-specialised fused step, 30000 + the same code;
+    // cfg[4] >= 50000: the wave-ordered step, 50000 + lag * 100 + planes * 10 + blocks
+    const int wv = cfg[4] >= 50000 ? cfg[4] - 50000 : 0;
+    const int wv_lag = wv / 100, wv_kz = (wv / 10) % 10, wv_mb = wv % 10;
+    if (wv) {
+        csem::StepParams<float> tp{};
+        tp.nx = c->nx; tp.nz = c->nz; tp.psiL = c->d_psiL; tp.cEm = c->d_cEm; tp.wave = c->d_wave;
+        tp.lx.ih_n = c->d_tabL ? (const float *)c->d_tabL : nullptr; tp.lzero = tp.lx.ih_n;
+        if (c->precision != 32 || c->order != 2 || wv_lag < 1 || !csem::wave_supported(tp, wv_kz, wv_mb))
+            return fail(CSEM_ERR_INVALID_ARG, "wave-ordered step: FP32, second order, nx a multiple of 4, lag >= 1, 2 or 4 planes, 6 or 8 blocks/SM");
+    }
+    const int ws = (!wv && cfg[4] >= 30000) ? 1 : 0;
+    const int fz = (!wv && cfg[4] >= 10000) ? cfg[4] - (ws ? 30000 : 10000) : 0, fkz = (fz || wv) ? 0 : cfg[4];
     const int fz_kz = fz / 100, fz_by = (fz / 10) % 10, fz_mb = fz % 10;
     if (fz && !ws && (c->precision != 32 || c->order != 2 || !c->d_q || c->nx % 2 != 0 || !csem::fz_supported(fz_by, fz_mb, fz_kz)))
         return fail(CSEM_ERR_INVALID_ARG, "fused one-pass step: FP32, second order, nx even, rows/blocks (4,4), (4,6), (8,2) or (8,3), 2-99 planes");
@@ -1948,6 +1982,7 @@ int csem_set_launch(csem_ctx *c, const int *cfg) {
     c->KZ_h = kzh; c->MB_h = mbh; c->KZ_e = kze; c->MB_e = mbe;
     c->fused_kz = fkz; c->flush_mode = fm; c->M = M;
     c->FZ_by = fz_by; c->FZ_mb = fz ? fz_mb : 4; c->FZ_kz = fz ? fz_kz : 16; c->FZ_ws = ws;
+    c->WAVE_lag = wv_lag; c->WAVE_kz = wv ? wv_kz : 4; c->WAVE_mb = wv ? wv_mb : 8;
     c->VEC_h = vh; c->VEC_e = ve;
     c->TMA_h = th; c->TMA_e = te;
     c->LEAN_h = lh; c->LEAN_e = le;
@@ -1962,7 +1997,7 @@ int csem_autotune(csem_ctx *c, int n_src, int *kz_out, void *stream) {
         kz_out[0] = (c->KZ_h * 16 + c->MB_h) + 256 * c->VEC_h + 1024 * c->TMA_h + 8192 * c->LEAN_h;
         kz_out[1] = (c->KZ_e * 16 + c->MB_e) + 256 * c->VEC_e + 1024 * c->TMA_e + 8192 * c->LEAN_e;
         kz_out[2] = c->M * 4 + c->flush_mode;
-        kz_out[3] = c->FZ_by ? 10000 + fz_code(c) : c->fused_kz;
+        kz_out[3] = (c->FZ_by || c->WAVE_lag) ? 10000 + fz_code(c) : c->fused_kz;
     }
     return CSEM_OK;
 }

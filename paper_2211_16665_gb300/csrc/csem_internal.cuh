@@ -57,6 +57,8 @@ constexpr int kErrNonfinite = 1;     // a resistivity was non-positive or non-fi
 constexpr int kErrFlushWait = 2;     // a bulk-copy transform flush gave up waiting for its copies
 constexpr int kErrStagedWait = 4;    // a row-staged H / E step kernel gave up waiting
 constexpr int kErrOnepassWait = 8;   // the fused one-pass step kernel gave up waiting
+constexpr int kErrWaveWait = 16;     // an E tile of the wave-ordered step gave up waiting for H
+constexpr int kMaxWaveChunks = 4096; // z blocks the wave-ordered step's counters cover
 
 template <typename R> struct C2;
 template <> struct C2<float> { typedef float2 T; };
@@ -123,6 +125,10 @@ struct StepParams {
     // unless the medium is VTI), per-axis widths, 2 w0 dt
     int FZ_by, FZ_mb, FZ_kz;
     int FZ_ws;                     // 1: the warp-specialised fused kernel with the same shape fields
+    // wave-ordered step (kern_lean.cu): the lean H and E tiles in one launch, E lagging H by
+    // WAVE_lag z blocks of WAVE_kz planes (WAVE_lag 0: off); wave: [2 + kMaxWaveChunks] counters
+    int WAVE_kz, WAVE_mb, WAVE_lag;
+    unsigned *wave;
     const float *qh, *qv;
     GeoTab gx, gy, gz;
     float k2w0dt;
@@ -211,6 +217,11 @@ bool ws_supported(int by, int mb, int kz);
 // mb (resident 128-thread blocks per SM) in {6,8} for w = 1 and {4,6,8} for w = 2
 cudaError_t launch_field_lean(const StepParams<float> &p, int S, int jstep, cudaStream_t st, bool h, int w, int kz,
                               int mb);
+// wave-ordered FP32 step (kern_lean.cu): the lean H and E tiles (2 cells per thread) of one step in one
+// launch, WAVE_kz in {2, 4}, WAVE_mb in {6, 8}, WAVE_lag >= 1; an E tile that gives up waiting raises
+// kErrWaveWait
+cudaError_t launch_step_wave(const StepParams<float> &p, int S, int jstep, cudaStream_t st);
+bool wave_supported(const StepParams<float> &p, int kz, int mb);
 // cEm = cE with the PEC edges zeroed
 cudaError_t launch_mask_coef(const StepParams<float> &p, const float *cE, float *cEm, cudaStream_t st);
 // p.inc for the steps jstep in [0, nsteps) after *p.step (zero past nt)

@@ -207,6 +207,37 @@ __device__ __forceinline__ void h_plane(const StepParams<float> &p, const float 
     eyc = eyk;
 }
 
+// H over the KZ planes from z block kb of the tile (xb, yb) of source s (the tile: 32 W
+// cells of 4 rows, one W-cell column per thread): k_h_lean's block with its coordinates
+// as arguments, for the wave-ordered step (k_h_lean keeps its own copy, compiled as tuned).
+template <int W, int KZ>
+__device__ __forceinline__ void h_tile(const StepParams<float> &p, const int jstep, int xb, int yb, int kb, int s) {
+    const int i = (xb * kLeanX + (int)threadIdx.x) * W;
+    const int j = yb * kLeanRows + (int)threadIdx.y;
+    const int k0 = kb * KZ;
+    if (i >= p.nx || j >= p.ny) return;
+    const int k1 = min(k0 + KZ, p.nz);
+    const int n = *p.step + jstep;
+    const int vol = (int)p.vol, plane = (int)p.plane, npml = p.npml;
+    const float *__restrict__ E = p.ering + (long long)s * p.ering_stride + (long long)(n % p.nslot) * 3 * p.vol;
+    float *__restrict__ H = p.H + (long long)s * 3 * vol;
+    float *__restrict__ ps = p.psiL + (long long)s * 12 * vol;
+    LeanRow<W> r;
+    lean_row<W>(p, p.lx, p.ly, true, i, j, r);
+    const int j0 = yb * kLeanRows;
+    const bool yblk = (j0 < npml) || (j0 + kLeanRows > p.ny - npml);
+
+    int idx = k0 * plane + j * p.pitch + i;
+    Vec<W> exc = ldc<W>(E + idx), eyc = ldc<W>(E + vol + idx);
+#pragma unroll
+    for (int kk = 0; kk < KZ; ++kk, idx += plane) {
+        const int k = k0 + kk;
+        if (k >= k1) break;
+        if (yblk || k < npml || k >= p.nz - npml) h_plane<W, true>(p, E, H, ps, r, k, idx, exc, eyc);
+        else h_plane<W, false>(p, E, H, ps, r, k, idx, exc, eyc);
+    }
+}
+
 template <int W, int KZ, int MINB>
 __global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_h_lean(const StepParams<float> p, const int jstep) {
     const int i = (blockIdx.x * kLeanX + threadIdx.x) * W;
@@ -238,8 +269,19 @@ __global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_h_lean(const StepPa
     }
 }
 
+// H loads of the E update: through the read-only path, or (CG) from L2 only, for H that
+// other blocks of the same launch wrote (the read-only path and L1 are not coherent with them).
+template <int W, bool CG> __device__ __forceinline__ Vec<W> ldh(const float *p) {
+    if constexpr (!CG) return ldc<W>(p);
+    Vec<W> r;
+    if constexpr (W == 1) r.v[0] = __ldcg(p);
+    else { const float2 t = __ldcg(reinterpret_cast<const float2 *>(p)); r.v[0] = t.x; r.v[1] = t.y; }
+    return r;
+}
+template <bool CG> __device__ __forceinline__ float ldh1(const float *p) { return CG ? __ldcg(p) : __ldg(p); }
+
 // One plane k of the E update; hxm, hym: Hx, Hy of plane k-1 (in), of plane k (out).
-template <int W, bool YZ>
+template <int W, bool YZ, bool CG>
 __device__ __forceinline__ void e_plane(const StepParams<float> &p, const float *__restrict__ Eo, float *__restrict__ En,
                                         const float *__restrict__ H, float *__restrict__ ps, const LeanRow<W> &r, int s,
                                         int S, int jstep, int k, int idx, bool taps, Vec<W> &hxm, Vec<W> &hym) {
@@ -247,9 +289,9 @@ __device__ __forceinline__ void e_plane(const StepParams<float> &p, const float 
     const float *__restrict__ cE = p.cEm;
     const int ij = (r.j > 0) ? idx - pitch : idx;    // lower neighbours, clamped on the outer faces
     const int ii = (r.i > 0) ? idx - 1 : idx;
-    const Vec<W> hxc = ldc<W>(H + idx), hyc = ldc<W>(H + vol + idx), hzc = ldc<W>(H + 2 * vol + idx);
-    const Vec<W> hxj = ldc<W>(H + ij), hzj = ldc<W>(H + 2 * vol + ij);
-    const float hyp = __ldg(H + vol + ii), hzp = __ldg(H + 2 * vol + ii);
+    const Vec<W> hxc = ldh<W, CG>(H + idx), hyc = ldh<W, CG>(H + vol + idx), hzc = ldh<W, CG>(H + 2 * vol + idx);
+    const Vec<W> hxj = ldh<W, CG>(H + ij), hzj = ldh<W, CG>(H + 2 * vol + ij);
+    const float hyp = ldh1<CG>(H + vol + ii), hzp = ldh1<CG>(H + 2 * vol + ii);
     const Vec<W> eo0 = ldc<W>(Eo + idx), eo1 = ldc<W>(Eo + vol + idx), eo2 = ldc<W>(Eo + 2 * vol + idx);
     const Vec<W> c0 = ldc<W>(cE + idx), c1 = ldc<W>(cE + vol + idx), c2 = ldc<W>(cE + 2 * vol + idx);
     const float ihz = __ldg(p.lz.ih_n + k);
@@ -304,6 +346,42 @@ __device__ __forceinline__ void e_plane(const StepParams<float> &p, const float 
     hym = hyc;
 }
 
+// E over the KZ planes from z block kb of the tile (xb, yb) of source s (S sources per
+// launch): k_e_lean's block with its coordinates as arguments, H read through ldh<CG>.
+template <int W, int KZ, bool CG>
+__device__ __forceinline__ void e_tile(const StepParams<float> &p, const int jstep, int xb, int yb, int kb, int s,
+                                       int S) {
+    const int i = (xb * kLeanX + (int)threadIdx.x) * W;
+    const int j = yb * kLeanRows + (int)threadIdx.y;
+    const int k0 = kb * KZ;
+    if (i >= p.nx || j >= p.ny) return;
+    const int k1 = min(k0 + KZ, p.nz);
+    const int n = *p.step + jstep;
+    const int vol = (int)p.vol, plane = (int)p.plane, pitch = p.pitch, npml = p.npml;
+    const float *__restrict__ ring = p.ering + (long long)s * p.ering_stride;
+    const float *__restrict__ Eo = ring + (long long)(n % p.nslot) * 3 * p.vol;
+    float *__restrict__ En = const_cast<float *>(ring) + (long long)((n + 1) % p.nslot) * 3 * p.vol;
+    const float *__restrict__ H = p.H + (long long)s * 3 * vol;
+    float *__restrict__ ps = p.psiL + (long long)s * 12 * vol + 6LL * vol;
+    LeanRow<W> r;
+    lean_row<W>(p, p.lx, p.ly, false, i, j, r);
+    const int j0 = yb * kLeanRows;
+    const bool yblk = (j0 < npml) || (j0 + kLeanRows - 1 > p.ny - npml);
+    const bool taps = p.colmap && p.inc && p.tflag[s * p.tflag_stride + j * p.nseg + (i >> 5)];
+
+    int idx = k0 * plane + j * pitch + i;
+    const int im = (k0 > 0) ? idx - plane : idx;      // clamped on the bottom face
+    Vec<W> hxm = ldh<W, CG>(H + im), hym = ldh<W, CG>(H + vol + im);
+#pragma unroll
+    for (int kk = 0; kk < KZ; ++kk, idx += plane) {
+        const int k = k0 + kk;
+        if (k >= k1) break;
+        if (yblk || k < npml || k > p.nz - npml)
+            e_plane<W, true, CG>(p, Eo, En, H, ps, r, s, S, jstep, k, idx, taps, hxm, hym);
+        else e_plane<W, false, CG>(p, Eo, En, H, ps, r, s, S, jstep, k, idx, taps, hxm, hym);
+    }
+}
+
 template <int W, int KZ, int MINB>
 __global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_e_lean(const StepParams<float> p, const int jstep) {
     const int i = (blockIdx.x * kLeanX + threadIdx.x) * W;
@@ -334,8 +412,103 @@ __global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_e_lean(const StepPa
     for (int kk = 0; kk < KZ; ++kk, idx += plane) {
         const int k = k0 + kk;
         if (k >= k1) break;
-        if (yblk || k < npml || k > p.nz - npml) e_plane<W, true>(p, Eo, En, H, ps, r, s, S, jstep, k, idx, taps, hxm, hym);
-        else e_plane<W, false>(p, Eo, En, H, ps, r, s, S, jstep, k, idx, taps, hxm, hym);
+        if (yblk || k < npml || k > p.nz - npml) e_plane<W, true, false>(p, Eo, En, H, ps, r, s, S, jstep, k, idx, taps, hxm, hym);
+        else e_plane<W, false, false>(p, Eo, En, H, ps, r, s, S, jstep, k, idx, taps, hxm, hym);
+    }
+}
+
+// One whole step (H then E) in one launch, ordered by tickets: every block takes the next
+// ticket from a counter, and the tickets run through the z blocks ("chunks") as
+//   H(0) .. H(lag-1), then H(c + lag), E(c) for c = 0, 1, .., then the remaining E(c),
+// each chunk being all tiles of its z block (the sources of a tile next to one another).
+// The E tiles of chunk c read H of chunks c and c-1, which the H tiles of those chunks
+// write in the same launch: the H tiles count themselves done per chunk (after a fence),
+// and an E tile's thread 0 waits (bounded, about a second) until both chunks are complete.
+// No H tile waits, and an E tile waits only for tiles that took earlier tickets, so every
+// wait ends.  The lag keeps the E tiles far enough behind that the H tiles they need have
+// usually finished, and near enough that the E^n and H^{n+1/2} they read were touched a few
+// chunks before and are still in L2: that is the point of the ordering -- E reads them
+// from L2 instead of DRAM.  H is read from L2 only (__ldcg) by the E tiles.  The last
+// block to finish resets the counters, so the next launch starts from zero.
+// wave[0]: ticket counter, wave[1]: finished blocks, wave[2 + c]: H tiles done in chunk c.
+// Chunks of the wave-ordered step: z blocks, and tiles per z block (every source).
+template <int W, int KZ> __device__ __forceinline__ unsigned wave_nkb(const StepParams<float> &p) {
+    return (unsigned)((p.nz + KZ - 1) / KZ);
+}
+template <int W, int KZ> __device__ __forceinline__ unsigned wave_tc(const StepParams<float> &p, int S) {
+    return (unsigned)((p.nx / W + kLeanX - 1) / kLeanX) * (unsigned)((p.ny + kLeanRows - 1) / kLeanRows) * (unsigned)S;
+}
+
+template <int W, int KZ, int MINB>
+__global__ void __launch_bounds__(kLeanX *kLeanRows, MINB) k_step_wave(const StepParams<float> p, const int jstep,
+                                                                     const int S, const int lag) {
+    __shared__ int tile[5];                        // H (1) or E (0), z block, source, x tile, y tile
+    const int tid = threadIdx.y * kLeanX + threadIdx.x;
+    if (tid == 0) {                                // thread 0 takes the ticket and decodes it
+        const unsigned t = atomicAdd(p.wave, 1u);
+        const unsigned nkb = wave_nkb<W, KZ>(p), tc = wave_tc<W, KZ>(p, S);
+        const unsigned nxb = (unsigned)((p.nx / W + kLeanX - 1) / kLeanX);
+        const unsigned L = (unsigned)min(max(lag, 1), (int)nkb);
+        bool h;
+        unsigned kb, r;
+        if (t < L * tc) {
+            h = true; kb = t / tc; r = t % tc;
+        } else {
+            const unsigned u = t - L * tc, mid = (nkb - L) * 2u * tc;
+            if (u < mid) {
+                const unsigned ph = u / (2u * tc), q = u % (2u * tc);
+                h = q < tc;
+                kb = h ? L + ph : ph;
+                r = h ? q : q - tc;
+            } else {
+                h = false; kb = (nkb - L) + (u - mid) / tc; r = (u - mid) % tc;
+            }
+        }
+        tile[0] = h ? 1 : 0;
+        tile[1] = (int)kb;
+        tile[2] = (int)(r % (unsigned)S);
+        tile[3] = (int)((r / (unsigned)S) % nxb);
+        tile[4] = (int)(r / ((unsigned)S * nxb));
+        if (!h) {                                  // E: wait until H of z blocks kb and kb - 1 is complete
+            // the test hook makes the wait unsatisfiable; once one wait gave up, the others skip it
+            const unsigned need = tc + (p.fault_tx ? 1u : 0u);
+            const unsigned *done = p.wave + 2;
+            const unsigned long long t0 = gtimer_ns();
+            for (unsigned it = 0;; ++it) {
+                const unsigned a = *(volatile const unsigned *)&done[kb];
+                const unsigned b = kb ? *(volatile const unsigned *)&done[kb - 1] : need;
+                if (a >= need && b >= need) break;
+                if ((*(volatile int *)p.err) & kErrWaveWait) break;
+                if (it >= (1u << 24) || ((it & 63) == 63 && gtimer_ns() - t0 > kWaitNs)) {
+                    atomicOr(p.err, kErrWaveWait);
+                    break;
+                }
+                __nanosleep(128);
+            }
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    if (tile[0]) {
+        h_tile<W, KZ>(p, jstep, tile[3], tile[4], tile[1], tile[2]);
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();                       // the block's H stores before the count
+            atomicAdd(p.wave + 2 + tile[1], 1u);
+        }
+    } else {
+        e_tile<W, KZ, true>(p, jstep, tile[3], tile[4], tile[1], tile[2], S);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned nkb = wave_nkb<W, KZ>(p);
+        if (atomicAdd(p.wave + 1, 1u) == 2u * nkb * wave_tc<W, KZ>(p, S) - 1u) {   // all others finished
+            p.wave[0] = 0u;
+            p.wave[1] = 0u;
+            for (unsigned c = 0; c < nkb; ++c) p.wave[2 + c] = 0u;
+            __threadfence();
+        }
     }
 }
 
@@ -413,6 +586,25 @@ cudaError_t launch_field_lean(const StepParams<float> &p, int S, int jstep, cuda
     else if (w == 2 && mb == 6) ok = lean_kz<2, 6>(p, S, jstep, st, h, kz);
     else if (w == 2 && mb == 8) ok = lean_kz<2, 8>(p, S, jstep, st, h, kz);
     if (!ok) return cudaErrorInvalidValue;
+    g_launches++;
+    return cudaGetLastError();
+}
+
+bool wave_supported(const StepParams<float> &p, int kz, int mb) {
+    return p.wave && p.nx % 4 == 0 && p.psiL && p.cEm && p.lx.ih_n && p.lzero && (kz == 2 || kz == 4) &&
+           (mb == 6 || mb == 8) && p.nz <= kMaxWaveChunks * kz;
+}
+
+cudaError_t launch_step_wave(const StepParams<float> &p, int S, int jstep, cudaStream_t st) {
+    const int kz = p.WAVE_kz, mb = p.WAVE_mb, lag = p.WAVE_lag;
+    if (!wave_supported(p, kz, mb) || lag < 1) return cudaErrorInvalidValue;
+    const long long nxb = (p.nx / 2 + kLeanX - 1) / kLeanX, nyb = (p.ny + kLeanRows - 1) / kLeanRows;
+    const long long nblk = 2LL * ((p.nz + kz - 1) / kz) * nxb * nyb * S;
+    const dim3 block(kLeanX, kLeanRows);
+    if (kz == 2 && mb == 6) k_step_wave<2, 2, 6><<<(unsigned)nblk, block, 0, st>>>(p, jstep, S, lag);
+    else if (kz == 2) k_step_wave<2, 2, 8><<<(unsigned)nblk, block, 0, st>>>(p, jstep, S, lag);
+    else if (mb == 6) k_step_wave<2, 4, 6><<<(unsigned)nblk, block, 0, st>>>(p, jstep, S, lag);
+    else k_step_wave<2, 4, 8><<<(unsigned)nblk, block, 0, st>>>(p, jstep, S, lag);
     g_launches++;
     return cudaGetLastError();
 }

@@ -835,6 +835,7 @@ cudaError_t launch_step(const StepParams<R> &p, const PointParams<R> &q, int S, 
     if constexpr (sizeof(R) == 4) {
         if (p.FZ_by > 0 && (which & 5) == 5)
             return p.FZ_ws ? launch_step_ws(p, S, jstep, st) : launch_step_fz(p, S, jstep, st);
+        if (p.WAVE_lag > 0 && (which & 5) == 5) return launch_step_wave(p, S, jstep, st);
     }
     if (p.fused_kz > 0 && (which & 5) == 5) return launch_fused<R>(p, S, jstep, p.fused_kz, st);
     if (which & 1) e = launch_field<R>(p, S, jstep, st, true, p.KZ_h, p.MB_h);

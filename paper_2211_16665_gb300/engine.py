@@ -237,17 +237,22 @@ class Engine:
         _capi.set_copy_fault(self.ctx, extra_bytes)
 
     def set_launch(self, kz_h=4, mb_h=4, kz_e=4, mb_e=4, fused_kz=0, flush_mode=0, block=16, vec_h=0, vec_e=0,
-                   tma_h=0, tma_e=0, lean_h=0, lean_e=0, onepass=None, wspec=None):
+                   tma_h=0, tma_e=0, lean_h=0, lean_e=0, onepass=None, wspec=None, wave=None):
         """Pins a launch configuration (see csem_set_launch); launch_config() then reports it.
         onepass = (z planes, rows per block, resident blocks per SM) selects the fused
         one-pass step kernel (code 10000 + planes * 100 + rows * 10 + blocks); wspec = (z planes,
-        rows per block, resident blocks per SM) the warp-specialised fused step (code 30000 + ...)."""
+        rows per block, resident blocks per SM) the warp-specialised fused step (code 30000 + ...);
+        wave = (lag in z blocks, z planes, resident blocks per SM) the wave-ordered step
+        (code 50000 + lag * 100 + planes * 10 + blocks)."""
         if onepass:
             kz, by, mb = onepass
             fused_kz = 10000 + kz * 100 + by * 10 + mb
         elif wspec:
             kz, by, mb = wspec
             fused_kz = 30000 + kz * 100 + by * 10 + mb
+        elif wave:
+            lag, kz, mb = wave
+            fused_kz = 50000 + lag * 100 + kz * 10 + mb
         _capi.set_launch(self.ctx, kz_h, mb_h, kz_e, mb_e, fused_kz, flush_mode, block, vec_h, vec_e, tma_h, tma_e,
                          lean_h, lean_e)
         self.kz = (kz_h * 16 + mb_h + 256 * vec_h + 1024 * tma_h + 8192 * lean_h,
@@ -270,7 +275,11 @@ class Engine:
                 return {"kernel": "bulk-copy staged", "rows_per_block": code // 1024, "z_planes": (code % 1024) // 16}
             return {"kernel": "four cells per thread" if code >= 256 else "one cell per thread",
                     "z_planes": (code % 256) // 16, "blocks_per_sm": code % 16}
-        if fz >= 10000:
+        if fz >= 50000:
+            c = fz - 50000
+            step = {"kernel": "wave-ordered H+E", "lag": c // 100, "z_planes": (c // 10) % 10,
+                    "blocks_per_sm": c % 10}
+        elif fz >= 10000:
             c = fz - (30000 if fz >= 30000 else 10000)
             step = {"kernel": "fused warp-specialised H+E" if fz >= 30000 else "fused one-pass H+E",
                     "z_planes": c // 100, "rows_per_block": (c // 10) % 10, "blocks_per_sm": c % 10}

@@ -126,6 +126,10 @@ LAUNCH_VARIANTS = [
     dict(kz_h=4, mb_h=4, kz_e=4, mb_e=4, flush_mode=0, block=128),
     dict(wspec=(8, 4, 3), flush_mode=1, block=32),
     dict(wspec=(16, 8, 2), flush_mode=3, block=16),
+    dict(wave=(2, 4, 8), flush_mode=1, block=32),
+    dict(wave=(1, 2, 6), flush_mode=3, block=16),
+    dict(wave=(4, 4, 6), flush_mode=0, block=64),
+    dict(wave=(99, 2, 8), flush_mode=1, block=128),     # lag beyond the z blocks: every H tile first
 ]
 
 LEAN_VARIANTS = [
@@ -143,6 +147,9 @@ LEAN_VARIANTS = [
     dict(wspec=(16, 6, 2), flush_mode=0, block=16),
     dict(wspec=(44, 8, 1), flush_mode=1, block=64),
     dict(wspec=(5, 8, 2), flush_mode=1, block=16),
+    dict(wave=(1, 4, 8), flush_mode=1, block=16),
+    dict(wave=(3, 2, 6), flush_mode=3, block=32),
+    dict(wave=(2, 4, 6), flush_mode=0, block=64),
 ]
 
 
@@ -233,6 +240,54 @@ def test_onepass_step_refused_where_it_does_not_apply():
     eng = Engine.from_workload(box, precision=64, autotune=False)
     with pytest.raises(CsemError):
         eng.set_launch(wspec=(8, 4, 3))
+    with pytest.raises(CsemError):
+        eng.set_launch(wave=(2, 4, 8))
+    eng.close()
+
+
+@pytest.mark.parametrize("wave", [(1, 4, 8), (2, 2, 6), (3, 4, 6), (99, 2, 8)])
+def test_wave_step_is_bitwise_the_lean_pair(ragged, wave):
+    """The wave-ordered step runs the lean H and E tiles' arithmetic in one launch, so a run
+    with it equals a run with the split lean pair bit for bit (receivers, traces, volumes,
+    adjoint volumes), on the ragged box with two sources per launch."""
+    wl, o = ragged
+    two = W.Points.make([[30.0, 0.0, wl.src.z[0]], [-250.0, 40.0, wl.src.z[0]]], 0)
+    out = []
+    for launch in (dict(kz_h=wave[1], mb_h=wave[2], lean_h=2, kz_e=wave[1], mb_e=wave[2], lean_e=2),
+                   dict(wave=wave)):
+        eng = Engine.from_workload(wl, precision=32, kahan=1, autotune=False, max_src=2)
+        eng.set_launch(flush_mode=1, block=64, **launch)
+        rho = eng.model_tensor(wl.rho)
+        d, E, tr = eng.fwd_model(rho, two, wl.rec, keep_volume=True, trace=True)
+        basis, _, _ = eng.estimate_adjoint_basis()
+        V = eng.adjoint_model(rho, wl.rec, d, basis)
+        eng.check()
+        out.append((d.clone(), E.clone(), tr.clone(), V.clone()))
+        eng.close()
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
+
+
+def test_wave_step_refused_where_it_does_not_apply():
+    """The wave-ordered step needs FP32, second order, nx a multiple of 4, a lag of at least
+    one z block, 2 or 4 planes and 6 or 8 blocks per SM."""
+    odd = W.small_box(n_core=20, h=100.0, npml=8, ratio=1.05, n_st=3, n_rec=6, n_freq=2)   # nx = 42
+    eng = Engine.from_workload(odd, precision=32, autotune=False)
+    with pytest.raises(CsemError):
+        eng.set_launch(wave=(2, 4, 8))
+    eng.close()
+    box = W.small_box(n_core=24, h=100.0, npml=8, ratio=1.08, n_st=4, n_rec=6, n_freq=2)
+    eng = Engine.from_workload(box, precision=32, autotune=False, order=4)
+    with pytest.raises(CsemError):
+        eng.set_launch(wave=(2, 4, 8))
+    eng.close()
+    eng = Engine.from_workload(box, precision=32, autotune=False)
+    for bad in ((0, 4, 8), (2, 8, 8), (2, 1, 8), (2, 4, 4), (2, 4, 7)):
+        with pytest.raises(CsemError):
+            eng.set_launch(wave=bad)
+    eng.set_launch(wave=(3, 2, 6))
+    assert eng.launch_config()["step"] == {"kernel": "wave-ordered H+E", "lag": 3, "z_planes": 2,
+                                           "blocks_per_sm": 6}
     eng.close()
 
 

@@ -85,6 +85,8 @@ TD_VARIANTS = [
     dict(onepass=(16, 8, 3)),
     dict(wspec=(8, 4, 3)),
     dict(wspec=(16, 8, 2)),
+    dict(wave=(2, 4, 8)),
+    dict(wave=(1, 2, 6)),
 ]
 
 

@@ -8,8 +8,10 @@ CSEM_ERR_TIMEOUT naming the kernel family.  The context stays usable: with the
 hook off, the next run gives the results of an engine that never saw the hook,
 bit for bit.  Covered: the transform flush (16 snapshots held at once, and 64
 streamed through a ring of stages), the row-staged H/E step kernels and the
-fused one-pass step kernel; and the warp-specialised fused step, whose producer
-warps skip their first hand-over under the hook.
+fused one-pass step kernel; the warp-specialised fused step, whose producer
+warps skip their first hand-over under the hook; and the wave-ordered step, whose E
+tiles wait under the hook for one H tile more than there are (the first ones give
+up, the rest skip the wait), after which its counters are back at zero for the next run.
 """
 import pytest
 
@@ -32,6 +34,7 @@ CASES = {
     "row-staged": (dict(kz_h=4, mb_h=4, kz_e=4, mb_e=4, tma_h=2, tma_e=2, flush_mode=0, block=16), 2, "row-staged"),
     "one-pass": (dict(onepass=(8, 4, 4), flush_mode=0, block=16), 2, "one-pass"),
     "warp-specialised": (dict(wspec=(8, 4, 3), flush_mode=0, block=16), 2, "warp-specialised"),
+    "wave-ordered": (dict(wave=(2, 4, 8), flush_mode=0, block=16), 2, "wave-ordered"),
 }
 
 

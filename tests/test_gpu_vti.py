@@ -77,10 +77,11 @@ def test_vti_forward_adjoint_gradient_match_oracle(case, precision):
 
 
 @pytest.mark.parametrize("launch", [dict(onepass=(8, 4, 4), flush_mode=1, block=32),
-                                    dict(wspec=(8, 4, 3), flush_mode=1, block=32)])
+                                    dict(wspec=(8, 4, 3), flush_mode=1, block=32),
+                                    dict(wave=(2, 4, 8), flush_mode=1, block=32)])
 def test_vti_onepass_step_matches_oracle(case, launch):
     """The fused one-pass step averages sigma_v on the z edges from its own per-cell values;
-    the warp-specialised fused step reads the edges' dt/eps."""
+    the warp-specialised fused step and the wave-ordered step read the edges' dt/eps."""
     wl, pb, model, o = case
     eng = Engine.from_workload(wl, precision=32, kahan=1, vti=True, autotune=False)
     eng.set_launch(**launch)
