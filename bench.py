@@ -186,11 +186,11 @@ def flush_bytes(wl, eng):
 # valid only while the kernel's source file and the shared header are the ones captured
 # (SHA-1 of each); the figure is scaled by the sources of a launch.  Anything else reports null.
 # Stencil pair on the 256x256x128 towline, 2 sources per launch, lean H (2 cells, 4 planes,
-# 8 blocks/SM) and lean E (the same): 654.0 + 776.3 MB per launch, cold cache, the mean of
+# 8 blocks/SM) and lean E (the same): 654.1 + 776.4 MB per launch, cold cache, the mean of
 # 149 launches of each in the profiling module's forward run (nt 256) under ncu.
 NCU_TRAFFIC = {
     ("batched_towline_256x256x128_32src", "k_h_lean+k_e_lean", "kern_lean.cu",
-     "f3f50ecc630a144b1535ba9d2bd1fad048d3ab91", "254b06ccdabadbb85a07498665ac26358fd9a10b"): (654.0e6 + 776.3e6) / 2,
+     "e04bd69a59f373a283c3077b61bb51e2bfd75cf6", "c841fae235235a812cf25a4a18317b28f55113ae"): (654.1e6 + 776.4e6) / 2,
 }
 
 

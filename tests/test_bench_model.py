@@ -37,6 +37,6 @@ def test_flush_bytes():
 def test_traffic_lookup_only_for_the_captured_kernel():
     wl = W.ALL["batched_towline"]()
     per_launch = bench.ncu_traffic(wl, "k_h_lean+k_e_lean", 2)
-    assert per_launch is None or per_launch == pytest.approx(1430.3e6)
+    assert per_launch is None or per_launch == pytest.approx(1430.5e6)
     assert bench.ncu_traffic(wl, "k_step_fz", 2) is None
     assert bench.ncu_traffic(W.ALL["thin_reservoir"](), "k_h_lean+k_e_lean", 1) is None
