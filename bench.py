@@ -337,7 +337,8 @@ def run_ours(args):
     st_name = ({"fused one-pass H+E": "k_step_fz", "fused warp-specialised H+E": "k_step_ws",
                 "wave-ordered H+E": "k_step_wave"}.get(
         lc["step"]["kernel"], "k_step")) if fused else \
-        "+".join(f"k_{w}_{lc['step'][w]['kernel'].split()[0]}" for w in ("h", "e"))
+        "+".join(f"k_{w}_{lc['step'][w]['kernel'].split()[0]}" if eng.order == 2 else
+                 (f"k_{w}_ho4" if lc["step"][w]["kernel"] == "lean" else f"k_{w}_ho") for w in ("h", "e"))
     b_cell = stencil_bytes(wl, eng)
     nodes = (wl.nx + 1) * (wl.ny + 1) * (wl.nz + 1)
     M = eng.flush_block()
