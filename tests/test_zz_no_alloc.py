@@ -36,9 +36,11 @@ def _rel_l2(a, b):
 
 
 CASES = [
-    # (dt, nt, freqs): the paper's worked example and the thin-reservoir workload's set
+    # (dt, nt, freqs): the paper's worked example, the thin-reservoir workload's set, and the
+    # 400x400x200 workload's eight log-spaced frequencies over 19 492 steps (a 16-column basis)
     (0.004, 1000, [0.25, 0.75, 2.25]),
     (9.0374e-4, 12328, [0.25, 0.5, 0.75, 1.0]),
+    (9.0374e-4, 19492, list(np.logspace(np.log10(0.1), np.log10(1.5), 8))),
 ]
 
 
