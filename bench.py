@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--td", type=int, default=0,
                     help="time this many time-domain adjoint gradients against the basis route")
     ap.add_argument("--cpu-steps", type=int, default=300, help="time steps in the oracle sample")
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="--impl reference: wall-clock budget of its warm-up and timed steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch", type=int, default=2,
@@ -481,11 +483,11 @@ def run_reference(args):
     wl = make_workload(args.workload, 0, 1, vti=args.vti)
     pb = fdtd.problem_from_workload(wl)
     src = wl.src.subset([0])
-    # calibrate: size each step so that warmup + steps take ~2.5 minutes
+    # calibrate: size each step so that warmup + steps take --ref-seconds (2.5 minutes by default)
     t0 = time.perf_counter()
     fdtd.forward(pb, wl.rho, src, wl.rec, keep_volume=True, nt_run=3)
     per = (time.perf_counter() - t0) / 3
-    nt_s = int(max(5, min(pb.nt, 150.0 / max(1, args.steps + args.warmup) / per)))
+    nt_s = int(max(5, min(pb.nt, args.ref_seconds / max(1, args.steps + args.warmup) / per)))
     for _ in range(args.warmup):
         fdtd.forward(pb, wl.rho, src, wl.rec, keep_volume=True, nt_run=nt_s)
     t0 = time.perf_counter()
