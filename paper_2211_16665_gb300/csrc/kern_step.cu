@@ -17,6 +17,7 @@
 // once per step, and the compensated addition runs once per block.
 // Threads of k_h / k_e are laid out flat over the (j, i) plane and march KZ
 // planes along z, keeping the z-neighbour in registers.
+#include <algorithm>
 #include <atomic>
 
 #include "csem_internal.cuh"
@@ -566,7 +567,8 @@ __global__ void __launch_bounds__(kBulkThreads, bulk_minb<MS>()) k_dft_bulk(cons
 // kStG rows each (one mbarrier per stage, 32 KB in all): while the block sums
 // the rows of one stage, the copies of the next kStN - 1 stages are in flight,
 // and four blocks fit an SM.  The accumulators (and compensation) arrive on a
-// barrier of their own and are added to once, at the end, as in k_dft_bulk;
+// barrier of their own (with eight frequencies they are read from global memory
+// at the end instead, see stream_stages_acc) and are added to once, at the end, as in k_dft_bulk;
 // the sums are the ones k_dft_bulk would form over the same snapshots, in the same order.
 // Each thread waits on each stage's barrier itself (bounded); a give-up
 // anywhere ends the loop for the whole block (__syncthreads_or), thread 0 then
@@ -574,19 +576,27 @@ __global__ void __launch_bounds__(kBulkThreads, bulk_minb<MS>()) k_dft_bulk(cons
 // returns with the flush bit of *err raised.
 constexpr int kStG = 8;                 // snapshot rows per stage
 constexpr int kStN = 4;                 // stages (a power of two)
+// With up to four frequencies the accumulator rows are staged in shared memory (on their own
+// barrier, while the snapshots stream); with eight they would take 32 KB and leave three blocks
+// per SM, so each thread reads its accumulators from global memory at the end instead and five
+// blocks fit.
+__host__ __device__ constexpr bool stream_stages_acc(int nf_padded) { return nf_padded <= 4; }
+__host__ __device__ constexpr int stream_minb(int nf_padded) { return stream_stages_acc(nf_padded) ? 3 : 5; }
 
 template <bool KAHAN, int NF, int kStMS>
-__global__ void __launch_bounds__(kBulkThreads, 3) k_dft_stream(const StepParams<float> p, const PointParams<float> q,
-                                                                const int n0_off, const int nvb, const int S,
-                                                                int *err) {
+__global__ void __launch_bounds__(kBulkThreads, stream_minb(NF)) k_dft_stream(const StepParams<float> p,
+                                                                              const PointParams<float> q,
+                                                                              const int n0_off, const int nvb,
+                                                                              const int S, int *err) {
     constexpr int NCH = kStMS / kStG;
+    constexpr bool SACC = stream_stages_acc(NF);
     __shared__ __align__(8) uint64_t full[kStN];
     __shared__ __align__(8) uint64_t abar;
     extern __shared__ __align__(128) unsigned char smem[];
     float *st_s = reinterpret_cast<float *>(smem);                          // [kStN][kStG][256]
-    float2 *acc_s = reinterpret_cast<float2 *>(st_s + kStN * kStG * kBlock);  // [nf][256]
-    float2 *cmp_s = acc_s + p.nf * kBlock;                                  // [nf][256] (Kahan)
-    float2 *w_s = cmp_s + (KAHAN ? p.nf * kBlock : 0);                      // [kStMS][NF], zero past nf
+    float2 *acc_s = reinterpret_cast<float2 *>(st_s + kStN * kStG * kBlock);  // [nf][256] (SACC)
+    float2 *cmp_s = acc_s + (SACC ? p.nf * kBlock : 0);                     // [nf][256] (SACC, Kahan)
+    float2 *w_s = cmp_s + (SACC && KAHAN ? p.nf * kBlock : 0);              // [kStMS][NF], zero past nf
     const int n0 = *p.step + n0_off;
     if (n0 < 0) return;
     const int nrec_blocks = q.n_rec > 0 ? S : 0;
@@ -623,10 +633,12 @@ __global__ void __launch_bounds__(kBulkThreads, 3) k_dft_stream(const StepParams
     };
     if (threadIdx.x == 0) {
         for (int ch = 0; ch < kStN; ++ch) issue(ch);
-        mbar_expect_tx(&abar, p.nf * cb * (KAHAN ? 2u : 1u));
-        for (int f = 0; f < p.nf; ++f) {
-            bulk_g2s(acc_s + f * kBlock, A + (long long)f * p.vol, cb, &abar);
-            if (KAHAN) bulk_g2s(cmp_s + f * kBlock, C + (long long)f * p.vol, cb, &abar);
+        if (SACC) {
+            mbar_expect_tx(&abar, p.nf * cb * (KAHAN ? 2u : 1u));
+            for (int f = 0; f < p.nf; ++f) {
+                bulk_g2s(acc_s + f * kBlock, A + (long long)f * p.vol, cb, &abar);
+                if (KAHAN) bulk_g2s(cmp_s + f * kBlock, C + (long long)f * p.vol, cb, &abar);
+            }
         }
     }
     for (int u = threadIdx.x; u < kStMS * NF; u += blockDim.x) {
@@ -665,14 +677,14 @@ __global__ void __launch_bounds__(kBulkThreads, 3) k_dft_stream(const StepParams
         }
     }
     const bool done = (ch == NCH);
-    if (done && ok) ok = mbar_wait_bounded(&abar, 0);
+    if (SACC && done && ok) ok = mbar_wait_bounded(&abar, 0);
     if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) {
             atomicOr(err, kErrFlushWait);
             // copies issued and not consumed: chunks ch .. issued - 1 (each in its own stage), and
             // the accumulators; a wait that already completed returns at once
             for (int x = ch; x < issued; ++x) mbar_wait_bounded(&full[x & (kStN - 1)], (uint32_t)(x / kStN) & 1u);
-            mbar_wait_bounded(&abar, 0);
+            if (SACC) mbar_wait_bounded(&abar, 0);
         }
         return;
     }
@@ -681,9 +693,12 @@ __global__ void __launch_bounds__(kBulkThreads, 3) k_dft_stream(const StepParams
     for (int f = 0; f < NF; ++f) {
         if (f >= p.nf) break;
         const float2 s0 = unpack_f32x2(p0[f]), s1 = unpack_f32x2(p1[f]);
-        float4 a = *reinterpret_cast<const float4 *>(acc_s + f * kBlock + t2);   // entries t2, t2+1
+        // entries t2, t2+1
+        float4 a = SACC ? *reinterpret_cast<const float4 *>(acc_s + f * kBlock + t2)
+                        : *reinterpret_cast<const float4 *>(A + (long long)f * p.vol + t2);
         if (KAHAN) {
-            float4 cc = *reinterpret_cast<const float4 *>(cmp_s + f * kBlock + t2);
+            float4 cc = SACC ? *reinterpret_cast<const float4 *>(cmp_s + f * kBlock + t2)
+                             : *reinterpret_cast<const float4 *>(C + (long long)f * p.vol + t2);
             kahan_add(a.x, cc.x, s0.x);
             kahan_add(a.y, cc.y, s0.y);
             kahan_add(a.z, cc.z, s1.x);
@@ -700,8 +715,8 @@ __global__ void __launch_bounds__(kBulkThreads, 3) k_dft_stream(const StepParams
 }
 
 size_t stream_smem_bytes(int nf, bool kahan, int ms) {
-    return (size_t)kStN * kStG * kBlock * sizeof(float) + (size_t)nf * kBlock * sizeof(float2) * (kahan ? 2 : 1) +
-           (size_t)ms * nf_pad(nf) * sizeof(float2);
+    const size_t acc = stream_stages_acc(nf_pad(nf)) ? (size_t)nf * kBlock * sizeof(float2) * (kahan ? 2 : 1) : 0;
+    return (size_t)kStN * kStG * kBlock * sizeof(float) + acc + (size_t)ms * nf_pad(nf) * sizeof(float2);
 }
 
 size_t bulk_smem_bytes(int ms, int nf, bool kahan) {
@@ -756,7 +771,7 @@ cudaError_t prepare_bulk_flush() {
     const int big = (int)bulk_smem_bytes(32, kMaxFreq, true);
     cudaError_t e = bulk_attr_ms<32>(big);
     if (e == cudaSuccess) e = bulk_attr_ms<16>(big);
-    const int sbig = (int)stream_smem_bytes(kMaxFreq, true, 128);
+    const int sbig = (int)std::max(stream_smem_bytes(4, true, 128), stream_smem_bytes(kMaxFreq, true, 128));
     if (e == cudaSuccess) e = stream_attr_ms<64>(sbig);
     if (e == cudaSuccess) e = stream_attr_ms<128>(sbig);
     return e;

@@ -13,6 +13,9 @@ warps skip their first hand-over under the hook; and the wave-ordered step, whos
 tiles wait under the hook for one H tile more than there are (the first ones give
 up, the rest skip the wait), after which its counters are back at zero for the next run.
 """
+import dataclasses
+
+import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -28,9 +31,12 @@ from paper_2211_16665_gb300.engine import Engine  # noqa: E402
 TIMEOUT = -6
 
 CASES = {
-    # family: (launch configuration, steps per run, words the timeout message names)
+    # family: (launch configuration, steps per run, words the timeout message names[, frequencies])
     "flush": (dict(kz_h=2, mb_h=8, lean_h=2, kz_e=2, mb_e=8, lean_e=2, flush_mode=1, block=16), 16, "flush"),
     "streamed flush": (dict(kz_h=2, mb_h=8, lean_h=2, kz_e=2, mb_e=8, lean_e=2, flush_mode=1, block=64), 64, "flush"),
+    # with eight frequencies the streamed flush reads its accumulators at the end, not on a barrier
+    "streamed flush, 8 frequencies": (dict(kz_h=2, mb_h=8, lean_h=2, kz_e=2, mb_e=8, lean_e=2, flush_mode=1,
+                                           block=64), 64, "flush", 8),
     "row-staged": (dict(kz_h=4, mb_h=4, kz_e=4, mb_e=4, tma_h=2, tma_e=2, flush_mode=0, block=16), 2, "row-staged"),
     "one-pass": (dict(onepass=(8, 4, 4), flush_mode=0, block=16), 2, "one-pass"),
     "warp-specialised": (dict(wspec=(8, 4, 3), flush_mode=0, block=16), 2, "warp-specialised"),
@@ -40,8 +46,10 @@ CASES = {
 
 @pytest.mark.parametrize("family", list(CASES))
 def test_bounded_wait_reports_timeout_and_context_recovers(family):
-    launch, nt, word = CASES[family]
+    launch, nt, word = CASES[family][:3]
     wl = W.small_box(n_core=24, h=100.0, npml=8, ratio=1.08, n_st=4, n_rec=6, n_freq=2)
+    if len(CASES[family]) > 3:
+        wl = dataclasses.replace(wl, freqs=np.linspace(0.25, 1.5, CASES[family][3]))
 
     def engine():
         e = Engine.from_workload(wl, precision=32, kahan=1, autotune=False, nt=nt)
